@@ -1,0 +1,607 @@
+"""Pins of the FP64 oracle against facts fixed by the mathematics (CPU only).
+
+Each test names the pin it is and what a plausible mistake in the oracle would break:
+  P1  uniform rest state on the stretched spherical grid (metrics, face-area pressure terms)
+  P1b uniform Cartesian flow + field written in spherical components (all geometric sources)
+  P2  conservation on flux-closed domains (flux form)
+  P3  Sod shock tube against the exact Riemann solution (flux, limiter, integrator), TVDLF + HLL
+  P4  linear MHD waves converge at second order with the right phase speed (magnetic fluxes)
+  P5  spherically symmetric wind with gravity (gravity in momentum and energy, stretched grid)
+  P6  Linde div-B term against its closed form on a Fourier mode; Gauss sum on the sphere
+  P7  rotating frame: inertially static fluid; inertially radial wind (Coriolis, centrifugal,
+      work of the centrifugal force, induction source of B_phi)
+  P8  boundary time interpolation; P9 probe sampling; P10 cone-CME footprint
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle, cons_from_prim, prim_from_cons
+from paper_2501_15923_gb300 import inputs as I
+
+from . import exact
+from .helpers import cart_grid, centres, l1, opts, sph_grid
+
+P, C, R, D, F = I.BC_PERIODIC, I.BC_CONT, I.BC_REFLECT, I.BC_DRIVEN, I.BC_FIXED
+T0 = I.AU / 1e5                       # code time unit, s
+OM_SI = I.OMEGA_SUN                   # rad/s (what the solvers take)
+OM = OM_SI * T0                       # rad per code time unit (what the states use)
+
+
+def padded_shape(g):
+    return (8, g.n3 + 4, g.n2 + 4, g.n1 + 4)
+
+
+def sph_mesh(g):
+    """Interior cell-centre coordinates, arrays shaped [n3][n2][n1]."""
+    rc, tc, pc = centres(g, 0)[2:-2], centres(g, 1)[2:-2], centres(g, 2)[2:-2]
+    PH, TH, RR = np.meshgrid(pc, tc, rc, indexing="ij")
+    return RR, TH, PH
+
+
+def cart_to_sph(vx, vy, vz, th, ph):
+    vr = vx * np.sin(th) * np.cos(ph) + vy * np.sin(th) * np.sin(ph) + vz * np.cos(th)
+    vt = vx * np.cos(th) * np.cos(ph) + vy * np.cos(th) * np.sin(ph) - vz * np.sin(th)
+    vp = -vx * np.sin(ph) + vy * np.cos(ph)
+    return vr, vt, vp
+
+
+# ---------------------------------------------------------------------------------------------
+def test_P1_uniform_rest_preserved():
+    g = sph_grid(24, 8, 12, bc=(R, C, R, R, P, P))
+    o = Oracle(g, 1.5, 0.0, opts(gravity=0, divb=I.DIVB_NONE))
+    W = np.zeros((8, g.n3, g.n2, g.n1))
+    W[0], W[4] = 2.0, 3.0
+    U0 = cons_from_prim(W, 1.5)
+    o.set_state(U0)
+    for _ in range(100):
+        o.step()
+    U, _ = o.get_state()
+    assert np.max(np.abs(U[0] - 2.0)) < 1e-13 * 2.0
+    assert np.max(np.abs(U[4] - U0[4])) < 1e-13 * U0[4].max()
+    assert np.max(np.abs(U[1:4])) < 1e-12
+
+
+def residual_l1(g, W_pad, gamma, omega, o_kw, which=None):
+    o = Oracle(g, gamma, omega, opts(**o_kw))
+    o.set_state_padded(cons_from_prim(W_pad, gamma))
+    L = o.residual(0.0, 1.0)
+    if which is None:
+        return [l1(L[v]) for v in range(8)]
+    return l1(L[which])
+
+
+def uniform_state_sph(g, rho, p, vcart, bcart):
+    """Uniform state on the padded grid (ghosts included), vectors given in Cartesian."""
+    PHI, THE, RAD = np.meshgrid(centres(g, 2), centres(g, 1), centres(g, 0), indexing="ij")
+    W = np.zeros((8,) + PHI.shape)
+    W[0], W[4] = rho, p
+    W[1], W[2], W[3] = cart_to_sph(*vcart, THE, PHI)
+    W[5], W[6], W[7] = cart_to_sph(*bcart, THE, PHI)
+    return W
+
+
+@pytest.mark.parametrize("lim", [I.LIM_VANLEER, I.LIM_MC, I.LIM_MINMOD])
+def test_P1b_uniform_flow_and_field_in_spherical_components(lim):
+    """A uniform (v, B, rho, p) is an exact steady state of ideal MHD; written in spherical
+    components, its discrete residual must vanish at second order (every geometric source; a
+    dropped or mis-signed term leaves an O(1) residual that does not shrink)."""
+    errs = []
+    for n in (32, 64):
+        g = sph_grid(n, n, 2 * n, bc=(F,) * 4 + (P, P), r=(0.5, 1.5), stretch=1)
+        W = uniform_state_sph(g, 1.0, 1.0, (0.3, -0.2, 0.5), (0.4, 0.7, -0.6))
+        errs.append(residual_l1(g, W, 1.5, 0.0, dict(gravity=0, divb=I.DIVB_NONE, limiter=lim)))
+    errs = np.array(errs)
+    order = np.log2(errs[0] / np.maximum(errs[1], 1e-300))
+    for v in range(8):
+        if errs[0][v] > 1e-12:
+            assert order[v] > 1.75, (v, errs[:, v], order[v])
+
+
+def test_P2_conservation_cartesian_periodic():
+    g = cart_grid(16, 12, 8)
+    o = Oracle(g, 5.0 / 3.0, 0.0, opts(divb=I.DIVB_NONE, cfl=0.5))
+    rng = np.random.default_rng(4)
+    X = np.meshgrid(*[(np.arange(n) + 0.5) / n for n in (g.n3, g.n2, g.n1)], indexing="ij")
+    W = np.zeros((8, g.n3, g.n2, g.n1))
+    W[0] = 1.0 + 0.3 * np.sin(2 * np.pi * X[2]) * np.cos(2 * np.pi * X[1])
+    W[1:4] = 0.5 * rng.uniform(-1, 1, (3, 1, 1, 1)) * np.cos(2 * np.pi * (X[0] + X[1] + X[2]))
+    W[4] = 1.0 + 0.2 * np.cos(2 * np.pi * X[0])
+    W[5:8] = 0.6 * np.sin(2 * np.pi * (X[2] - X[0]))[None] + rng.uniform(-0.3, 0.3, (3, 1, 1, 1))
+    U = cons_from_prim(W, 5.0 / 3.0)
+    o.set_state(U)
+    tot0 = U.reshape(8, -1).sum(1)
+    scale = np.abs(U).reshape(8, -1).sum(1)
+    for _ in range(30):
+        o.step()
+    U1, _ = o.get_state()
+    tot1 = U1.reshape(8, -1).sum(1)
+    assert np.all(np.abs(tot1 - tot0) <= 1e-13 * scale), (tot1 - tot0) / scale
+
+
+def test_P2_conservation_spherical_shell_reflecting():
+    g = sph_grid(20, 10, 16, bc=(R, R, R, R, P, P), r=(0.3, 1.0))
+    o = Oracle(g, 1.5, 0.0, opts(divb=I.DIVB_NONE, gravity=0, cfl=0.5))
+    RR, TH, PH = sph_mesh(g)
+    W = np.zeros((8,) + RR.shape)
+    W[0] = 1.0 + 0.2 * np.sin(3 * PH) * np.sin(2 * TH) + 0.1 * RR
+    W[1] = 0.3 * np.sin(np.pi * (RR - 0.3) / 0.7)
+    W[2] = 0.2 * np.cos(PH) * np.sin(3 * TH)
+    W[3] = 0.4 * np.sin(TH)
+    W[4] = 1.0 + 0.1 * np.cos(2 * PH)
+    W[5], W[6], W[7] = 0.3 * np.cos(TH), -0.3 * np.sin(TH), 0.2 * np.sin(PH)
+    U = cons_from_prim(W, 1.5)
+    o.set_state(U)
+    V = o.volumes()
+    m0, e0 = (U[0] * V).sum(), (U[4] * V).sum()
+    for _ in range(30):
+        o.step()
+    U1, _ = o.get_state()
+    assert abs((U1[0] * V).sum() - m0) < 1e-13 * m0
+    assert abs((U1[4] * V).sum() - e0) < 1e-13 * e0
+
+
+# ---------------------------------------------------------------------------------------------
+def run_to(o, t_end, max_steps=20000):
+    assert math.isfinite(t_end)
+    for _ in range(max_steps):
+        if o.t >= t_end * (1 - 1e-14):
+            return
+        o.step(t_end - o.t)
+    raise AssertionError("run_to did not reach t_end")
+
+
+def shock_tube(n, d, flux, lim, wl, wr, b=(0.0, 0.0, 0.0), gamma=1.4, t_end=0.2):
+    """1-D Riemann problem along direction d (0, 1, 2) on a Cartesian grid."""
+    L = [1e3, 1e3, 1e3]
+    L[d] = 1.0
+    nn = [1, 1, 1]
+    nn[d] = n
+    bc = [P] * 6
+    bc[2 * d], bc[2 * d + 1] = C, C
+    g = cart_grid(*nn, L=L, bc=bc)
+    o = Oracle(g, gamma, 0.0, opts(divb=I.DIVB_NONE, limiter=lim, flux=flux, cfl=0.8))
+    x = (np.arange(n) + 0.5) / n
+    W = np.zeros((8, n))
+    left = x < 0.5
+    W[0] = np.where(left, wl[0], wr[0])
+    W[1 + d] = np.where(left, wl[1], wr[1])
+    W[4] = np.where(left, wl[2], wr[2])
+    for c in range(3):
+        W[5 + c] = b[c]
+    shape = (8, nn[2], nn[1], nn[0])
+    o.set_state(cons_from_prim(W, gamma).reshape(shape))
+    run_to(o, t_end)
+    U, _ = o.get_state()
+    Wn = prim_from_cons(U.reshape(8, n), gamma)
+    return x, Wn
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+@pytest.mark.parametrize("flux", [I.FLUX_TVDLF, I.FLUX_HLL])
+def test_P3_sod_against_exact_riemann(d, flux):
+    wl, wr = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    errs = []
+    for n in (100, 200):
+        x, W = shock_tube(n, d, flux, I.LIM_VANLEER, wl, wr)
+        rho, u, p = exact.riemann_profile(wl, wr, 1.4, x, 0.5, 0.2)
+        errs.append((l1(W[0] - rho), l1(W[1 + d] - u), l1(W[4] - p)))
+        # transverse velocity and field stay exactly zero
+        assert np.all(W[[1 + (d + 1) % 3, 1 + (d + 2) % 3, 5, 6, 7]] == 0.0)
+    errs = np.array(errs)
+    assert errs[1, 0] < (0.012 if flux == I.FLUX_TVDLF else 0.009), errs
+    assert np.all(errs[1] < errs[0] * 0.8), errs   # converging (first order at discontinuities)
+
+
+def test_P3_sod_star_state():
+    """Plateau between the contact and the shock equals the exact star state."""
+    wl, wr = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    ps, us = exact.riemann_star(wl, wr, 1.4)
+    x, W = shock_tube(400, 0, I.FLUX_HLL, I.LIM_MC, wl, wr)
+    sel = (x > 0.72) & (x < 0.80)   # between contact (0.686) and shock (0.850) at t = 0.2
+    assert np.max(np.abs(W[4][sel] - ps)) < 2e-3 * ps
+    assert np.max(np.abs(W[1][sel] - us)) < 5e-3 * us
+
+
+def test_P3_brio_wu_invariants():
+    """Brio-Wu (gamma = 2) has no closed form; check what is fixed: B_x stays exactly constant,
+    mass, energy and B_y are conserved (the end states are still at rest at t = 0.1, so their
+    boundary fluxes vanish)."""
+    wl, wr = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    n = 200
+    g = cart_grid(n, 1, 1, L=(1.0, 1e3, 1e3), bc=(C, C, P, P, P, P))
+    o = Oracle(g, 2.0, 0.0, opts(divb=I.DIVB_NONE, cfl=0.8))
+    x = (np.arange(n) + 0.5) / n
+    W = np.zeros((8, n))
+    W[0] = np.where(x < 0.5, 1.0, 0.125)
+    W[4] = np.where(x < 0.5, 1.0, 0.1)
+    W[5] = 0.75
+    W[6] = np.where(x < 0.5, 1.0, -1.0)
+    U = cons_from_prim(W, 2.0).reshape(8, 1, 1, n)
+    o.set_state(U)
+    run_to(o, 0.1)
+    U1, _ = o.get_state()
+    U1 = U1.reshape(8, n)
+    assert np.all(U1[5] == 0.75)
+    tot0, tot1 = U.reshape(8, n).sum(1), U1.sum(1)
+    for v in (0, 4, 6):
+        assert abs(tot1[v] - tot0[v]) < 1e-12 * np.abs(U.reshape(8, n)[v]).sum()
+    Wn = prim_from_cons(U1, 2.0)
+    assert Wn[0].min() > 0 and Wn[4].min() > 0
+    # the compound wave and slow shock exist: density has its classic range
+    assert 0.1 < Wn[0].min() < 0.2 and 0.9 < Wn[0].max() < 1.01
+
+
+# ---------------------------------------------------------------------------------------------
+def wave_error(n, d, mode, lim, gamma=5.0 / 3.0, eps=1e-6):
+    """Linear MHD eigenmode along direction d: L1 error after one wave period."""
+    # background flow 0.25 along the wave so that no mode (entropy included) stands still
+    w0 = np.array([1.0, 0.25, 0.0, 0.0, 1.0 / gamma, 1.0, math.sqrt(2.0), 0.5])
+    lam, Rv = exact.mhd_modes(w0, gamma)
+    speed = lam[mode]
+    L = [1e3, 1e3, 1e3]
+    L[d] = 1.0
+    nn = [1, 1, 1]
+    nn[d] = n
+    g = cart_grid(*nn, L=L)
+    o = Oracle(g, gamma, 0.0, opts(divb=I.DIVB_NONE, limiter=lim, cfl=0.8))
+    x = (np.arange(n) + 0.5) / n
+    avg = math.sin(math.pi / n) / (math.pi / n)           # cell average of cos(2 pi x)
+    pert = np.outer(Rv[:, mode], np.cos(2 * np.pi * x) * avg) * eps
+    def lay(wfull):
+        # map x-oriented (rho, vx, vy, vz, p, By, Bz) + Bx onto direction d (cyclic)
+        W = np.zeros((8, n))
+        W[0], W[4] = wfull[0], wfull[4]
+        for c in range(3):
+            W[1 + (d + c) % 3] = wfull[1 + c]
+        W[5 + d] = w0[5]
+        W[5 + (d + 1) % 3] = wfull[5]
+        W[5 + (d + 2) % 3] = wfull[6]
+        return W
+    wfull = np.array([w0[0], w0[1], w0[2], w0[3], w0[4], w0[6], w0[7]])[:, None] + pert
+    Winit = lay(wfull)
+    shape = (8, nn[2], nn[1], nn[0])
+    o.set_state(cons_from_prim(Winit, gamma).reshape(shape))
+    run_to(o, 1.0 / abs(speed))
+    U, _ = o.get_state()
+    Wn = prim_from_cons(U.reshape(8, n), gamma)
+    return sum(l1(Wn[v] - Winit[v]) for v in range(8)) / eps
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 6])   # fast-, Alfven-, slow-, entropy, fast+
+@pytest.mark.parametrize("lim", [I.LIM_MC, I.LIM_VANLEER])
+def test_P4_linear_waves_second_order(d, mode, lim):
+    """Second order (L1, 64 -> 128 cells) with the eigen-speed of the mode: a wrong magnetic flux
+    term changes the propagation speed or shape and the error stays O(1)."""
+    e1 = wave_error(64, d, mode, lim)
+    e2 = wave_error(128, d, mode, lim)
+    order = math.log2(e1 / e2)
+    assert order > 1.8, (e1, e2, order)
+    assert e2 < 0.02, e2
+
+
+def test_P4_harness_detects_wrong_speed():
+    """The comparison after one period is sensitive to the phase: the same run compared with the
+    initial mode shifted by a tenth of a wavelength is far off."""
+    e = wave_error(64, 0, 1, I.LIM_MC)
+    x = (np.arange(64) + 0.5) / 64
+    shift = np.abs(np.cos(2 * np.pi * x) - np.cos(2 * np.pi * (x - 0.1))).mean()
+    assert e < 0.1 * shift
+
+
+# ---------------------------------------------------------------------------------------------
+def wind_setup(n, omega=0.0, n2=2, th=(math.radians(85), math.radians(95)), br0=20.0):
+    g = sph_grid(n, n2, 2, bc=(F, F, F, F, P, P), th=th)
+    gm = 1.32712440018e20 / (1.495978707e11 * 1e10)
+    rho0, v0, p0, gamma = 300.0, 4.0, 300.0, 1.5
+    rc, tc, pc = centres(g, 0), centres(g, 1), centres(g, 2)
+    rho, v, p = exact.wind_profile(rc, 0.1, rho0, v0, p0, gamma, gm)
+    PHI, THE, RAD = np.meshgrid(pc, tc, rc, indexing="ij")
+    W = np.zeros((8,) + RAD.shape)
+    W[0] = rho[None, None, :]
+    W[1] = v[None, None, :]
+    W[3] = -omega * RAD * np.sin(THE)
+    W[4] = p[None, None, :]
+    W[5] = br0 * (0.1 / RAD) ** 2
+    return g, W, gamma, gm
+
+
+@pytest.mark.parametrize("omega", [0.0, OM])
+def test_P5_P7_wind_residual_second_order(omega):
+    """Exact spherically symmetric wind with gravity and a radial monopole field; with omega != 0
+    the same inertial flow seen from the co-rotating frame (v_phi = -Omega r sin(theta))."""
+    errs = []
+    for n in (48, 96):
+        if omega:
+            g, W, gamma, gm = wind_setup(n, omega, n2=n // 6, th=(math.radians(40), math.radians(140)))
+        else:
+            g, W, gamma, gm = wind_setup(n)
+        errs.append(residual_l1(g, W, gamma, omega / T0, dict(divb=I.DIVB_NONE, gravity=1)))
+    errs = np.array(errs)
+    for v in (0, 1, 2, 3, 4, 7):
+        if errs[0][v] > 1e-10:
+            assert math.log2(errs[0][v] / errs[1][v]) > 1.8, (v, errs[:, v])
+
+
+def test_P5_gravity_sign_matters():
+    """Flip the sign of gravity in the exact solution: the residual becomes O(1), not O(dx^2)."""
+    g, W, gamma, gm = wind_setup(96)
+    good = residual_l1(g, W, gamma, 0.0, dict(divb=I.DIVB_NONE, gravity=1), which=1)
+    bad = residual_l1(g, W, gamma, 0.0, dict(divb=I.DIVB_NONE, gravity=0), which=1)
+    assert bad > 20 * good
+
+
+def test_P5_steady_wind_converges():
+    """Time-march from the exact profile with the driven (map) inner boundary: the discrete steady
+    state converges to the exact wind. Putting the boundary value into every ghost layer (the
+    paper's new treatment, Sect. 2.1) places it half a cell off, so the boundary is first order:
+    the pin is order >= 0.8 and a small error, while the interior consistency is second order
+    (test_P5_P7_wind_residual_second_order)."""
+    errs = []
+    for n in (32, 64):
+        g, W, gamma, gm = wind_setup(n, br0=0.0)
+        g.bc = (D, C, C, C, P, P)
+        o = Oracle(g, gamma, 0.0, opts(divb=I.DIVB_NONE, gravity=1))
+        # one static map of the inner-boundary state (SI)
+        mp = np.zeros((1, 5, g.n2, g.n3))
+        mp[0, 0], mp[0, 1] = 4.0e5, 300e6
+        mp[0, 2] = 300.0 * 1.67262192369e-27 * 1e6 * 1e10
+        o.set_boundary(np.zeros(1), mp)
+        Wi = W[:, 2:-2, 2:-2, 2:-2]
+        o.set_state(cons_from_prim(Wi, gamma))
+        run_to(o, 0.8)
+        U, _ = o.get_state()
+        Wn = prim_from_cons(U, gamma)
+        errs.append(l1((Wn[1] - Wi[1]) / Wi[1]))
+    assert math.log2(errs[0] / errs[1]) > 0.8 and errs[1] < 2e-3, errs
+
+
+def test_P7_inertially_static_fluid_residual():
+    errs = []
+    om = OM
+    for n in (16, 32):
+        g = sph_grid(n, n, 8, bc=(F,) * 4 + (P, P), r=(0.5, 1.5))
+        PHI, THE, RAD = np.meshgrid(centres(g, 2), centres(g, 1), centres(g, 0), indexing="ij")
+        W = np.zeros((8,) + RAD.shape)
+        W[0], W[4] = 1.0, 50.0
+        W[3] = -om * RAD * np.sin(THE)
+        errs.append(residual_l1(g, W, 1.5, OM_SI, dict(divb=I.DIVB_NONE, gravity=0)))
+    errs = np.array(errs)
+    for v in (1, 2, 3, 4):
+        if errs[0][v] > 1e-10:
+            assert math.log2(errs[0][v] / errs[1][v]) > 1.8, (v, errs[:, v])
+    # with the Coriolis term of the wrong sign the residual would not vanish: compare against
+    # the co-rotating (v = 0) fluid, which is NOT steady in the rotating frame
+    g = sph_grid(32, 32, 8, bc=(F,) * 4 + (P, P), r=(0.5, 1.5))
+    W = np.zeros(padded_shape(g))
+    W[0], W[4] = 1.0, 50.0
+    not_steady = residual_l1(g, W, 1.5, OM_SI, dict(divb=I.DIVB_NONE, gravity=0), which=1)
+    assert not_steady > 50 * errs[1][1]
+
+
+# ---------------------------------------------------------------------------------------------
+def test_P6_linde_closed_form_fourier_mode():
+    """B_x = eps sin(k x) on a periodic box: the discrete div B (face averages) and its central
+    gradient act on the mode with symbol -sin^2(k dx)/dx^2, so the Linde term in dB_x/dt is
+    -eta sin^2(k dx)/dx^2 B_x with eta = C_d / (dt sum_d 1/dx_d^2)."""
+    n, kx, eps, cd, dt = 32, 3, 1e-3, 0.8, 0.37
+    g = cart_grid(n, 4, 2, L=(1.0, 0.5, 0.25))
+    x = (np.arange(n) + 0.5) / n
+    W = np.zeros((8, 2, 4, n))
+    W[0], W[4] = 1.0, 1.0
+    W[5] = eps * np.sin(2 * np.pi * kx * x)
+    W[6] = 0.2
+    U = cons_from_prim(W, 5 / 3)
+    res = {}
+    for divb in (I.DIVB_NONE, I.DIVB_LINDE):
+        o = Oracle(g, 5 / 3, 0.0, opts(divb=divb, divb_coef=cd))
+        o.set_state(U)
+        res[divb] = o.residual(0.0, dt)
+    dL = res[I.DIVB_LINDE] - res[I.DIVB_NONE]
+    dx, dy, dz = 1.0 / n, 0.5 / 4, 0.25 / 2
+    eta = cd / (dt * (1 / dx ** 2 + 1 / dy ** 2 + 1 / dz ** 2))
+    expect = -eta * np.sin(2 * np.pi * kx * dx) ** 2 / dx ** 2 * W[5]
+    assert np.allclose(dL[5], expect, rtol=1e-10, atol=1e-14)
+    assert np.allclose(dL[6], 0.0, atol=1e-14) and np.allclose(dL[7], 0.0, atol=1e-14)
+    assert np.allclose(dL[4], W[5] * expect, rtol=1e-10, atol=1e-16)
+
+
+def test_P6_divb_gauss_and_convergence_spherical():
+    """sum_cells V div B telescopes to the boundary flux; for a uniform Cartesian field written in
+    spherical components, div B -> 0 at second order."""
+    vals = []
+    for n in (16, 32):
+        g = sph_grid(n, n, 2 * n, bc=(F,) * 4 + (P, P), r=(0.5, 1.5))
+        W = uniform_state_sph(g, 1.0, 1.0, (0, 0, 0), (0.3, -0.5, 0.8))
+        o = Oracle(g, 1.5, 0.0, opts())
+        o.set_state_padded(cons_from_prim(W, 1.5))
+        vals.append(l1(o.divb()))
+    assert math.log2(vals[0] / vals[1]) > 1.8, vals
+
+
+def test_P6_divb_telescoping_sum():
+    g = sph_grid(12, 10, 16, bc=(F,) * 4 + (P, P), r=(0.4, 1.2))
+    rng = np.random.default_rng(7)
+    W = np.zeros(padded_shape(g))
+    W[0], W[4] = 1.0, 1.0
+    W[5:8] = rng.normal(size=(3,) + W.shape[1:])
+    o = Oracle(g, 1.5, 0.0, opts())
+    o.set_state_padded(cons_from_prim(W, 1.5))
+    V = o.volumes()
+    total = (o.divb() * V).sum()
+    # boundary flux from the same face averages on the six boundary faces of the block
+    re = np.array([0.4 * 3.0 ** (i / 12) for i in range(13)])
+    te = g.x2min + np.arange(11) * (g.x2max - g.x2min) / 10
+    dph = 2 * np.pi / 16
+    Br = W[5][2:-2, 2:-2, :]
+    Bt = W[6][2:-2, :, 2:-2]
+    fr_in = 0.5 * (Br[:, :, 1] + Br[:, :, 2]) * re[0] ** 2 * (np.cos(te[:-1]) - np.cos(te[1:]))[None, :] * dph
+    fr_out = 0.5 * (Br[:, :, -3] + Br[:, :, -2]) * re[-1] ** 2 * (np.cos(te[:-1]) - np.cos(te[1:]))[None, :] * dph
+    ar = 0.5 * (re[1:] ** 2 - re[:-1] ** 2)
+    ft_in = 0.5 * (Bt[:, 1, :] + Bt[:, 2, :]) * ar[None, :] * np.sin(te[0]) * dph
+    ft_out = 0.5 * (Bt[:, -3, :] + Bt[:, -2, :]) * ar[None, :] * np.sin(te[-1]) * dph
+    Bp = W[7][:, 2:-2, 2:-2]
+    dth = (g.x2max - g.x2min) / 10
+    fp_in = 0.5 * (Bp[1] + Bp[2]) * ar[None, :] * dth
+    fp_out = 0.5 * (Bp[-3] + Bp[-2]) * ar[None, :] * dth
+    expect = fr_out.sum() - fr_in.sum() + ft_out.sum() - ft_in.sum() + fp_out.sum() - fp_in.sum()
+    assert abs(total - expect) < 1e-11 * np.abs(W[5:8]).sum() * V.mean()
+
+
+# ---------------------------------------------------------------------------------------------
+def test_P8_boundary_time_interpolation():
+    g = sph_grid(8, 6, 8, bc=(D, C, C, C, P, P))
+    rng = np.random.default_rng(1)
+    maps = rng.uniform(1.0, 2.0, size=(3, 5, 6, 8)) * np.array([4e5, 1e8, 1e-9, 1e-7, 1e-8])[None, :, None, None]
+    t_maps = np.array([0.0, 86400.0, 2 * 86400.0])
+    o = Oracle(g, 1.5, 2.8e-6, opts())
+    o.set_boundary(t_maps, maps)
+    sc = o.scales()
+    conv = np.array([1e5, 1e6, sc["p0"], sc["b0"], sc["b0"]])
+    order = [1, 0, 2, 3, 4]    # oracle returns (rho, v_r, p, B_r, B_phi)
+    code = maps / conv[None, :, None, None]
+    code = code[:, order]
+    for k in range(3):
+        vals, _ = o.boundary_values(t_maps[k] / sc["t0"])
+        assert np.array_equal(vals, code[k])
+    vals, _ = o.boundary_values(0.5 * 86400.0 / sc["t0"])
+    assert np.allclose(vals, 0.5 * (code[0] + code[1]), rtol=1e-15)
+    vals, _ = o.boundary_values(0.25 * 86400.0 / sc["t0"])
+    assert np.allclose(vals, 0.75 * code[0] + 0.25 * code[1], rtol=1e-14)
+    vals, _ = o.boundary_values(-5.0)
+    assert np.array_equal(vals, code[0])
+    vals, _ = o.boundary_values(1e3)
+    assert np.array_equal(vals, code[2])
+
+
+def test_P8_ghost_layers_same_value_and_asymm():
+    w = I.config0()
+    from oracle.oracle import from_workload
+    o = from_workload(w)
+    o.fill_ghosts(0.0)
+    Up = o.get_state_padded()
+    Wp = prim_from_cons(Up, 1.5)
+    vals, _ = o.boundary_values(0.0)
+    for gidx in (0, 1):     # padded index of ghosts -2, -1
+        for f, v in zip((0, 1, 4, 5, 7), range(5)):
+            got = Wp[f, 2:-2, 2:-2, gidx].T
+            assert np.allclose(got, vals[v], rtol=1e-12, atol=1e-12 * np.abs(vals[v]).max())
+    # asymm: ghost -1 mirrors interior 0, ghost -2 mirrors interior 1, sign flipped
+    for f in (2, 3, 6):
+        assert np.allclose(Wp[f, 2:-2, 2:-2, 1], -Wp[f, 2:-2, 2:-2, 2], atol=1e-13)
+        assert np.allclose(Wp[f, 2:-2, 2:-2, 0], -Wp[f, 2:-2, 2:-2, 3], atol=1e-13)
+
+
+def test_IC_radial_expansion():
+    w = I.config0()
+    from oracle.oracle import from_workload
+    o = from_workload(w)
+    U, _ = o.get_state()
+    W = prim_from_cons(U, 1.5)
+    g = w.grid
+    rc, tc = centres(g, 0)[2:-2], centres(g, 1)[2:-2]
+    m = w.maps[0]
+    sc = o.scales()
+    x = (0.1 / rc)[None, None, :]
+    vr = (m[0].T / 1e5)[:, :, None]
+    assert np.allclose(W[1], vr, rtol=1e-13)
+    assert np.allclose(W[0], (m[1].T / 1e6)[:, :, None] * x ** 2, rtol=1e-12)
+    assert np.allclose(W[4], (m[2].T / sc["p0"])[:, :, None] * x ** 3, rtol=1e-9)
+    br = (m[3].T / sc["b0"])[:, :, None] * x ** 2
+    assert np.allclose(W[5], br, rtol=1e-12)
+    bphi = -br * sc["omega"] * rc[None, None, :] * np.sin(tc)[None, :, None] / vr
+    assert np.allclose(W[7], bphi, rtol=1e-12)
+    assert np.all(W[2] == 0) and np.all(W[3] == 0) and np.all(W[6] == 0)
+
+
+# ---------------------------------------------------------------------------------------------
+def test_P9_sampling_cell_centre_linear_fields_and_indices():
+    g = sph_grid(40, 12, 24, bc=(C, C, C, C, P, P), r=(0.1, 2.0))
+    o = Oracle(g, 1.5, 0.0, opts())
+    PHI, THE, RAD = np.meshgrid(centres(g, 2)[2:-2], centres(g, 1)[2:-2], centres(g, 0)[2:-2], indexing="ij")
+    W = np.zeros((8,) + RAD.shape)
+    W[0] = 2.0 + 3.0 * RAD - 1.0 * THE
+    W[1] = 4.0 + 0.5 * THE + 0.1 * RAD
+    W[4] = 5.0 + RAD
+    W[5] = 1.0 - 0.3 * RAD + 0.2 * THE
+    W[7] = 0.25 * PHI        # linear in phi (away from the wrap)
+    o.set_state(cons_from_prim(W, 1.5), 0.0)
+    AU = 1.495978707e11
+    rc, tc, pc = centres(g, 0)[2:-2], centres(g, 1)[2:-2], centres(g, 2)[2:-2]
+    rng = np.random.default_rng(3)
+    pts = []
+    for _ in range(40):
+        r = rng.uniform(rc[0], rc[-1]); th = rng.uniform(tc[0], tc[-1]); ph = rng.uniform(pc[0], pc[-1])
+        pts.append((r, th, ph))
+    pts.append((rc[7], tc[3], pc[5]))
+    traj = np.array([[[0.0, r * AU, np.pi / 2 - th, ph]] for r, th, ph in pts])
+    out = o.sample(traj)
+    for q, (r, th, ph) in zip(out, pts):
+        r_, th_, ph_ = q[0] * 0 + r, th, ph
+        assert abs(q[1] / 1e6 - (2.0 + 3.0 * r - th)) < 1e-12 * 10
+        assert abs(q[2] / 1e5 - (4.0 + 0.5 * th + 0.1 * r)) < 1e-12 * 10
+        # indices: brute-force bracketing by an independent search
+        i = int(np.clip(np.searchsorted(rc, (r * AU) / AU, side="right") - 1, 0, len(rc) - 2))
+        j = int(np.clip(np.searchsorted(tc, np.pi / 2 - (np.pi / 2 - th), side="right") - 1, 0, len(tc) - 2))
+        k = int(np.searchsorted(pc, ph, side="right") - 1) % len(pc)
+        assert (q[10], q[11], q[12]) == (i, j, k)
+    # a point exactly at a cell centre returns that cell's value
+    last = out[-1]
+    assert abs(last[8] / o.scales()["p0"] - W[4][5, 3, 7]) < 1e-12 * W[4][5, 3, 7]
+    assert abs(last[7] / o.scales()["b0"] - W[7][5, 3, 7]) < 1e-12
+
+
+def test_P9_phi_wrap_and_corotation():
+    g = sph_grid(10, 6, 16, bc=(C, C, C, C, P, P))
+    om = 2.8e-6
+    o = Oracle(g, 1.5, om, opts())
+    PHI, THE, RAD = np.meshgrid(centres(g, 2)[2:-2], centres(g, 1)[2:-2], centres(g, 0)[2:-2], indexing="ij")
+    W = np.zeros((8,) + RAD.shape)
+    W[0] = 1.0 + 0.5 * np.cos(PHI)      # periodic in phi
+    W[4] = 1.0
+    sc = o.scales()
+    t_code = 0.3
+    o.set_state(cons_from_prim(W, 1.5), t_code)
+    AU = 1.495978707e11
+    pc = centres(g, 2)[2:-2]
+    tsi = t_code * sc["t0"]
+    # co-rotating longitude just below the first centre (wraps to the last cell)
+    for phc in (0.5 * pc[0], 2 * np.pi - 0.25 * pc[0], pc[3] + 0.1 * (pc[4] - pc[3])):
+        lon = phc + om * tsi
+        traj = np.array([[[0.0, 1.0 * AU, 0.0, lon]]])
+        q = o.sample(traj)[0]
+        kk = int(np.searchsorted(pc, phc, side="right") - 1) % 16
+        assert q[12] == kk
+        # linear interpolation in phi between the bracketing centres (with the 2 pi wrap)
+        p0 = pc[kk] if phc >= pc[0] else pc[-1] - 2 * np.pi
+        wgt = (phc - p0) / (2 * np.pi / 16)
+        f = lambda p: 1.0 + 0.5 * np.cos(p)
+        expect = (1 - wgt) * f(p0) + wgt * f(p0 + 2 * np.pi / 16)
+        assert abs(q[1] / 1e6 - expect) < 1e-9
+
+
+def test_P10_cme_footprint_brute_force():
+    g = sph_grid(8, 24, 48, bc=(D, C, C, C, P, P))
+    o = Oracle(g, 1.5, 0.0, opts())
+    mp = np.ones((1, 5, 24, 48))
+    cme = np.array([[3600.0, 8 * 3600.0, math.radians(10.0), math.radians(200.0), math.radians(30.0), 1.2e6, 1e9, 8e5]])
+    o.set_boundary(np.zeros(1), mp, cme)
+    t0 = o.scales()["t0"]
+    tc, pc = centres(g, 1)[2:-2], centres(g, 2)[2:-2]
+    TH, PH = np.meshgrid(tc, pc, indexing="ij")
+    lat = np.pi / 2 - TH
+    # haversine angular distance (independent of the dot-product test used by the oracle)
+    dlat, dlon = lat - cme[0, 2], PH - cme[0, 3]
+    a = np.sin(dlat / 2) ** 2 + np.cos(lat) * np.cos(cme[0, 2]) * np.sin(dlon / 2) ** 2
+    dist = 2 * np.arcsin(np.sqrt(a))
+    inside = dist <= cme[0, 4]
+    assert np.all(np.abs(dist - cme[0, 4]) > 1e-9)        # no point on the rim
+    vals, hit = o.boundary_values(2 * 3600.0 / t0)
+    assert np.array_equal(hit.astype(bool), inside) and inside.sum() > 10
+    assert np.all(vals[1][inside] == 1.2e6 / 1e5)
+    assert np.allclose(vals[2][inside], 2 * 1e9 * 1.380649e-23 * 8e5 / o.scales()["p0"], rtol=1e-15)
+    for tt in (0.0, 3599.0, 9 * 3600.0, 20 * 3600.0):
+        _, hit = o.boundary_values(tt / t0)
+        assert hit.sum() == 0
