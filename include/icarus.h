@@ -1,0 +1,170 @@
+/*
+ * icarus.h -- C ABI of libicarus, the GB300 (sm_103a) hot path of the Icarus 3.0 dynamic
+ * heliosphere model (Baratashvili et al., arXiv 2501.15923).
+ *
+ * What the library computes (paper references are to that article):
+ *   - ideal MHD (Sect. 2, Eqs. 1-6: density, momentum, total energy, induction; p_tot =
+ *     p + B^2/2, mu0 = 1, gamma given at init) in the frame co-rotating with the Sun
+ *     (Sect. 2, Eqs. 2-3: F = rho (Omega x r) x Omega + 2 rho v x Omega in momentum, v.F in
+ *     energy) with solar gravity (Sect. 2, g = GM/r^2, applied as an inward pull);
+ *   - on a fixed spherical grid, radially stretched (dr ~ r) between r_in and r_out (Sect. 2,
+ *     Sect. 3.2: stretched grid, latitude +-60 deg);
+ *   - the r = r_in boundary driven by boundary maps interpolated linearly in time (Sect. 3),
+ *     the same value in every ghost layer (Sect. 2.1), asymm for v_theta, v_phi, B_theta
+ *     (Sect. 2.1), cone-CME injection (Sect. 3.2, "bc_icarus");
+ *   - the solution sampled along moving spacecraft trajectories (Sect. 2, particle sampling).
+ * The paper defers the scheme to its host framework; this library takes: limited linear
+ * reconstruction of primitives (minmod / van Leer / MC), TVDLF or HLL fluxes, SSP-RK2,
+ * two ghost layers, Linde-type div-B diffusion, dt = CFL / max_cells sum_d (|v_d|+c_f,d)/dx_d.
+ *
+ * Conventions
+ *   - Every call returns 0 on success or a negative ICARUS_E* code; icarus_last_error() gives a
+ *     message (thread-local). Host pointers are borrowed for the duration of the call only; the
+ *     library copies what it keeps. Device memory belongs to the context (allocated at init
+ *     through the allocator in icarus_options, cudaMalloc when none) and is released by
+ *     icarus_destroy.
+ *   - Units at the boundary of this API are SI unless a name says otherwise. Internally the
+ *     library works in code units: L0 = 1 AU, v0 = 100 km/s, n0 = 1 cm^-3 (rho0 = m_p * 1e6
+ *     kg/m^3), t0 = L0/v0, p0 = rho0 v0^2, B0 = sqrt(mu0 rho0) v0. State arrays exchanged by
+ *     icarus_get_state / icarus_set_state are in code units.
+ *   - State layout: [8][n3][n2][n1] doubles, index 1 (r) fastest; variables (rho, m_r, m_theta,
+ *     m_phi, e, B_r, B_theta, B_phi). Theta is the colatitude.
+ *   - icarus_step is asynchronous on the context stream. Device-side faults of the solution
+ *     (non-finite state) are recorded in a sticky status word and reported by the next
+ *     synchronising call (icarus_sample, icarus_get_state, icarus_status).
+ */
+#ifndef ICARUS_H
+#define ICARUS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ICARUS_OK = 0,
+    ICARUS_EINVAL = -1,      /* bad argument (sizes, NULL pointers, unsupported option) */
+    ICARUS_ESTATE = -2,      /* call made in the wrong order (e.g. step before boundary) */
+    ICARUS_ENOMEM = -3,      /* device allocation failed */
+    ICARUS_ECUDA = -4,       /* a CUDA runtime call failed */
+    ICARUS_ENONFINITE = -5,  /* the solution became non-finite (sticky) */
+    ICARUS_ETIMEOUT = -6     /* a bounded device wait gave up (batched form) */
+};
+
+enum { ICARUS_BC_PERIODIC = 0, ICARUS_BC_CONT = 1, ICARUS_BC_REFLECT = 2, ICARUS_BC_DRIVEN = 3 };
+enum { ICARUS_GEOM_SPHERICAL = 0, ICARUS_GEOM_CARTESIAN = 1 };
+enum { ICARUS_LIM_MINMOD = 0, ICARUS_LIM_VANLEER = 1, ICARUS_LIM_MC = 2 };
+enum { ICARUS_FLUX_TVDLF = 0, ICARUS_FLUX_HLL = 1 };
+enum { ICARUS_DIVB_NONE = 0, ICARUS_DIVB_LINDE = 1 };
+/* FP64: everything in double. FP32: state and arithmetic in float. MIXED: state, update
+ * accumulation and the dt reduction in double; primitives, reconstruction, fluxes and sources in
+ * float, except the primitive (pressure / positivity) recovery of the first four radial cells,
+ * which stays in double. */
+enum { ICARUS_FP64 = 0, ICARUS_FP32 = 1, ICARUS_MIXED = 2 };
+
+typedef struct {
+    int n1, n2, n3;        /* cells along r, theta, phi (x, y, z for Cartesian); each >= 1 */
+    int geometry;          /* ICARUS_GEOM_* (Cartesian is for verification problems) */
+    int stretch;           /* 1: r edges r_in (r_out/r_in)^(i/n1) (dr ~ r); 0: uniform */
+    double x1min, x1max;   /* r range in AU (spherical) */
+    double x2min, x2max;   /* colatitude range in rad (spherical; inside (0, pi)) */
+    double x3min, x3max;   /* longitude range in rad, co-rotating frame (spherical) */
+    int bc[6];             /* ICARUS_BC_* for (1-, 1+, 2-, 2+, 3-, 3+); DRIVEN only at 1- */
+} icarus_grid;
+
+typedef void *(*icarus_alloc_fn)(size_t bytes, void *user);
+typedef void (*icarus_free_fn)(void *ptr, void *user);
+
+typedef struct {
+    double cfl;            /* Courant number (0, 1] */
+    int limiter;           /* ICARUS_LIM_* */
+    int flux;              /* ICARUS_FLUX_* */
+    int gravity;           /* 1: solar gravity on */
+    int divb;              /* ICARUS_DIVB_* */
+    double divb_coef;      /* Linde coefficient C_d */
+    double rho_floor;      /* density floor, code units */
+    double p_floor;        /* pressure floor, code units */
+    int precision;         /* ICARUS_FP64 | ICARUS_FP32 | ICARUS_MIXED */
+    int ring_capacity;     /* probe records kept on the device between drains (>= 1) */
+    void *cuda_stream;     /* cudaStream_t to run on; NULL: the library creates its own */
+    icarus_alloc_fn alloc; /* device allocator (NULL: cudaMalloc); must return 256-B aligned */
+    icarus_free_fn free;   /* matching free (NULL: cudaFree) */
+    void *alloc_user;      /* passed to alloc / free */
+} icarus_options;
+
+typedef struct icarus_ctx icarus_ctx;
+
+/* Create a solver context on the current CUDA device: uploads the grid metrics (computed on
+ * the host in double), allocates the state, flux and scratch buffers.
+ * gamma: adiabatic index (Sect. 2: 1.5). omega_rot: rotation rate of the frame in rad/s (Sect. 2,
+ * the Sun's rotation). *out receives the context. EINVAL on bad sizes or options. */
+int icarus_init(const icarus_grid *grid, double gamma, double omega_rot,
+                const icarus_options *opts, icarus_ctx **out);
+
+/* Set the inner-boundary driving (Sect. 3): n_maps >= 1 maps at times t_maps[n_maps] (s,
+ * strictly increasing), maps[n_maps][5][n2][n3] in SI with fields (v_r m/s, n m^-3, p Pa,
+ * B_r T, B_phi T) at the grid's angular cell centres; between map times the values are linear
+ * in time, outside the table they are clamped to the first / last map. n_cme cone CMEs
+ * cmes[n_cme][8] = (t_on s, duration s, lat rad, lon rad (co-rotating), half_width rad,
+ * speed m/s, n m^-3, T K); inside the cone during [t_on, t_on + duration) the boundary takes
+ * v_r = speed, n, p = 2 n k_B T (Sect. 3.2). The first call also sets the initial state from
+ * the maps at the current time by radial expansion (Sect. 2.1) and computes the first dt.
+ * Later calls replace the maps and CMEs only. Synchronous. */
+int icarus_set_boundary(icarus_ctx *ctx, int n_maps, const double *t_maps, const double *maps,
+                        int n_cme, const double *cmes);
+
+/* Advance n >= 0 time steps (each: dt from the CFL bound, SSP-RK2 with the boundary refilled at
+ * each stage time, probes recorded at the new time). Asynchronous on the context stream; the
+ * steps run as replays of a captured CUDA graph. ESTATE before the first set_boundary /
+ * set_state. Returns the sticky status of earlier steps without synchronising. */
+int icarus_step(icarus_ctx *ctx, int n);
+
+/* Probe sampling (Sect. 2). traj[n_probes][n_knots][4] = (t s, r m, lat rad, lon rad in the
+ * inertial frame, unwrapped), knots in increasing t. If traj is non-NULL it is registered for
+ * the following steps and the current state is sampled once at the current time. Then the
+ * records kept on the device since the last drain are copied, oldest first, into
+ * out[cap][n_probes][13] = (t s, n m^-3, v_r, v_theta, v_phi (inertial) m/s, B_r, B_theta,
+ * B_phi T, p Pa, |B| T, i, j, k), with (i, j, k) the lower corner of the 2x2x2 cell-centre
+ * stencil used for the trilinear interpolation. *n_written receives the number of records
+ * (at most cap; older records beyond the ring capacity are lost). Synchronous. */
+int icarus_sample(icarus_ctx *ctx, int n_probes, int n_knots, const double *traj,
+                  double *out, int cap, int *n_written);
+
+/* Release all device memory of the context (synchronises its stream first). */
+int icarus_destroy(icarus_ctx *ctx);
+
+/* Copy the interior state [8][n3][n2][n1] (code units, double) and the time (code units) to
+ * the host. Synchronous; returns ENONFINITE if the status word is set. */
+int icarus_get_state(icarus_ctx *ctx, double *U, double *t);
+
+/* Replace the interior state (code units, double) and the time (code units); recomputes dt.
+ * Synchronous. Enables stepping without boundary maps when no face is DRIVEN. */
+int icarus_set_state(icarus_ctx *ctx, const double *U, double t);
+
+/* Cap dt so that the run stops exactly at t_stop (code units); t_stop <= 0 removes the cap. */
+int icarus_set_stop_time(icarus_ctx *ctx, double t_stop);
+
+/* Current time and the dt of the next step (code units). Synchronous. */
+int icarus_time(icarus_ctx *ctx, double *t, double *dt);
+
+/* Sticky status (0 or ENONFINITE) and the number of floor activations. Synchronous. */
+int icarus_status(icarus_ctx *ctx, long long *floor_hits);
+
+/* Code-unit scales: s[0] = t0 s, s[1] = p0 Pa, s[2] = B0 T, s[3] = Omega in rad per t0,
+ * s[4] = GM in code units. */
+int icarus_scales(icarus_ctx *ctx, double *s);
+
+/* Number of kernel launches one step makes (for launch accounting). */
+int icarus_launches_per_step(icarus_ctx *ctx);
+
+/* The cudaStream_t the context runs on (for events and ordering with other work). */
+void *icarus_get_stream(icarus_ctx *ctx);
+
+/* Message of the last failing call on this thread. */
+const char *icarus_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

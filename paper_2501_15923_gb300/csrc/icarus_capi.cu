@@ -1,0 +1,583 @@
+// icarus_capi.cu -- host runtime behind include/icarus.h: context, device memory, grid metrics,
+// boundary tables, CUDA-graph replay of the time step, probe ring drain, error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/icarus.h"
+#include "icarus_internal.cuh"
+#include "icarus_ops.h"
+
+using namespace icarus;
+
+namespace {
+
+// SI constants (CODATA 2018, IAU nominal) and code-unit scales
+const double AU = 1.495978707e11, MP = 1.67262192369e-27, KB = 1.380649e-23, MU0 = 1.25663706212e-6,
+             GMSUN = 1.32712440018e20, V0 = 1.0e5, N0 = 1.0e6, PI = 3.14159265358979323846;
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(ICARUS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+
+}  // namespace
+
+struct icarus_ctx {
+    Params P{};
+    Ops ops{};
+    icarus_grid grid{};
+    icarus_options opts{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void *> allocs;
+    void *U = nullptr, *U1 = nullptr, *W = nullptr, *W1 = nullptr;
+    void *F1 = nullptr, *F2 = nullptr, *F3 = nullptr, *divB = nullptr;
+    double *metric = nullptr, *partial = nullptr, *stage_buf = nullptr;
+    Scalars *sc = nullptr;
+    double *maps = nullptr, *tmaps = nullptr, *cme = nullptr, *traj = nullptr, *ring = nullptr;
+    size_t maps_cap = 0, cme_cap = 0, traj_cap = 0;
+    bool have_state = false, have_boundary = false;
+    cudaGraphExec_t graph = nullptr;
+    long long ring_tail = 0;
+    double t0, p0, b0, omega_code, gm_code;
+    int launches_per_step = 0;
+    std::vector<double> colvec_host;
+};
+
+namespace {
+
+void *dalloc(icarus_ctx *c, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (c->opts.alloc) p = c->opts.alloc(bytes, c->opts.alloc_user);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) c->allocs.push_back(p);
+    return p;
+}
+
+void dfree_all(icarus_ctx *c)
+{
+    for (void *p : c->allocs) {
+        if (c->opts.free) c->opts.free(p, c->opts.alloc_user);
+        else if (!c->opts.alloc) cudaFree(p);
+    }
+    c->allocs.clear();
+}
+
+void drop_graph(icarus_ctx *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
+// edges of direction d at padded edge index e (cell i has lower edge i, i in [-2, n+2])
+double edge(const icarus_grid &g, int d, int i)
+{
+    const int n = d == 0 ? g.n1 : (d == 1 ? g.n2 : g.n3);
+    const double lo = d == 0 ? g.x1min : (d == 1 ? g.x2min : g.x3min);
+    const double hi = d == 0 ? g.x1max : (d == 1 ? g.x2max : g.x3max);
+    if (g.geometry == ICARUS_GEOM_SPHERICAL && d == 0 && g.stretch) return lo * pow(hi / lo, (double)i / n);
+    return lo + i * ((hi - lo) / n);
+}
+
+// host-side metric tables (double), uploaded once; see Metrics for the meaning of each array
+int build_metrics(icarus_ctx *c)
+{
+    const icarus_grid &g = c->grid;
+    const Params &P = c->P;
+    const bool sph = g.geometry == ICARUS_GEOM_SPHERICAL;
+    const int p1 = P.p1, p2 = P.p2, p3 = P.p3;
+    std::vector<double> e1(p1 + 1), e2(p2 + 1), e3(p3 + 1);
+    for (int i = 0; i <= p1; ++i) e1[i] = edge(g, 0, i - NG);
+    for (int j = 0; j <= p2; ++j) e2[j] = edge(g, 1, j - NG);
+    for (int k = 0; k <= p3; ++k) e3[k] = edge(g, 2, k - NG);
+    auto ctr = [](const std::vector<double> &e, int i) { return 0.5 * (e[i] + e[i + 1]); };
+    const double d2 = (g.x2max - g.x2min) / g.n2, d3 = (g.x3max - g.x3min) / g.n3;
+    // layout of the single metric buffer
+    std::vector<double> buf;
+    std::vector<size_t> off;
+    auto push = [&](const std::vector<double> &v) { off.push_back(buf.size()); buf.insert(buf.end(), v.begin(), v.end()); };
+    std::vector<double> x1c(p1), a1(p1 + 1), iv1(p1), q1(p1), gp1(p1), iw1(p1), ih2(p1), ig1(p1), gmr2(p1);
+    for (int i = 0; i <= p1; ++i) a1[i] = sph ? e1[i] * e1[i] : 1.0;
+    for (int i = 0; i < p1; ++i) {
+        double rm = e1[i], rp = e1[i + 1];
+        x1c[i] = ctr(e1, i);
+        double v1 = sph ? (rp * rp * rp - rm * rm * rm) / 3.0 : (rp - rm);
+        iv1[i] = 1.0 / v1;
+        q1[i] = sph ? 0.5 * (rp * rp - rm * rm) / v1 : 1.0;
+        iw1[i] = 1.0 / (rp - rm);
+        ih2[i] = sph ? 1.0 / x1c[i] : 1.0;
+        gmr2[i] = sph ? c->gm_code / (x1c[i] * x1c[i]) : 0.0;
+    }
+    for (int i = 0; i < p1; ++i) {
+        gp1[i] = (a1[i + 1] - a1[i]) * iv1[i];
+        double xm = i > 0 ? x1c[i - 1] : x1c[i] - (x1c[i + 1] - x1c[i]);
+        double xp = i + 1 < p1 ? x1c[i + 1] : x1c[i] + (x1c[i] - x1c[i - 1]);
+        ig1[i] = 1.0 / (xp - xm);
+    }
+    std::vector<double> x2c(p2), a2(p2 + 1), iv2(p2), q2(p2), gq2(p2), sn(p2), cs(p2), ct(p2), is3(p2), ig2(p2);
+    for (int j = 0; j <= p2; ++j) a2[j] = sph ? sin(e2[j]) : 1.0;
+    for (int j = 0; j < p2; ++j) {
+        x2c[j] = ctr(e2, j);
+        double v2 = sph ? (cos(e2[j]) - cos(e2[j + 1])) : (e2[j + 1] - e2[j]);
+        iv2[j] = 1.0 / v2;
+        q2[j] = sph ? (e2[j + 1] - e2[j]) / v2 : 1.0;
+        gq2[j] = sph ? (a2[j + 1] - a2[j]) / v2 : 0.0;
+        sn[j] = sph ? sin(x2c[j]) : 1.0;
+        cs[j] = sph ? cos(x2c[j]) : 0.0;
+        ct[j] = sph ? cos(x2c[j]) / sin(x2c[j]) : 0.0;
+        is3[j] = sph ? 1.0 / sin(x2c[j]) : 1.0;
+    }
+    for (int j = 0; j < p2; ++j) {
+        double xm = j > 0 ? x2c[j - 1] : x2c[j] - d2;
+        double xp = j + 1 < p2 ? x2c[j + 1] : x2c[j] + d2;
+        ig2[j] = 1.0 / (xp - xm);
+    }
+    std::vector<double> x3c(p3), ig3(p3);
+    for (int k = 0; k < p3; ++k) x3c[k] = ctr(e3, k);
+    for (int k = 0; k < p3; ++k) {
+        double xm = k > 0 ? x3c[k - 1] : x3c[k] - d3;
+        double xp = k + 1 < p3 ? x3c[k + 1] : x3c[k] + d3;
+        ig3[k] = 1.0 / (xp - xm);
+    }
+    // CME footprint unit vectors of the boundary columns [3][n2][n3]
+    std::vector<double> col(3 * (size_t)g.n2 * g.n3);
+    const size_t per = (size_t)g.n2 * g.n3;
+    for (int j = 0; j < g.n2; ++j)
+        for (int k = 0; k < g.n3; ++k) {
+            double th = x2c[j + NG], ph = x3c[k + NG];
+            col[j * g.n3 + k] = sin(th) * cos(ph);
+            col[per + j * g.n3 + k] = sin(th) * sin(ph);
+            col[2 * per + j * g.n3 + k] = cos(th);
+        }
+    push(x1c); push(a1); push(iv1); push(q1); push(gp1); push(iw1); push(ih2); push(ig1); push(gmr2);
+    push(x2c); push(a2); push(iv2); push(q2); push(gq2); push(sn); push(cs); push(ct); push(is3); push(ig2);
+    push(x3c); push(ig3); push(col);
+    c->metric = (double *)dalloc(c, buf.size() * sizeof(double));
+    if (!c->metric) return fail(ICARUS_ENOMEM, "metric allocation failed");
+    CK(cudaMemcpyAsync(c->metric, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double *b = c->metric;
+    Metrics &m = c->P.m;
+    int q = 0;
+    m.x1c = b + off[q++]; m.a1 = b + off[q++]; m.iv1 = b + off[q++]; m.q1 = b + off[q++]; m.gp1 = b + off[q++];
+    m.iw1 = b + off[q++]; m.ih2 = b + off[q++]; m.ig1 = b + off[q++]; m.gm_r2 = b + off[q++];
+    m.x2c = b + off[q++]; m.a2 = b + off[q++]; m.iv2 = b + off[q++]; m.q2 = b + off[q++]; m.gq2 = b + off[q++];
+    m.sn = b + off[q++]; m.cs = b + off[q++]; m.ct = b + off[q++]; m.is3 = b + off[q++]; m.ig2 = b + off[q++];
+    m.x3c = b + off[q++]; m.ig3 = b + off[q++]; m.colvec = b + off[q++];
+    m.d2 = d2; m.d3 = d3;
+    m.id2 = 1.0 / d2; m.id3 = 1.0 / d3;
+    m.iv3 = sph ? 1.0 / d3 : 1.0 / d3;
+    return ICARUS_OK;
+}
+
+void enqueue_step(icarus_ctx *c)
+{
+    const Params &P = c->P;
+    cudaStream_t s = c->stream;
+    // stage 1: U, W at t  ->  U1, W1
+    c->ops.fill_ghosts(P, c->U, c->W, 1, s);
+    c->ops.fluxes(P, c->W, c->F1, c->F2, c->F3, s);
+    if (P.divb == 1) c->ops.divb(P, c->W, c->divB, s);
+    c->ops.update(P, 1, c->U, c->W, c->U1, c->W1, c->F1, c->F2, c->F3, c->divB, s);
+    // stage 2: U1, W1 at t + dt  ->  U, W (in place), next dt, t += dt
+    c->ops.fill_ghosts(P, c->U1, c->W1, 2, s);
+    c->ops.fluxes(P, c->W1, c->F1, c->F2, c->F3, s);
+    if (P.divb == 1) c->ops.divb(P, c->W1, c->divB, s);
+    c->ops.update(P, 2, c->U1, c->W1, c->U, c->W, c->F1, c->F2, c->F3, c->divB, s);
+    if (P.n_probes > 0) c->ops.probe(P, c->W, s);
+}
+
+int count_launches(const icarus_ctx *c)
+{
+    int per_stage = 3 + 3 + (c->P.divb == 1 ? 1 : 0) + 1;
+    return 2 * per_stage + (c->P.n_probes > 0 ? 1 : 0);
+}
+
+int build_graph(icarus_ctx *c)
+{
+    drop_graph(c);
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(c);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return fail(ICARUS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ICARUS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    c->launches_per_step = count_launches(c);
+    return ICARUS_OK;
+}
+
+int first_dt(icarus_ctx *c)
+{
+    c->ops.fill_ghosts(c->P, c->U, c->W, 1, c->stream);
+    c->ops.cfl(c->P, c->W, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return ICARUS_OK;
+}
+
+int check_grid(const icarus_grid *g)
+{
+    if (g->n1 < 1 || g->n2 < 1 || g->n3 < 1) return fail(ICARUS_EINVAL, "cell counts must be >= 1");
+    if ((long long)(g->n1 + 4) * (g->n2 + 4) * (g->n3 + 4) > (1LL << 31))
+        return fail(ICARUS_EINVAL, "grid too large (padded cells must fit in 2^31)");
+    if (g->geometry != ICARUS_GEOM_SPHERICAL && g->geometry != ICARUS_GEOM_CARTESIAN)
+        return fail(ICARUS_EINVAL, "unknown geometry %d", g->geometry);
+    if (!(g->x1max > g->x1min) || !(g->x2max > g->x2min) || !(g->x3max > g->x3min))
+        return fail(ICARUS_EINVAL, "empty coordinate range");
+    if (g->geometry == ICARUS_GEOM_SPHERICAL) {
+        if (!(g->x1min > 0)) return fail(ICARUS_EINVAL, "r_in must be > 0");
+        double d2 = (g->x2max - g->x2min) / g->n2;
+        if (!(g->x2min - 2 * d2 > 0) || !(g->x2max + 2 * d2 < PI))
+            return fail(ICARUS_EINVAL, "colatitude range with its ghost cells must stay inside (0, pi)");
+    }
+    for (int s = 0; s < 6; ++s) {
+        int b = g->bc[s];
+        if (b < 0 || b > 3) return fail(ICARUS_EINVAL, "bad boundary code %d on face %d", b, s);
+        if (b == ICARUS_BC_DRIVEN && (s != 0 || g->geometry != ICARUS_GEOM_SPHERICAL))
+            return fail(ICARUS_EINVAL, "DRIVEN is only valid on the inner radial face of a spherical grid");
+        int n = s < 2 ? g->n1 : (s < 4 ? g->n2 : g->n3);
+        if (b == ICARUS_BC_REFLECT && n < 2) return fail(ICARUS_EINVAL, "REFLECT needs >= 2 cells");
+    }
+    return ICARUS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *icarus_last_error(void) { return g_err.c_str(); }
+
+int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const icarus_options *opts, icarus_ctx **out)
+{
+    if (!grid || !opts || !out) return fail(ICARUS_EINVAL, "NULL argument");
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    if (!(gamma > 1.0)) return fail(ICARUS_EINVAL, "gamma must be > 1");
+    if (!(opts->cfl > 0.0 && opts->cfl <= 1.0)) return fail(ICARUS_EINVAL, "cfl must be in (0, 1]");
+    if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 1 || opts->divb < 0 || opts->divb > 1)
+        return fail(ICARUS_EINVAL, "bad limiter / flux / divb option");
+    if (opts->precision < 0 || opts->precision > 2) return fail(ICARUS_EINVAL, "bad precision");
+    if (opts->ring_capacity < 1) return fail(ICARUS_EINVAL, "ring_capacity must be >= 1");
+    icarus_ctx *c = new icarus_ctx();
+    c->grid = *grid;
+    c->opts = *opts;
+    c->ops = opts->precision == ICARUS_FP64 ? ops_fp64() : (opts->precision == ICARUS_FP32 ? ops_fp32() : ops_mixed());
+    if (opts->cuda_stream) c->stream = (cudaStream_t)opts->cuda_stream;
+    else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return fail(ICARUS_ECUDA, "stream creation failed");
+        }
+        c->own_stream = true;
+    }
+    Params &P = c->P;
+    P.n1 = grid->n1; P.n2 = grid->n2; P.n3 = grid->n3;
+    P.p1 = P.n1 + 2 * NG; P.p2 = P.n2 + 2 * NG; P.p3 = P.n3 + 2 * NG;
+    P.nt = (long long)P.p1 * P.p2 * P.p3;
+    P.geom = grid->geometry;
+    for (int s = 0; s < 6; ++s) P.bc[s] = grid->bc[s];
+    P.limiter = opts->limiter; P.flux = opts->flux; P.gravity = opts->gravity; P.divb = opts->divb;
+    P.gamma = gamma;
+    P.divb_coef = opts->divb_coef; P.rho_floor = opts->rho_floor; P.p_floor = opts->p_floor;
+    c->t0 = AU / V0;
+    const double rho0 = MP * N0;
+    c->p0 = rho0 * V0 * V0;
+    c->b0 = sqrt(MU0 * rho0) * V0;
+    c->omega_code = grid->geometry == ICARUS_GEOM_SPHERICAL ? omega_rot * c->t0 : 0.0;
+    c->gm_code = GMSUN / (AU * V0 * V0);
+    if (grid->geometry != ICARUS_GEOM_SPHERICAL) P.gravity = 0;
+    P.omega = c->omega_code;
+    P.omega_si = grid->geometry == ICARUS_GEOM_SPHERICAL ? omega_rot : 0.0;
+    P.t0 = c->t0; P.b0 = c->b0; P.p0 = c->p0;
+    P.ring_cap = opts->ring_capacity;
+    rc = build_metrics(c);
+    if (rc) { icarus_destroy(c); return rc; }
+    const size_t nt = P.nt, ts = c->ops.ts_size, tw = c->ops.tw_size;
+    c->U = dalloc(c, NV * nt * ts);
+    c->U1 = dalloc(c, NV * nt * ts);
+    c->W = dalloc(c, NV * nt * tw);
+    c->W1 = dalloc(c, NV * nt * tw);
+    c->F1 = dalloc(c, NV * (size_t)P.n3 * P.n2 * (P.n1 + 1) * tw);
+    c->F2 = dalloc(c, NV * (size_t)P.n3 * (P.n2 + 1) * P.n1 * tw);
+    c->F3 = dalloc(c, NV * (size_t)(P.n3 + 1) * P.n2 * P.n1 * tw);
+    c->divB = dalloc(c, nt * tw);
+    const long long ncell = (long long)P.n1 * P.n2 * P.n3;
+    const long long nblk = (ncell + 255) / 256;
+    c->partial = (double *)dalloc(c, (size_t)nblk * sizeof(double));
+    c->sc = (Scalars *)dalloc(c, sizeof(Scalars));
+    c->stage_buf = (double *)dalloc(c, NV * (size_t)ncell * sizeof(double));
+    if (!c->U || !c->U1 || !c->W || !c->W1 || !c->F1 || !c->F2 || !c->F3 || !c->divB || !c->partial || !c->sc || !c->stage_buf) {
+        icarus_destroy(c);
+        return fail(ICARUS_ENOMEM, "device allocation failed");
+    }
+    P.partial = c->partial;
+    P.sc = c->sc;
+    Scalars s0{};
+    s0.cfl = opts->cfl;
+    CK(cudaMemsetAsync(c->U, 0, NV * nt * ts, c->stream));
+    CK(cudaMemsetAsync(c->U1, 0, NV * nt * ts, c->stream));
+    CK(cudaMemsetAsync(c->W, 0, NV * nt * tw, c->stream));
+    CK(cudaMemsetAsync(c->W1, 0, NV * nt * tw, c->stream));
+    CK(cudaMemsetAsync(c->divB, 0, nt * tw, c->stream));
+    CK(cudaMemcpyAsync(c->sc, &s0, sizeof s0, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *out = c;
+    return ICARUS_OK;
+}
+
+int icarus_set_boundary(icarus_ctx *c, int n_maps, const double *t_maps, const double *maps, int n_cme, const double *cmes)
+{
+    if (!c) return fail(ICARUS_EINVAL, "NULL context");
+    if (n_maps < 1 || !t_maps || !maps) return fail(ICARUS_EINVAL, "need n_maps >= 1 maps with their times");
+    if (n_cme < 0 || (n_cme > 0 && !cmes)) return fail(ICARUS_EINVAL, "bad CME table");
+    for (int m = 1; m < n_maps; ++m)
+        if (!(t_maps[m] > t_maps[m - 1])) return fail(ICARUS_EINVAL, "map times must increase");
+    Params &P = c->P;
+    const size_t per = (size_t)P.n2 * P.n3;
+    std::vector<double> hm((size_t)n_maps * 5 * per), ht(n_maps);
+    for (int m = 0; m < n_maps; ++m) {
+        ht[m] = t_maps[m] / c->t0;
+        const double *src = maps + (size_t)m * 5 * per;
+        double *dst = hm.data() + (size_t)m * 5 * per;
+        for (size_t q = 0; q < per; ++q) {
+            dst[q] = src[q] / V0;
+            dst[per + q] = src[per + q] / N0;
+            dst[2 * per + q] = src[2 * per + q] / c->p0;
+            dst[3 * per + q] = src[3 * per + q] / c->b0;
+            dst[4 * per + q] = src[4 * per + q] / c->b0;
+        }
+    }
+    std::vector<double> hc(9 * (size_t)(n_cme > 0 ? n_cme : 1));
+    for (int q = 0; q < n_cme; ++q) {
+        const double *s = cmes + 8 * q;
+        double *d = hc.data() + 9 * q;
+        d[0] = s[0] / c->t0;
+        d[1] = s[1] / c->t0;
+        d[2] = cos(s[2]) * cos(s[3]);
+        d[3] = cos(s[2]) * sin(s[3]);
+        d[4] = sin(s[2]);
+        d[5] = cos(s[4]);
+        d[6] = s[5] / V0;
+        d[7] = s[6] / N0;
+        d[8] = 2.0 * s[6] * KB * s[7] / c->p0;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    if (hm.size() > c->maps_cap) {
+        c->maps = (double *)dalloc(c, hm.size() * sizeof(double));
+        c->tmaps = (double *)dalloc(c, n_maps * sizeof(double));
+        if (!c->maps || !c->tmaps) return fail(ICARUS_ENOMEM, "map allocation failed");
+        c->maps_cap = hm.size();
+    }
+    if (hc.size() > c->cme_cap) {
+        c->cme = (double *)dalloc(c, hc.size() * sizeof(double));
+        if (!c->cme) return fail(ICARUS_ENOMEM, "CME allocation failed");
+        c->cme_cap = hc.size();
+    }
+    CK(cudaMemcpyAsync(c->maps, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->tmaps, ht.data(), ht.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->cme, hc.data(), hc.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    P.maps = c->maps; P.t_maps = c->tmaps; P.cme = c->cme;
+    P.n_maps = n_maps; P.n_cme = n_cme;
+    drop_graph(c);
+    c->have_boundary = true;
+    if (!c->have_state) {
+        if (c->grid.geometry != ICARUS_GEOM_SPHERICAL) return fail(ICARUS_EINVAL, "initial state from maps needs a spherical grid");
+        c->ops.init_state(P, c->U, c->W, c->grid.x1min, c->stream);
+        CK(cudaGetLastError());
+        c->have_state = true;
+        int rc = first_dt(c);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return ICARUS_OK;
+}
+
+int icarus_step(icarus_ctx *c, int n)
+{
+    if (!c) return fail(ICARUS_EINVAL, "NULL context");
+    if (n < 0) return fail(ICARUS_EINVAL, "n must be >= 0");
+    if (!c->have_state) return fail(ICARUS_ESTATE, "no state: call icarus_set_boundary or icarus_set_state first");
+    if (c->grid.bc[0] == ICARUS_BC_DRIVEN && !c->have_boundary) return fail(ICARUS_ESTATE, "DRIVEN boundary without maps");
+    if (!c->graph) {
+        int rc = build_graph(c);
+        if (rc) return rc;
+    }
+    for (int q = 0; q < n; ++q) CK(cudaGraphLaunch(c->graph, c->stream));
+    return ICARUS_OK;
+}
+
+int icarus_sample(icarus_ctx *c, int n_probes, int n_knots, const double *traj, double *out, int cap, int *n_written)
+{
+    if (!c) return fail(ICARUS_EINVAL, "NULL context");
+    if (traj) {
+        if (n_probes < 1 || n_probes > 1024 || n_knots < 1) return fail(ICARUS_EINVAL, "need 1..1024 probes and >= 1 knot");
+        if (!c->have_state) return fail(ICARUS_ESTATE, "no state to sample");
+        size_t tn = (size_t)n_probes * n_knots * 4;
+        CK(cudaStreamSynchronize(c->stream));
+        if (tn > c->traj_cap) {
+            c->traj = (double *)dalloc(c, tn * sizeof(double));
+            if (!c->traj) return fail(ICARUS_ENOMEM, "trajectory allocation failed");
+            c->traj_cap = tn;
+        }
+        if (n_probes != c->P.n_probes || !c->ring) {
+            c->ring = (double *)dalloc(c, (size_t)c->P.ring_cap * n_probes * IC_NPROBE_REC * sizeof(double));
+            if (!c->ring) return fail(ICARUS_ENOMEM, "ring allocation failed");
+        }
+        CK(cudaMemcpyAsync(c->traj, traj, tn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        // a new registration starts an empty ring
+        long long head = 0;
+        CK(cudaMemcpyAsync(&c->sc->ring_head, &head, sizeof head, cudaMemcpyHostToDevice, c->stream));
+        c->ring_tail = 0;
+        c->P.traj = c->traj; c->P.ring = c->ring;
+        c->P.n_probes = n_probes; c->P.n_knots = n_knots;
+        drop_graph(c);
+        c->ops.probe(c->P, c->W, c->stream);
+        CK(cudaGetLastError());
+    }
+    if (n_written) *n_written = 0;
+    if (c->P.n_probes == 0) return ICARUS_OK;
+    Scalars s;
+    CK(cudaMemcpyAsync(&s, c->sc, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    long long head = s.ring_head, tail = c->ring_tail;
+    if (head - tail > c->P.ring_cap) tail = head - c->P.ring_cap;
+    long long avail = head - tail;
+    if (out && cap > 0) {
+        long long nrec = avail < cap ? avail : cap;
+        const size_t rec = (size_t)c->P.n_probes * IC_NPROBE_REC;
+        for (long long q = 0; q < nrec; ++q) {
+            long long slot = (tail + q) % c->P.ring_cap;
+            CK(cudaMemcpyAsync(out + q * rec, c->ring + slot * rec, rec * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        }
+        CK(cudaStreamSynchronize(c->stream));
+        c->ring_tail = tail + nrec;
+        if (n_written) *n_written = (int)nrec;
+    }
+    if (s.status & 1) return fail(ICARUS_ENONFINITE, "the solution became non-finite");
+    return ICARUS_OK;
+}
+
+int icarus_destroy(icarus_ctx *c)
+{
+    if (!c) return ICARUS_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    dfree_all(c);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return ICARUS_OK;
+}
+
+int icarus_get_state(icarus_ctx *c, double *U, double *t)
+{
+    if (!c || !U) return fail(ICARUS_EINVAL, "NULL argument");
+    const Params &P = c->P;
+    const size_t n = NV * (size_t)P.n1 * P.n2 * P.n3;
+    c->ops.pack(P, c->U, c->stage_buf, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(U, c->stage_buf, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    Scalars s;
+    CK(cudaMemcpyAsync(&s, c->sc, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (t) *t = s.t;
+    if (s.status & 1) return fail(ICARUS_ENONFINITE, "the solution became non-finite");
+    return ICARUS_OK;
+}
+
+int icarus_set_state(icarus_ctx *c, const double *U, double t)
+{
+    if (!c || !U) return fail(ICARUS_EINVAL, "NULL argument");
+    const Params &P = c->P;
+    const size_t n = NV * (size_t)P.n1 * P.n2 * P.n3;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(c->stage_buf, U, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    c->ops.unpack(P, c->U, c->stage_buf, c->stream);
+    c->ops.prims(P, c->U, c->W, c->stream);
+    Scalars s;
+    CK(cudaMemcpyAsync(&s, c->sc, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    s.t = t;
+    s.status = 0;
+    s.done = 0;
+    CK(cudaMemcpyAsync(c->sc, &s, sizeof s, cudaMemcpyHostToDevice, c->stream));
+    c->have_state = true;
+    if (c->grid.bc[0] == ICARUS_BC_DRIVEN && !c->have_boundary) {
+        CK(cudaStreamSynchronize(c->stream));
+        return ICARUS_OK;   // dt is computed once the maps arrive
+    }
+    return first_dt(c);
+}
+
+int icarus_set_stop_time(icarus_ctx *c, double t_stop)
+{
+    if (!c) return fail(ICARUS_EINVAL, "NULL context");
+    Scalars s;
+    CK(cudaMemcpyAsync(&s, c->sc, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    s.t_stop = t_stop;
+    CK(cudaMemcpyAsync(c->sc, &s, sizeof s, cudaMemcpyHostToDevice, c->stream));
+    if (c->have_state && (c->grid.bc[0] != ICARUS_BC_DRIVEN || c->have_boundary)) return first_dt(c);
+    CK(cudaStreamSynchronize(c->stream));
+    return ICARUS_OK;
+}
+
+int icarus_time(icarus_ctx *c, double *t, double *dt)
+{
+    if (!c) return fail(ICARUS_EINVAL, "NULL context");
+    Scalars s;
+    CK(cudaMemcpyAsync(&s, c->sc, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (t) *t = s.t;
+    if (dt) *dt = s.dt;
+    return ICARUS_OK;
+}
+
+int icarus_status(icarus_ctx *c, long long *floor_hits)
+{
+    if (!c) return fail(ICARUS_EINVAL, "NULL context");
+    Scalars s;
+    CK(cudaMemcpyAsync(&s, c->sc, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (floor_hits) *floor_hits = (long long)s.floor_hits;
+    if (s.status & 1) return fail(ICARUS_ENONFINITE, "the solution became non-finite");
+    return ICARUS_OK;
+}
+
+int icarus_scales(icarus_ctx *c, double *s)
+{
+    if (!c || !s) return fail(ICARUS_EINVAL, "NULL argument");
+    s[0] = c->t0; s[1] = c->p0; s[2] = c->b0; s[3] = c->omega_code; s[4] = c->gm_code;
+    return ICARUS_OK;
+}
+
+int icarus_launches_per_step(icarus_ctx *c)
+{
+    if (!c) return fail(ICARUS_EINVAL, "NULL context");
+    return count_launches(c);
+}
+
+void *icarus_get_stream(icarus_ctx *c) { return c ? (void *)c->stream : nullptr; }
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// icarus_internal.cuh -- device-side data layout and physics of libicarus (sm_103a).
+//
+// Layout in HBM: every cell field is a structure-of-arrays plane over the padded grid
+// (n1+4) x (n2+4) x (n3+4) (two ghost layers per side), index 1 (r) fastest, field-major:
+// U[f * nt + ((k + 2) * p2 + (j + 2)) * p1 + (i + 2)]. Face fluxes live in three arrays
+// F1[8][n3][n2][n1+1], F2[8][n3][n2+1][n1], F3[8][n3+1][n2][n1]. Grid metrics are small 1-D
+// arrays computed on the host in double (products of per-axis factors for volumes and areas).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define NV 8
+#define NG 2
+#define IC_NPROBE_REC 13
+
+namespace icarus {
+
+enum { RHO = 0, M1 = 1, M2 = 2, M3 = 3, EN = 4, B1 = 5, B2 = 6, B3 = 7 };
+
+// per-axis metric arrays (device pointers). Index convention: padded index ip = i + NG.
+struct Metrics {
+    // r (or x): [p1] unless noted
+    const double *x1c;   // centres
+    const double *a1;    // lower-face area factor, [p1 + 1] (r^2 | 1)
+    const double *iv1;   // 1 / volume factor ((r+^3 - r-^3)/3 | dx)
+    const double *q1;    // (r+^2 - r-^2)/2 / v1  (| 1)
+    const double *gp1;   // (a1[i+1] - a1[i]) / v1 (geometric pressure term in m_r)
+    const double *iw1;   // 1 / radial width
+    const double *ih2;   // 1 / r_c (| 1)
+    const double *ig1;   // 1 / (x1c[i+1] - x1c[i-1])
+    const double *gm_r2; // GM / r_c^2
+    // theta (or y): [p2] unless noted
+    const double *x2c;
+    const double *a2;    // lower-face area factor, [p2 + 1] (sin theta- | 1)
+    const double *iv2;   // 1 / (cos theta- - cos theta+ | dy)
+    const double *q2;    // dtheta / v2 (| 1)
+    const double *gq2;   // (a2[j+1] - a2[j]) / v2 (geometric pressure term in m_theta)
+    const double *sn;    // sin theta_c (| 1)
+    const double *cs;    // cos theta_c (| 0)
+    const double *ct;    // cot theta_c (| 0)
+    const double *is3;   // 1 / sin theta_c (| 1)
+    const double *ig2;   // 1 / (x2c[j+1] - x2c[j-1])
+    // phi (or z): [p3]
+    const double *x3c;
+    const double *ig3;   // 1 / (x3c[k+1] - x3c[k-1])
+    double id2, id3, iv3;  // 1/dtheta, 1/dphi, 1/v3 (1/dphi | 1/dz)
+    double d2, d3;
+    // CME footprint: unit vector of each boundary column centre, [3][n2][n3]
+    const double *colvec;
+};
+
+struct Scalars {               // device-resident step state
+    double t, dt, t_stop, cfl;
+    unsigned long long smax_bits;   // unused slot kept for alignment
+    unsigned int done;              // last-block counter of the CFL reduction
+    int status;                     // bit 0: non-finite state
+    unsigned long long floor_hits;
+    long long ring_head;            // probe records written so far
+};
+
+struct Params {
+    int n1, n2, n3, p1, p2, p3;
+    long long nt;
+    int geom, bc[6];
+    int limiter, flux, gravity, divb;
+    double gamma, omega, divb_coef, rho_floor, p_floor;
+    Metrics m;
+    // boundary driving (code units)
+    int n_maps, n_cme;
+    const double *t_maps;   // [n_maps]
+    const double *maps;     // [n_maps][5][n2][n3] (v_r, rho, p, B_r, B_phi)
+    const double *cme;      // [n_cme][8] (t_on, dur, ax, ay, az, cos_hw, v_r, rho) + p in [n_cme] extra
+    // probes
+    int n_probes, n_knots, ring_cap;
+    const double *traj;     // [P][K][4] SI
+    double *ring;           // [cap][P][13]
+    double t0, omega_si, b0, p0;
+    Scalars *sc;
+    double *partial;        // [n_blocks] CFL partial maxima (scratch)
+};
+
+__host__ __device__ inline long long cidx(const Params &P, int i, int j, int k)
+{
+    return ((long long)(k + NG) * P.p2 + (j + NG)) * P.p1 + (i + NG);
+}
+
+// ---- physics (templated on the arithmetic type R) --------------------------------------------
+template <typename R> struct Prim { R v[NV]; };   // rho, v1, v2, v3, p, B1, B2, B3
+
+template <typename R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
+template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+template <typename R> __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
+
+// conserved -> primitive: v = m / rho, p = (gamma - 1)(e - rho v^2 / 2 - B^2 / 2)
+template <typename R> __device__ __forceinline__ void cons2prim(const R *u, R *w, R gm1)
+{
+    R irho = R(1) / u[RHO];
+    w[0] = u[RHO];
+    w[1] = u[M1] * irho;
+    w[2] = u[M2] * irho;
+    w[3] = u[M3] * irho;
+    R ke = R(0.5) * (u[M1] * w[1] + u[M2] * w[2] + u[M3] * w[3]);
+    R me = R(0.5) * (u[B1] * u[B1] + u[B2] * u[B2] + u[B3] * u[B3]);
+    w[4] = gm1 * (u[EN] - ke - me);
+    w[5] = u[B1];
+    w[6] = u[B2];
+    w[7] = u[B3];
+}
+
+template <typename R> __device__ __forceinline__ void prim2cons(const R *w, R *u, R igm1)
+{
+    u[RHO] = w[0];
+    u[M1] = w[0] * w[1];
+    u[M2] = w[0] * w[2];
+    u[M3] = w[0] * w[3];
+    u[EN] = w[4] * igm1 + R(0.5) * (u[M1] * w[1] + u[M2] * w[2] + u[M3] * w[3])
+          + R(0.5) * (w[5] * w[5] + w[6] * w[6] + w[7] * w[7]);
+    u[B1] = w[5];
+    u[B2] = w[6];
+    u[B3] = w[7];
+}
+
+// fast magnetosonic speed along direction d:
+// c_f^2 = ((a^2 + b^2) + sqrt((a^2 + b^2)^2 - 4 a^2 B_d^2 / rho)) / 2, a^2 = gamma p / rho
+template <typename R> __device__ __forceinline__ R fast_speed(const R *w, R irho, int d, R gamma)
+{
+    R a2 = gamma * w[4] * irho;
+    R bb = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
+    R s = a2 + bb * irho;
+    R bn = w[5 + d];
+    R disc = s * s - R(4) * a2 * (bn * bn * irho);
+    disc = rmax(disc, R(0));
+    return sqrt(R(0.5) * (s + sqrt(disc)));
+}
+
+template <typename R> __device__ __forceinline__ R limiter(int lim, R a, R b)
+{
+    bool same = (a > R(0) && b > R(0)) || (a < R(0) && b < R(0));
+    if (!same) return R(0);
+    if (lim == 1) return R(2) * a * b / (a + b);                 // van Leer
+    if (lim == 0) return rabs(a) < rabs(b) ? a : b;             // minmod
+    R m = rmin(rmin(R(2) * rabs(a), R(2) * rabs(b)), R(0.5) * rabs(a + b));   // MC
+    return a > R(0) ? m : -m;
+}
+
+// Riemann flux across a face normal to d from left / right primitive states.
+// TVDLF: (F_L + F_R)/2 - c_max (U_R - U_L)/2; HLL with signal speeds from the fast speeds.
+template <typename R>
+__device__ __forceinline__ void riemann(const R *wl, const R *wr, int d, int flux, R gamma, R igm1, R *f)
+{
+    R ul[NV], ur[NV];
+    prim2cons(wl, ul, igm1);
+    prim2cons(wr, ur, igm1);
+    R irl = R(1) / wl[0], irr = R(1) / wr[0];
+    R cl = fast_speed(wl, irl, d, gamma), cr = fast_speed(wr, irr, d, gamma);
+    R fl[NV], fr[NV];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const R *w = s ? wr : wl;
+        const R *u = s ? ur : ul;
+        R *ff = s ? fr : fl;
+        R vn = w[1 + d], bn = w[5 + d];
+        R bb = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
+        R bv = w[5] * w[1] + w[6] * w[2] + w[7] * w[3];
+        R pt = w[4] + R(0.5) * bb;
+        ff[RHO] = u[RHO] * vn;
+        ff[M1] = u[M1] * vn - w[5] * bn;
+        ff[M2] = u[M2] * vn - w[6] * bn;
+        ff[M3] = u[M3] * vn - w[7] * bn;
+        ff[M1 + d] += pt;
+        ff[EN] = (u[EN] + pt) * vn - bn * bv;
+        ff[B1] = vn * w[5] - bn * w[1];
+        ff[B2] = vn * w[6] - bn * w[2];
+        ff[B3] = vn * w[7] - bn * w[3];
+    }
+    if (flux == 0) {
+        R c = rmax(rabs(wl[1 + d]) + cl, rabs(wr[1 + d]) + cr);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * c * (ur[v] - ul[v]);
+    } else {
+        R sl = rmin(wl[1 + d] - cl, wr[1 + d] - cr);
+        R sr = rmax(wl[1 + d] + cl, wr[1 + d] + cr);
+        if (sl >= R(0)) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) f[v] = fl[v];
+        } else if (sr <= R(0)) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) f[v] = fr[v];
+        } else {
+            R idn = R(1) / (sr - sl);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) f[v] = (sr * fl[v] - sl * fr[v] + sl * sr * (ur[v] - ul[v])) * idn;
+        }
+    }
+}
+
+}  // namespace icarus

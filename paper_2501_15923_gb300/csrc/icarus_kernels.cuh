@@ -1,0 +1,755 @@
+// icarus_kernels.cuh -- the hot-path kernels of libicarus, templated on the state type TS and the
+// arithmetic / primitive type TW:
+//   FP64  : TS = double, TW = double
+//   FP32  : TS = float,  TW = float
+//   MIXED : TS = double, TW = float (update accumulation, dt reduction and the primitive recovery
+//           of the first four radial cells in double)
+// One time step = ghost fill (3 kernels) + face fluxes (3 kernels, one per direction) + div B +
+// update, twice (SSP-RK2 stages), then the probe kernel. dt and t stay on the device.
+#pragma once
+#include <cstdio>
+
+#include "icarus_internal.cuh"
+#include "icarus_ops.h"
+
+namespace icarus {
+
+template <typename TS, typename TW> struct Prec {
+    static constexpr bool mixed = sizeof(TS) == 8 && sizeof(TW) == 4;
+};
+
+// ---------------------------------------------------------------------------------------------
+// primitive recovery of one cell in the precision the mode asks for
+template <typename TS, typename TW>
+__device__ __forceinline__ void recover(const TS *u, TW *w, double gamma, int i)
+{
+    if (Prec<TS, TW>::mixed && i < 4) {
+        double ud[NV], wd[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) ud[v] = (double)u[v];
+        cons2prim<double>(ud, wd, gamma - 1.0);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w[v] = (TW)wd[v];
+    } else {
+        TW uw[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) uw[v] = (TW)u[v];
+        cons2prim<TW>(uw, w, TW(gamma - 1.0));
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// ghost fill along r: inner side driven by the maps (+ CME) or a plain rule, outer side a plain
+// rule. One thread per interior (j, k) column.
+template <typename TS, typename TW>
+__global__ void k_bnd1(Params P, TS *__restrict__ U, TW *__restrict__ W, int stage)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int k = blockIdx.y;
+    if (j >= P.n2 || k >= P.n3) return;
+    const long long nt = P.nt;
+    // inner face
+    int bc = P.bc[0];
+    if (bc == 3) {
+        double tau = P.sc->t;
+        if (stage == 2) tau = __dadd_rn(tau, P.sc->dt);
+        // time bracket (clamped outside the table)
+        int m0 = 0, m1 = 0;
+        double w = 0.0;
+        int nm = P.n_maps;
+        if (nm > 1 && tau > P.t_maps[0]) {
+            if (tau >= P.t_maps[nm - 1]) {
+                m0 = m1 = nm - 1;
+            } else {
+                int m = 0;
+                while (m + 1 < nm - 1 && P.t_maps[m + 1] <= tau) ++m;
+                m0 = m; m1 = m + 1;
+                w = __ddiv_rn(__dsub_rn(tau, P.t_maps[m]), __dsub_rn(P.t_maps[m + 1], P.t_maps[m]));
+                w = fmin(fmax(w, 0.0), 1.0);
+            }
+        }
+        const long long per = (long long)P.n2 * P.n3;
+        const long long col = (long long)j * P.n3 + k;
+        double q[5];
+        const int ord[5] = {1, 0, 2, 3, 4};   // maps hold (v_r, rho, p, B_r, B_phi)
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            double a = P.maps[((long long)m0 * 5 + ord[f]) * per + col];
+            double b = P.maps[((long long)m1 * 5 + ord[f]) * per + col];
+            q[f] = __dadd_rn(__dmul_rn(__dsub_rn(1.0, w), a), __dmul_rn(w, b));
+        }
+        // cone CME: footprint by the dot product of unit vectors against cos(half-width)
+        for (int c = 0; c < P.n_cme; ++c) {
+            const double *cm = P.cme + 9 * c;
+            if (!(tau >= cm[0] && tau < __dadd_rn(cm[0], cm[1]))) continue;
+            double ex = P.m.colvec[col], ey = P.m.colvec[per + col], ez = P.m.colvec[2 * per + col];
+            double dot = __dadd_rn(__dadd_rn(__dmul_rn(ex, cm[2]), __dmul_rn(ey, cm[3])), __dmul_rn(ez, cm[4]));
+            if (dot >= cm[5]) { q[0] = cm[7]; q[1] = cm[6]; q[2] = cm[8]; }
+        }
+        const double igm1 = 1.0 / (P.gamma - 1.0);
+#pragma unroll
+        for (int g = 1; g <= NG; ++g) {
+            long long cm_ = cidx(P, g - 1, j, k);
+            long long cg = cidx(P, -g, j, k);
+            double wg[NV], ug[NV];
+            wg[0] = q[0]; wg[1] = q[1]; wg[4] = q[2]; wg[5] = q[3]; wg[7] = q[4];
+            // asymm: v_theta, v_phi, B_theta of the mirror cell with the sign flipped
+            wg[2] = -(double)W[2 * nt + cm_];
+            wg[3] = -(double)W[3 * nt + cm_];
+            wg[6] = -(double)W[6 * nt + cm_];
+            prim2cons<double>(wg, ug, igm1);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                U[v * nt + cg] = (TS)ug[v];
+                W[v * nt + cg] = (TW)wg[v];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int g = 1; g <= NG; ++g) {
+            int src = bc == 1 ? 0 : (bc == 2 ? g - 1 : ((-g % P.n1) + P.n1) % P.n1);
+            long long cs = cidx(P, src, j, k), cg = cidx(P, -g, j, k);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                TS uu = U[v * nt + cs];
+                TW ww = W[v * nt + cs];
+                if (bc == 2 && (v == M1 || v == B1)) { uu = -uu; ww = -ww; }
+                U[v * nt + cg] = uu;
+                W[v * nt + cg] = ww;
+            }
+        }
+    }
+    // outer face
+    bc = P.bc[1];
+#pragma unroll
+    for (int g = 1; g <= NG; ++g) {
+        int gi = P.n1 - 1 + g;
+        int src = bc == 1 ? P.n1 - 1 : (bc == 2 ? P.n1 - g : (gi % P.n1));
+        long long cs = cidx(P, src, j, k), cg = cidx(P, gi, j, k);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            TS uu = U[v * nt + cs];
+            TW ww = W[v * nt + cs];
+            if (bc == 2 && (v == M1 || v == B1)) { uu = -uu; ww = -ww; }
+            U[v * nt + cg] = uu;
+            W[v * nt + cg] = ww;
+        }
+    }
+}
+
+// ghost fill along theta (D = 1) or phi (D = 2) by copy / reflection / periodic images.
+// D = 1 covers every r (ghosts included) and interior phi; D = 2 covers everything.
+template <int D, typename TS, typename TW>
+__global__ void k_bnd23(Params P, TS *__restrict__ U, TW *__restrict__ W)
+{
+    int ip = blockIdx.x * blockDim.x + threadIdx.x;     // padded r index
+    int o = blockIdx.y;                                 // other index
+    if (ip >= P.p1) return;
+    int i = ip - NG;
+    const int n = D == 1 ? P.n2 : P.n3;
+    const long long nt = P.nt;
+    if (D == 1 && o >= P.n3) return;
+    if (D == 2 && o >= P.p2) return;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        int bc = P.bc[2 * D + side];
+#pragma unroll
+        for (int g = 1; g <= NG; ++g) {
+            int gi = side == 0 ? -g : n - 1 + g;
+            int src;
+            if (bc == 1) src = side == 0 ? 0 : n - 1;
+            else if (bc == 2) src = side == 0 ? g - 1 : n - g;
+            else src = ((gi % n) + n) % n;
+            long long cs, cg;
+            if (D == 1) { cs = cidx(P, i, src, o); cg = cidx(P, i, gi, o); }
+            else { cs = cidx(P, i, o - NG, src); cg = cidx(P, i, o - NG, gi); }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                TS uu = U[v * nt + cs];
+                TW ww = W[v * nt + cs];
+                if (bc == 2 && (v == M1 + D || v == B1 + D)) { uu = -uu; ww = -ww; }
+                U[v * nt + cg] = uu;
+                W[v * nt + cg] = ww;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// fused reconstruction + face flux along direction D. Threads sweep S cells along D; each cell's
+// limited slopes are computed once, its face states are exchanged through shared memory and
+// every thread but the first computes the flux through the lower face of its cell.
+// D = 0: block (128, 1), faces f0 .. f0+126 of one (j, k) row.
+// D = 1, 2: block (16 r, 16 sweep), 15 faces along D for 16 consecutive r.
+template <int D, typename TW> struct FluxShape {
+    static constexpr int BX = D == 0 ? 128 : 16;
+    static constexpr int BY = D == 0 ? 1 : 16;
+    static constexpr int S = D == 0 ? BX : BY;
+};
+
+template <int D, typename TW>
+__global__ void __launch_bounds__(FluxShape<D, TW>::BX * FluxShape<D, TW>::BY)
+k_flux(Params P, const TW *__restrict__ W, TW *__restrict__ F)
+{
+    constexpr int BX = FluxShape<D, TW>::BX, BY = FluxShape<D, TW>::BY, S = FluxShape<D, TW>::S;
+    __shared__ TW sW[NV][BY][BX];
+    __shared__ TW sP[NV][BY][BX];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ts = D == 0 ? tx : ty;
+    int i, j, k, s, nD;
+    if (D == 0) {
+        nD = P.n1;
+        s = blockIdx.x * (S - 1) - 1 + tx;
+        i = s; j = blockIdx.y; k = blockIdx.z;
+    } else if (D == 1) {
+        nD = P.n2;
+        i = blockIdx.x * BX + tx;
+        s = blockIdx.y * (S - 1) - 1 + ty;
+        j = s; k = blockIdx.z;
+    } else {
+        nD = P.n3;
+        i = blockIdx.x * BX + tx;
+        s = blockIdx.y * (S - 1) - 1 + ty;
+        k = s; j = blockIdx.z;
+    }
+    const bool valid = s <= nD && i < P.n1 + (D == 0 ? 1 : 0) && (D == 0 || i < P.n1);
+    const long long nt = P.nt;
+    const long long st = D == 0 ? 1 : (D == 1 ? (long long)P.p1 : (long long)P.p1 * P.p2);
+    TW wc[NV], wm[NV];
+    if (valid) {
+        const long long c = cidx(P, i, j, k);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            TW a = W[v * nt + c - st], b = W[v * nt + c], e = W[v * nt + c + st];
+            TW dl = limiter<TW>(P.limiter, b - a, e - b);
+            wc[v] = b;
+            wm[v] = b - TW(0.5) * dl;
+            sW[v][ty][tx] = b;
+            sP[v][ty][tx] = b + TW(0.5) * dl;
+        }
+    }
+    __syncthreads();
+    if (!valid || ts == 0 || s < 0) return;
+    TW wl[NV], wr[NV], f[NV];
+    const int px = D == 0 ? tx - 1 : tx, py = D == 0 ? ty : ty - 1;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { wl[v] = sP[v][py][px]; wr[v] = wm[v]; }
+    if (wl[0] <= TW(0) || wr[0] <= TW(0) || wl[4] <= TW(0) || wr[4] <= TW(0)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { wl[v] = sW[v][py][px]; wr[v] = wc[v]; }
+    }
+    riemann<TW>(wl, wr, D, P.flux, TW(P.gamma), TW(1.0 / (P.gamma - 1.0)), f);
+    long long fi, fs;
+    if (D == 0) { fi = ((long long)k * P.n2 + j) * (P.n1 + 1) + s; fs = (long long)P.n3 * P.n2 * (P.n1 + 1); }
+    else if (D == 1) { fi = ((long long)k * (P.n2 + 1) + s) * P.n1 + i; fs = (long long)P.n3 * (P.n2 + 1) * P.n1; }
+    else { fi = ((long long)s * P.n2 + j) * P.n1 + i; fs = (long long)(P.n3 + 1) * P.n2 * P.n1; }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v * fs + fi] = f[v];
+}
+
+// ---------------------------------------------------------------------------------------------
+// div B at every cell of [-1, n]^3 from face averages of the cell-centred field
+template <typename TW>
+__global__ void k_divb(Params P, const TW *__restrict__ W, TW *__restrict__ divB)
+{
+    const int e1 = P.n1 + 2, e2 = P.n2 + 2, e3 = P.n3 + 2;
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)e1 * e2 * e3) return;
+    int i = (int)(tid % e1) - 1;
+    long long r = tid / e1;
+    int j = (int)(r % e2) - 1;
+    int k = (int)(r / e2) - 1;
+    const Metrics &m = P.m;
+    const long long nt = P.nt, c = cidx(P, i, j, k);
+    const int ip = i + NG, jp = j + NG;
+    const TW *b1 = W + 5 * nt, *b2 = W + 6 * nt, *b3 = W + 7 * nt;
+    const long long s2 = P.p1, s3 = (long long)P.p1 * P.p2;
+    TW d1 = (TW(m.a1[ip + 1]) * (b1[c] + b1[c + 1]) - TW(m.a1[ip]) * (b1[c - 1] + b1[c])) * TW(m.iv1[ip]);
+    TW d2 = (TW(m.a2[jp + 1]) * (b2[c] + b2[c + s2]) - TW(m.a2[jp]) * (b2[c - s2] + b2[c])) * TW(m.q1[ip] * m.iv2[jp]);
+    TW d3 = (b3[c + s3] - b3[c - s3]) * TW(m.q1[ip] * m.q2[jp] * m.iv3);
+    divB[c] = TW(0.5) * (d1 + d2 + d3);
+}
+
+// ---------------------------------------------------------------------------------------------
+// block-wide max and the last-block finalisation of dt (scratch: P.partial[gridDim.x])
+__device__ __forceinline__ double block_max(double v)
+{
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    v = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+    if (wid == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    return v;   // valid in thread 0
+}
+
+// advance_t: 1 after the second stage (t <- t + dt), 0 for a plain dt evaluation
+__device__ __forceinline__ void finish_dt(Params &P, double smax_block, int advance_t)
+{
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        P.partial[blockIdx.x] = smax_block;
+        __threadfence();
+        unsigned int ticket = atomicAdd(&P.sc->done, 1u);
+        last = ticket == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) v = fmax(v, ((volatile double *)P.partial)[b]);
+    v = block_max(v);
+    if (threadIdx.x == 0) {
+        Scalars *sc = P.sc;
+        double t = sc->t;
+        if (advance_t) t = __dadd_rn(t, sc->dt);
+        double dt = sc->cfl / v;
+        if (sc->t_stop > 0.0) dt = fmin(dt, fmax(__dsub_rn(sc->t_stop, t), 0.0));
+        if (!(v > 0.0)) dt = 0.0;
+        sc->t = t;
+        sc->dt = dt;
+        sc->done = 0;
+    }
+}
+
+// CFL signal speed of one cell: sum_d (|v_d| + c_f,d) / dx_d
+template <typename TW>
+__device__ __forceinline__ double cell_speed(const Params &P, const TW *w, int ip, int jp)
+{
+    const Metrics &m = P.m;
+    TW irho = TW(1) / w[0];
+    TW g = TW(P.gamma);
+    TW s1 = (rabs(w[1]) + fast_speed<TW>(w, irho, 0, g)) * TW(m.iw1[ip]);
+    TW s2 = (rabs(w[2]) + fast_speed<TW>(w, irho, 1, g)) * TW(m.ih2[ip] * m.id2);
+    TW s3 = (rabs(w[3]) + fast_speed<TW>(w, irho, 2, g)) * TW(m.ih2[ip] * m.is3[jp] * m.id3);
+    return (double)(s1 + s2 + s3);
+}
+
+template <typename TW>
+__global__ void __launch_bounds__(256) k_cfl(Params P, const TW *__restrict__ W)
+{
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (tid < (long long)P.n1 * P.n2 * P.n3) {
+        int i = (int)(tid % P.n1);
+        long long r = tid / P.n1;
+        int j = (int)(r % P.n2), k = (int)(r / P.n2);
+        long long c = cidx(P, i, j, k);
+        TW w[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w[v] = W[v * P.nt + c];
+        s = cell_speed<TW>(P, w, i + NG, j + NG);
+    }
+    s = block_max(s);
+    finish_dt(P, s, 0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// conservative update of one stage:
+//   L = -(1/V) sum_d (A+ F+ - A- F-) + S (geometric, rotating frame, gravity) ; Linde term
+//   stage 1: U1 = U + dt L ; stage 2: U <- U/2 + (U1 + dt L)/2 ; floors ; primitives ; CFL (2)
+template <int STAGE, typename TS, typename TW>
+__global__ void __launch_bounds__(256)
+k_update(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo, TW *__restrict__ Wo,
+         const TW *__restrict__ F1, const TW *__restrict__ F2, const TW *__restrict__ F3,
+         const TW *__restrict__ divB)
+{
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double smax = 0.0;
+    const long long N = (long long)P.n1 * P.n2 * P.n3;
+    if (tid < N) {
+        const int i = (int)(tid % P.n1);
+        const long long r_ = tid / P.n1;
+        const int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
+        const int ip = i + NG, jp = j + NG;
+        const Metrics &m = P.m;
+        const long long nt = P.nt, c = cidx(P, i, j, k);
+        const double dt = P.sc->dt;
+        TW w[NV], L[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w[v] = Ws[v * nt + c];
+        // flux divergence
+        {
+            const long long s1 = (long long)P.n3 * P.n2 * (P.n1 + 1);
+            const long long f1 = ((long long)k * P.n2 + j) * (P.n1 + 1) + i;
+            const TW am = TW(m.a1[ip]), ap = TW(m.a1[ip + 1]), iv = TW(m.iv1[ip]);
+            const long long s2 = (long long)P.n3 * (P.n2 + 1) * P.n1;
+            const long long f2 = ((long long)k * (P.n2 + 1) + j) * P.n1 + i;
+            const TW bm = TW(m.a2[jp]), bp = TW(m.a2[jp + 1]), jv = TW(m.q1[ip] * m.iv2[jp]);
+            const long long s3 = (long long)(P.n3 + 1) * P.n2 * P.n1;
+            const long long f3 = ((long long)k * P.n2 + j) * P.n1 + i;
+            const long long o3 = (long long)P.n2 * P.n1;
+            const TW kv = TW(m.q1[ip] * m.q2[jp] * m.iv3);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                TW l = -(ap * F1[v * s1 + f1 + 1] - am * F1[v * s1 + f1]) * iv;
+                l -= (bp * F2[v * s2 + f2 + P.n1] - bm * F2[v * s2 + f2]) * jv;
+                l -= (F3[v * s3 + f3 + o3] - F3[v * s3 + f3]) * kv;
+                L[v] = l;
+            }
+        }
+        if (P.geom == 0) {
+            const TW rho = w[0], vr = w[1], vt = w[2], vp = w[3];
+            const TW br = w[5], bt = w[6], bp = w[7];
+            const TW ir = TW(m.ih2[ip]), cot = TW(m.ct[jp]);
+            const TW pt = w[4] + TW(0.5) * (br * br + bt * bt + bp * bp);
+            // geometric terms of the spherical divergence; p_tot through face-area differences
+            L[M1] += pt * TW(m.gp1[ip]) + (rho * (vt * vt + vp * vp) - (bt * bt + bp * bp)) * ir;
+            L[M2] += pt * TW(m.q1[ip] * m.gq2[jp]) + (-(rho * vr * vt - br * bt) + cot * (rho * vp * vp - bp * bp)) * ir;
+            L[M3] -= ((rho * vp * vr - bp * br) + cot * (rho * vp * vt - bp * bt)) * ir;
+            L[B2] += (vr * bt - vt * br) * ir;
+            L[B3] += ((vr * bp - vp * br) + cot * (vt * bp - vp * bt)) * ir;
+            if (P.omega != 0.0) {
+                // co-rotating frame, Omega along the polar axis: centrifugal rho Omega^2 r sin(th)
+                // (sin th, cos th, 0), Coriolis 2 rho Omega (v_phi sin th, v_phi cos th,
+                // -(v_r sin th + v_th cos th)), work of the centrifugal force in e
+                const TW Om = TW(P.omega), sn = TW(m.sn[jp]), cs = TW(m.cs[jp]), rc = TW(m.x1c[ip]);
+                const TW cen = rho * Om * Om * rc * sn;
+                const TW vpar = vr * sn + vt * cs;
+                L[M1] += cen * sn + TW(2) * rho * Om * vp * sn;
+                L[M2] += cen * cs + TW(2) * rho * Om * vp * cs;
+                L[M3] -= TW(2) * rho * Om * vpar;
+                L[EN] += cen * vpar;
+            }
+            if (P.gravity) {
+                const TW g = TW(m.gm_r2[ip]);
+                L[M1] -= rho * g;
+                L[EN] -= rho * vr * g;
+            }
+        }
+        // Linde div-B diffusion: increment C_d / (sum_d 1/dx_d^2) grad(div B) per stage
+        TW lb[3] = {TW(0), TW(0), TW(0)};
+        if (P.divb == 1 && dt > 0.0) {
+            const long long s2 = P.p1, s3 = (long long)P.p1 * P.p2;
+            const TW iw1 = TW(m.iw1[ip]), iw2 = TW(m.ih2[ip] * m.id2), iw3 = TW(m.ih2[ip] * m.is3[jp] * m.id3);
+            const TW coef = TW(P.divb_coef) / (iw1 * iw1 + iw2 * iw2 + iw3 * iw3);
+            lb[0] = coef * (divB[c + 1] - divB[c - 1]) * TW(m.ig1[ip]);
+            lb[1] = coef * (divB[c + s2] - divB[c - s2]) * TW(m.ih2[ip] * m.ig2[jp]);
+            lb[2] = coef * (divB[c + s3] - divB[c - s3]) * TW(m.ih2[ip] * m.is3[jp] * m.ig3[k + NG]);
+        }
+        TS uo[NV];
+        const TS dts = (TS)dt;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            TW inc = v >= B1 ? lb[v - B1] : (v == EN ? w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2] : TW(0));
+            if (STAGE == 1) {
+                uo[v] = Us[v * nt + c] + dts * (TS)L[v] + (TS)inc;
+            } else {
+                TS un = Uo[v * nt + c];     // U^n (updated in place)
+                uo[v] = TS(0.5) * un + TS(0.5) * (Us[v * nt + c] + dts * (TS)L[v] + (TS)inc);
+            }
+        }
+        // floors
+        bool bad = false;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) bad |= !isfinite((double)uo[v]);
+        if (bad) atomicOr(&P.sc->status, 1);
+        TW wo[NV];
+        int hits = 0;
+        if (uo[RHO] < (TS)P.rho_floor) { uo[RHO] = (TS)P.rho_floor; ++hits; }
+        recover<TS, TW>(uo, wo, P.gamma, i);
+        if (wo[4] < TW(P.p_floor)) {
+            // reset e so that p = p_floor, keeping rho, m, B
+            TS ke = TS(0.5) * (uo[M1] * uo[M1] + uo[M2] * uo[M2] + uo[M3] * uo[M3]) / uo[RHO];
+            TS me = TS(0.5) * (uo[B1] * uo[B1] + uo[B2] * uo[B2] + uo[B3] * uo[B3]);
+            uo[EN] = (TS)P.p_floor / (TS)(P.gamma - 1.0) + ke + me;
+            wo[4] = TW(P.p_floor);
+            ++hits;
+        }
+        if (hits) atomicAdd(&P.sc->floor_hits, (unsigned long long)hits);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            Uo[v * nt + c] = uo[v];
+            Wo[v * nt + c] = wo[v];
+        }
+        if (STAGE == 2) smax = cell_speed<TW>(P, wo, ip, jp);
+    }
+    if (STAGE == 2) {
+        smax = block_max(smax);
+        finish_dt(P, smax, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// primitives of every padded cell (after a state upload)
+template <typename TS, typename TW>
+__global__ void k_prims(Params P, const TS *__restrict__ U, TW *__restrict__ W)
+{
+    long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.nt) return;
+    int i = (int)(c % P.p1) - NG;
+    TS u[NV];
+    TW w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = U[v * P.nt + c];
+    if (u[RHO] == TS(0)) return;      // untouched ghost corner before the first fill
+    recover<TS, TW>(u, w, P.gamma, i < 0 ? 0 : i);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) W[v * P.nt + c] = w[v];
+}
+
+// initial state from the maps at the current time by radial expansion:
+// v_r const, rho ~ r^-2, p ~ r^-2 gamma, B_r ~ r^-2, B_phi = -B_r Omega r sin(theta) / v_r
+template <typename TS, typename TW>
+__global__ void k_init_state(Params P, TS *__restrict__ U, TW *__restrict__ W, double r_in)
+{
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)P.n1 * P.n2 * P.n3) return;
+    int i = (int)(tid % P.n1);
+    long long r_ = tid / P.n1;
+    int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
+    double tau = P.sc->t;
+    int m0 = 0, m1 = 0;
+    double w = 0.0;
+    int nm = P.n_maps;
+    if (nm > 1 && tau > P.t_maps[0]) {
+        if (tau >= P.t_maps[nm - 1]) m0 = m1 = nm - 1;
+        else {
+            int m = 0;
+            while (m + 1 < nm - 1 && P.t_maps[m + 1] <= tau) ++m;
+            m0 = m; m1 = m + 1;
+            w = fmin(fmax((tau - P.t_maps[m]) / (P.t_maps[m + 1] - P.t_maps[m]), 0.0), 1.0);
+        }
+    }
+    const long long per = (long long)P.n2 * P.n3, col = (long long)j * P.n3 + k;
+    double b[5];
+    for (int f = 0; f < 5; ++f)
+        b[f] = (1.0 - w) * P.maps[((long long)m0 * 5 + f) * per + col] + w * P.maps[((long long)m1 * 5 + f) * per + col];
+    const double r = P.m.x1c[i + NG], x = r_in / r, x2 = x * x;
+    double wd[NV], ud[NV];
+    wd[0] = b[1] * x2;
+    wd[1] = b[0]; wd[2] = 0.0; wd[3] = 0.0;
+    wd[4] = b[2] * pow(x, 2.0 * P.gamma);
+    wd[5] = b[3] * x2; wd[6] = 0.0;
+    wd[7] = -wd[5] * P.omega * r * P.m.sn[j + NG] / wd[1];
+    prim2cons<double>(wd, ud, 1.0 / (P.gamma - 1.0));
+    long long c = cidx(P, i, j, k);
+    TS us[NV];
+    TW ws[NV];
+    for (int v = 0; v < NV; ++v) us[v] = (TS)ud[v];
+    recover<TS, TW>(us, ws, P.gamma, i);
+    for (int v = 0; v < NV; ++v) {
+        U[v * P.nt + c] = us[v];
+        W[v * P.nt + c] = ws[v];
+    }
+}
+
+// interior state <-> packed double array [8][n3][n2][n1]
+template <typename TS>
+__global__ void k_pack(Params P, const TS *__restrict__ U, double *__restrict__ out)
+{
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long N = (long long)P.n1 * P.n2 * P.n3;
+    if (tid >= N * NV) return;
+    int v = (int)(tid / N);
+    long long q = tid % N;
+    int i = (int)(q % P.n1);
+    long long r_ = q / P.n1;
+    int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
+    out[tid] = (double)U[v * P.nt + cidx(P, i, j, k)];
+}
+
+template <typename TS>
+__global__ void k_unpack(Params P, TS *__restrict__ U, const double *__restrict__ in)
+{
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long N = (long long)P.n1 * P.n2 * P.n3;
+    if (tid >= N * NV) return;
+    int v = (int)(tid / N);
+    long long q = tid % N;
+    int i = (int)(q % P.n1);
+    long long r_ = q / P.n1;
+    int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
+    U[v * P.nt + cidx(P, i, j, k)] = (TS)in[tid];
+}
+
+// ---------------------------------------------------------------------------------------------
+// probe sampling at the current time: one thread per probe, one block. Positions use only
+// correctly rounded operations in a fixed order; the stencil is found by comparisons against
+// the cell-centre arrays, so the indices do not depend on the arithmetic of the search.
+template <typename TW>
+__global__ void k_probe(Params P, const TW *__restrict__ W)
+{
+    const int p = threadIdx.x;
+    Scalars *sc = P.sc;
+    const long long head = sc->ring_head;
+    if (p < P.n_probes) {
+        const double AU = 1.495978707e11, PI = 3.14159265358979323846, TWO_PI = 2.0 * 3.14159265358979323846;
+        const double tsi = __dmul_rn(sc->t, P.t0);
+        const double *kn = P.traj + (long long)p * P.n_knots * 4;
+        const int K = P.n_knots;
+        int a = 0;
+        double w = 0.0;
+        if (K == 1 || tsi <= kn[0]) { a = 0; w = 0.0; }
+        else if (tsi >= kn[(K - 1) * 4]) { a = K - 2; w = 1.0; }
+        else {
+            int lo = 0, hi = K - 1;              // largest a with kn[a] <= tsi, a <= K-2
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (kn[mid * 4] <= tsi) lo = mid; else hi = mid;
+            }
+            a = lo;
+            w = __ddiv_rn(__dsub_rn(tsi, kn[a * 4]), __dsub_rn(kn[(a + 1) * 4], kn[a * 4]));
+        }
+        const int b = K == 1 ? 0 : a + 1;
+        const double rm = __dadd_rn(kn[a * 4 + 1], __dmul_rn(w, __dsub_rn(kn[b * 4 + 1], kn[a * 4 + 1])));
+        const double lat = __dadd_rn(kn[a * 4 + 2], __dmul_rn(w, __dsub_rn(kn[b * 4 + 2], kn[a * 4 + 2])));
+        const double lon = __dadd_rn(kn[a * 4 + 3], __dmul_rn(w, __dsub_rn(kn[b * 4 + 3], kn[a * 4 + 3])));
+        const double r = __ddiv_rn(rm, AU);
+        const double th = __dsub_rn(PI / 2.0, lat);
+        double ph = __dsub_rn(lon, __dmul_rn(P.omega_si, tsi));
+        ph = __dsub_rn(ph, __dmul_rn(TWO_PI, floor(__ddiv_rn(ph, TWO_PI))));
+        if (ph >= TWO_PI) ph = 0.0;
+        const Metrics &m = P.m;
+        const double *xc = m.x1c + NG, *yc = m.x2c + NG, *zc = m.x3c + NG;
+        // r: estimate from the position, then move to the largest q in [0, n1-2] with xc[q] <= r
+        int n1 = P.n1, n2 = P.n2, n3 = P.n3;
+        int i = 0, j = 0, k;
+        if (n1 > 1) {
+            double est = (r - xc[0]) / (xc[1] - xc[0]);
+            if (xc[1] / xc[0] > 1.0 + 1e-12 && P.geom == 0) est = log(r / xc[0]) / log(xc[1] / xc[0]);
+            i = (int)fmin(fmax(floor(est), 0.0), (double)(n1 - 2));
+            for (int it = 0; it < n1 && i < n1 - 2 && xc[i + 1] <= r; ++it) ++i;
+            for (int it = 0; it < n1 && i > 0 && xc[i] > r; ++it) --i;
+        }
+        if (n2 > 1) {
+            double est = (th - yc[0]) / (yc[1] - yc[0]);
+            j = (int)fmin(fmax(floor(est), 0.0), (double)(n2 - 2));
+            for (int it = 0; it < n2 && j < n2 - 2 && yc[j + 1] <= th; ++it) ++j;
+            for (int it = 0; it < n2 && j > 0 && yc[j] > th; ++it) --j;
+        }
+        double phk;
+        if (zc[0] > ph) { k = n3 - 1; phk = __dsub_rn(zc[n3 - 1], TWO_PI); }
+        else {
+            double est = floor((ph - zc[0]) * m.id3);
+            k = (int)fmin(fmax(est, 0.0), (double)(n3 - 1));
+            for (int it = 0; it < n3 && k < n3 - 1 && zc[k + 1] <= ph; ++it) ++k;
+            for (int it = 0; it < n3 && k > 0 && zc[k] > ph; ++it) --k;
+            phk = zc[k];
+        }
+        double wr = n1 > 1 ? (r - xc[i]) / (xc[i + 1] - xc[i]) : 0.0;
+        double wt = n2 > 1 ? (th - yc[j]) / (yc[j + 1] - yc[j]) : 0.0;
+        double wp = (ph - phk) * m.id3;
+        wr = fmin(fmax(wr, 0.0), 1.0);
+        wt = fmin(fmax(wt, 0.0), 1.0);
+        wp = fmin(fmax(wp, 0.0), 1.0);
+        const int i1 = n1 > 1 ? i + 1 : i, j1 = n2 > 1 ? j + 1 : j, k1 = (k + 1) % n3;
+        double acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+        for (int cc = 0; cc < 8; ++cc) {
+            int ci = (cc & 1) ? i1 : i, cj = (cc & 2) ? j1 : j, ck = (cc & 4) ? k1 : k;
+            double f = ((cc & 1) ? wr : 1.0 - wr) * ((cc & 2) ? wt : 1.0 - wt) * ((cc & 4) ? wp : 1.0 - wp);
+            long long c = cidx(P, ci, cj, ck);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[v] += f * (double)W[v * P.nt + c];
+        }
+        const long long slot = head % P.ring_cap;
+        double *q = P.ring + (slot * P.n_probes + p) * IC_NPROBE_REC;
+        q[0] = tsi;
+        q[1] = acc[0] * 1e6;
+        q[2] = acc[1] * 1e5;
+        q[3] = acc[2] * 1e5;
+        q[4] = (acc[3] + P.omega * r * sin(th)) * 1e5;
+        q[5] = acc[5] * P.b0;
+        q[6] = acc[6] * P.b0;
+        q[7] = acc[7] * P.b0;
+        q[8] = acc[4] * P.p0;
+        q[9] = sqrt(acc[5] * acc[5] + acc[6] * acc[6] + acc[7] * acc[7]) * P.b0;
+        q[10] = i; q[11] = j; q[12] = k;
+    }
+    __syncthreads();
+    if (p == 0) sc->ring_head = head + 1;
+}
+
+// ---------------------------------------------------------------------------------------------
+// host-side launchers (one set per precision)
+static inline unsigned int cdiv(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
+
+template <typename TS, typename TW> struct Launch {
+    static void fill_ghosts(const Params &P, void *U, void *W, int stage, cudaStream_t s)
+    {
+        TS *u = (TS *)U;
+        TW *w = (TW *)W;
+        k_bnd1<TS, TW><<<dim3(cdiv(P.n2, 64), P.n3), 64, 0, s>>>(P, u, w, stage);
+        k_bnd23<1, TS, TW><<<dim3(cdiv(P.p1, 64), P.n3), 64, 0, s>>>(P, u, w);
+        k_bnd23<2, TS, TW><<<dim3(cdiv(P.p1, 64), P.p2), 64, 0, s>>>(P, u, w);
+    }
+    static void fluxes(const Params &P, const void *W, void *F1, void *F2, void *F3, cudaStream_t s)
+    {
+        const TW *w = (const TW *)W;
+        k_flux<0, TW><<<dim3(cdiv(P.n1 + 1, 127), P.n2, P.n3), dim3(128, 1), 0, s>>>(P, w, (TW *)F1);
+        k_flux<1, TW><<<dim3(cdiv(P.n1, 16), cdiv(P.n2 + 1, 15), P.n3), dim3(16, 16), 0, s>>>(P, w, (TW *)F2);
+        k_flux<2, TW><<<dim3(cdiv(P.n1, 16), cdiv(P.n3 + 1, 15), P.n2), dim3(16, 16), 0, s>>>(P, w, (TW *)F3);
+    }
+    static void divb(const Params &P, const void *W, void *D, cudaStream_t s)
+    {
+        long long n = (long long)(P.n1 + 2) * (P.n2 + 2) * (P.n3 + 2);
+        k_divb<TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TW *)W, (TW *)D);
+    }
+    static void update(const Params &P, int stage, const void *Us, const void *Ws, void *Uo, void *Wo,
+                       const void *F1, const void *F2, const void *F3, const void *D, cudaStream_t s)
+    {
+        long long n = (long long)P.n1 * P.n2 * P.n3;
+        if (stage == 1)
+            k_update<1, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo, (TW *)Wo,
+                (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
+        else
+            k_update<2, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo, (TW *)Wo,
+                (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
+    }
+    static void cfl(const Params &P, const void *W, cudaStream_t s)
+    {
+        long long n = (long long)P.n1 * P.n2 * P.n3;
+        k_cfl<TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TW *)W);
+    }
+    static void probe(const Params &P, const void *W, cudaStream_t s)
+    {
+        k_probe<TW><<<1, ((P.n_probes + 31) / 32) * 32, 0, s>>>(P, (const TW *)W);
+    }
+    static void prims(const Params &P, const void *U, void *W, cudaStream_t s)
+    {
+        k_prims<TS, TW><<<cdiv(P.nt, 256), 256, 0, s>>>(P, (const TS *)U, (TW *)W);
+    }
+    static void init_state(const Params &P, void *U, void *W, double r_in, cudaStream_t s)
+    {
+        long long n = (long long)P.n1 * P.n2 * P.n3;
+        k_init_state<TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (TS *)U, (TW *)W, r_in);
+    }
+    static void pack(const Params &P, const void *U, double *out, cudaStream_t s)
+    {
+        long long n = (long long)P.n1 * P.n2 * P.n3 * NV;
+        k_pack<TS><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)U, out);
+    }
+    static void unpack(const Params &P, void *U, const double *in, cudaStream_t s)
+    {
+        long long n = (long long)P.n1 * P.n2 * P.n3 * NV;
+        k_unpack<TS><<<cdiv(n, 256), 256, 0, s>>>(P, (TS *)U, in);
+    }
+    static Ops make()
+    {
+        Ops o;
+        o.fill_ghosts = fill_ghosts;
+        o.fluxes = fluxes;
+        o.divb = divb;
+        o.update = update;
+        o.cfl = cfl;
+        o.probe = probe;
+        o.prims = prims;
+        o.init_state = init_state;
+        o.pack = pack;
+        o.unpack = unpack;
+        o.ts_size = sizeof(TS);
+        o.tw_size = sizeof(TW);
+        return o;
+    }
+};
+
+}  // namespace icarus

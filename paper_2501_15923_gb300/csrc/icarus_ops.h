@@ -1,0 +1,25 @@
+// icarus_ops.h -- per-precision launcher table (one instantiation per precision mode)
+#pragma once
+#include <cstddef>
+#include <cuda_runtime.h>
+
+namespace icarus {
+struct Params;
+struct Ops {
+    void (*fill_ghosts)(const Params &, void *U, void *W, int stage, cudaStream_t);
+    void (*fluxes)(const Params &, const void *W, void *F1, void *F2, void *F3, cudaStream_t);
+    void (*divb)(const Params &, const void *W, void *divB, cudaStream_t);
+    void (*update)(const Params &, int stage, const void *Us, const void *Ws, void *Uo, void *Wo,
+                   const void *F1, const void *F2, const void *F3, const void *divB, cudaStream_t);
+    void (*cfl)(const Params &, const void *W, cudaStream_t);
+    void (*probe)(const Params &, const void *W, cudaStream_t);
+    void (*prims)(const Params &, const void *U, void *W, cudaStream_t);
+    void (*init_state)(const Params &, void *U, void *W, double r_in, cudaStream_t);
+    void (*pack)(const Params &, const void *U, double *out, cudaStream_t);
+    void (*unpack)(const Params &, void *U, const double *in, cudaStream_t);
+    size_t ts_size, tw_size;
+};
+Ops ops_fp64();
+Ops ops_fp32();
+Ops ops_mixed();
+}  // namespace icarus

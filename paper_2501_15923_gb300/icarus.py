@@ -1,0 +1,282 @@
+"""Python binding of libicarus (include/icarus.h): argument marshalling only.
+
+Every function named icarus_* here calls the C entry point of the same name; all computation
+runs in the CUDA kernels of libicarus.so. Device memory comes from PyTorch's caching allocator
+(registered through the allocator callbacks of icarus_options); the solver runs on its own CUDA
+stream, exposed as a torch.cuda.ExternalStream for event timing. There is no CPU fallback: if the
+library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs as I
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libicarus.so")
+
+ICARUS_FP64, ICARUS_FP32, ICARUS_MIXED = 0, 1, 2
+NREC = 13
+ERRORS = {-1: "EINVAL", -2: "ESTATE", -3: "ENOMEM", -4: "ECUDA", -5: "ENONFINITE", -6: "ETIMEOUT"}
+
+
+class IcarusError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class icarus_grid(C.Structure):
+    _fields_ = [("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int), ("geometry", C.c_int), ("stretch", C.c_int),
+                ("x1min", C.c_double), ("x1max", C.c_double), ("x2min", C.c_double), ("x2max", C.c_double),
+                ("x3min", C.c_double), ("x3max", C.c_double), ("bc", C.c_int * 6)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class icarus_options(C.Structure):
+    _fields_ = [("cfl", C.c_double), ("limiter", C.c_int), ("flux", C.c_int), ("gravity", C.c_int),
+                ("divb", C.c_int), ("divb_coef", C.c_double), ("rho_floor", C.c_double),
+                ("p_floor", C.c_double), ("precision", C.c_int), ("ring_capacity", C.c_int),
+                ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+_lib = None
+
+# exported symbols and their signatures (kept in step with include/icarus.h)
+SIGNATURES = {
+    "icarus_init": (C.c_int, [C.POINTER(icarus_grid), C.c_double, C.c_double, C.POINTER(icarus_options), C.POINTER(C.c_void_p)]),
+    "icarus_set_boundary": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "icarus_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "icarus_sample": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "icarus_destroy": (C.c_int, [C.c_void_p]),
+    "icarus_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
+    "icarus_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
+    "icarus_set_stop_time": (C.c_int, [C.c_void_p, C.c_double]),
+    "icarus_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "icarus_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
+    "icarus_scales": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "icarus_launches_per_step": (C.c_int, [C.c_void_p]),
+    "icarus_get_stream": (C.c_void_p, [C.c_void_p]),
+    "icarus_last_error": (C.c_char_p, []),
+}
+
+
+def load():
+    """Load libicarus.so (built by __graft_entry__.build() or paper_2501_15923_gb300/build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libicarus.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype, f.argtypes = res, args
+        _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise IcarusError(rc, load().icarus_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator, handed to the C library by callbacks."""
+
+    def __init__(self, device):
+        import torch
+        self.torch, self.device, self.live = torch, device, {}
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, user):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:
+            return None
+        self.live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(self, ptr, user):
+        self.live.pop(ptr, None)
+
+
+def make_grid(g: I.Grid) -> icarus_grid:
+    return icarus_grid(g.n1, g.n2, g.n3, g.geometry, g.stretch, g.x1min, g.x1max, g.x2min, g.x2max,
+                       g.x3min, g.x3max, (C.c_int * 6)(*g.bc))
+
+
+def make_options(o: I.Options, precision=ICARUS_FP64, ring=4096, stream=None, allocator=None) -> icarus_options:
+    opt = icarus_options()
+    opt.cfl, opt.limiter, opt.flux, opt.gravity, opt.divb = o.cfl, o.limiter, o.flux, o.gravity, o.divb
+    opt.divb_coef, opt.rho_floor, opt.p_floor = o.divb_coef, o.rho_floor, o.p_floor
+    opt.precision, opt.ring_capacity = precision, ring
+    opt.cuda_stream = stream
+    if allocator is not None:
+        opt.alloc, opt.free = allocator.alloc_cb, allocator.free_cb
+    return opt
+
+
+# ---- the C entry points under their own names ------------------------------------------------
+def icarus_init(grid: icarus_grid, gamma: float, omega_rot: float, opts: icarus_options) -> C.c_void_p:
+    ctx = C.c_void_p()
+    _check(load().icarus_init(C.byref(grid), gamma, omega_rot, C.byref(opts), C.byref(ctx)))
+    return ctx
+
+
+def icarus_set_boundary(ctx, t_maps, maps, cmes=None):
+    t_maps, maps = _f64(t_maps), _f64(maps)
+    cm = _f64(cmes if cmes is not None and len(cmes) else np.zeros((0, 8)))
+    _check(load().icarus_set_boundary(ctx, int(t_maps.size), _ptr(t_maps), _ptr(maps), int(cm.shape[0]),
+                                      _ptr(cm) if cm.size else None))
+
+
+def icarus_step(ctx, n: int = 1):
+    _check(load().icarus_step(ctx, int(n)))
+
+
+_registered_probes = {}
+
+
+def icarus_sample(ctx, traj=None, cap: int = 1, out=None):
+    """Returns (records [n][n_probes][13], n_written). traj registers / samples now when given."""
+    lib = load()
+    nw = C.c_int(0)
+    key = ctx.value if isinstance(ctx, C.c_void_p) else int(ctx)
+    if traj is not None:
+        traj = _f64(traj)
+        P, K = traj.shape[0], traj.shape[1]
+        _registered_probes[key] = P
+    else:
+        P, K = 0, 0
+    nprobe = _registered_probes.get(key, 0)
+    if out is None:
+        out = np.zeros((max(cap, 1), max(nprobe, 1), NREC))
+    _check(lib.icarus_sample(ctx, P, K, _ptr(traj) if traj is not None else None, _ptr(out), int(cap), C.byref(nw)))
+    return out[: nw.value], nw.value
+
+
+def icarus_destroy(ctx):
+    _check(load().icarus_destroy(ctx))
+
+
+def icarus_get_state(ctx, shape):
+    U = np.empty(shape)
+    t = C.c_double()
+    _check(load().icarus_get_state(ctx, _ptr(U), C.byref(t)))
+    return U, t.value
+
+
+def icarus_set_state(ctx, U, t=0.0):
+    U = _f64(U)
+    _check(load().icarus_set_state(ctx, _ptr(U), float(t)))
+
+
+def icarus_set_stop_time(ctx, t_stop):
+    _check(load().icarus_set_stop_time(ctx, float(t_stop)))
+
+
+def icarus_time(ctx):
+    t, dt = C.c_double(), C.c_double()
+    _check(load().icarus_time(ctx, C.byref(t), C.byref(dt)))
+    return t.value, dt.value
+
+
+def icarus_status(ctx):
+    fh = C.c_longlong()
+    rc = load().icarus_status(ctx, C.byref(fh))
+    return rc, fh.value
+
+
+def icarus_scales(ctx):
+    s = np.empty(5)
+    _check(load().icarus_scales(ctx, _ptr(s)))
+    return dict(t0=s[0], p0=s[1], b0=s[2], omega=s[3], gm=s[4])
+
+
+def icarus_launches_per_step(ctx) -> int:
+    return int(load().icarus_launches_per_step(ctx))
+
+
+def icarus_get_stream(ctx) -> int:
+    return int(load().icarus_get_stream(ctx) or 0)
+
+
+# ---- convenience wrapper -----------------------------------------------------------------------
+class Solver:
+    """One solver context on the current CUDA device, memory from torch's caching allocator."""
+
+    def __init__(self, grid: I.Grid, gamma: float, omega: float, opts: I.Options, precision=ICARUS_FP64,
+                 ring=4096, device="cuda"):
+        import torch
+        self.torch = torch
+        self.grid, self.precision = grid, precision
+        self._alloc = _TorchAllocator(torch.device(device))
+        self._opts = make_options(opts, precision, ring, None, self._alloc)
+        self._grid = make_grid(grid)
+        self.ctx = icarus_init(self._grid, gamma, omega, self._opts)
+        self.shape = (8, grid.n3, grid.n2, grid.n1)
+        self.stream = torch.cuda.ExternalStream(icarus_get_stream(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            icarus_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_boundary(self, t_maps, maps, cmes=None):
+        icarus_set_boundary(self.ctx, t_maps, maps, cmes)
+
+    def step(self, n=1):
+        icarus_step(self.ctx, n)
+
+    def sample(self, traj=None, cap=1):
+        return icarus_sample(self.ctx, traj, cap)
+
+    def get_state(self):
+        return icarus_get_state(self.ctx, self.shape)
+
+    def set_state(self, U, t=0.0):
+        icarus_set_state(self.ctx, U, t)
+
+    def set_stop_time(self, t_stop):
+        icarus_set_stop_time(self.ctx, t_stop)
+
+    def time(self):
+        return icarus_time(self.ctx)
+
+    def status(self):
+        return icarus_status(self.ctx)
+
+    def scales(self):
+        return icarus_scales(self.ctx)
+
+    @property
+    def launches_per_step(self):
+        return icarus_launches_per_step(self.ctx)
+
+
+def from_workload(w: I.Workload, precision=ICARUS_FP64, ring=4096) -> Solver:
+    s = Solver(w.grid, w.gamma, w.omega, w.opts, precision, ring)
+    s.set_boundary(w.t_maps, w.maps, w.cmes)
+    return s
