@@ -1,0 +1,332 @@
+"""Throughput of the Icarus heliosphere hot path on GB300: Mcell-updates/s.
+
+Default workload: the production-size run (512 x 64 x 128 stretched spherical grid, 0.1-2 AU,
+10 daily boundary maps with a random-walk tilt, one cone CME, four probes), plain FP64. One
+"step" is one solver time step: ghost fill with the time-interpolated inner boundary + CME,
+reconstruction + fluxes in r, theta, phi, div B, update with sources (two SSP-RK2 stages), the
+CFL reduction, and the probe sampling. The state of one copy is 296 MB, larger than the 129 MB
+L2, so consecutive steps cannot run from cache (no flush needed).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain, untuned checker) on the host cores on a
+bounded sample of the same workload; its line carries "impl": "reference". Under torchrun (N > 1)
+every rank runs an independent replica on its own GPU (the single-domain solve is not sharded);
+value = cell-updates of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2501_15923_gb300 import inputs as I  # noqa: E402
+
+METRIC = "Mcell-updates/s on one GB300: FP64 plain vs mixed/batched/learned at stated error"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 ALU peak of GB300: 152 SMs x 2 DFMA/clk/SM (4 flop) x 2070 MHz max SM clock
+FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+# FP64 flops per face of the flux kernels (2 x DFMA + DADD + DMUL thread-instructions per face)
+# and their DRAM bytes per face come from the committed ncu summary below.
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_flux_r_fp64_256x64x128.md")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--grid", default="512x64x128")
+    p.add_argument("--precision", default="f64", choices=["f64", "f32", "mixed"])
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    p.add_argument("--no-forms", action="store_true", help="skip the FP32 / mixed side measurements")
+    return p.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(grid_s: str):
+    n1, n2, n3 = (int(x) for x in grid_s.split("x"))
+    return I.config1(grid=I.Grid(n1, n2, n3))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.path = index, None, None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2501_15923_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")) and not f.startswith("icarus_capi"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_numbers():
+    """FP64 flops/face and DRAM bytes/face of the flux kernels from the committed ncu summary; the
+    traffic is dropped when the kernel sources changed since the capture."""
+    try:
+        txt = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return {}, {}
+    vals = {}
+    for line in txt.splitlines():
+        if line.startswith("machine:"):
+            for kv in line[len("machine:"):].split(";"):
+                if "=" in kv:
+                    k, v = kv.split("=", 1)
+                    vals[k.strip()] = v.strip()
+    flops = {d: float(vals[f"fp64_flops_per_face_{d[0]}"]) for d in ("r", "theta", "phi")
+             if f"fp64_flops_per_face_{d[0]}" in vals}
+    dram = {d: float(vals[f"dram_bytes_per_face_{d[0]}"]) for d in ("r", "theta", "phi")
+            if f"dram_bytes_per_face_{d[0]}" in vals}
+    if vals.get("kernel_hash") != kernel_source_hash():
+        dram = {}
+    return flops, dram
+
+
+# ---------------------------------------------------------------------------------------------
+def cpu_oracle_rate(w, steps: int, max_seconds: float = 30.0):
+    """Time the FP64 oracle as it stands on the host cores (OpenMP, all cores)."""
+    from oracle.oracle import from_workload as ofw
+    o = ofw(w)
+    t0 = time.perf_counter()
+    n = 0
+    while n < steps:
+        o.step()
+        n += 1
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    el = time.perf_counter() - t0
+    return w.grid.ncell * n / el / 1e6, n, el
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    w = workload(args.grid)
+    cores = os.cpu_count()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    from oracle.oracle import from_workload as ofw
+    o = ofw(w)
+    for _ in range(args.warmup):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step()
+    el = time.perf_counter() - t0
+    v = w.grid.ncell * args.steps / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mcell-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": args.grid, "precision": "f64"},
+            "cpu_baseline": {"value": v, "unit": "Mcell-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full steps of {w.name} ({w.grid.ncell} cells) after {args.warmup} warm-up steps"},
+            "e2e": {"value": v, "unit": "Mcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2501_15923_gb300 import build
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_2501_15923_gb300", "libicarus.so")):
+        build.build()
+    if dist:
+        dist.barrier()
+    from paper_2501_15923_gb300 import icarus as ic
+    prec = {"f64": ic.ICARUS_FP64, "f32": ic.ICARUS_FP32, "mixed": ic.ICARUS_MIXED}[args.precision]
+    w = workload(args.grid)
+    ncell = w.grid.ncell
+    s = ic.from_workload(w, precision=prec)
+    s.sample(w.traj, cap=1)
+    stream = s.stream
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    s.step(args.warmup)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        s.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    rc, floor_hits = s.status()
+    if rc != 0:
+        raise RuntimeError(f"solver status {rc} after the timed steps")
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ncell * args.steps * world / (ms * 1e-3) / 1e6
+    clocks = clk.summary()
+    s.sample(None, cap=1 << 20)          # drain the timed steps' records
+
+    # per-kernel durations (events around each launch, eager) -> roofline of the dominant kernel
+    kms = s.time_kernels(3)
+    per_step = {k: v * (2 if k not in ("probe", "update_1", "update_2") else 1) for k, v in kms.items()}
+    dom = max(per_step, key=per_step.get)
+    flops_face, dram_face = profile_numbers()
+    n1, n2, n3 = w.grid.n1, w.grid.n2, w.grid.n3
+    faces = {"flux_r": (n1 + 1) * n2 * n3, "flux_theta": n1 * (n2 + 1) * n3, "flux_phi": n1 * n2 * (n3 + 1)}
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    dkey = dom.split("_")[-1] if dom in faces else None
+    if dkey in flops_face and args.precision == "f64":
+        ach = flops_face[dkey] * faces[dom] / (kms[dom] * 1e-3) / 1e12
+        roof = {"kernel": f"k_flux ({dom})", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": dram_face[dkey] * faces[dom] if dkey in dram_face else None,
+                "traffic_note": "DRAM bytes/face from the 256x64x128 ncu capture scaled by the faces of one launch",
+                "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2070 MHz (derived; measured DFMA rate 594 G/s)"}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "note": "flop count of this kernel not profiled yet"}
+    bytes_cell_update = 128 if args.precision in ("f64", "mixed") else 64
+    roof["hbm_view"] = {"algorithmic_bytes_per_cell_update": bytes_cell_update,
+                        "achieved_gbs": value / world * 1e6 * bytes_cell_update / 1e9, "peak_gbs": hbm_peak,
+                        "frac": value / world * 1e6 * bytes_cell_update / 1e9 / hbm_peak, "peak_source": "measured"}
+    roof["kernel_ms"] = kms
+
+    # end to end through the C ABI with host buffers: per step the boundary maps go host -> device
+    # (icarus_set_boundary), one step runs, and the probe records come back (icarus_sample)
+    maps_bytes = w.maps.nbytes + w.t_maps.nbytes + w.cmes.nbytes
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ne = max(3, min(args.steps, 10))
+    for _ in range(ne):
+        s.set_boundary(w.t_maps, w.maps, w.cmes)
+        s.step(1)
+        rec, _ = s.sample(None, cap=4)
+    el = time.perf_counter() - t0
+    e2e = {"value": ncell * ne * world / el / 1e6, "unit": "Mcell-updates/s", "h2d_bytes_per_step": int(maps_bytes),
+           "d2h_bytes_per_step": int(len(w.traj) * 13 * 8)}
+
+    forms = {}
+    if not args.no_forms and args.precision == "f64":
+        for name, pr in (("fp32_state", ic.ICARUS_FP32), ("mixed", ic.ICARUS_MIXED)):
+            sf = ic.from_workload(w, precision=pr)
+            sf.step(args.warmup)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(sf.stream)
+            sf.step(args.steps)
+            b.record(sf.stream)
+            b.synchronize()
+            fms = a.elapsed_time(b)
+            forms[name] = {"value": ncell * args.steps / (fms * 1e-3) / 1e6, "unit": "Mcell-updates/s",
+                           "ms_per_step": fms / args.steps}
+            sf.close()
+
+    line = {"metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": w.name, "grid": args.grid, "cells": ncell, "precision": args.precision,
+                       "l2": "inputs larger than L2 (state 8 x 8 B x padded cells per copy)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clocks": clocks, "roofline": roof, "e2e": e2e, "floor_hits": floor_hits,
+            "gpu_launches": s.launches_per_step * args.steps, "forms": forms}
+    if rank == 0 and not args.no_cpu and world == 1:
+        v, n, el = cpu_oracle_rate(w, steps=3, max_seconds=25.0)
+        line["cpu_baseline"] = {"value": v, "unit": "Mcell-updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{n} full steps of {w.name} ({el:.1f} s, OpenMP)"}
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

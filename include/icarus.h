@@ -161,6 +161,13 @@ int icarus_launches_per_step(icarus_ctx *ctx);
 /* The cudaStream_t the context runs on (for events and ordering with other work). */
 void *icarus_get_stream(icarus_ctx *ctx);
 
+/* Measurement helper: run n_steps steps launching the kernels one by one (no graph) with CUDA
+ * events around each launch on the context stream, and return the average duration in ms of one
+ * launch of each kernel class: ms[8] = (ghost fill (3 kernels), flux r, flux theta, flux phi,
+ * div B, update stage 1, update stage 2, probes). The steps advance the solution like
+ * icarus_step. Synchronous. */
+int icarus_time_kernels(icarus_ctx *ctx, int n_steps, double *ms);
+
 /* Message of the last failing call on this thread. */
 const char *icarus_last_error(void);
 

@@ -580,4 +580,49 @@ int icarus_launches_per_step(icarus_ctx *c)
 
 void *icarus_get_stream(icarus_ctx *c) { return c ? (void *)c->stream : nullptr; }
 
+int icarus_time_kernels(icarus_ctx *c, int n_steps, double *ms)
+{
+    if (!c || !ms || n_steps < 1) return fail(ICARUS_EINVAL, "bad argument");
+    if (!c->have_state) return fail(ICARUS_ESTATE, "no state");
+    const int NCLS = 8;
+    cudaEvent_t ev[2];
+    CK(cudaEventCreate(&ev[0]));
+    CK(cudaEventCreate(&ev[1]));
+    double acc[NCLS] = {0};
+    int cnt[NCLS] = {0};
+    const Params &P = c->P;
+    cudaStream_t s = c->stream;
+    auto timed = [&](int cls, auto &&fn) -> int {
+        CK(cudaEventRecord(ev[0], s));
+        fn();
+        CK(cudaEventRecord(ev[1], s));
+        CK(cudaEventSynchronize(ev[1]));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ev[0], ev[1]));
+        acc[cls] += t;
+        cnt[cls] += 1;
+        return 0;
+    };
+    int rc = 0;
+    for (int q = 0; q < n_steps && !rc; ++q) {
+        for (int stage = 1; stage <= 2 && !rc; ++stage) {
+            void *Us = stage == 1 ? c->U : c->U1, *Ws = stage == 1 ? c->W : c->W1;
+            void *Uo = stage == 1 ? c->U1 : c->U, *Wo = stage == 1 ? c->W1 : c->W;
+            rc |= timed(0, [&] { c->ops.fill_ghosts(P, Us, Ws, stage, s); });
+            rc |= timed(1, [&] { c->ops.flux_dir(P, 0, Ws, c->F1, s); });
+            rc |= timed(2, [&] { c->ops.flux_dir(P, 1, Ws, c->F2, s); });
+            rc |= timed(3, [&] { c->ops.flux_dir(P, 2, Ws, c->F3, s); });
+            if (P.divb == 1) rc |= timed(4, [&] { c->ops.divb(P, Ws, c->divB, s); });
+            rc |= timed(4 + stage, [&] { c->ops.update(P, stage, Us, Ws, Uo, Wo, c->F1, c->F2, c->F3, c->divB, s); });
+        }
+        if (P.n_probes > 0) rc |= timed(7, [&] { c->ops.probe(P, c->W, s); });
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc) return rc;
+    CK(cudaGetLastError());
+    for (int k = 0; k < NCLS; ++k) ms[k] = cnt[k] ? acc[k] / cnt[k] : 0.0;
+    return ICARUS_OK;
+}
+
 }  // extern "C"

@@ -682,12 +682,18 @@ template <typename TS, typename TW> struct Launch {
         k_bnd23<1, TS, TW><<<dim3(cdiv(P.p1, 64), P.n3), 64, 0, s>>>(P, u, w);
         k_bnd23<2, TS, TW><<<dim3(cdiv(P.p1, 64), P.p2), 64, 0, s>>>(P, u, w);
     }
-    static void fluxes(const Params &P, const void *W, void *F1, void *F2, void *F3, cudaStream_t s)
+    static void flux_dir(const Params &P, int dir, const void *W, void *F, cudaStream_t s)
     {
         const TW *w = (const TW *)W;
-        k_flux<0, TW><<<dim3(cdiv(P.n1 + 1, 127), P.n2, P.n3), dim3(128, 1), 0, s>>>(P, w, (TW *)F1);
-        k_flux<1, TW><<<dim3(cdiv(P.n1, 16), cdiv(P.n2 + 1, 15), P.n3), dim3(16, 16), 0, s>>>(P, w, (TW *)F2);
-        k_flux<2, TW><<<dim3(cdiv(P.n1, 16), cdiv(P.n3 + 1, 15), P.n2), dim3(16, 16), 0, s>>>(P, w, (TW *)F3);
+        if (dir == 0) k_flux<0, TW><<<dim3(cdiv(P.n1 + 1, 127), P.n2, P.n3), dim3(128, 1), 0, s>>>(P, w, (TW *)F);
+        else if (dir == 1) k_flux<1, TW><<<dim3(cdiv(P.n1, 16), cdiv(P.n2 + 1, 15), P.n3), dim3(16, 16), 0, s>>>(P, w, (TW *)F);
+        else k_flux<2, TW><<<dim3(cdiv(P.n1, 16), cdiv(P.n3 + 1, 15), P.n2), dim3(16, 16), 0, s>>>(P, w, (TW *)F);
+    }
+    static void fluxes(const Params &P, const void *W, void *F1, void *F2, void *F3, cudaStream_t s)
+    {
+        flux_dir(P, 0, W, F1, s);
+        flux_dir(P, 1, W, F2, s);
+        flux_dir(P, 2, W, F3, s);
     }
     static void divb(const Params &P, const void *W, void *D, cudaStream_t s)
     {
@@ -738,6 +744,7 @@ template <typename TS, typename TW> struct Launch {
         Ops o;
         o.fill_ghosts = fill_ghosts;
         o.fluxes = fluxes;
+        o.flux_dir = flux_dir;
         o.divb = divb;
         o.update = update;
         o.cfl = cfl;

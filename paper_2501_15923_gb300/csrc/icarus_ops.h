@@ -8,6 +8,7 @@ struct Params;
 struct Ops {
     void (*fill_ghosts)(const Params &, void *U, void *W, int stage, cudaStream_t);
     void (*fluxes)(const Params &, const void *W, void *F1, void *F2, void *F3, cudaStream_t);
+    void (*flux_dir)(const Params &, int dir, const void *W, void *F, cudaStream_t);
     void (*divb)(const Params &, const void *W, void *divB, cudaStream_t);
     void (*update)(const Params &, int stage, const void *Us, const void *Ws, void *Uo, void *Wo,
                    const void *F1, const void *F2, const void *F3, const void *divB, cudaStream_t);

@@ -63,6 +63,7 @@ SIGNATURES = {
     "icarus_scales": (C.c_int, [C.c_void_p, C.c_void_p]),
     "icarus_launches_per_step": (C.c_int, [C.c_void_p]),
     "icarus_get_stream": (C.c_void_p, [C.c_void_p]),
+    "icarus_time_kernels": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "icarus_last_error": (C.c_char_p, []),
 }
 
@@ -217,6 +218,15 @@ def icarus_get_stream(ctx) -> int:
     return int(load().icarus_get_stream(ctx) or 0)
 
 
+KERNEL_CLASSES = ("ghost_fill", "flux_r", "flux_theta", "flux_phi", "divb", "update_1", "update_2", "probe")
+
+
+def icarus_time_kernels(ctx, n_steps: int) -> dict:
+    ms = np.zeros(8)
+    _check(load().icarus_time_kernels(ctx, int(n_steps), _ptr(ms)))
+    return dict(zip(KERNEL_CLASSES, ms.tolist()))
+
+
 # ---- convenience wrapper -----------------------------------------------------------------------
 class Solver:
     """One solver context on the current CUDA device, memory from torch's caching allocator."""
@@ -270,6 +280,9 @@ class Solver:
 
     def scales(self):
         return icarus_scales(self.ctx)
+
+    def time_kernels(self, n_steps):
+        return icarus_time_kernels(self.ctx, n_steps)
 
     @property
     def launches_per_step(self):
