@@ -168,6 +168,33 @@ void *icarus_get_stream(icarus_ctx *ctx);
  * icarus_step. Synchronous. */
 int icarus_time_kernels(icarus_ctx *ctx, int n_steps, double *ms);
 
+/* Largest grid (interior cells) icarus_cfl_dt_noalloc accepts: 16384 blocks of 256 cells. */
+#define ICARUS_NOALLOC_MAX_CELLS 4194304LL
+
+/* CFL time step of a caller-owned state without allocating anything. The paper has no
+ * counterpart: this serves callers that cannot allocate device memory where they need a time
+ * step (a framework's fixed pool, a real-time loop that forbids allocation after start-up, an
+ * embedder that only owns its own buffers). It computes the same quantity as the dt that
+ * icarus_set_state / icarus_time report: CFL / max over cells of sum_d (|v_d| + c_f,d) / dx_d.
+ *   grid   : the grid (as for icarus_init); at most ICARUS_NOALLOC_MAX_CELLS interior cells,
+ *            otherwise EINVAL and nothing is launched
+ *   gamma  : adiabatic index; cfl: Courant number in (0, 1]
+ *   U      : DEVICE pointer, interior conserved state [8][n3][n2][n1] doubles in code units
+ *            (the layout of icarus_get_state)
+ *   dt     : DEVICE pointer to one double that receives the time step (code units)
+ *   stream : cudaStream_t to run on (NULL: the legacy default stream); the call returns
+ *            without synchronising
+ * Scratch: the reduction's partial maxima and its completion counter live in one file-scope
+ * __device__ array of (32 + 16384) doubles (128 KiB) that every GPU loading the library holds
+ * until the process exits. The call never allocates or frees (no cudaMalloc / cudaFree, no
+ * library allocator). The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress while that device is current; make that first call before any stream
+ * capture. All calls on a device share the array and its counter (cleared at the start of every
+ * call), so calls that overlap on the GPU (different streams, concurrently) race and must be
+ * ordered by the caller. */
+int icarus_cfl_dt_noalloc(const icarus_grid *grid, double gamma, double cfl, const double *U, double *dt,
+                          void *stream);
+
 /* Message of the last failing call on this thread. */
 const char *icarus_last_error(void);
 

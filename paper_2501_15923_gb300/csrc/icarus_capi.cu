@@ -40,6 +40,11 @@ int fail(int code, const char *fmt, ...)
 
 }  // namespace
 
+namespace icarus {
+// lets other translation units report through icarus_last_error()
+int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace icarus
+
 struct icarus_ctx {
     Params P{};
     Ops ops{};

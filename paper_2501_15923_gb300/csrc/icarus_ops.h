@@ -20,6 +20,7 @@ struct Ops {
     void (*unpack)(const Params &, void *U, const double *in, cudaStream_t);
     size_t ts_size, tw_size;
 };
+int report_error(int code, const char *msg);
 Ops ops_fp64();
 Ops ops_fp32();
 Ops ops_mixed();

@@ -64,6 +64,7 @@ SIGNATURES = {
     "icarus_launches_per_step": (C.c_int, [C.c_void_p]),
     "icarus_get_stream": (C.c_void_p, [C.c_void_p]),
     "icarus_time_kernels": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "icarus_cfl_dt_noalloc": (C.c_int, [C.POINTER(icarus_grid), C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "icarus_last_error": (C.c_char_p, []),
 }
 
@@ -225,6 +226,13 @@ def icarus_time_kernels(ctx, n_steps: int) -> dict:
     ms = np.zeros(8)
     _check(load().icarus_time_kernels(ctx, int(n_steps), _ptr(ms)))
     return dict(zip(KERNEL_CLASSES, ms.tolist()))
+
+
+def icarus_cfl_dt_noalloc(grid: icarus_grid, gamma: float, cfl: float, U_dev_ptr: int, dt_dev_ptr: int, stream=None):
+    """Allocation-free CFL time step of a state the caller already holds on the device (device
+    pointers in and out; see include/icarus.h)."""
+    _check(load().icarus_cfl_dt_noalloc(C.byref(grid), float(gamma), float(cfl), C.c_void_p(U_dev_ptr),
+                                        C.c_void_p(dt_dev_ptr), C.c_void_p(stream or 0)))
 
 
 # ---- convenience wrapper -----------------------------------------------------------------------
