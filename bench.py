@@ -52,7 +52,8 @@ def parse_args(argv=None):
     p.add_argument("--grid", default="512x64x128")
     p.add_argument("--precision", default="f64", choices=["f64", "f32", "mixed"])
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
-    p.add_argument("--no-forms", action="store_true", help="skip the FP32 / mixed side measurements")
+    p.add_argument("--no-forms", action="store_true", help="skip the FP32 / mixed / batched side measurements")
+    p.add_argument("--batch-members", type=int, default=64, help="members of the batched cone-CME ensemble")
     return p.parse_args(argv)
 
 
@@ -201,6 +202,36 @@ def run_reference(args):
         dist.barrier()
 
 
+def run_batched(ic, torch, args):
+    """Cone-CME ensemble (seed 3, uneven grids) in mixed precision: one persistent launch per step,
+    each member with its own dt. value = sum of member cells x steps / time."""
+    members = I.ensemble(seed=3, n_members=args.batch_members)
+    b = ic.Batch(members, precision=ic.ICARUS_MIXED)
+    b.register_probes()
+    tiles = b.autotune(2)
+    steps = max(2, min(args.steps, 10))
+    b.step(max(1, args.warmup))
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(b.stream)
+    b.step(steps)
+    e.record(b.stream)
+    e.synchronize()
+    ms = a.elapsed_time(e)
+    rc = b.status()
+    info = b.info()
+    cells = b.ncell
+    dts = sorted(b.time(m)[1] for m in range(len(members)))
+    out = {"value": cells * steps / (ms * 1e-3) / 1e6, "unit": "Mcell-updates/s", "members": len(members),
+           "cells": cells, "steps": steps, "ms_per_step": ms / steps, "status": rc, "persistent_blocks": info["blocks"],
+           "graph": info["graph"], "launches_per_step": 1,
+           "tiles_chosen": {f"{r}/{t}": sum(1 for x in tiles if x == (r, t)) for r in range(3) for t in range(2)
+                            if any(x == (r, t) for x in tiles)},
+           "member_dt_range_code": [dts[0], dts[-1]]}
+    b.close()
+    return out
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -307,6 +338,8 @@ def main(argv=None):
             forms[name] = {"value": ncell * args.steps / (fms * 1e-3) / 1e6, "unit": "Mcell-updates/s",
                            "ms_per_step": fms / args.steps}
             sf.close()
+        if args.batch_members > 0:
+            forms["batched_ensemble"] = run_batched(ic, torch, args)
 
     line = {"metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -168,6 +168,52 @@ void *icarus_get_stream(icarus_ctx *ctx);
  * icarus_step. Synchronous. */
 int icarus_time_kernels(icarus_ctx *ctx, int n_steps, double *ms);
 
+/* ---- batched ensemble -------------------------------------------------------------------
+ * Many independent solves (members) with their own grids, drivers, CMEs, probes, dt and t,
+ * advanced together: each batched step is ONE persistent, cooperatively launched kernel that runs
+ * every phase of every member's step, with grid-wide barriers between phases (bounded waits: a
+ * barrier that does not complete within about two seconds records ETIMEOUT and the kernel
+ * returns). Steps are replayed from a CUDA graph when the driver allows capturing the
+ * cooperative launch, else launched directly. Each member is an icarus_ctx (icarus_batch_member)
+ * on which icarus_set_boundary / icarus_sample / icarus_get_state / icarus_time work as usual;
+ * stepping a member with icarus_step runs it alone. */
+typedef struct icarus_batch icarus_batch;
+#define ICARUS_BATCH_MAX_MEMBERS 1024
+
+/* n_members (1..ICARUS_BATCH_MAX_MEMBERS) contexts with grids[n_members] and shared gamma,
+ * omega_rot and options (precision included), all on one stream (opts->cuda_stream or a new one). */
+int icarus_batch_init(int n_members, const icarus_grid *grids, double gamma, double omega_rot,
+                      const icarus_options *opts, icarus_batch **out);
+
+/* The member context m (owned by the batch; do not destroy it). */
+int icarus_batch_member(icarus_batch *b, int m, icarus_ctx **ctx);
+
+/* Pick the flux tile shape of every member by timed trials (reps launches per candidate) on its
+ * current state, once per distinct grid shape (cached in the batch). Synchronous. */
+int icarus_batch_autotune(icarus_batch *b, int reps);
+
+/* The chosen tile candidates of member m: cfg[0] radial (0: 128x2, 1: 64x4, 2: 32x8 threads),
+ * cfg[1] theta / phi (0: 16x16, 1: 32x8). */
+int icarus_batch_tiles(icarus_batch *b, int m, int *cfg);
+
+/* Set the tile candidates of member m by hand (same codes as icarus_batch_tiles). */
+int icarus_batch_set_tiles(icarus_batch *b, int m, int cfg_r, int cfg_t);
+
+/* Advance every member by n steps, each member with its own dt. Asynchronous. */
+int icarus_batch_step(icarus_batch *b, int n);
+
+/* ETIMEOUT if a barrier wait gave up, else the first member's sticky status. Synchronous. */
+int icarus_batch_status(icarus_batch *b);
+
+/* info[3] = (members, blocks of the persistent launch, 1 if steps replay a CUDA graph). */
+int icarus_batch_info(icarus_batch *b, int *info);
+
+/* The cudaStream_t of the batch. */
+void *icarus_batch_stream(icarus_batch *b);
+
+/* Release the batch and all member contexts. */
+int icarus_batch_destroy(icarus_batch *b);
+
 /* Largest grid (interior cells) icarus_cfl_dt_noalloc accepts: 16384 blocks of 256 cells. */
 #define ICARUS_NOALLOC_MAX_CELLS 4194304LL
 

@@ -12,7 +12,7 @@ LIB = os.path.join(HERE, "libicarus.so")
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
-         "-I" + os.path.join(HERE, "..", "include")]
+         "-I" + os.path.join(HERE, "..", "include")] + os.environ.get("ICARUS_NVCC_EXTRA", "").split()
 
 
 def sources():

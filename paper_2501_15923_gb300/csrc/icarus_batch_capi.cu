@@ -1,0 +1,318 @@
+// icarus_batch_capi.cu -- host side of the batched ensemble (include/icarus.h, icarus_batch_*):
+// member contexts, work-item tables, the tile autotuner, and the one-launch-per-step graph.
+#include <chrono>
+#include <cstdio>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "icarus_batch.cuh"
+#include "icarus_ctx.h"
+
+using namespace icarus;
+
+struct icarus_batch {
+    std::vector<icarus_ctx *> members;
+    std::vector<int> versions;
+    std::vector<int> cfg_r, cfg_t;
+    icarus_options opts{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    BatchOps ops{};
+    Member *d_members = nullptr;
+    long long *d_off = nullptr;
+    BarrierState *d_bar = nullptr;
+    size_t members_cap = 0;
+    int blocks = 0;
+    cudaGraphExec_t graph = nullptr;
+    bool use_graph = true;
+    bool dirty = true;
+    long long spin_limit = 4000000000LL;
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> tune_cache;   // grid shape -> (cfg_r, cfg_t)
+};
+
+namespace {
+
+#define BCK(call)                                                                                    \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return report_error(ICARUS_ECUDA, cudaGetErrorString(e_));            \
+    } while (0)
+
+void *balloc(icarus_batch *b, size_t bytes)
+{
+    // batch-level tables live in the first member's context (released with it)
+    return ctx_alloc(b->members[0], bytes);
+}
+
+template <int D, int BX, int BY> void tiles_of(const Params &P, int *t, long long *items)
+{
+    int nx, ny, nz;
+    flux_tiles<D, BX, BY>(P, nx, ny, nz);
+    t[0] = nx; t[1] = ny; t[2] = nz;
+    *items = (long long)nx * ny * nz;
+}
+
+int build_tables(icarus_batch *b)
+{
+    const int n = (int)b->members.size();
+    std::vector<Member> hm(n);
+    std::vector<long long> off((size_t)BPH_N * (n + 1), 0);
+    for (int m = 0; m < n; ++m) {
+        icarus_ctx *c = b->members[m];
+        Member &M = hm[m];
+        M.P = c->P;
+        M.U = c->U; M.U1 = c->U1; M.W = c->W; M.W1 = c->W1;
+        M.F1 = c->F1; M.F2 = c->F2; M.F3 = c->F3; M.divB = c->divB;
+        M.cfg_r = b->cfg_r[m];
+        M.cfg_t = b->cfg_t[m];
+        if (M.cfg_r == 0) tiles_of<0, 128, 2>(M.P, M.tr, &M.items_r);
+        else if (M.cfg_r == 1) tiles_of<0, 64, 4>(M.P, M.tr, &M.items_r);
+        else tiles_of<0, 32, 8>(M.P, M.tr, &M.items_r);
+        if (M.cfg_t == 0) { tiles_of<1, 16, 16>(M.P, M.tt, &M.items_t); tiles_of<2, 16, 16>(M.P, M.tp, &M.items_p); }
+        else { tiles_of<1, 32, 8>(M.P, M.tt, &M.items_t); tiles_of<2, 32, 8>(M.P, M.tp, &M.items_p); }
+        const Params &P = M.P;
+        auto chunks = [](long long x) { return (x + BATCH_THREADS - 1) / BATCH_THREADS; };
+        long long it[BPH_N];
+        it[BPH_BND1] = chunks((long long)P.n2 * P.n3);
+        it[BPH_BND2] = chunks((long long)P.p1 * P.n3);
+        it[BPH_BND3] = chunks((long long)P.p1 * P.p2);
+        it[BPH_FLUX] = M.items_r + M.items_t + M.items_p;
+        it[BPH_DIVB] = P.divb == 1 ? chunks((long long)(P.n1 + 2) * (P.n2 + 2) * (P.n3 + 2)) : 0;
+        it[BPH_UPD] = chunks((long long)P.n1 * P.n2 * P.n3);
+        it[BPH_PROBE] = P.n_probes > 0 ? 1 : 0;
+        for (int ph = 0; ph < BPH_N; ++ph) off[(size_t)ph * (n + 1) + m + 1] = off[(size_t)ph * (n + 1) + m] + it[ph];
+        b->versions[m] = c->p_version;
+    }
+    if (!b->d_members) {
+        b->d_members = (Member *)balloc(b, sizeof(Member) * n);
+        b->d_off = (long long *)balloc(b, sizeof(long long) * off.size());
+        b->d_bar = (BarrierState *)balloc(b, sizeof(BarrierState));
+        if (!b->d_members || !b->d_off || !b->d_bar) return report_error(ICARUS_ENOMEM, "batch table allocation failed");
+        BCK(cudaMemsetAsync(b->d_bar, 0, sizeof(BarrierState), b->stream));
+    }
+    BCK(cudaMemcpyAsync(b->d_members, hm.data(), sizeof(Member) * n, cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaMemcpyAsync(b->d_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return ICARUS_OK;
+}
+
+int enqueue(icarus_batch *b)
+{
+    BatchArgs A;
+    A.m = b->d_members;
+    A.off = b->d_off;
+    A.n = (int)b->members.size();
+    A.bar = b->d_bar;
+    A.spin_limit = b->spin_limit;
+    // the barrier counters start from zero at every step (the error word is kept)
+    BCK(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned int), b->stream));
+    BCK(b->ops.launch(A, b->blocks, b->stream));
+    return ICARUS_OK;
+}
+
+int prepare(icarus_batch *b)
+{
+    bool changed = b->dirty;
+    for (size_t m = 0; m < b->members.size(); ++m)
+        if (b->versions[m] != b->members[m]->p_version) changed = true;
+    if (!changed) return ICARUS_OK;
+    for (icarus_ctx *c : b->members)
+        if (!c->have_state) return report_error(ICARUS_ESTATE, "every member needs a state (icarus_set_boundary / icarus_set_state)");
+    int rc = build_tables(b);
+    if (rc) return rc;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    if (b->use_graph) {
+        cudaGraph_t g;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            int erc = enqueue(b);
+            cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+            if (erc == 0 && e == cudaSuccess) {
+                if (cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess) b->graph = nullptr;
+                cudaGraphDestroy(g);
+            }
+        }
+        cudaGetLastError();
+        if (!b->graph) b->use_graph = false;   // cooperative node not capturable here: launch directly
+    }
+    b->dirty = false;
+    return ICARUS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int icarus_batch_init(int n_members, const icarus_grid *grids, double gamma, double omega_rot,
+                      const icarus_options *opts, icarus_batch **out)
+{
+    if (n_members < 1 || !grids || !opts || !out) return report_error(ICARUS_EINVAL, "bad argument");
+    if (n_members > ICARUS_BATCH_MAX_MEMBERS) return report_error(ICARUS_EINVAL, "too many members (ICARUS_BATCH_MAX_MEMBERS)");
+    icarus_batch *b = new icarus_batch();
+    b->opts = *opts;
+    if (opts->cuda_stream) b->stream = (cudaStream_t)opts->cuda_stream;
+    else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return report_error(ICARUS_ECUDA, "stream creation failed");
+        }
+        b->own_stream = true;
+    }
+    b->ops = opts->precision == ICARUS_FP64 ? batch_ops_fp64()
+           : (opts->precision == ICARUS_FP32 ? batch_ops_fp32() : batch_ops_mixed());
+    icarus_options mo = *opts;
+    mo.cuda_stream = b->stream;
+    for (int m = 0; m < n_members; ++m) {
+        icarus_ctx *c = nullptr;
+        int rc = icarus_init(&grids[m], gamma, omega_rot, &mo, &c);
+        if (rc) {
+            for (icarus_ctx *x : b->members) icarus_destroy(x);
+            if (b->own_stream) cudaStreamDestroy(b->stream);
+            delete b;
+            return rc;
+        }
+        b->members.push_back(c);
+        b->versions.push_back(-1);
+        b->cfg_r.push_back(0);
+        b->cfg_t.push_back(0);
+    }
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = b->ops.blocks_per_sm(n_members);
+    if (per_sm < 1) {
+        icarus_batch_destroy(b);
+        return report_error(ICARUS_ECUDA, "batched kernel cannot be resident (occupancy 0)");
+    }
+    b->blocks = per_sm * nsm;
+    *out = b;
+    return ICARUS_OK;
+}
+
+int icarus_batch_member(icarus_batch *b, int m, icarus_ctx **ctx)
+{
+    if (!b || !ctx || m < 0 || m >= (int)b->members.size()) return report_error(ICARUS_EINVAL, "bad member index");
+    *ctx = b->members[m];
+    return ICARUS_OK;
+}
+
+int icarus_batch_autotune(icarus_batch *b, int reps)
+{
+    if (!b || reps < 1) return report_error(ICARUS_EINVAL, "bad argument");
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    for (size_t m = 0; m < b->members.size(); ++m) {
+        icarus_ctx *c = b->members[m];
+        const Params &P = c->P;
+        auto key = std::make_tuple(P.n1, P.n2, P.n3);
+        auto hit = b->tune_cache.find(key);
+        if (hit == b->tune_cache.end()) {
+            if (!c->have_state) return report_error(ICARUS_ESTATE, "autotune needs member states");
+            float best_r = 1e30f, best_t = 1e30f;
+            int cr = 0, ct = 0;
+            for (int cfg = 0; cfg < NCFG_R + NCFG_T; ++cfg) {
+                const bool is_r = cfg < NCFG_R;
+                const int v = is_r ? cfg : cfg - NCFG_R;
+                // one untimed launch, then reps timed ones
+                for (int q = 0; q <= reps; ++q) {
+                    if (q == 1) BCK(cudaEventRecord(e0, b->stream));
+                    if (is_r) b->ops.flux_variant(P, 0, v, c->W, c->F1, b->stream);
+                    else {
+                        b->ops.flux_variant(P, 1, v, c->W, c->F2, b->stream);
+                        b->ops.flux_variant(P, 2, v, c->W, c->F3, b->stream);
+                    }
+                }
+                BCK(cudaEventRecord(e1, b->stream));
+                BCK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                BCK(cudaEventElapsedTime(&ms, e0, e1));
+                if (is_r && ms < best_r) { best_r = ms; cr = v; }
+                if (!is_r && ms < best_t) { best_t = ms; ct = v; }
+            }
+            hit = b->tune_cache.emplace(key, std::make_pair(cr, ct)).first;
+        }
+        b->cfg_r[m] = hit->second.first;
+        b->cfg_t[m] = hit->second.second;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    BCK(cudaGetLastError());
+    b->dirty = true;
+    return ICARUS_OK;
+}
+
+int icarus_batch_tiles(icarus_batch *b, int m, int *cfg)
+{
+    if (!b || !cfg || m < 0 || m >= (int)b->members.size()) return report_error(ICARUS_EINVAL, "bad argument");
+    cfg[0] = b->cfg_r[m];
+    cfg[1] = b->cfg_t[m];
+    return ICARUS_OK;
+}
+
+int icarus_batch_set_tiles(icarus_batch *b, int m, int cfg_r, int cfg_t)
+{
+    if (!b || m < 0 || m >= (int)b->members.size() || cfg_r < 0 || cfg_r >= NCFG_R || cfg_t < 0 || cfg_t >= NCFG_T)
+        return report_error(ICARUS_EINVAL, "bad argument");
+    b->cfg_r[m] = cfg_r;
+    b->cfg_t[m] = cfg_t;
+    b->dirty = true;
+    return ICARUS_OK;
+}
+
+int icarus_batch_step(icarus_batch *b, int n)
+{
+    if (!b || n < 0) return report_error(ICARUS_EINVAL, "bad argument");
+    int rc = prepare(b);
+    if (rc) return rc;
+    for (int q = 0; q < n; ++q) {
+        if (b->graph) BCK(cudaGraphLaunch(b->graph, b->stream));
+        else {
+            rc = enqueue(b);
+            if (rc) return rc;
+        }
+    }
+    return ICARUS_OK;
+}
+
+int icarus_batch_status(icarus_batch *b)
+{
+    if (!b) return report_error(ICARUS_EINVAL, "NULL batch");
+    if (b->d_bar) {
+        BarrierState s;
+        BCK(cudaMemcpyAsync(&s, b->d_bar, sizeof s, cudaMemcpyDeviceToHost, b->stream));
+        BCK(cudaStreamSynchronize(b->stream));
+        if (s.err) return report_error(ICARUS_ETIMEOUT, "a grid barrier of the batched step gave up waiting");
+    }
+    for (icarus_ctx *c : b->members) {
+        int rc = icarus_status(c, nullptr);
+        if (rc) return rc;
+    }
+    return ICARUS_OK;
+}
+
+int icarus_batch_info(icarus_batch *b, int *info)
+{
+    if (!b || !info) return report_error(ICARUS_EINVAL, "bad argument");
+    info[0] = (int)b->members.size();
+    info[1] = b->blocks;
+    info[2] = b->graph != nullptr;
+    return ICARUS_OK;
+}
+
+void *icarus_batch_stream(icarus_batch *b) { return b ? (void *)b->stream : nullptr; }
+
+int icarus_batch_destroy(icarus_batch *b)
+{
+    if (!b) return ICARUS_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    // members other than the first, then the first (it owns the batch tables)
+    for (size_t m = b->members.size(); m-- > 0;) icarus_destroy(b->members[m]);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return ICARUS_OK;
+}
+
+}  // extern "C"

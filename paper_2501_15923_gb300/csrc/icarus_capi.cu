@@ -10,6 +10,7 @@
 #include "../../include/icarus.h"
 #include "icarus_internal.cuh"
 #include "icarus_ops.h"
+#include "icarus_ctx.h"
 
 using namespace icarus;
 
@@ -45,27 +46,7 @@ namespace icarus {
 int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
 }  // namespace icarus
 
-struct icarus_ctx {
-    Params P{};
-    Ops ops{};
-    icarus_grid grid{};
-    icarus_options opts{};
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    std::vector<void *> allocs;
-    void *U = nullptr, *U1 = nullptr, *W = nullptr, *W1 = nullptr;
-    void *F1 = nullptr, *F2 = nullptr, *F3 = nullptr, *divB = nullptr;
-    double *metric = nullptr, *partial = nullptr, *stage_buf = nullptr;
-    Scalars *sc = nullptr;
-    double *maps = nullptr, *tmaps = nullptr, *cme = nullptr, *traj = nullptr, *ring = nullptr;
-    size_t maps_cap = 0, cme_cap = 0, traj_cap = 0;
-    bool have_state = false, have_boundary = false;
-    cudaGraphExec_t graph = nullptr;
-    long long ring_tail = 0;
-    double t0, p0, b0, omega_code, gm_code;
-    int launches_per_step = 0;
-    std::vector<double> colvec_host;
-};
+// struct icarus_ctx is defined in icarus_ctx.h
 
 namespace {
 
@@ -78,6 +59,12 @@ void *dalloc(icarus_ctx *c, size_t bytes)
     if (p) c->allocs.push_back(p);
     return p;
 }
+
+}  // namespace
+
+void *icarus::ctx_alloc(icarus_ctx *c, size_t bytes) { return dalloc(c, bytes); }
+
+namespace {
 
 void dfree_all(icarus_ctx *c)
 {
@@ -92,6 +79,7 @@ void drop_graph(icarus_ctx *c)
 {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
+    c->p_version++;
 }
 
 // edges of direction d at padded edge index e (cell i has lower edge i, i in [-2, n+2])

@@ -1,0 +1,36 @@
+// icarus_ctx.h -- the solver context behind the opaque icarus_ctx handle (host side)
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/icarus.h"
+#include "icarus_internal.cuh"
+#include "icarus_ops.h"
+
+struct icarus_ctx {
+    icarus::Params P{};
+    icarus::Ops ops{};
+    icarus_grid grid{};
+    icarus_options opts{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void *> allocs;
+    void *U = nullptr, *U1 = nullptr, *W = nullptr, *W1 = nullptr;
+    void *F1 = nullptr, *F2 = nullptr, *F3 = nullptr, *divB = nullptr;
+    double *metric = nullptr, *partial = nullptr, *stage_buf = nullptr;
+    icarus::Scalars *sc = nullptr;
+    double *maps = nullptr, *tmaps = nullptr, *cme = nullptr, *traj = nullptr, *ring = nullptr;
+    size_t maps_cap = 0, cme_cap = 0, traj_cap = 0;
+    bool have_state = false, have_boundary = false;
+    cudaGraphExec_t graph = nullptr;
+    long long ring_tail = 0;
+    double t0, p0, b0, omega_code, gm_code;
+    int launches_per_step = 0;
+    int p_version = 0;      // bumped whenever P changes (the batched form re-reads it)
+    std::vector<double> colvec_host;
+};
+
+namespace icarus {
+// allocate through the context's allocator (tracked, released by icarus_destroy)
+void *ctx_alloc(icarus_ctx *c, size_t bytes);
+}  // namespace icarus

@@ -51,7 +51,7 @@ struct Metrics {
 
 struct Scalars {               // device-resident step state
     double t, dt, t_stop, cfl;
-    unsigned long long smax_bits;   // unused slot kept for alignment
+    unsigned long long smax_bits;   // batched form: this member's CFL maximum (bits of a double >= 0)
     unsigned int done;              // last-block counter of the CFL reduction
     int status;                     // bit 0: non-finite state
     unsigned long long floor_hits;

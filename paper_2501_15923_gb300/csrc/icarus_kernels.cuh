@@ -42,11 +42,8 @@ __device__ __forceinline__ void recover(const TS *u, TW *w, double gamma, int i)
 // ghost fill along r: inner side driven by the maps (+ CME) or a plain rule, outer side a plain
 // rule. One thread per interior (j, k) column.
 template <typename TS, typename TW>
-__global__ void k_bnd1(Params P, TS *__restrict__ U, TW *__restrict__ W, int stage)
+__device__ __forceinline__ void bnd1_col(const Params &P, TS *__restrict__ U, TW *__restrict__ W, int stage, int j, int k)
 {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int k = blockIdx.y;
-    if (j >= P.n2 || k >= P.n3) return;
     const long long nt = P.nt;
     // inner face
     int bc = P.bc[0];
@@ -137,19 +134,23 @@ __global__ void k_bnd1(Params P, TS *__restrict__ U, TW *__restrict__ W, int sta
     }
 }
 
+template <typename TS, typename TW>
+__global__ void k_bnd1(Params P, TS *__restrict__ U, TW *__restrict__ W, int stage)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int k = blockIdx.y;
+    if (j >= P.n2 || k >= P.n3) return;
+    bnd1_col<TS, TW>(P, U, W, stage, j, k);
+}
+
 // ghost fill along theta (D = 1) or phi (D = 2) by copy / reflection / periodic images.
 // D = 1 covers every r (ghosts included) and interior phi; D = 2 covers everything.
 template <int D, typename TS, typename TW>
-__global__ void k_bnd23(Params P, TS *__restrict__ U, TW *__restrict__ W)
+__device__ __forceinline__ void bnd23_cell(const Params &P, TS *__restrict__ U, TW *__restrict__ W, int ip, int o)
 {
-    int ip = blockIdx.x * blockDim.x + threadIdx.x;     // padded r index
-    int o = blockIdx.y;                                 // other index
-    if (ip >= P.p1) return;
     int i = ip - NG;
     const int n = D == 1 ? P.n2 : P.n3;
     const long long nt = P.nt;
-    if (D == 1 && o >= P.n3) return;
-    if (D == 2 && o >= P.p2) return;
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
         int bc = P.bc[2 * D + side];
@@ -175,46 +176,54 @@ __global__ void k_bnd23(Params P, TS *__restrict__ U, TW *__restrict__ W)
     }
 }
 
+template <int D, typename TS, typename TW>
+__global__ void k_bnd23(Params P, TS *__restrict__ U, TW *__restrict__ W)
+{
+    int ip = blockIdx.x * blockDim.x + threadIdx.x;     // padded r index
+    int o = blockIdx.y;                                 // other index
+    if (ip >= P.p1) return;
+    if (D == 1 && o >= P.n3) return;
+    if (D == 2 && o >= P.p2) return;
+    bnd23_cell<D, TS, TW>(P, U, W, ip, o);
+}
+
 // ---------------------------------------------------------------------------------------------
 // fused reconstruction + face flux along direction D. Threads sweep S cells along D; each cell's
 // limited slopes are computed once, its face states are exchanged through shared memory and
 // every thread but the first computes the flux through the lower face of its cell.
-// D = 0: block (128, 1), faces f0 .. f0+126 of one (j, k) row.
-// D = 1, 2: block (16 r, 16 sweep), 15 faces along D for 16 consecutive r.
-template <int D, typename TW> struct FluxShape {
-    static constexpr int BX = D == 0 ? 128 : 16;
-    static constexpr int BY = D == 0 ? 1 : 16;
-    static constexpr int S = D == 0 ? BX : BY;
-};
-
-template <int D, typename TW>
-__global__ void __launch_bounds__(FluxShape<D, TW>::BX * FluxShape<D, TW>::BY)
-k_flux(Params P, const TW *__restrict__ W, TW *__restrict__ F)
+// A tile is BX x BY threads; along D it covers S - 1 faces (S = BX for D = 0, BY otherwise).
+// D = 0: faces f0 .. f0+BX-2 of BY consecutive (j) rows; D = 1, 2: BY-1 faces along D for BX
+// consecutive r. Must be called by every thread of the block (it synchronises the block).
+template <int D, int BX, int BY, typename TW>
+__device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict__ W, TW *__restrict__ F,
+                                          int bx, int by, int bz, int tx, int ty, TW *sW, TW *sP)
 {
-    constexpr int BX = FluxShape<D, TW>::BX, BY = FluxShape<D, TW>::BY, S = FluxShape<D, TW>::S;
-    __shared__ TW sW[NV][BY][BX];
-    __shared__ TW sP[NV][BY][BX];
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    constexpr int S = D == 0 ? BX : BY;
     const int ts = D == 0 ? tx : ty;
     int i, j, k, s, nD;
+    bool inrange;
     if (D == 0) {
         nD = P.n1;
-        s = blockIdx.x * (S - 1) - 1 + tx;
-        i = s; j = blockIdx.y; k = blockIdx.z;
+        s = bx * (S - 1) - 1 + tx;
+        i = s; j = by * BY + ty; k = bz;
+        inrange = j < P.n2;
     } else if (D == 1) {
         nD = P.n2;
-        i = blockIdx.x * BX + tx;
-        s = blockIdx.y * (S - 1) - 1 + ty;
-        j = s; k = blockIdx.z;
+        i = bx * BX + tx;
+        s = by * (S - 1) - 1 + ty;
+        j = s; k = bz;
+        inrange = i < P.n1;
     } else {
         nD = P.n3;
-        i = blockIdx.x * BX + tx;
-        s = blockIdx.y * (S - 1) - 1 + ty;
-        k = s; j = blockIdx.z;
+        i = bx * BX + tx;
+        s = by * (S - 1) - 1 + ty;
+        k = s; j = bz;
+        inrange = i < P.n1;
     }
-    const bool valid = s <= nD && i < P.n1 + (D == 0 ? 1 : 0) && (D == 0 || i < P.n1);
+    const bool valid = inrange && s <= nD;
     const long long nt = P.nt;
     const long long st = D == 0 ? 1 : (D == 1 ? (long long)P.p1 : (long long)P.p1 * P.p2);
+    const int sl = ty * BX + tx, sz = BX * BY;
     TW wc[NV], wm[NV];
     if (valid) {
         const long long c = cidx(P, i, j, k);
@@ -224,37 +233,59 @@ k_flux(Params P, const TW *__restrict__ W, TW *__restrict__ F)
             TW dl = limiter<TW>(P.limiter, b - a, e - b);
             wc[v] = b;
             wm[v] = b - TW(0.5) * dl;
-            sW[v][ty][tx] = b;
-            sP[v][ty][tx] = b + TW(0.5) * dl;
+            sW[v * sz + sl] = b;
+            sP[v * sz + sl] = b + TW(0.5) * dl;
         }
     }
     __syncthreads();
-    if (!valid || ts == 0 || s < 0) return;
-    TW wl[NV], wr[NV], f[NV];
-    const int px = D == 0 ? tx - 1 : tx, py = D == 0 ? ty : ty - 1;
+    if (valid && ts > 0 && s >= 0) {
+        TW wl[NV], wr[NV], f[NV];
+        const int pl = D == 0 ? sl - 1 : sl - BX;      // the neighbour one cell below along D
 #pragma unroll
-    for (int v = 0; v < NV; ++v) { wl[v] = sP[v][py][px]; wr[v] = wm[v]; }
-    if (wl[0] <= TW(0) || wr[0] <= TW(0) || wl[4] <= TW(0) || wr[4] <= TW(0)) {
+        for (int v = 0; v < NV; ++v) { wl[v] = sP[v * sz + pl]; wr[v] = wm[v]; }
+        if (wl[0] <= TW(0) || wr[0] <= TW(0) || wl[4] <= TW(0) || wr[4] <= TW(0)) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) { wl[v] = sW[v][py][px]; wr[v] = wc[v]; }
+            for (int v = 0; v < NV; ++v) { wl[v] = sW[v * sz + pl]; wr[v] = wc[v]; }
+        }
+        riemann<TW>(wl, wr, D, P.flux, TW(P.gamma), TW(1.0 / (P.gamma - 1.0)), f);
+        long long fi, fs;
+        if (D == 0) { fi = ((long long)k * P.n2 + j) * (P.n1 + 1) + s; fs = (long long)P.n3 * P.n2 * (P.n1 + 1); }
+        else if (D == 1) { fi = ((long long)k * (P.n2 + 1) + s) * P.n1 + i; fs = (long long)P.n3 * (P.n2 + 1) * P.n1; }
+        else { fi = ((long long)s * P.n2 + j) * P.n1 + i; fs = (long long)(P.n3 + 1) * P.n2 * P.n1; }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v * fs + fi] = f[v];
     }
-    riemann<TW>(wl, wr, D, P.flux, TW(P.gamma), TW(1.0 / (P.gamma - 1.0)), f);
-    long long fi, fs;
-    if (D == 0) { fi = ((long long)k * P.n2 + j) * (P.n1 + 1) + s; fs = (long long)P.n3 * P.n2 * (P.n1 + 1); }
-    else if (D == 1) { fi = ((long long)k * (P.n2 + 1) + s) * P.n1 + i; fs = (long long)P.n3 * (P.n2 + 1) * P.n1; }
-    else { fi = ((long long)s * P.n2 + j) * P.n1 + i; fs = (long long)(P.n3 + 1) * P.n2 * P.n1; }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) F[v * fs + fi] = f[v];
+}
+
+// number of tiles of a BX x BY flux tile along each launch axis
+template <int D, int BX, int BY> __host__ __device__ inline void flux_tiles(const Params &P, int &nx, int &ny, int &nz)
+{
+    if (D == 0) { nx = (P.n1 + 1 + BX - 2) / (BX - 1); ny = (P.n2 + BY - 1) / BY; nz = P.n3; }
+    else if (D == 1) { nx = (P.n1 + BX - 1) / BX; ny = (P.n2 + 1 + BY - 2) / (BY - 1); nz = P.n3; }
+    else { nx = (P.n1 + BX - 1) / BX; ny = (P.n3 + 1 + BY - 2) / (BY - 1); nz = P.n2; }
+}
+
+template <int D> struct FluxShape {
+    static constexpr int BX = D == 0 ? 128 : 16;
+    static constexpr int BY = D == 0 ? 1 : 16;
+};
+
+template <int D, typename TW>
+__global__ void __launch_bounds__(FluxShape<D>::BX * FluxShape<D>::BY)
+k_flux(Params P, const TW *__restrict__ W, TW *__restrict__ F)
+{
+    constexpr int BX = FluxShape<D>::BX, BY = FluxShape<D>::BY;
+    __shared__ TW sW[NV * BY * BX];
+    __shared__ TW sP[NV * BY * BX];
+    flux_tile<D, BX, BY, TW>(P, W, F, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, sW, sP);
 }
 
 // ---------------------------------------------------------------------------------------------
 // div B at every cell of [-1, n]^3 from face averages of the cell-centred field
 template <typename TW>
-__global__ void k_divb(Params P, const TW *__restrict__ W, TW *__restrict__ divB)
+__device__ __forceinline__ void divb_cell(const Params &P, const TW *__restrict__ W, TW *__restrict__ divB, long long tid)
 {
-    const int e1 = P.n1 + 2, e2 = P.n2 + 2, e3 = P.n3 + 2;
-    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (long long)e1 * e2 * e3) return;
+    const int e1 = P.n1 + 2, e2 = P.n2 + 2;
     int i = (int)(tid % e1) - 1;
     long long r = tid / e1;
     int j = (int)(r % e2) - 1;
@@ -268,6 +299,14 @@ __global__ void k_divb(Params P, const TW *__restrict__ W, TW *__restrict__ divB
     TW d2 = (TW(m.a2[jp + 1]) * (b2[c] + b2[c + s2]) - TW(m.a2[jp]) * (b2[c - s2] + b2[c])) * TW(m.q1[ip] * m.iv2[jp]);
     TW d3 = (b3[c + s3] - b3[c - s3]) * TW(m.q1[ip] * m.q2[jp] * m.iv3);
     divB[c] = TW(0.5) * (d1 + d2 + d3);
+}
+
+template <typename TW>
+__global__ void k_divb(Params P, const TW *__restrict__ W, TW *__restrict__ divB)
+{
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)(P.n1 + 2) * (P.n2 + 2) * (P.n3 + 2)) return;
+    divb_cell<TW>(P, W, divB, tid);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -355,16 +394,15 @@ __global__ void __launch_bounds__(256) k_cfl(Params P, const TW *__restrict__ W)
 // conservative update of one stage:
 //   L = -(1/V) sum_d (A+ F+ - A- F-) + S (geometric, rotating frame, gravity) ; Linde term
 //   stage 1: U1 = U + dt L ; stage 2: U <- U/2 + (U1 + dt L)/2 ; floors ; primitives ; CFL (2)
+// returns the cell's CFL signal speed after a second stage (0 otherwise)
 template <int STAGE, typename TS, typename TW>
-__global__ void __launch_bounds__(256)
-k_update(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo, TW *__restrict__ Wo,
-         const TW *__restrict__ F1, const TW *__restrict__ F2, const TW *__restrict__ F3,
-         const TW *__restrict__ divB)
+__device__ __forceinline__ double update_cell(const Params &P, const TS *__restrict__ Us, const TW *__restrict__ Ws,
+                                              TS *Uo, TW *__restrict__ Wo, const TW *__restrict__ F1,
+                                              const TW *__restrict__ F2, const TW *__restrict__ F3,
+                                              const TW *__restrict__ divB, long long tid)
 {
-    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double smax = 0.0;
-    const long long N = (long long)P.n1 * P.n2 * P.n3;
-    if (tid < N) {
+    {
         const int i = (int)(tid % P.n1);
         const long long r_ = tid / P.n1;
         const int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
@@ -471,6 +509,19 @@ k_update(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo,
         }
         if (STAGE == 2) smax = cell_speed<TW>(P, wo, ip, jp);
     }
+    return smax;
+}
+
+template <int STAGE, typename TS, typename TW>
+__global__ void __launch_bounds__(256)
+k_update(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo, TW *__restrict__ Wo,
+         const TW *__restrict__ F1, const TW *__restrict__ F2, const TW *__restrict__ F3,
+         const TW *__restrict__ divB)
+{
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double smax = 0.0;
+    if (tid < (long long)P.n1 * P.n2 * P.n3)
+        smax = update_cell<STAGE, TS, TW>(P, Us, Ws, Uo, Wo, F1, F2, F3, divB, tid);
     if (STAGE == 2) {
         smax = block_max(smax);
         finish_dt(P, smax, 1);
@@ -575,12 +626,10 @@ __global__ void k_unpack(Params P, TS *__restrict__ U, const double *__restrict_
 // correctly rounded operations in a fixed order; the stencil is found by comparisons against
 // the cell-centre arrays, so the indices do not depend on the arithmetic of the search.
 template <typename TW>
-__global__ void k_probe(Params P, const TW *__restrict__ W)
+__device__ __forceinline__ void probe_one(const Params &P, const TW *__restrict__ W, int p, long long head)
 {
-    const int p = threadIdx.x;
     Scalars *sc = P.sc;
-    const long long head = sc->ring_head;
-    if (p < P.n_probes) {
+    {
         const double AU = 1.495978707e11, PI = 3.14159265358979323846, TWO_PI = 2.0 * 3.14159265358979323846;
         const double tsi = __dmul_rn(sc->t, P.t0);
         const double *kn = P.traj + (long long)p * P.n_knots * 4;
@@ -665,8 +714,16 @@ __global__ void k_probe(Params P, const TW *__restrict__ W)
         q[9] = sqrt(acc[5] * acc[5] + acc[6] * acc[6] + acc[7] * acc[7]) * P.b0;
         q[10] = i; q[11] = j; q[12] = k;
     }
+}
+
+template <typename TW>
+__global__ void k_probe(Params P, const TW *__restrict__ W)
+{
+    const int p = threadIdx.x;
+    const long long head = P.sc->ring_head;
+    if (p < P.n_probes) probe_one<TW>(P, W, p, head);
     __syncthreads();
-    if (p == 0) sc->ring_head = head + 1;
+    if (p == 0) P.sc->ring_head = head + 1;
 }
 
 // ---------------------------------------------------------------------------------------------

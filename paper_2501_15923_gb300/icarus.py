@@ -64,6 +64,16 @@ SIGNATURES = {
     "icarus_launches_per_step": (C.c_int, [C.c_void_p]),
     "icarus_get_stream": (C.c_void_p, [C.c_void_p]),
     "icarus_time_kernels": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "icarus_batch_init": (C.c_int, [C.c_int, C.c_void_p, C.c_double, C.c_double, C.POINTER(icarus_options), C.POINTER(C.c_void_p)]),
+    "icarus_batch_member": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "icarus_batch_autotune": (C.c_int, [C.c_void_p, C.c_int]),
+    "icarus_batch_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "icarus_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "icarus_batch_set_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "icarus_batch_status": (C.c_int, [C.c_void_p]),
+    "icarus_batch_info": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "icarus_batch_stream": (C.c_void_p, [C.c_void_p]),
+    "icarus_batch_destroy": (C.c_int, [C.c_void_p]),
     "icarus_cfl_dt_noalloc": (C.c_int, [C.POINTER(icarus_grid), C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "icarus_last_error": (C.c_char_p, []),
 }
@@ -301,3 +311,116 @@ def from_workload(w: I.Workload, precision=ICARUS_FP64, ring=4096) -> Solver:
     s = Solver(w.grid, w.gamma, w.omega, w.opts, precision, ring)
     s.set_boundary(w.t_maps, w.maps, w.cmes)
     return s
+
+
+# ---- batched ensemble ---------------------------------------------------------------------------
+def icarus_batch_init(grids, gamma, omega_rot, opts):
+    arr = (icarus_grid * len(grids))(*grids)
+    b = C.c_void_p()
+    _check(load().icarus_batch_init(len(grids), C.cast(arr, C.c_void_p), gamma, omega_rot, C.byref(opts), C.byref(b)))
+    return b
+
+
+def icarus_batch_member(b, m):
+    c = C.c_void_p()
+    _check(load().icarus_batch_member(b, int(m), C.byref(c)))
+    return c
+
+
+def icarus_batch_autotune(b, reps=3):
+    _check(load().icarus_batch_autotune(b, int(reps)))
+
+
+def icarus_batch_tiles(b, m):
+    cfg = np.zeros(2, dtype=np.int32)
+    _check(load().icarus_batch_tiles(b, int(m), _ptr(cfg)))
+    return tuple(int(x) for x in cfg)
+
+
+def icarus_batch_set_tiles(b, m, cfg_r, cfg_t):
+    _check(load().icarus_batch_set_tiles(b, int(m), int(cfg_r), int(cfg_t)))
+
+
+def icarus_batch_step(b, n=1):
+    _check(load().icarus_batch_step(b, int(n)))
+
+
+def icarus_batch_status(b):
+    return load().icarus_batch_status(b)
+
+
+def icarus_batch_info(b):
+    info = np.zeros(3, dtype=np.int32)
+    _check(load().icarus_batch_info(b, _ptr(info)))
+    return dict(members=int(info[0]), blocks=int(info[1]), graph=bool(info[2]))
+
+
+def icarus_batch_destroy(b):
+    _check(load().icarus_batch_destroy(b))
+
+
+class Batch:
+    """An ensemble of independent members advanced by one persistent launch per step."""
+
+    def __init__(self, workloads, precision=ICARUS_MIXED, ring=4096, device="cuda"):
+        import torch
+        self.torch = torch
+        self._alloc = _TorchAllocator(torch.device(device))
+        w0 = workloads[0]
+        self._opts = make_options(w0.opts, precision, ring, None, self._alloc)
+        self._grids = [make_grid(w.grid) for w in workloads]
+        self.b = icarus_batch_init(self._grids, w0.gamma, w0.omega, self._opts)
+        self.workloads = workloads
+        self.ctx = [icarus_batch_member(self.b, m) for m in range(len(workloads))]
+        self.shapes = [(8, w.grid.n3, w.grid.n2, w.grid.n1) for w in workloads]
+        for c, w in zip(self.ctx, workloads):
+            icarus_set_boundary(c, w.t_maps, w.maps, w.cmes)
+        self.stream = torch.cuda.ExternalStream(int(load().icarus_batch_stream(self.b) or 0))
+
+    def register_probes(self):
+        for c, w in zip(self.ctx, self.workloads):
+            icarus_sample(c, w.traj, cap=1)
+
+    def autotune(self, reps=3):
+        icarus_batch_autotune(self.b, reps)
+        return [icarus_batch_tiles(self.b, m) for m in range(len(self.ctx))]
+
+    def set_tiles(self, cfg_r, cfg_t):
+        for m in range(len(self.ctx)):
+            icarus_batch_set_tiles(self.b, m, cfg_r, cfg_t)
+
+    def step(self, n=1):
+        icarus_batch_step(self.b, n)
+
+    def status(self):
+        return icarus_batch_status(self.b)
+
+    def info(self):
+        return icarus_batch_info(self.b)
+
+    def get_state(self, m):
+        return icarus_get_state(self.ctx[m], self.shapes[m])
+
+    def set_state(self, m, U, t):
+        icarus_set_state(self.ctx[m], U, t)
+
+    def time(self, m):
+        return icarus_time(self.ctx[m])
+
+    def sample(self, m, cap=1):
+        return icarus_sample(self.ctx[m], None, cap)
+
+    @property
+    def ncell(self):
+        return sum(w.grid.ncell for w in self.workloads)
+
+    def close(self):
+        if getattr(self, "b", None):
+            icarus_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

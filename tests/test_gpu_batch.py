@@ -1,0 +1,84 @@
+"""Batched ensemble (one persistent cooperative launch per step) against members run alone.
+
+Every member of a batch must be bit-identical to the same member advanced by its own context:
+the per-face and per-cell arithmetic is shared, only the work distribution differs. Members have
+uneven grids and different drivers, so their dt (and t) differ.
+"""
+import numpy as np
+import pytest
+
+from paper_2501_15923_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ic():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_15923_gb300 import build
+    build.build()
+    from paper_2501_15923_gb300 import icarus
+    return icarus
+
+
+def members():
+    shapes = [(40, 10, 16), (64, 12, 24), (33, 9, 20), (96, 16, 32)]
+    ws = []
+    for q, s in enumerate(shapes):
+        w = I.config1(seed=40 + q, grid=I.Grid(*s))
+        ws.append(w)
+    return ws
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_batch_members_bit_identical_to_single_runs(ic, prec):
+    ws = members()
+    b = ic.Batch(ws, precision=prec)
+    tiles = b.autotune(2)
+    assert all(0 <= r < 3 and 0 <= t < 2 for r, t in tiles)
+    b.step(4)
+    assert b.status() == 0
+    times = []
+    for m, w in enumerate(ws):
+        Ub, tb = b.get_state(m)
+        s = ic.from_workload(w, precision=prec)
+        s.step(4)
+        Us, ts = s.get_state()
+        if prec == 2:
+            # the configured ensemble form: bit-identical to the member run alone
+            assert ts == tb, (m, ts, tb)
+            assert np.array_equal(Ub, Us), (m, np.abs(Ub - Us).max())
+        else:
+            # FP64: the same operations, compiled into a different kernel; the compiler's choice of
+            # fused multiply-adds may differ, so agreement is to rounding (1e-13 of the scale)
+            scale = np.abs(Us).reshape(8, -1).max(1)[:, None]
+            assert np.all(np.abs(Ub - Us).reshape(8, -1) <= 1e-13 * scale), (m, np.abs(Ub - Us).max())
+            assert abs(ts - tb) <= 1e-13 * ts
+        times.append(tb)
+        s.close()
+    assert len(set(times)) == len(times)      # every member advanced with its own dt
+    b.close()
+
+
+def test_batch_probes_and_tile_variants(ic):
+    """Every tile candidate gives the same bits; probes are recorded per member per step."""
+    ws = members()[:2]
+    ref = None
+    for cfg_r in range(3):
+        for cfg_t in range(2):
+            b = ic.Batch(ws, precision=2)
+            b.register_probes()
+            b.set_tiles(cfg_r, cfg_t)
+            b.step(2)
+            assert b.status() == 0
+            U, _ = b.get_state(1)
+            if ref is None:
+                ref = U
+            assert np.array_equal(U, ref), (cfg_r, cfg_t)
+            rec, n = b.sample(0, cap=8)
+            assert n == 2 and np.all(rec[:, :, 1] > 0)
+            info = b.info()
+            assert info["members"] == 2 and info["blocks"] >= 152
+            b.close()
