@@ -49,9 +49,12 @@ def lib():
             f = getattr(_lib, name)
             f.restype = res
             f.argtypes = args
-        if hasattr(_lib, "orc_conv3d_forward"):
-            _lib.orc_conv3d_forward.restype = None
-        _lib._has_conv = hasattr(_lib, "orc_conv3d_forward")
+        for name, args in {"orc_conv3d_forward": [P, P, P, P, I, I, I, I, I, I],
+                           "orc_conv3d_backward": [P, P, P, P, P, P, P, I, I, I, I, I, I],
+                           "orc_restrict": [P, P, P, I, I, I]}.items():
+            f = getattr(_lib, name)
+            f.restype = None
+            f.argtypes = args
     return _lib
 
 
@@ -197,3 +200,33 @@ def prim_from_cons(U: np.ndarray, gamma: float) -> np.ndarray:
     W[4] = (gamma - 1.0) * (U[4] - 0.5 * U[0] * (W[1:4] ** 2).sum(0) - 0.5 * (U[5:8] ** 2).sum(0))
     W[5:8] = U[5:8]
     return W
+
+
+# ---- learned-closure layers -------------------------------------------------------------------
+def conv3d_forward(x, w, b, act):
+    """x [n3][n2][n1][C], w [O][27][C], b [O] -> y [n3][n2][n1][O] (FP64)."""
+    x, w, b = _c(x), _c(w), _c(b)
+    n3, n2, n1, Cc = x.shape
+    O = w.shape[0]
+    y = np.empty((n3, n2, n1, O))
+    lib().orc_conv3d_forward(_ptr(x), _ptr(w), _ptr(b), _ptr(y), n1, n2, n3, Cc, O, int(act))
+    return y
+
+
+def conv3d_backward(x, w, y, g, act):
+    """Gradients (dx, dw, db) of L with dL/dy = g, y the forward output."""
+    x, w, y, g = _c(x), _c(w), _c(y), _c(g)
+    n3, n2, n1, Cc = x.shape
+    O = w.shape[0]
+    dx, dw, db = np.empty_like(x), np.empty_like(w), np.empty(O)
+    lib().orc_conv3d_backward(_ptr(x), _ptr(w), _ptr(y), _ptr(g), _ptr(dx), _ptr(dw), _ptr(db), n1, n2, n3, Cc, O, int(act))
+    return dx, dw, db
+
+
+def restrict(Uf, vol_f):
+    """Volume-weighted 2x2x2 restriction of a fine state [8][2n3][2n2][2n1]."""
+    Uf, vol_f = _c(Uf), _c(vol_f)
+    _, f3, f2, f1 = Uf.shape
+    Uc = np.empty((8, f3 // 2, f2 // 2, f1 // 2))
+    lib().orc_restrict(_ptr(Uf), _ptr(vol_f), _ptr(Uc), f1 // 2, f2 // 2, f3 // 2)
+    return Uc
