@@ -142,6 +142,10 @@ int icarus_get_state(icarus_ctx *ctx, double *U, double *t);
  * Synchronous. Enables stepping without boundary maps when no face is DRIVEN. */
 int icarus_set_state(icarus_ctx *ctx, const double *U, double t);
 
+/* Copy the interior state into a DEVICE buffer U_dev [8][n3][n2][n1] (double, code units).
+ * Synchronous. */
+int icarus_copy_state(icarus_ctx *ctx, double *U_dev);
+
 /* Cap dt so that the run stops exactly at t_stop (code units); t_stop <= 0 removes the cap. */
 int icarus_set_stop_time(icarus_ctx *ctx, double t_stop);
 
@@ -213,6 +217,52 @@ void *icarus_batch_stream(icarus_batch *b);
 
 /* Release the batch and all member contexts. */
 int icarus_batch_destroy(icarus_batch *b);
+
+/* ---- learned closure ---------------------------------------------------------------------
+ * A 4-layer 3-D convolutional network (8 -> 32 -> 32 -> 32 -> 8 channels, 3x3x3 kernels, ReLU,
+ * phi circular / r and theta replicate padding) that predicts the correction of a coarse state
+ * towards the restricted fine solution (not in the paper). BF16 weights and activations, FP32
+ * accumulation on the tensor cores (mma.sync), FP32 Adam master weights; device memory from
+ * cudaMalloc, released by icarus_closure_destroy. */
+typedef struct icarus_closure icarus_closure;
+
+/* Network for a coarse grid n1 x n2 x n3, weights initialised from seed; runs on cuda_stream. */
+int icarus_closure_create(int n1, int n2, int n3, unsigned long long seed, void *cuda_stream,
+                          icarus_closure **out);
+int icarus_closure_destroy(icarus_closure *c);
+
+/* Field-wise normalisation per radial index (host arrays [8][n1]): the input is (U - in_mean) /
+ * in_scale, the network's output is multiplied by out_scale to give the correction dU. */
+int icarus_closure_set_norm(icarus_closure *c, const double *in_mean, const double *in_scale,
+                            const double *out_scale);
+
+/* One Adam step (learning rate lr) on one pair: U_in and dU_target are DEVICE arrays
+ * [8][n3][n2][n1] (code units); the loss is the mean squared error of the normalised correction.
+ * *loss (host, may be NULL) receives the loss before the update; synchronous when loss != NULL. */
+int icarus_closure_train_step(icarus_closure *c, const double *U_in, const double *dU_target, double lr,
+                              double *loss);
+
+/* Predicted correction dU_out (DEVICE [8][n3][n2][n1]) for a coarse state U_in (DEVICE). */
+int icarus_closure_predict(icarus_closure *c, const double *U_in, double *dU_out);
+
+/* Add the predicted correction to an FP64 coarse context's state in place (primitives, ghosts
+ * and the next dt refreshed), on the context's stream. */
+int icarus_closure_apply(icarus_closure *c, icarus_ctx *ctx);
+
+/* Get (set = 0) or set (set = 1) the FP32 weights of one layer as host arrays w [O][27][C],
+ * b [O] with the padded channel counts (C, O) = (16, 32), (32, 32), (32, 32), (32, 16). */
+int icarus_closure_weights(icarus_closure *c, int layer, float *w, float *b, int set);
+
+/* Volume-weighted 2x2x2 restriction of a fine context's state onto a coarse context whose grid is
+ * half as fine in every direction (state, primitives, time and dt of the coarse context set). */
+int icarus_restrict(icarus_ctx *fine, icarus_ctx *coarse);
+
+/* One convolution layer on host FP32 arrays (channels last, x [n3][n2][n1][C], w [O][27][C],
+ * b [O], g = dL/dy [n3][n2][n1][O]): y = act(conv(x) + b) and the gradients dx, dw, db, with
+ * the tensor-core kernels of the closure (inputs rounded to BF16). (C, O, act) in {(16, 32, ReLU),
+ * (32, 32, ReLU), (32, 16, linear)}. For checking the kernels against a reference. */
+int icarus_conv3d_layer(int n1, int n2, int n3, int C, int O, int act, const float *x, const float *w,
+                        const float *b, const float *g, float *y, float *dx, float *dw, float *db);
 
 /* Largest grid (interior cells) icarus_cfl_dt_noalloc accepts: 16384 blocks of 256 cells. */
 #define ICARUS_NOALLOC_MAX_CELLS 4194304LL

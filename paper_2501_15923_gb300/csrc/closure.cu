@@ -1,0 +1,850 @@
+// closure.cu -- learned closure for a coarse solve: a 4-layer 3-D convolutional network
+// (8 -> 32 -> 32 -> 32 -> 8 channels, 3x3x3 kernels, ReLU between layers, phi circular and
+// r / theta replicate padding) that predicts the correction of a coarse state towards the
+// restricted fine solution; trained on the GPU by the kernels below.
+//
+// Every convolution runs on the tensor cores as an implicit GEMM with BF16 operands and FP32
+// accumulation (mma.sync m16n8k16): forward (rows = voxels, K = 27 taps x C_in), data gradient
+// (rows = padded voxels, K = 27 x C_out, transposed weights), weight gradient (rows = C_out,
+// columns = C_in, K = voxels, split over blocks and summed with atomics). Activations are stored
+// channels-last on a grid padded by one ghost layer; a pad kernel fills the ghosts (replicate /
+// circular) and a fold kernel adds ghost gradients back to the cells they copy (the adjoint).
+// Channel counts are padded to multiples of 16 (layer 0 input 8 -> 16 zero channels, layer 3
+// output 8 -> 16 with zero weights); the padding never carries a gradient.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "icarus_ctx.h"
+#include "icarus_kernels.cuh"
+
+using namespace icarus;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+struct Geo {
+    int n1, n2, n3, q1, q2, q3;   // interior and padded (n + 2) extents
+    long long N, NP;
+};
+
+Geo make_geo(int n1, int n2, int n3)
+{
+    Geo g;
+    g.n1 = n1; g.n2 = n2; g.n3 = n3;
+    g.q1 = n1 + 2; g.q2 = n2 + 2; g.q3 = n3 + 2;
+    g.N = (long long)n1 * n2 * n3;
+    g.NP = (long long)g.q1 * g.q2 * g.q3;
+    return g;
+}
+
+__host__ __device__ __forceinline__ long long pidx(const Geo &g, int i, int j, int k)
+{
+    return ((long long)(k + 1) * g.q2 + (j + 1)) * g.q1 + (i + 1);
+}
+
+__device__ __forceinline__ long long pidx_of_voxel(const Geo &g, long long v)
+{
+    int i = (int)(v % g.n1);
+    long long r = v / g.n1;
+    int j = (int)(r % g.n2), k = (int)(r / g.n2);
+    return pidx(g, i, j, k);
+}
+
+// padded-index offset of tap t = (d3 + 1) * 9 + (d2 + 1) * 3 + (d1 + 1)
+__device__ __forceinline__ long long tap_off(const Geo &g, int t)
+{
+    int d1 = t % 3 - 1, d2 = (t / 3) % 3 - 1, d3 = t / 9 - 1;
+    return ((long long)d3 * g.q2 + d2) * g.q1 + d1;
+}
+
+__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// D = A (16x16, row) * B (16x8, col) + D, BF16 inputs, FP32 accumulators
+__device__ __forceinline__ void mma16816(float *d, const uint32_t *a, uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ---- forward: y = act(conv(P(x)) + b) -----------------------------------------------------------
+// block = 4 warps, 128 voxels (each warp 2 m16 row tiles); all O output channels per block.
+// out_pad (bf16, padded, may be null) receives act(y); out_f (fp32 [N][O], may be null) too.
+template <int C, int O, int ACT>
+__global__ void __launch_bounds__(128) k_conv_fwd(Geo g, const bf16 *__restrict__ in, const bf16 *__restrict__ w,
+                                                  const float *__restrict__ b, bf16 *out_pad, float *out_f)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 2, tig = lane & 3;
+    const long long v0 = (long long)blockIdx.x * 128 + warp * 32;
+    long long pb[2][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            long long v = v0 + mt * 16 + grp + 8 * h;
+            pb[mt][h] = pidx_of_voxel(g, v < g.N ? v : 0);
+        }
+    float acc[2][O / 8][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < O / 8; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+    for (int t = 0; t < 27; ++t) {
+        const long long off = tap_off(g, t);
+#pragma unroll
+        for (int ks = 0; ks < C / 16; ++ks) {
+            uint32_t a[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const bf16 *r0 = in + (pb[mt][0] + off) * C + ks * 16 + tig * 2;
+                const bf16 *r1 = in + (pb[mt][1] + off) * C + ks * 16 + tig * 2;
+                a[mt][0] = ld32(r0);
+                a[mt][1] = ld32(r1);
+                a[mt][2] = ld32(r0 + 8);
+                a[mt][3] = ld32(r1 + 8);
+            }
+#pragma unroll
+            for (int nt = 0; nt < O / 8; ++nt) {
+                const bf16 *wb = w + ((long long)(nt * 8 + grp) * 27 + t) * C + ks * 16 + tig * 2;
+                const uint32_t b0 = ld32(wb), b1 = ld32(wb + 8);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], a[mt], b0, b1);
+            }
+        }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < O / 8; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int h = e >> 1, col = nt * 8 + tig * 2 + (e & 1);
+                const long long v = v0 + mt * 16 + grp + 8 * h;
+                if (v >= g.N) continue;
+                float val = acc[mt][nt][e] + b[col];
+                if (ACT) val = fmaxf(val, 0.f);
+                if (out_pad) out_pad[pb[mt][h] * O + col] = __float2bfloat16_rn(val);
+                if (out_f) out_f[v * O + col] = val;
+            }
+}
+
+// ---- padding and its adjoint ------------------------------------------------------------------
+template <typename T>
+__global__ void k_pad_fill(Geo g, T *buf, int C)
+{
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= g.NP) return;
+    int ip = (int)(q % g.q1);
+    long long r = q / g.q1;
+    int jp = (int)(r % g.q2), kp = (int)(r / g.q2);
+    int i = ip - 1, j = jp - 1, k = kp - 1;
+    if (i >= 0 && i < g.n1 && j >= 0 && j < g.n2 && k >= 0 && k < g.n3) return;
+    int si = min(max(i, 0), g.n1 - 1), sj = min(max(j, 0), g.n2 - 1), sk = (k + g.n3) % g.n3;
+    long long src = pidx(g, si, sj, sk);
+    for (int c = 0; c < C; ++c) buf[q * C + c] = buf[src * C + c];
+}
+
+// add every ghost cell's gradient to the interior cell it copies (in place, interior = result)
+__global__ void k_pad_fold(Geo g, float *buf, int C)
+{
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= g.NP) return;
+    int ip = (int)(q % g.q1);
+    long long r = q / g.q1;
+    int jp = (int)(r % g.q2), kp = (int)(r / g.q2);
+    int i = ip - 1, j = jp - 1, k = kp - 1;
+    if (i >= 0 && i < g.n1 && j >= 0 && j < g.n2 && k >= 0 && k < g.n3) return;
+    int si = min(max(i, 0), g.n1 - 1), sj = min(max(j, 0), g.n2 - 1), sk = (k + g.n3) % g.n3;
+    long long src = pidx(g, si, sj, sk);
+    for (int c = 0; c < C; ++c) atomicAdd(&buf[src * C + c], buf[q * C + c]);
+}
+
+// ---- gradient w.r.t. the pre-activation, bias gradient ------------------------------------------
+// dout: fp32, padded layout [NP][O] (pad = 1) or interior [N][O] (pad = 0); act_out: the layer's
+// activated output (bf16 padded) for the ReLU mask (null for a linear layer). dpre: bf16 padded
+// with zero ghosts. db += sum over voxels.
+template <int O>
+__global__ void __launch_bounds__(256) k_dpre(Geo g, const float *__restrict__ dout, int dout_padded,
+                                              const bf16 *__restrict__ act_out, bf16 *dpre, float *db)
+{
+    __shared__ float sdb[O];
+    if (threadIdx.x < O) sdb[threadIdx.x] = 0.f;
+    __syncthreads();
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < g.NP) {
+        int ip = (int)(q % g.q1);
+        long long r = q / g.q1;
+        int jp = (int)(r % g.q2), kp = (int)(r / g.q2);
+        int i = ip - 1, j = jp - 1, k = kp - 1;
+        bool inside = i >= 0 && i < g.n1 && j >= 0 && j < g.n2 && k >= 0 && k < g.n3;
+        for (int o = 0; o < O; ++o) {
+            float d = 0.f;
+            if (inside) {
+                long long s = dout_padded ? q : ((long long)k * g.n2 + j) * g.n1 + i;
+                d = dout[s * O + o];
+                if (act_out && !(__bfloat162float(act_out[q * O + o]) > 0.f)) d = 0.f;
+                d = __bfloat162float(__float2bfloat16_rn(d));
+                atomicAdd(&sdb[o], d);
+            }
+            dpre[q * O + o] = __float2bfloat16_rn(d);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < O) atomicAdd(&db[threadIdx.x], sdb[threadIdx.x]);
+}
+
+// ---- weight gradient: dw[o][t][c] += sum_x dpre[x][o] in[x + off_t][c] ----------------------------
+// block = 4 warps over a chunk of voxels; per tap the (O x C) tile is accumulated over the chunk
+// (K = 64 voxels per shared-memory stage) and added to dw with atomics.
+template <int C, int O>
+__global__ void __launch_bounds__(128) k_conv_wgrad(Geo g, const bf16 *__restrict__ dpre, const bf16 *__restrict__ in,
+                                                    float *dw, long long chunk)
+{
+    constexpr int MT = O / 16, NT = C / 8, TILES = MT * NT, PER = (TILES + 3) / 4;
+    __shared__ __align__(16) bf16 sD[64][O];
+    __shared__ __align__(16) bf16 sX[64][C];
+    __shared__ long long spb[64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 2, tig = lane & 3;
+    const long long vb = (long long)blockIdx.x * chunk;
+    const long long ve = min(g.N, vb + chunk);
+    for (int t = 0; t < 27; ++t) {
+        const long long off = tap_off(g, t);
+        float acc[PER][4];
+#pragma unroll
+        for (int p = 0; p < PER; ++p)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[p][e] = 0.f;
+        for (long long sv = vb; sv < ve; sv += 64) {
+            if (threadIdx.x < 64) {
+                long long v = sv + threadIdx.x;
+                spb[threadIdx.x] = v < ve ? pidx_of_voxel(g, v) : -1;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < 64 * (O / 2); e += 128) {
+                int row = e / (O / 2), cp = e % (O / 2);
+                uint32_t val = spb[row] >= 0 ? ld32(dpre + spb[row] * O + cp * 2) : 0u;
+                *reinterpret_cast<uint32_t *>(&sD[row][cp * 2]) = val;
+            }
+            for (int e = threadIdx.x; e < 64 * (C / 2); e += 128) {
+                int row = e / (C / 2), cp = e % (C / 2);
+                uint32_t val = spb[row] >= 0 ? ld32(in + (spb[row] + off) * C + cp * 2) : 0u;
+                *reinterpret_cast<uint32_t *>(&sX[row][cp * 2]) = val;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const int k0 = kk * 16 + tig * 2;
+#pragma unroll
+                for (int p = 0; p < PER; ++p) {
+                    const int tile = warp + 4 * p;
+                    if (tile >= TILES) break;
+                    const int mt = tile / NT, nt = tile % NT;
+                    const int o0 = mt * 16 + grp, c0 = nt * 8 + grp;
+                    uint32_t a[4];
+                    a[0] = pack2(sD[k0][o0], sD[k0 + 1][o0]);
+                    a[1] = pack2(sD[k0][o0 + 8], sD[k0 + 1][o0 + 8]);
+                    a[2] = pack2(sD[k0 + 8][o0], sD[k0 + 9][o0]);
+                    a[3] = pack2(sD[k0 + 8][o0 + 8], sD[k0 + 9][o0 + 8]);
+                    const uint32_t b0 = pack2(sX[k0][c0], sX[k0 + 1][c0]);
+                    const uint32_t b1 = pack2(sX[k0 + 8][c0], sX[k0 + 9][c0]);
+                    mma16816(acc[p], a, b0, b1);
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+            const int tile = warp + 4 * p;
+            if (tile >= TILES) break;
+            const int mt = tile / NT, nt = tile % NT;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int o = mt * 16 + grp + 8 * (e >> 1), c = nt * 8 + tig * 2 + (e & 1);
+                atomicAdd(&dw[((long long)o * 27 + t) * C + c], acc[p][e]);
+            }
+        }
+    }
+}
+
+// ---- data gradient over the padded grid: din[z][c] = sum_{t,o} w[o][t][c] dpre[z - off_t][o] ----
+// wt is the transposed weight copy [C][27][O]; dpre has zero ghosts; sources outside the padded
+// box contribute nothing. The result is folded into the interior by k_pad_fold.
+template <int C, int O>
+__global__ void __launch_bounds__(128) k_conv_dgrad(Geo g, const bf16 *__restrict__ dpre, const bf16 *__restrict__ wt,
+                                                    float *din)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 2, tig = lane & 3;
+    const long long z0 = (long long)blockIdx.x * 128 + warp * 32;
+    int zc[2][2][3];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            long long z = z0 + mt * 16 + grp + 8 * h;
+            if (z >= g.NP) z = 0;
+            zc[mt][h][0] = (int)(z % g.q1);
+            long long r = z / g.q1;
+            zc[mt][h][1] = (int)(r % g.q2);
+            zc[mt][h][2] = (int)(r / g.q2);
+        }
+    float acc[2][C / 8][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < C / 8; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
+    for (int t = 0; t < 27; ++t) {
+        const int d1 = t % 3 - 1, d2 = (t / 3) % 3 - 1, d3 = t / 9 - 1;
+        long long src[2][2];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int a = zc[mt][h][0] - d1, b = zc[mt][h][1] - d2, c = zc[mt][h][2] - d3;
+                bool ok = a >= 0 && a < g.q1 && b >= 0 && b < g.q2 && c >= 0 && c < g.q3;
+                src[mt][h] = ok ? ((long long)c * g.q2 + b) * g.q1 + a : -1;
+            }
+#pragma unroll
+        for (int ks = 0; ks < O / 16; ++ks) {
+            uint32_t a[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const long long s0 = src[mt][0], s1 = src[mt][1];
+                const int cb = ks * 16 + tig * 2;
+                a[mt][0] = s0 >= 0 ? ld32(dpre + s0 * O + cb) : 0u;
+                a[mt][1] = s1 >= 0 ? ld32(dpre + s1 * O + cb) : 0u;
+                a[mt][2] = s0 >= 0 ? ld32(dpre + s0 * O + cb + 8) : 0u;
+                a[mt][3] = s1 >= 0 ? ld32(dpre + s1 * O + cb + 8) : 0u;
+            }
+#pragma unroll
+            for (int nt = 0; nt < C / 8; ++nt) {
+                const bf16 *wb = wt + ((long long)(nt * 8 + grp) * 27 + t) * O + ks * 16 + tig * 2;
+                const uint32_t b0 = ld32(wb), b1 = ld32(wb + 8);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], a[mt], b0, b1);
+            }
+        }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < C / 8; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const long long z = z0 + mt * 16 + grp + 8 * (e >> 1);
+                if (z >= g.NP) continue;
+                din[z * C + nt * 8 + tig * 2 + (e & 1)] = acc[mt][nt][e];
+            }
+}
+
+// ---- normalisation, loss, correction, optimiser --------------------------------------------------
+// x[z][c] = (U[c][v] - mean[c][i]) / scale[c][i] for c < 8, 0 for c in [8, 16)
+__global__ void k_norm_in(Geo g, const double *__restrict__ U, const double *__restrict__ mean,
+                          const double *__restrict__ scale, bf16 *x)
+{
+    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.N) return;
+    const int i = (int)(v % g.n1);
+    const long long q = pidx_of_voxel(g, v);
+    for (int c = 0; c < 16; ++c) {
+        float val = 0.f;
+        if (c < NV) val = (float)((U[c * g.N + v] - mean[c * g.n1 + i]) / scale[c * g.n1 + i]);
+        x[q * 16 + c] = __float2bfloat16_rn(val);
+    }
+}
+
+// loss = mean over voxels and the 8 fields of (y - dU / oscale)^2; dy = its gradient
+__global__ void __launch_bounds__(256) k_mse(Geo g, const float *__restrict__ y, const double *__restrict__ dU,
+                                             const double *__restrict__ oscale, float *dy, double *loss)
+{
+    __shared__ double red[8];
+    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (v < g.N) {
+        const int i = (int)(v % g.n1);
+        const double norm = 1.0 / (8.0 * (double)g.N);
+        for (int c = 0; c < 16; ++c) {
+            float d = 0.f;
+            if (c < NV) {
+                double tgt = dU[c * g.N + v] / oscale[c * g.n1 + i];
+                double e = (double)y[v * 16 + c] - tgt;
+                s += e * e * norm;
+                d = (float)(2.0 * e * norm);
+            }
+            dy[v * 16 + c] = d;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        atomicAdd(loss, t);
+    }
+}
+
+// correction in the solver's padded FP64 layout: U[c] += y[c] * oscale[c][i]
+__global__ void k_apply(Params P, Geo g, const float *__restrict__ y, const double *__restrict__ oscale, double *U)
+{
+    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.N) return;
+    const int i = (int)(v % g.n1);
+    const long long r = v / g.n1;
+    const int j = (int)(r % g.n2), k = (int)(r / g.n2);
+    const long long c = cidx(P, i, j, k);
+    for (int f = 0; f < NV; ++f) U[f * P.nt + c] += (double)y[v * 16 + f] * oscale[f * g.n1 + i];
+}
+
+__global__ void k_unpack_dU(Geo g, const float *__restrict__ y, const double *__restrict__ oscale, double *dU)
+{
+    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.N) return;
+    const int i = (int)(v % g.n1);
+    for (int f = 0; f < NV; ++f) dU[f * g.N + v] = (double)y[v * 16 + f] * oscale[f * g.n1 + i];
+}
+
+// Adam (FP32 master weights) and refresh of the BF16 copies w[O][27][C] and wt[C][27][O]
+__global__ void k_adam(int n, float *w, float *m, float *v, const float *grad, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    float gq = grad[q];
+    float mq = b1 * m[q] + (1.f - b1) * gq;
+    float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+    m[q] = mq;
+    v[q] = vq;
+    w[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+}
+
+__global__ void k_weights_bf16(int O, int C, const float *w, bf16 *wb, bf16 *wt)
+{
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= O * 27 * C) return;
+    int c = q % C, t = (q / C) % 27, o = q / (27 * C);
+    bf16 x = __float2bfloat16_rn(w[q]);
+    wb[q] = x;
+    wt[((long long)c * 27 + t) * O + o] = x;
+}
+
+// volume-weighted 2x2x2 restriction of a fine solver state onto a coarse one (padded layouts)
+__global__ void k_restrict(Params F, Params Cc, const double *__restrict__ Uf, double *Uc)
+{
+    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= (long long)Cc.n1 * Cc.n2 * Cc.n3) return;
+    const int i = (int)(v % Cc.n1);
+    const long long r = v / Cc.n1;
+    const int j = (int)(r % Cc.n2), k = (int)(r / Cc.n2);
+    double s[NV] = {0}, vs = 0.0;
+    for (int q = 0; q < 8; ++q) {
+        const int a = 2 * i + (q & 1), b = 2 * j + ((q >> 1) & 1), cc = 2 * k + ((q >> 2) & 1);
+        const double vol = 1.0 / (F.m.iv1[a + NG] * F.m.iv2[b + NG] * F.m.iv3);
+        const long long id = cidx(F, a, b, cc);
+        for (int f = 0; f < NV; ++f) s[f] += vol * Uf[f * F.nt + id];
+        vs += vol;
+    }
+    const long long id = cidx(Cc, i, j, k);
+    for (int f = 0; f < NV; ++f) Uc[f * Cc.nt + id] = s[f] / vs;
+}
+
+unsigned int ccdiv(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
+
+// layer shapes (C_in padded, C_out padded, real C_in, real C_out)
+const int LC[4] = {16, 32, 32, 32}, LO[4] = {32, 32, 32, 16}, RC[4] = {8, 32, 32, 32}, RO[4] = {32, 32, 32, 8};
+
+void launch_fwd(int l, Geo g, const bf16 *in, const bf16 *w, const float *b, bf16 *out_pad, float *out_f, cudaStream_t s)
+{
+    const unsigned int nb = ccdiv(g.N, 128);
+    if (l == 0) k_conv_fwd<16, 32, 1><<<nb, 128, 0, s>>>(g, in, w, b, out_pad, out_f);
+    else if (l < 3) k_conv_fwd<32, 32, 1><<<nb, 128, 0, s>>>(g, in, w, b, out_pad, out_f);
+    else k_conv_fwd<32, 16, 0><<<nb, 128, 0, s>>>(g, in, w, b, out_pad, out_f);
+}
+
+void launch_wgrad(int l, Geo g, const bf16 *dpre, const bf16 *in, float *dw, cudaStream_t s)
+{
+    const long long chunk = 2048;
+    const unsigned int nb = ccdiv(g.N, chunk);
+    if (l == 0) k_conv_wgrad<16, 32><<<nb, 128, 0, s>>>(g, dpre, in, dw, chunk);
+    else if (l < 3) k_conv_wgrad<32, 32><<<nb, 128, 0, s>>>(g, dpre, in, dw, chunk);
+    else k_conv_wgrad<32, 16><<<nb, 128, 0, s>>>(g, dpre, in, dw, chunk);
+}
+
+void launch_dgrad(int l, Geo g, const bf16 *dpre, const bf16 *wt, float *din, cudaStream_t s)
+{
+    const unsigned int nb = ccdiv(g.NP, 128);
+    if (l == 3) k_conv_dgrad<32, 16><<<nb, 128, 0, s>>>(g, dpre, wt, din);
+    else k_conv_dgrad<32, 32><<<nb, 128, 0, s>>>(g, dpre, wt, din);   // layers 1, 2 (layer 0 needs none)
+}
+
+void launch_dpre(int O, Geo g, const float *dout, int padded, const bf16 *act, bf16 *dpre, float *db, cudaStream_t s)
+{
+    const unsigned int nb = ccdiv(g.NP, 256);
+    if (O == 32) k_dpre<32><<<nb, 256, 0, s>>>(g, dout, padded, act, dpre, db);
+    else k_dpre<16><<<nb, 256, 0, s>>>(g, dout, padded, act, dpre, db);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------------
+struct icarus_closure {
+    Geo g;
+    cudaStream_t stream = nullptr;
+    std::vector<void *> allocs;
+    float *w[4], *b[4], *mw[4], *vw[4], *mb[4], *vb[4], *dw[4], *db[4];
+    bf16 *wb[4], *wt[4];
+    bf16 *act[4];          // padded activations: act[0] = normalised input (16 ch), act[l] = output of layer l-1
+    bf16 *dpre;            // padded, max 32 channels
+    float *din;            // padded fp32, 32 channels
+    float *y, *dy;         // [N][16]
+    double *mean, *scale, *oscale, *loss, *upack;
+    int step = 0;
+    bool have_norm = false;
+};
+
+namespace {
+
+#define CCK(call)                                                                                    \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return report_error(ICARUS_ECUDA, cudaGetErrorString(e_));            \
+    } while (0)
+
+void *cl_alloc(icarus_closure *c, size_t bytes)
+{
+    void *p = nullptr;
+    if (cudaMalloc(&p, (bytes + 255) & ~(size_t)255) != cudaSuccess) return nullptr;
+    c->allocs.push_back(p);
+    return p;
+}
+
+uint64_t splitmix(uint64_t &s)
+{
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double gauss(uint64_t &s)
+{
+    double u1 = ((splitmix(s) >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+    double u2 = (splitmix(s) >> 11) * (1.0 / 9007199254740992.0);
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.14159265358979323846 * u2);
+}
+
+int refresh_bf16(icarus_closure *c)
+{
+    for (int l = 0; l < 4; ++l) {
+        int n = LO[l] * 27 * LC[l];
+        k_weights_bf16<<<ccdiv(n, 256), 256, 0, c->stream>>>(LO[l], LC[l], c->w[l], c->wb[l], c->wt[l]);
+    }
+    CCK(cudaGetLastError());
+    return ICARUS_OK;
+}
+
+// forward of the whole network from act[0] (already normalised and padded); y = fp32 [N][16]
+void forward(icarus_closure *c)
+{
+    cudaStream_t s = c->stream;
+    Geo g = c->g;
+    for (int l = 0; l < 4; ++l) {
+        if (l < 3) {
+            launch_fwd(l, g, c->act[l], c->wb[l], c->b[l], c->act[l + 1], nullptr, s);
+            k_pad_fill<bf16><<<ccdiv(g.NP, 256), 256, 0, s>>>(g, c->act[l + 1], LO[l]);
+        } else {
+            launch_fwd(l, g, c->act[l], c->wb[l], c->b[l], nullptr, c->y, s);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int icarus_closure_create(int n1, int n2, int n3, unsigned long long seed, void *cuda_stream, icarus_closure **out)
+{
+    if (n1 < 1 || n2 < 1 || n3 < 1 || !out) return report_error(ICARUS_EINVAL, "bad argument");
+    icarus_closure *c = new icarus_closure();
+    c->g = make_geo(n1, n2, n3);
+    c->stream = (cudaStream_t)cuda_stream;
+    const Geo &g = c->g;
+    bool ok = true;
+    uint64_t st = seed;
+    for (int l = 0; l < 4; ++l) {
+        const int n = LO[l] * 27 * LC[l];
+        std::vector<float> hw(n, 0.f), hb(LO[l], 0.f);
+        const double sd = (l < 3 ? sqrt(2.0 / (27.0 * RC[l])) : 0.1 * sqrt(1.0 / (27.0 * RC[l])));
+        for (int o = 0; o < RO[l]; ++o)
+            for (int t = 0; t < 27; ++t)
+                for (int ci = 0; ci < RC[l]; ++ci) hw[((size_t)o * 27 + t) * LC[l] + ci] = (float)(sd * gauss(st));
+        c->w[l] = (float *)cl_alloc(c, n * 4); c->mw[l] = (float *)cl_alloc(c, n * 4);
+        c->vw[l] = (float *)cl_alloc(c, n * 4); c->dw[l] = (float *)cl_alloc(c, n * 4);
+        c->b[l] = (float *)cl_alloc(c, LO[l] * 4); c->mb[l] = (float *)cl_alloc(c, LO[l] * 4);
+        c->vb[l] = (float *)cl_alloc(c, LO[l] * 4); c->db[l] = (float *)cl_alloc(c, LO[l] * 4);
+        c->wb[l] = (bf16 *)cl_alloc(c, n * 2); c->wt[l] = (bf16 *)cl_alloc(c, n * 2);
+        if (!c->w[l] || !c->mw[l] || !c->vw[l] || !c->dw[l] || !c->b[l] || !c->mb[l] || !c->vb[l] || !c->db[l] ||
+            !c->wb[l] || !c->wt[l]) { ok = false; break; }
+        cudaMemcpy(c->w[l], hw.data(), n * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(c->b[l], hb.data(), LO[l] * 4, cudaMemcpyHostToDevice);
+        cudaMemset(c->mw[l], 0, n * 4); cudaMemset(c->vw[l], 0, n * 4);
+        cudaMemset(c->mb[l], 0, LO[l] * 4); cudaMemset(c->vb[l], 0, LO[l] * 4);
+    }
+    for (int l = 0; ok && l < 4; ++l) {
+        c->act[l] = (bf16 *)cl_alloc(c, g.NP * LC[l] * 2);
+        ok = c->act[l] != nullptr;
+        if (ok) cudaMemset(c->act[l], 0, g.NP * LC[l] * 2);
+    }
+    if (ok) {
+        c->dpre = (bf16 *)cl_alloc(c, g.NP * 32 * 2);
+        c->din = (float *)cl_alloc(c, g.NP * 32 * 4);
+        c->y = (float *)cl_alloc(c, g.N * 16 * 4);
+        c->dy = (float *)cl_alloc(c, g.N * 16 * 4);
+        c->mean = (double *)cl_alloc(c, 8 * n1 * 8);
+        c->scale = (double *)cl_alloc(c, 8 * n1 * 8);
+        c->oscale = (double *)cl_alloc(c, 8 * n1 * 8);
+        c->loss = (double *)cl_alloc(c, 8);
+        c->upack = (double *)cl_alloc(c, 8 * g.N * 8);
+        ok = c->dpre && c->din && c->y && c->dy && c->mean && c->scale && c->oscale && c->loss && c->upack;
+    }
+    if (!ok) {
+        for (void *p : c->allocs) cudaFree(p);
+        delete c;
+        return report_error(ICARUS_ENOMEM, "closure allocation failed");
+    }
+    int rc = refresh_bf16(c);
+    if (rc) return rc;
+    CCK(cudaStreamSynchronize(c->stream));
+    *out = c;
+    return ICARUS_OK;
+}
+
+int icarus_closure_destroy(icarus_closure *c)
+{
+    if (!c) return ICARUS_OK;
+    cudaStreamSynchronize(c->stream);
+    for (void *p : c->allocs) cudaFree(p);
+    delete c;
+    return ICARUS_OK;
+}
+
+int icarus_closure_set_norm(icarus_closure *c, const double *in_mean, const double *in_scale, const double *out_scale)
+{
+    if (!c || !in_mean || !in_scale || !out_scale) return report_error(ICARUS_EINVAL, "NULL argument");
+    const size_t n = 8 * (size_t)c->g.n1 * sizeof(double);
+    CCK(cudaMemcpyAsync(c->mean, in_mean, n, cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaMemcpyAsync(c->scale, in_scale, n, cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaMemcpyAsync(c->oscale, out_scale, n, cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaStreamSynchronize(c->stream));
+    c->have_norm = true;
+    return ICARUS_OK;
+}
+
+int icarus_closure_train_step(icarus_closure *c, const double *U_in, const double *dU_target, double lr, double *loss)
+{
+    if (!c || !U_in || !dU_target) return report_error(ICARUS_EINVAL, "NULL argument");
+    if (!c->have_norm) return report_error(ICARUS_ESTATE, "set the normalisation first");
+    cudaStream_t s = c->stream;
+    const Geo g = c->g;
+    k_norm_in<<<ccdiv(g.N, 256), 256, 0, s>>>(g, U_in, c->mean, c->scale, c->act[0]);
+    k_pad_fill<bf16><<<ccdiv(g.NP, 256), 256, 0, s>>>(g, c->act[0], 16);
+    forward(c);
+    CCK(cudaMemsetAsync(c->loss, 0, 8, s));
+    k_mse<<<ccdiv(g.N, 256), 256, 0, s>>>(g, c->y, dU_target, c->oscale, c->dy, c->loss);
+    for (int l = 0; l < 4; ++l) {
+        CCK(cudaMemsetAsync(c->dw[l], 0, LO[l] * 27 * LC[l] * 4, s));
+        CCK(cudaMemsetAsync(c->db[l], 0, LO[l] * 4, s));
+    }
+    // layer 3 (linear): gradient from the loss; then ReLU layers with the mask of their output
+    for (int l = 3; l >= 0; --l) {
+        if (l == 3) launch_dpre(LO[l], g, c->dy, 0, nullptr, c->dpre, c->db[l], s);
+        else launch_dpre(LO[l], g, c->din, 1, c->act[l + 1], c->dpre, c->db[l], s);
+        launch_wgrad(l, g, c->dpre, c->act[l], c->dw[l], s);
+        if (l > 0) {
+            launch_dgrad(l, g, c->dpre, c->wt[l], c->din, s);
+            k_pad_fold<<<ccdiv(g.NP, 256), 256, 0, s>>>(g, c->din, LC[l]);
+        }
+    }
+    c->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)c->step), c2 = 1.f - powf(b2, (float)c->step);
+    for (int l = 0; l < 4; ++l) {
+        int n = LO[l] * 27 * LC[l];
+        k_adam<<<ccdiv(n, 256), 256, 0, s>>>(n, c->w[l], c->mw[l], c->vw[l], c->dw[l], (float)lr, b1, b2, 1e-8f, c1, c2);
+        k_adam<<<1, 64, 0, s>>>(LO[l], c->b[l], c->mb[l], c->vb[l], c->db[l], (float)lr, b1, b2, 1e-8f, c1, c2);
+    }
+    int rc = refresh_bf16(c);
+    if (rc) return rc;
+    if (loss) {
+        CCK(cudaMemcpyAsync(loss, c->loss, 8, cudaMemcpyDeviceToHost, s));
+        CCK(cudaStreamSynchronize(s));
+    }
+    CCK(cudaGetLastError());
+    return ICARUS_OK;
+}
+
+// correction dU [8][n3][n2][n1] (device, code units) predicted for a coarse state U (device)
+int icarus_closure_predict(icarus_closure *c, const double *U_in, double *dU_out)
+{
+    if (!c || !U_in || !dU_out) return report_error(ICARUS_EINVAL, "NULL argument");
+    if (!c->have_norm) return report_error(ICARUS_ESTATE, "set the normalisation first");
+    cudaStream_t s = c->stream;
+    const Geo g = c->g;
+    k_norm_in<<<ccdiv(g.N, 256), 256, 0, s>>>(g, U_in, c->mean, c->scale, c->act[0]);
+    k_pad_fill<bf16><<<ccdiv(g.NP, 256), 256, 0, s>>>(g, c->act[0], 16);
+    forward(c);
+    k_unpack_dU<<<ccdiv(g.N, 256), 256, 0, s>>>(g, c->y, c->oscale, dU_out);
+    CCK(cudaGetLastError());
+    return ICARUS_OK;
+}
+
+// apply the correction to a coarse FP64 context in place: U += net(U); primitives refreshed
+int icarus_closure_apply(icarus_closure *c, icarus_ctx *ctx)
+{
+    if (!c || !ctx) return report_error(ICARUS_EINVAL, "NULL argument");
+    if (ctx->opts.precision != ICARUS_FP64) return report_error(ICARUS_EINVAL, "closure needs an FP64 context");
+    if (ctx->P.n1 != c->g.n1 || ctx->P.n2 != c->g.n2 || ctx->P.n3 != c->g.n3)
+        return report_error(ICARUS_EINVAL, "context grid differs from the closure grid");
+    if (!c->have_norm) return report_error(ICARUS_ESTATE, "set the normalisation first");
+    cudaStream_t s = ctx->stream;
+    CCK(cudaStreamSynchronize(c->stream));
+    ctx->ops.pack(ctx->P, ctx->U, c->upack, s);
+    const Geo g = c->g;
+    k_norm_in<<<ccdiv(g.N, 256), 256, 0, s>>>(g, c->upack, c->mean, c->scale, c->act[0]);
+    k_pad_fill<bf16><<<ccdiv(g.NP, 256), 256, 0, s>>>(g, c->act[0], 16);
+    cudaStream_t keep = c->stream;
+    c->stream = s;
+    forward(c);
+    c->stream = keep;
+    k_apply<<<ccdiv(g.N, 256), 256, 0, s>>>(ctx->P, g, c->y, c->oscale, (double *)ctx->U);
+    ctx->ops.prims(ctx->P, ctx->U, ctx->W, s);
+    ctx->ops.fill_ghosts(ctx->P, ctx->U, ctx->W, 1, s);
+    ctx->ops.cfl(ctx->P, ctx->W, s);
+    CCK(cudaGetLastError());
+    return ICARUS_OK;
+}
+
+// weights out / in as FP32 host arrays, layer by layer: w[l] [O_l][27][C_l], b[l] [O_l] with the
+// padded channel counts (16/32, 32/32, 32/32, 32/16)
+int icarus_closure_weights(icarus_closure *c, int layer, float *w, float *b, int set)
+{
+    if (!c || layer < 0 || layer > 3 || !w || !b) return report_error(ICARUS_EINVAL, "bad argument");
+    const size_t n = (size_t)LO[layer] * 27 * LC[layer];
+    if (set) {
+        CCK(cudaMemcpy(c->w[layer], w, n * 4, cudaMemcpyHostToDevice));
+        CCK(cudaMemcpy(c->b[layer], b, LO[layer] * 4, cudaMemcpyHostToDevice));
+        return refresh_bf16(c);
+    }
+    CCK(cudaMemcpy(w, c->w[layer], n * 4, cudaMemcpyDeviceToHost));
+    CCK(cudaMemcpy(b, c->b[layer], LO[layer] * 4, cudaMemcpyDeviceToHost));
+    return ICARUS_OK;
+}
+
+// restriction of a fine context's state onto a coarse context (2x in every direction)
+int icarus_restrict(icarus_ctx *fine, icarus_ctx *coarse)
+{
+    if (!fine || !coarse) return report_error(ICARUS_EINVAL, "NULL argument");
+    if (fine->P.n1 != 2 * coarse->P.n1 || fine->P.n2 != 2 * coarse->P.n2 || fine->P.n3 != 2 * coarse->P.n3)
+        return report_error(ICARUS_EINVAL, "fine grid must be 2x the coarse grid");
+    if (fine->opts.precision == ICARUS_FP32 || coarse->opts.precision == ICARUS_FP32)
+        return report_error(ICARUS_EINVAL, "restriction needs double states");
+    CCK(cudaStreamSynchronize(fine->stream));
+    long long n = (long long)coarse->P.n1 * coarse->P.n2 * coarse->P.n3;
+    k_restrict<<<ccdiv(n, 256), 256, 0, coarse->stream>>>(fine->P, coarse->P, (const double *)fine->U, (double *)coarse->U);
+    coarse->ops.prims(coarse->P, coarse->U, coarse->W, coarse->stream);
+    Scalars s;
+    CCK(cudaMemcpyAsync(&s, fine->sc, sizeof s, cudaMemcpyDeviceToHost, fine->stream));
+    CCK(cudaStreamSynchronize(fine->stream));
+    Scalars sc;
+    CCK(cudaMemcpyAsync(&sc, coarse->sc, sizeof sc, cudaMemcpyDeviceToHost, coarse->stream));
+    CCK(cudaStreamSynchronize(coarse->stream));
+    sc.t = s.t;
+    sc.done = 0;
+    CCK(cudaMemcpyAsync(coarse->sc, &sc, sizeof sc, cudaMemcpyHostToDevice, coarse->stream));
+    coarse->have_state = true;
+    coarse->ops.fill_ghosts(coarse->P, coarse->U, coarse->W, 1, coarse->stream);
+    coarse->ops.cfl(coarse->P, coarse->W, coarse->stream);
+    CCK(cudaGetLastError());
+    CCK(cudaStreamSynchronize(coarse->stream));
+    return ICARUS_OK;
+}
+
+// one layer on host FP32 arrays (values should be BF16-representable): forward y = act(conv +
+// b) and, with g = dL/dy, the gradients dx, dw, db. Channel counts C, O in {16, 32}.
+int icarus_conv3d_layer(int n1, int n2, int n3, int C, int O, int act, const float *x, const float *w, const float *b,
+                        const float *g, float *y, float *dx, float *dw, float *db)
+{
+    if ((C != 16 && C != 32) || (O != 16 && O != 32) || (C == 16 && O == 16) || n1 < 1 || n2 < 1 || n3 < 1)
+        return report_error(ICARUS_EINVAL, "supported (C, O): (16, 32), (32, 32), (32, 16)");
+    if ((C == 16 && act != 1) || (O == 16 && act != 0))
+        return report_error(ICARUS_EINVAL, "(16, 32) layers are ReLU, (32, 16) layers are linear");
+    const Geo gg = make_geo(n1, n2, n3);
+    const int l = C == 16 ? 0 : (O == 16 ? 3 : 1);
+    std::vector<void *> mem;
+    auto A = [&](size_t bytes) { void *p = nullptr; cudaMalloc(&p, bytes); mem.push_back(p); return p; };
+    bf16 *din_ = (bf16 *)A(gg.NP * C * 2), *dout_ = (bf16 *)A(gg.NP * O * 2), *wb = (bf16 *)A(O * 27 * C * 2),
+         *wt = (bf16 *)A(O * 27 * C * 2), *dpre = (bf16 *)A(gg.NP * O * 2);
+    float *wf = (float *)A(O * 27 * C * 4), *bf = (float *)A(O * 4), *yf = (float *)A(gg.N * O * 4),
+          *gf = (float *)A(gg.N * O * 4), *dinf = (float *)A(gg.NP * C * 4), *dwf = (float *)A(O * 27 * C * 4),
+          *dbf = (float *)A(O * 4);
+    int rc = ICARUS_OK;
+    for (void *p : mem) if (!p) rc = report_error(ICARUS_ENOMEM, "allocation failed");
+    if (!rc) {
+        std::vector<bf16> hx(gg.NP * C, __float2bfloat16_rn(0.f));
+        for (int k = 0; k < n3; ++k)
+            for (int j = 0; j < n2; ++j)
+                for (int i = 0; i < n1; ++i)
+                    for (int c = 0; c < C; ++c)
+                        hx[pidx(gg, i, j, k) * C + c] = __float2bfloat16_rn(x[(((size_t)k * n2 + j) * n1 + i) * C + c]);
+        cudaMemcpy(din_, hx.data(), hx.size() * 2, cudaMemcpyHostToDevice);
+        cudaMemcpy(wf, w, O * 27 * C * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(bf, b, O * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(gf, g, gg.N * O * 4, cudaMemcpyHostToDevice);
+        cudaMemset(dwf, 0, O * 27 * C * 4);
+        cudaMemset(dbf, 0, O * 4);
+        k_weights_bf16<<<ccdiv(O * 27 * C, 256), 256>>>(O, C, wf, wb, wt);
+        k_pad_fill<bf16><<<ccdiv(gg.NP, 256), 256>>>(gg, din_, C);
+        launch_fwd(l, gg, din_, wb, bf, act ? dout_ : nullptr, yf, 0);
+        if (act) k_pad_fill<bf16><<<ccdiv(gg.NP, 256), 256>>>(gg, dout_, O);
+        launch_dpre(O, gg, gf, 0, act ? dout_ : nullptr, dpre, dbf, 0);
+        launch_wgrad(l, gg, dpre, din_, dwf, 0);
+        if (C == 32) {
+            if (O == 16) k_conv_dgrad<32, 16><<<ccdiv(gg.NP, 128), 128>>>(gg, dpre, wt, dinf);
+            else k_conv_dgrad<32, 32><<<ccdiv(gg.NP, 128), 128>>>(gg, dpre, wt, dinf);
+        } else {
+            k_conv_dgrad<16, 32><<<ccdiv(gg.NP, 128), 128>>>(gg, dpre, wt, dinf);
+        }
+        k_pad_fold<<<ccdiv(gg.NP, 256), 256>>>(gg, dinf, C);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = report_error(ICARUS_ECUDA, cudaGetErrorString(e));
+        if (!rc) {
+            cudaMemcpy(y, yf, gg.N * O * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(dw, dwf, O * 27 * C * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(db, dbf, O * 4, cudaMemcpyDeviceToHost);
+            std::vector<float> hd(gg.NP * C);
+            cudaMemcpy(hd.data(), dinf, hd.size() * 4, cudaMemcpyDeviceToHost);
+            for (int k = 0; k < n3; ++k)
+                for (int j = 0; j < n2; ++j)
+                    for (int i = 0; i < n1; ++i)
+                        for (int c = 0; c < C; ++c)
+                            dx[(((size_t)k * n2 + j) * n1 + i) * C + c] = hd[pidx(gg, i, j, k) * C + c];
+        }
+    }
+    for (void *p : mem) cudaFree(p);
+    return rc;
+}
+
+}  // extern "C"

@@ -523,6 +523,15 @@ int icarus_set_state(icarus_ctx *c, const double *U, double t)
     return first_dt(c);
 }
 
+int icarus_copy_state(icarus_ctx *c, double *U_dev)
+{
+    if (!c || !U_dev) return fail(ICARUS_EINVAL, "NULL argument");
+    c->ops.pack(c->P, c->U, U_dev, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return ICARUS_OK;
+}
+
 int icarus_set_stop_time(icarus_ctx *c, double t_stop)
 {
     if (!c) return fail(ICARUS_EINVAL, "NULL context");

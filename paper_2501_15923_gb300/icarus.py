@@ -58,6 +58,7 @@ SIGNATURES = {
     "icarus_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "icarus_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
     "icarus_set_stop_time": (C.c_int, [C.c_void_p, C.c_double]),
+    "icarus_copy_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "icarus_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "icarus_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "icarus_scales": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -74,6 +75,15 @@ SIGNATURES = {
     "icarus_batch_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "icarus_batch_stream": (C.c_void_p, [C.c_void_p]),
     "icarus_batch_destroy": (C.c_int, [C.c_void_p]),
+    "icarus_closure_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "icarus_closure_destroy": (C.c_int, [C.c_void_p]),
+    "icarus_closure_set_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "icarus_closure_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
+    "icarus_closure_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "icarus_closure_apply": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "icarus_closure_weights": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "icarus_restrict": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "icarus_conv3d_layer": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int] + [C.c_void_p] * 8),
     "icarus_cfl_dt_noalloc": (C.c_int, [C.POINTER(icarus_grid), C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "icarus_last_error": (C.c_char_p, []),
 }
@@ -197,6 +207,10 @@ def icarus_get_state(ctx, shape):
 def icarus_set_state(ctx, U, t=0.0):
     U = _f64(U)
     _check(load().icarus_set_state(ctx, _ptr(U), float(t)))
+
+
+def icarus_copy_state(ctx, U_dev_ptr):
+    _check(load().icarus_copy_state(ctx, C.c_void_p(U_dev_ptr)))
 
 
 def icarus_set_stop_time(ctx, t_stop):
@@ -418,6 +432,74 @@ class Batch:
         if getattr(self, "b", None):
             icarus_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- learned closure ----------------------------------------------------------------------------
+LAYER_SHAPES = ((16, 32), (32, 32), (32, 32), (32, 16))   # padded (C_in, C_out) per layer
+
+
+def icarus_conv3d_layer(x, w, b, g, act):
+    """One layer through the closure's tensor-core kernels. x [n3][n2][n1][C], w [O][27][C]."""
+    x, w, b, g = (np.ascontiguousarray(a, dtype=np.float32) for a in (x, w, b, g))
+    n3, n2, n1, Cc = x.shape
+    O = w.shape[0]
+    y = np.empty((n3, n2, n1, O), np.float32)
+    dx, dw, db = np.empty_like(x), np.empty_like(w), np.empty(O, np.float32)
+    _check(load().icarus_conv3d_layer(n1, n2, n3, Cc, O, int(act), *(_ptr(a) for a in (x, w, b, g, y, dx, dw, db))))
+    return y, dx, dw, db
+
+
+def icarus_restrict(fine_ctx, coarse_ctx):
+    _check(load().icarus_restrict(fine_ctx, coarse_ctx))
+
+
+class Closure:
+    """The learned correction network of a coarse grid (weights on the GPU)."""
+
+    def __init__(self, n1, n2, n3, seed=0, stream=0):
+        self.shape = (n1, n2, n3)
+        self.h = C.c_void_p()
+        _check(load().icarus_closure_create(n1, n2, n3, seed, C.c_void_p(stream), C.byref(self.h)))
+
+    def set_norm(self, in_mean, in_scale, out_scale):
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (in_mean, in_scale, out_scale)]
+        _check(load().icarus_closure_set_norm(self.h, *(_ptr(x) for x in a)))
+
+    def train_step(self, U_dev_ptr, dU_dev_ptr, lr):
+        loss = C.c_double()
+        _check(load().icarus_closure_train_step(self.h, C.c_void_p(U_dev_ptr), C.c_void_p(dU_dev_ptr), float(lr),
+                                                C.byref(loss)))
+        return loss.value
+
+    def predict(self, U_dev_ptr, dU_dev_ptr):
+        _check(load().icarus_closure_predict(self.h, C.c_void_p(U_dev_ptr), C.c_void_p(dU_dev_ptr)))
+
+    def apply(self, ctx):
+        _check(load().icarus_closure_apply(self.h, ctx))
+
+    def weights(self):
+        out = []
+        for l, (ci, co) in enumerate(LAYER_SHAPES):
+            w, b = np.empty((co, 27, ci), np.float32), np.empty(co, np.float32)
+            _check(load().icarus_closure_weights(self.h, l, _ptr(w), _ptr(b), 0))
+            out.append((w, b))
+        return out
+
+    def set_weights(self, wb):
+        for l, (w, b) in enumerate(wb):
+            w, b = np.ascontiguousarray(w, np.float32), np.ascontiguousarray(b, np.float32)
+            _check(load().icarus_closure_weights(self.h, l, _ptr(w), _ptr(b), 1))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().icarus_closure_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

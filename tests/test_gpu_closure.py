@@ -1,0 +1,51 @@
+"""The closure's tensor-core conv kernels against the FP64 oracle layer.
+
+Inputs, weights and output gradients are rounded to BF16 first and handed to both sides, so the
+GPU result differs from the oracle only by its FP32 accumulation (relative ~1e-6); the bar is
+2e-5 of each tensor's largest magnitude. This checks the forward pass and the three gradients the
+GPU training uses (data, weight, bias), including the ReLU mask and the padding's adjoint.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ic():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_15923_gb300 import build
+    build.build()
+    from paper_2501_15923_gb300 import icarus
+    return icarus
+
+
+def bf16(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16      # round to nearest even
+    return r.astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("C,Oc,act,shape", [(16, 32, 1, (11, 6, 5)), (32, 32, 1, (9, 7, 4)), (32, 16, 0, (13, 5, 6)),
+                                            (32, 32, 1, (40, 12, 10))])
+def test_layer_forward_and_gradients_match_oracle(ic, C, Oc, act, shape):
+    n1, n2, n3 = shape
+    rng = np.random.default_rng(C * 100 + Oc + n1)
+    x = bf16(rng.standard_normal((n3, n2, n1, C)))
+    w = bf16(rng.standard_normal((Oc, 27, C)) * 0.1)
+    b = bf16(rng.standard_normal(Oc) * 0.1)
+    g = bf16(rng.standard_normal((n3, n2, n1, Oc)))
+    y, dx, dw, db = ic.icarus_conv3d_layer(x, w, b, g, act)
+    yo = O.conv3d_forward(x.astype(np.float64), w.astype(np.float64), b.astype(np.float64), act)
+    # the oracle's ReLU mask is taken from the GPU's activation (values within FP32 rounding of 0
+    # could otherwise fall on different sides of it)
+    dxo, dwo, dbo = O.conv3d_backward(x.astype(np.float64), w.astype(np.float64), y.astype(np.float64),
+                                      g.astype(np.float64), act)
+    for got, ref in ((y, yo), (dx, dxo), (dw, dwo), (db, dbo)):
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= 2e-5 * scale, (np.abs(got - ref).max(), scale)
