@@ -232,6 +232,69 @@ def run_batched(ic, torch, args):
     return out
 
 
+def profile_machine(name):
+    """key=value pairs of the 'machine:' line of a committed profile summary."""
+    vals = {}
+    try:
+        for line in open(os.path.join(ROOT, "profiles", name)):
+            if line.startswith("machine:"):
+                for kv in line[len("machine:"):].split(";"):
+                    if "=" in kv:
+                        k, v = kv.split("=", 1)
+                        vals[k.strip()] = v.strip()
+    except OSError:
+        pass
+    return vals
+
+
+def run_learned(ic, torch, args, fine_dt: float, fine_cells: int):
+    """Coarse (2x) FP64 solve with the closure applied every 10 coarse steps. Throughput counted
+    in fine-equivalent cell-updates: fine cells x (simulated time / the fine solve's dt) / wall
+    time. The timing uses a freshly initialised network (its cost does not depend on the weights);
+    the accuracy of the trained network comes from its committed evaluation."""
+    from paper_2501_15923_gb300 import learned
+    w = workload(args.grid)
+    wc = learned.coarse_workload(w)
+    c = ic.from_workload(wc, precision=ic.ICARUS_FP64)
+    n1, n2, n3 = wc.grid.n1, wc.grid.n2, wc.grid.n3
+    net = ic.Closure(n1, n2, n3, seed=1)
+    net.set_norm(np.zeros((8, n1)), np.ones((8, n1)), np.full((8, n1), 1e-12))
+    c.step(10)
+    net.apply(c.ctx)
+    torch.cuda.synchronize()
+    t_a, _ = c.time()
+    rounds = max(2, min(args.steps // 5, 6))
+    t0 = time.perf_counter()
+    for _ in range(rounds):
+        c.step(10)
+        net.apply(c.ctx)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    t_b, _ = c.time()
+    fine_steps = (t_b - t_a) / fine_dt
+    acc = profile_machine("learned_closure_512x64x128.md")
+    out = {"value": fine_cells * fine_steps / secs / 1e6, "unit": "Mcell-updates/s (fine-equivalent)",
+           "coarse_grid": f"{n1}x{n2}x{n3}", "coarse_steps": 10 * rounds, "closure_every": 10,
+           "probe_error_trained": {k: float(v) for k, v in acc.items() if k.endswith("_err")},
+           "fallback_to_fine": acc.get("fallback") == "true"}
+    net.close()
+    c.close()
+    return out
+
+
+def aggregate(ms_local: float, cells_per_rank: int, steps: int, dist=None, device=None):
+    """Whole-job throughput of independent replicas: the slowest rank's time bounds the job;
+    value = cells of all ranks x steps / that time (Mcell-updates/s)."""
+    import torch
+    world = dist.get_world_size() if dist else 1
+    ms = ms_local
+    if dist:
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, cells_per_rank * steps * world / (ms * 1e-3) / 1e6
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -275,11 +338,8 @@ def main(argv=None):
     rc, floor_hits = s.status()
     if rc != 0:
         raise RuntimeError(f"solver status {rc} after the timed steps")
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ncell * args.steps * world / (ms * 1e-3) / 1e6
+    _, fine_dt = s.time()
+    ms, value = aggregate(ms, ncell, args.steps, dist, torch.device("cuda", local))
     clocks = clk.summary()
     s.sample(None, cap=1 << 20)          # drain the timed steps' records
 
@@ -340,6 +400,7 @@ def main(argv=None):
             sf.close()
         if args.batch_members > 0:
             forms["batched_ensemble"] = run_batched(ic, torch, args)
+        forms["learned_closure"] = run_learned(ic, torch, args, fine_dt, ncell)
 
     line = {"metric": METRIC, "value": value, "unit": "Mcell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -620,8 +620,10 @@ int orc_set_boundary(orc_t *o, int n_maps, const double *t_si, const double *map
     return 0;
 }
 
-/* initial state (Sect. 2.1): the boundary map at the current time, extended radially:
- * v_r const, n ~ r^-2, p ~ r^-2gamma, B_r ~ r^-2, B_phi = -B_r Omega r sin(theta) / v_r */
+/* initial state (Sect. 2.1): the boundary map at the current time, extended radially as a Parker
+ * wind: v_r const, n ~ r^-2, p ~ r^-2gamma, B_r ~ r^-2, B_phi = -B_r Omega r sin(theta) / v_r; the
+ * flow is radial in the inertial frame, so in the co-rotating frame v_phi = -Omega r sin(theta)
+ * (velocity parallel to the spiral field, no electric field in the rotating frame) */
 int orc_init_state(orc_t *o)
 {
     if (o->geom != GEOM_SPH || o->n_maps < 1) return -1;
@@ -635,7 +637,8 @@ int orc_init_state(orc_t *o)
                 double x = rin / r;
                 double w[NV], u[NV];
                 w[0] = b[1] * x * x;
-                w[1] = b[0]; w[2] = 0.0; w[3] = 0.0;
+                w[1] = b[0]; w[2] = 0.0;
+                w[3] = -o->omega * r * sin(th);   /* inertially radial (Parker) flow seen co-rotating */
                 w[4] = b[2] * pow(x, 2.0 * o->gamma);
                 w[5] = b[3] * x * x; w[6] = 0.0;
                 w[7] = -w[5] * o->omega * r * sin(th) / w[1];

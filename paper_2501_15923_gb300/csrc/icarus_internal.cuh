@@ -133,14 +133,30 @@ template <typename R> __device__ __forceinline__ R fast_speed(const R *w, R irho
     return sqrt(R(0.5) * (s + sqrt(disc)));
 }
 
+// sign and zero tests on the bit patterns (integer pipe; the FP64 pipe is the scarce one)
+__device__ __forceinline__ int hi_bits(double x) { return __double2hiint(x); }
+__device__ __forceinline__ int hi_bits(float x) { return __float_as_int(x); }
+__device__ __forceinline__ bool is_zero(double x) { return ((__double2hiint(x) & 0x7fffffff) | __double2loint(x)) == 0; }
+__device__ __forceinline__ bool is_zero(float x) { return (__float_as_int(x) & 0x7fffffff) == 0; }
+__device__ __forceinline__ unsigned long long abs_bits(double x) { return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull; }
+__device__ __forceinline__ unsigned int abs_bits(float x) { return (unsigned int)__float_as_int(x) & 0x7fffffffu; }
+// x <= 0 (for non-NaN x)
+template <typename R> __device__ __forceinline__ bool not_positive(R x) { return hi_bits(x) < 0 || is_zero(x); }
+
+// limited slope from the backward and forward differences a, b: zero unless a and b have the
+// same sign; van Leer 2ab/(a+b), minmod, or monotonised central
 template <typename R> __device__ __forceinline__ R limiter(int lim, R a, R b)
 {
-    bool same = (a > R(0) && b > R(0)) || (a < R(0) && b < R(0));
-    if (!same) return R(0);
-    if (lim == 1) return R(2) * a * b / (a + b);                 // van Leer
-    if (lim == 0) return rabs(a) < rabs(b) ? a : b;             // minmod
+    const bool same = (hi_bits(a) ^ hi_bits(b)) >= 0;          // equal sign bits
+    if (lim == 1) {                                               // van Leer
+        const R s = a + b;
+        const R r = R(2) * a * b / s;
+        return (same && !is_zero(s)) ? r : R(0);
+    }
+    if (!same || is_zero(a) || is_zero(b)) return R(0);
+    if (lim == 0) return abs_bits(a) < abs_bits(b) ? a : b;      // minmod
     R m = rmin(rmin(R(2) * rabs(a), R(2) * rabs(b)), R(0.5) * rabs(a + b));   // MC
-    return a > R(0) ? m : -m;
+    return hi_bits(a) >= 0 ? m : -m;
 }
 
 // Riemann flux across a face normal to d from left / right primitive states.

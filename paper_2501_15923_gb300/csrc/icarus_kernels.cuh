@@ -227,14 +227,53 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
     TW wc[NV], wm[NV];
     if (valid) {
         const long long c = cidx(P, i, j, k);
+        TW da[NV], db[NV], dl[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             TW a = W[v * nt + c - st], b = W[v * nt + c], e = W[v * nt + c + st];
-            TW dl = limiter<TW>(P.limiter, b - a, e - b);
             wc[v] = b;
-            wm[v] = b - TW(0.5) * dl;
-            sW[v * sz + sl] = b;
-            sP[v * sz + sl] = b + TW(0.5) * dl;
+            da[v] = b - a;
+            db[v] = e - b;
+        }
+        if (P.limiter == 1 && sizeof(TW) == 8) {
+            // FP64 van Leer 2ab/(a+b) for the eight fields with ONE division: batch inversion of
+            // the eight sums (prefix products, one reciprocal, then peel off; zero sums replaced
+            // by 1); the product stays far inside the double range unless all eight sums are
+            // extreme, in which case the eight divisions are done one by one
+            TW s[NV], pre[NV];
+            bool ok[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                s[v] = da[v] + db[v];
+                ok[v] = ((hi_bits(da[v]) ^ hi_bits(db[v])) >= 0) && !is_zero(s[v]);
+                if (!ok[v]) s[v] = TW(1);
+            }
+            pre[0] = s[0];
+#pragma unroll
+            for (int v = 1; v < NV; ++v) pre[v] = pre[v - 1] * s[v];
+            const int ex = (hi_bits(pre[NV - 1]) >> 20) & 0x7ff;     // biased exponent of the product
+            if (ex > 60 && ex < 1990) {
+                TW inv = TW(1) / pre[NV - 1];
+#pragma unroll
+                for (int v = NV - 1; v > 0; --v) {
+                    const TW iv = inv * pre[v - 1];     // 1 / s[v]
+                    inv = inv * s[v];                   // 1 / (s[0] ... s[v-1])
+                    dl[v] = ok[v] ? TW(2) * da[v] * db[v] * iv : TW(0);
+                }
+                dl[0] = ok[0] ? TW(2) * da[0] * db[0] * inv : TW(0);
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) dl[v] = ok[v] ? TW(2) * da[v] * db[v] / s[v] : TW(0);
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) dl[v] = limiter<TW>(P.limiter, da[v], db[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            wm[v] = wc[v] - TW(0.5) * dl[v];
+            sW[v * sz + sl] = wc[v];
+            sP[v * sz + sl] = wc[v] + TW(0.5) * dl[v];
         }
     }
     __syncthreads();
@@ -243,7 +282,7 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
         const int pl = D == 0 ? sl - 1 : sl - BX;      // the neighbour one cell below along D
 #pragma unroll
         for (int v = 0; v < NV; ++v) { wl[v] = sP[v * sz + pl]; wr[v] = wm[v]; }
-        if (wl[0] <= TW(0) || wr[0] <= TW(0) || wl[4] <= TW(0) || wr[4] <= TW(0)) {
+        if (not_positive(wl[0]) || not_positive(wr[0]) || not_positive(wl[4]) || not_positive(wr[4])) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) { wl[v] = sW[v * sz + pl]; wr[v] = wc[v]; }
         }
@@ -395,121 +434,144 @@ __global__ void __launch_bounds__(256) k_cfl(Params P, const TW *__restrict__ W)
 //   L = -(1/V) sum_d (A+ F+ - A- F-) + S (geometric, rotating frame, gravity) ; Linde term
 //   stage 1: U1 = U + dt L ; stage 2: U <- U/2 + (U1 + dt L)/2 ; floors ; primitives ; CFL (2)
 // returns the cell's CFL signal speed after a second stage (0 otherwise)
+// the update of one interior cell (i, j, k) from its primitives w, the fluxes through its six
+// faces (lower / upper along r, theta, phi) and div B at its six neighbours; returns the cell's
+// CFL signal speed after a second stage (0 otherwise)
+// area / volume factors of the flux divergence of cell (i, j, k)
+template <typename TW> struct DivFactors {
+    TW am, ap, iv, bm, bp, jv, kv;
+    __device__ __forceinline__ DivFactors(const Metrics &m, int ip, int jp)
+        : am(TW(m.a1[ip])), ap(TW(m.a1[ip + 1])), iv(TW(m.iv1[ip])), bm(TW(m.a2[jp])), bp(TW(m.a2[jp + 1])),
+          jv(TW(m.q1[ip] * m.iv2[jp])), kv(TW(m.q1[ip] * m.q2[jp] * m.iv3)) {}
+    // -(1/V) sum_d (A+ F+ - A- F-) of one field
+    __device__ __forceinline__ TW div(TW fr0, TW fr1, TW ft0, TW ft1, TW fp0, TW fp1) const
+    {
+        TW l = -(ap * fr1 - am * fr0) * iv;
+        l -= (bp * ft1 - bm * ft0) * jv;
+        l -= (fp1 - fp0) * kv;
+        return l;
+    }
+};
+
+// the update of one interior cell (i, j, k) from its primitives w, the flux divergence L (in:
+// per field, out: the full residual) and div B at its six neighbours; returns the cell's CFL
+// signal speed after a second stage (0 otherwise)
+template <int STAGE, typename TS, typename TW>
+__device__ __forceinline__ double update_core(const Params &P, int i, int j, int k, const TW *w, TW *L,
+                                              const TW *dbn, const TS *__restrict__ Us, TS *Uo, TW *__restrict__ Wo)
+{
+    const int ip = i + NG, jp = j + NG;
+    const Metrics &m = P.m;
+    const long long nt = P.nt, c = cidx(P, i, j, k);
+    const double dt = P.sc->dt;
+    if (P.geom == 0) {
+        const TW rho = w[0], vr = w[1], vt = w[2], vp = w[3];
+        const TW br = w[5], bt = w[6], bp = w[7];
+        const TW ir = TW(m.ih2[ip]), cot = TW(m.ct[jp]);
+        const TW pt = w[4] + TW(0.5) * (br * br + bt * bt + bp * bp);
+        // geometric terms of the spherical divergence; p_tot through face-area differences
+        L[M1] += pt * TW(m.gp1[ip]) + (rho * (vt * vt + vp * vp) - (bt * bt + bp * bp)) * ir;
+        L[M2] += pt * TW(m.q1[ip] * m.gq2[jp]) + (-(rho * vr * vt - br * bt) + cot * (rho * vp * vp - bp * bp)) * ir;
+        L[M3] -= ((rho * vp * vr - bp * br) + cot * (rho * vp * vt - bp * bt)) * ir;
+        L[B2] += (vr * bt - vt * br) * ir;
+        L[B3] += ((vr * bp - vp * br) + cot * (vt * bp - vp * bt)) * ir;
+        if (P.omega != 0.0) {
+            // co-rotating frame, Omega along the polar axis: centrifugal rho Omega^2 r sin(th)
+            // (sin th, cos th, 0), Coriolis 2 rho Omega (v_phi sin th, v_phi cos th,
+            // -(v_r sin th + v_th cos th)), work of the centrifugal force in e
+            const TW Om = TW(P.omega), sn = TW(m.sn[jp]), cs = TW(m.cs[jp]), rc = TW(m.x1c[ip]);
+            const TW cen = rho * Om * Om * rc * sn;
+            const TW vpar = vr * sn + vt * cs;
+            L[M1] += cen * sn + TW(2) * rho * Om * vp * sn;
+            L[M2] += cen * cs + TW(2) * rho * Om * vp * cs;
+            L[M3] -= TW(2) * rho * Om * vpar;
+            L[EN] += cen * vpar;
+        }
+        if (P.gravity) {
+            const TW g = TW(m.gm_r2[ip]);
+            L[M1] -= rho * g;
+            L[EN] -= rho * vr * g;
+        }
+    }
+    // Linde div-B diffusion: increment C_d / (sum_d 1/dx_d^2) grad(div B) per stage;
+    // dbn = div B at (i-1, i+1, j-1, j+1, k-1, k+1)
+    TW lb[3] = {TW(0), TW(0), TW(0)};
+    if (P.divb == 1 && dt > 0.0) {
+        const TW iw1 = TW(m.iw1[ip]), iw2 = TW(m.ih2[ip] * m.id2), iw3 = TW(m.ih2[ip] * m.is3[jp] * m.id3);
+        const TW coef = TW(P.divb_coef) / (iw1 * iw1 + iw2 * iw2 + iw3 * iw3);
+        lb[0] = coef * (dbn[1] - dbn[0]) * TW(m.ig1[ip]);
+        lb[1] = coef * (dbn[3] - dbn[2]) * TW(m.ih2[ip] * m.ig2[jp]);
+        lb[2] = coef * (dbn[5] - dbn[4]) * TW(m.ih2[ip] * m.is3[jp] * m.ig3[k + NG]);
+    }
+    TS uo[NV];
+    const TS dts = (TS)dt;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        TW inc = v >= B1 ? lb[v - B1] : (v == EN ? w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2] : TW(0));
+        if (STAGE == 1) {
+            uo[v] = Us[v * nt + c] + dts * (TS)L[v] + (TS)inc;
+        } else {
+            TS un = Uo[v * nt + c];     // U^n (updated in place)
+            uo[v] = TS(0.5) * un + TS(0.5) * (Us[v * nt + c] + dts * (TS)L[v] + (TS)inc);
+        }
+    }
+    // non-finite check and floors
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) bad |= (hi_bits(uo[v]) & (sizeof(TS) == 8 ? 0x7ff00000 : 0x7f800000)) ==
+                                        (sizeof(TS) == 8 ? 0x7ff00000 : 0x7f800000);   // inf or NaN
+    if (bad) atomicOr(&P.sc->status, 1);
+    TW wo[NV];
+    int hits = 0;
+    if (uo[RHO] < (TS)P.rho_floor) { uo[RHO] = (TS)P.rho_floor; ++hits; }
+    recover<TS, TW>(uo, wo, P.gamma, i);
+    if (wo[4] < TW(P.p_floor)) {
+        // reset e so that p = p_floor, keeping rho, m, B
+        TS ke = TS(0.5) * (uo[M1] * uo[M1] + uo[M2] * uo[M2] + uo[M3] * uo[M3]) / uo[RHO];
+        TS me = TS(0.5) * (uo[B1] * uo[B1] + uo[B2] * uo[B2] + uo[B3] * uo[B3]);
+        uo[EN] = (TS)P.p_floor / (TS)(P.gamma - 1.0) + ke + me;
+        wo[4] = TW(P.p_floor);
+        ++hits;
+    }
+    if (hits) atomicAdd(&P.sc->floor_hits, (unsigned long long)hits);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        Uo[v * nt + c] = uo[v];
+        Wo[v * nt + c] = wo[v];
+    }
+    return STAGE == 2 ? cell_speed<TW>(P, wo, ip, jp) : 0.0;
+}
+
+// the update of cell number tid (r fastest) with fluxes and div B read from their global arrays
 template <int STAGE, typename TS, typename TW>
 __device__ __forceinline__ double update_cell(const Params &P, const TS *__restrict__ Us, const TW *__restrict__ Ws,
                                               TS *Uo, TW *__restrict__ Wo, const TW *__restrict__ F1,
                                               const TW *__restrict__ F2, const TW *__restrict__ F3,
                                               const TW *__restrict__ divB, long long tid)
 {
-    double smax = 0.0;
-    {
-        const int i = (int)(tid % P.n1);
-        const long long r_ = tid / P.n1;
-        const int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
-        const int ip = i + NG, jp = j + NG;
-        const Metrics &m = P.m;
-        const long long nt = P.nt, c = cidx(P, i, j, k);
-        const double dt = P.sc->dt;
-        TW w[NV], L[NV];
+    const int i = (int)(tid % P.n1);
+    const long long r_ = tid / P.n1;
+    const int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
+    const long long nt = P.nt, c = cidx(P, i, j, k);
+    TW w[NV], L[NV], dbn[6];
+    const long long s1 = (long long)P.n3 * P.n2 * (P.n1 + 1), f1 = ((long long)k * P.n2 + j) * (P.n1 + 1) + i;
+    const long long s2 = (long long)P.n3 * (P.n2 + 1) * P.n1, f2 = ((long long)k * (P.n2 + 1) + j) * P.n1 + i;
+    const long long s3 = (long long)(P.n3 + 1) * P.n2 * P.n1, f3 = ((long long)k * P.n2 + j) * P.n1 + i;
+    const long long o3 = (long long)P.n2 * P.n1;
+    const DivFactors<TW> dv(P.m, i + NG, j + NG);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) w[v] = Ws[v * nt + c];
-        // flux divergence
-        {
-            const long long s1 = (long long)P.n3 * P.n2 * (P.n1 + 1);
-            const long long f1 = ((long long)k * P.n2 + j) * (P.n1 + 1) + i;
-            const TW am = TW(m.a1[ip]), ap = TW(m.a1[ip + 1]), iv = TW(m.iv1[ip]);
-            const long long s2 = (long long)P.n3 * (P.n2 + 1) * P.n1;
-            const long long f2 = ((long long)k * (P.n2 + 1) + j) * P.n1 + i;
-            const TW bm = TW(m.a2[jp]), bp = TW(m.a2[jp + 1]), jv = TW(m.q1[ip] * m.iv2[jp]);
-            const long long s3 = (long long)(P.n3 + 1) * P.n2 * P.n1;
-            const long long f3 = ((long long)k * P.n2 + j) * P.n1 + i;
-            const long long o3 = (long long)P.n2 * P.n1;
-            const TW kv = TW(m.q1[ip] * m.q2[jp] * m.iv3);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                TW l = -(ap * F1[v * s1 + f1 + 1] - am * F1[v * s1 + f1]) * iv;
-                l -= (bp * F2[v * s2 + f2 + P.n1] - bm * F2[v * s2 + f2]) * jv;
-                l -= (F3[v * s3 + f3 + o3] - F3[v * s3 + f3]) * kv;
-                L[v] = l;
-            }
-        }
-        if (P.geom == 0) {
-            const TW rho = w[0], vr = w[1], vt = w[2], vp = w[3];
-            const TW br = w[5], bt = w[6], bp = w[7];
-            const TW ir = TW(m.ih2[ip]), cot = TW(m.ct[jp]);
-            const TW pt = w[4] + TW(0.5) * (br * br + bt * bt + bp * bp);
-            // geometric terms of the spherical divergence; p_tot through face-area differences
-            L[M1] += pt * TW(m.gp1[ip]) + (rho * (vt * vt + vp * vp) - (bt * bt + bp * bp)) * ir;
-            L[M2] += pt * TW(m.q1[ip] * m.gq2[jp]) + (-(rho * vr * vt - br * bt) + cot * (rho * vp * vp - bp * bp)) * ir;
-            L[M3] -= ((rho * vp * vr - bp * br) + cot * (rho * vp * vt - bp * bt)) * ir;
-            L[B2] += (vr * bt - vt * br) * ir;
-            L[B3] += ((vr * bp - vp * br) + cot * (vt * bp - vp * bt)) * ir;
-            if (P.omega != 0.0) {
-                // co-rotating frame, Omega along the polar axis: centrifugal rho Omega^2 r sin(th)
-                // (sin th, cos th, 0), Coriolis 2 rho Omega (v_phi sin th, v_phi cos th,
-                // -(v_r sin th + v_th cos th)), work of the centrifugal force in e
-                const TW Om = TW(P.omega), sn = TW(m.sn[jp]), cs = TW(m.cs[jp]), rc = TW(m.x1c[ip]);
-                const TW cen = rho * Om * Om * rc * sn;
-                const TW vpar = vr * sn + vt * cs;
-                L[M1] += cen * sn + TW(2) * rho * Om * vp * sn;
-                L[M2] += cen * cs + TW(2) * rho * Om * vp * cs;
-                L[M3] -= TW(2) * rho * Om * vpar;
-                L[EN] += cen * vpar;
-            }
-            if (P.gravity) {
-                const TW g = TW(m.gm_r2[ip]);
-                L[M1] -= rho * g;
-                L[EN] -= rho * vr * g;
-            }
-        }
-        // Linde div-B diffusion: increment C_d / (sum_d 1/dx_d^2) grad(div B) per stage
-        TW lb[3] = {TW(0), TW(0), TW(0)};
-        if (P.divb == 1 && dt > 0.0) {
-            const long long s2 = P.p1, s3 = (long long)P.p1 * P.p2;
-            const TW iw1 = TW(m.iw1[ip]), iw2 = TW(m.ih2[ip] * m.id2), iw3 = TW(m.ih2[ip] * m.is3[jp] * m.id3);
-            const TW coef = TW(P.divb_coef) / (iw1 * iw1 + iw2 * iw2 + iw3 * iw3);
-            lb[0] = coef * (divB[c + 1] - divB[c - 1]) * TW(m.ig1[ip]);
-            lb[1] = coef * (divB[c + s2] - divB[c - s2]) * TW(m.ih2[ip] * m.ig2[jp]);
-            lb[2] = coef * (divB[c + s3] - divB[c - s3]) * TW(m.ih2[ip] * m.is3[jp] * m.ig3[k + NG]);
-        }
-        TS uo[NV];
-        const TS dts = (TS)dt;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            TW inc = v >= B1 ? lb[v - B1] : (v == EN ? w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2] : TW(0));
-            if (STAGE == 1) {
-                uo[v] = Us[v * nt + c] + dts * (TS)L[v] + (TS)inc;
-            } else {
-                TS un = Uo[v * nt + c];     // U^n (updated in place)
-                uo[v] = TS(0.5) * un + TS(0.5) * (Us[v * nt + c] + dts * (TS)L[v] + (TS)inc);
-            }
-        }
-        // floors
-        bool bad = false;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) bad |= !isfinite((double)uo[v]);
-        if (bad) atomicOr(&P.sc->status, 1);
-        TW wo[NV];
-        int hits = 0;
-        if (uo[RHO] < (TS)P.rho_floor) { uo[RHO] = (TS)P.rho_floor; ++hits; }
-        recover<TS, TW>(uo, wo, P.gamma, i);
-        if (wo[4] < TW(P.p_floor)) {
-            // reset e so that p = p_floor, keeping rho, m, B
-            TS ke = TS(0.5) * (uo[M1] * uo[M1] + uo[M2] * uo[M2] + uo[M3] * uo[M3]) / uo[RHO];
-            TS me = TS(0.5) * (uo[B1] * uo[B1] + uo[B2] * uo[B2] + uo[B3] * uo[B3]);
-            uo[EN] = (TS)P.p_floor / (TS)(P.gamma - 1.0) + ke + me;
-            wo[4] = TW(P.p_floor);
-            ++hits;
-        }
-        if (hits) atomicAdd(&P.sc->floor_hits, (unsigned long long)hits);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            Uo[v * nt + c] = uo[v];
-            Wo[v * nt + c] = wo[v];
-        }
-        if (STAGE == 2) smax = cell_speed<TW>(P, wo, ip, jp);
+    for (int v = 0; v < NV; ++v) {
+        w[v] = Ws[v * nt + c];
+        L[v] = dv.div(F1[v * s1 + f1], F1[v * s1 + f1 + 1], F2[v * s2 + f2], F2[v * s2 + f2 + P.n1],
+                      F3[v * s3 + f3], F3[v * s3 + f3 + o3]);
     }
-    return smax;
+    if (P.divb == 1) {
+        const long long q2 = P.p1, q3 = (long long)P.p1 * P.p2;
+        dbn[0] = divB[c - 1]; dbn[1] = divB[c + 1];
+        dbn[2] = divB[c - q2]; dbn[3] = divB[c + q2];
+        dbn[4] = divB[c - q3]; dbn[5] = divB[c + q3];
+    }
+    return update_core<STAGE, TS, TW>(P, i, j, k, w, L, dbn, Us, Uo, Wo);
 }
 
 template <int STAGE, typename TS, typename TW>
@@ -546,8 +608,10 @@ __global__ void k_prims(Params P, const TS *__restrict__ U, TW *__restrict__ W)
     for (int v = 0; v < NV; ++v) W[v * P.nt + c] = w[v];
 }
 
-// initial state from the maps at the current time by radial expansion:
-// v_r const, rho ~ r^-2, p ~ r^-2 gamma, B_r ~ r^-2, B_phi = -B_r Omega r sin(theta) / v_r
+// initial state from the maps at the current time by radial expansion as a Parker wind:
+// v_r const, rho ~ r^-2, p ~ r^-2 gamma, B_r ~ r^-2, B_phi = -B_r Omega r sin(theta) / v_r, and the
+// flow radial in the inertial frame: v_phi = -Omega r sin(theta) in the co-rotating frame (the
+// velocity is then parallel to the spiral field)
 template <typename TS, typename TW>
 __global__ void k_init_state(Params P, TS *__restrict__ U, TW *__restrict__ W, double r_in)
 {
@@ -576,7 +640,8 @@ __global__ void k_init_state(Params P, TS *__restrict__ U, TW *__restrict__ W, d
     const double r = P.m.x1c[i + NG], x = r_in / r, x2 = x * x;
     double wd[NV], ud[NV];
     wd[0] = b[1] * x2;
-    wd[1] = b[0]; wd[2] = 0.0; wd[3] = 0.0;
+    wd[1] = b[0]; wd[2] = 0.0;
+    wd[3] = -P.omega * r * P.m.sn[j + NG];   // inertially radial flow, seen from the rotating frame
     wd[4] = b[2] * pow(x, 2.0 * P.gamma);
     wd[5] = b[3] * x2; wd[6] = 0.0;
     wd[7] = -wd[5] * P.omega * r * P.m.sn[j + NG] / wd[1];

@@ -132,7 +132,7 @@ class Workload:
 
 # --- boundary maps ---------------------------------------------------------------------------
 def current_sheet_map(theta_c: np.ndarray, phi_c: np.ndarray, tilt: float, phase: float,
-                      omega: float, r_in_au: float) -> np.ndarray:
+                      omega: float, r_in_au: float, n_scale: float = 1.0) -> np.ndarray:
     """One boundary map [5][n_theta][n_phi] of a tilted current sheet (SI).
 
     Sheet normal n = (sin a sin p0, -sin a cos p0, cos a) for tilt a and phase p0. The angular
@@ -140,6 +140,8 @@ def current_sheet_map(theta_c: np.ndarray, phi_c: np.ndarray, tilt: float, phase
     the clamped smoothstep S(x) = 3x^2 - 2x^3; n = 300 (350 km/s / v_r)^2 cm^-3; T = 1.5 MK and
     p = 2 n k_B T (protons + electrons); B_r = +-300 nT by the side of the sheet;
     B_phi = -B_r omega r_in sin(theta) / v_r (Parker spiral at the inner radius).
+    With n_scale = 1 (the stated recipe) the Alfven Mach number of the inflow is 0.926 everywhere
+    (n ~ v^-2 at fixed |B| keeps v / v_A constant); n_scale = 2 makes it 1.31.
     """
     th, ph = np.meshgrid(theta_c, phi_c, indexing="ij")
     rx, ry, rz = np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)
@@ -149,7 +151,7 @@ def current_sheet_map(theta_c: np.ndarray, phi_c: np.ndarray, tilt: float, phase
     x = np.clip((d - math.radians(5.0)) / math.radians(15.0), 0.0, 1.0)
     s = 3.0 * x * x - 2.0 * x * x * x
     vr = (350.0 + 350.0 * s) * 1e3
-    n = 300e6 * (350e3 / vr) ** 2
+    n = n_scale * 300e6 * (350e3 / vr) ** 2
     p = 2.0 * n * K_B * 1.5e6
     br = np.where(dot >= 0.0, 300e-9, -300e-9)
     bphi = -br * omega * (r_in_au * AU) * np.sin(th) / vr
@@ -220,7 +222,7 @@ def config0(seed: int = 0, n_steps: int = 200, grid: Grid | None = None) -> Work
                     np.zeros((0, 8)), traj, t_end=0.0, n_steps=n_steps, meta={"phase": phase})
 
 
-def config1(seed: int = 1, grid: Grid | None = None, days: float = 10.0) -> Workload:
+def config1(seed: int = 1, grid: Grid | None = None, days: float = 10.0, n_scale: float = 1.0) -> Workload:
     """512x64x128 stretched grid, 10 daily maps with a random-walk tilt, one cone CME
     (1200 km/s, half-width 30 deg, 1000 cm^-3, 0.8 MK, 8 h, onset U(1, 3) d, aimed at probe 1),
     four Keplerian-like probes between 0.7 and 1.5 AU, 10 simulated days."""
@@ -229,7 +231,7 @@ def config1(seed: int = 1, grid: Grid | None = None, days: float = 10.0) -> Work
     phase = 2.0 * math.pi * rng.uniform()
     tilts = tilt_walk(rng, 10, math.radians(15.0))
     th, ph = g.theta_centres(), g.phi_centres()
-    maps = np.stack([current_sheet_map(th, ph, a, phase, OMEGA_SUN, g.x1min) for a in tilts])
+    maps = np.stack([current_sheet_map(th, ph, a, phase, OMEGA_SUN, g.x1min, n_scale) for a in tilts])
     t_maps = np.arange(10) * DAY
     t_knots = np.arange(0.0, (days + 1.0) * DAY + 1.0, 3600.0)
     probes = []

@@ -513,7 +513,12 @@ def test_IC_radial_expansion():
     assert np.allclose(W[5], br, rtol=1e-12)
     bphi = -br * sc["omega"] * rc[None, None, :] * np.sin(tc)[None, :, None] / vr
     assert np.allclose(W[7], bphi, rtol=1e-12)
-    assert np.all(W[2] == 0) and np.all(W[3] == 0) and np.all(W[6] == 0)
+    # inertially radial flow: v_phi = -Omega r sin(theta) in the co-rotating frame, so the velocity
+    # is parallel to the spiral field (v_phi / v_r = B_phi / B_r) and the rotating-frame E vanishes
+    vphi = -sc["omega"] * rc[None, None, :] * np.sin(tc)[None, :, None] * np.ones_like(W[3])
+    assert np.allclose(W[3], vphi, rtol=1e-12)
+    assert np.allclose(W[3] * W[5], W[1] * W[7], rtol=1e-10, atol=1e-12)
+    assert np.all(W[2] == 0) and np.all(W[6] == 0)
 
 
 # ---------------------------------------------------------------------------------------------
