@@ -122,11 +122,15 @@ class Clocks:
 
 
 def kernel_source_hash():
+    """Hash of the sources the FP64 flux kernels are compiled from (device code and its
+    instantiation); the Ops table assignments at the end of the kernel header are excluded."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2501_15923_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")) and not f.startswith("icarus_capi"):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in ("icarus_internal.cuh", "icarus_kernels.cuh", "kern_fp64.cu"):
+        txt = open(os.path.join(csrc, f), "rb").read()
+        if f == "icarus_kernels.cuh":
+            txt = txt.split(b"static Ops make()")[0]
+        h.update(txt)
     return h.hexdigest()[:16]
 
 
@@ -345,7 +349,7 @@ def main(argv=None):
 
     # per-kernel durations (events around each launch, eager) -> roofline of the dominant kernel
     kms = s.time_kernels(3)
-    per_step = {k: v * (2 if k not in ("probe", "update_1", "update_2") else 1) for k, v in kms.items()}
+    per_step = {k: v * (2 if k not in ("probe", "update_1", "update_2", "fused_1", "fused_2") else 1) for k, v in kms.items()}
     dom = max(per_step, key=per_step.get)
     flops_face, dram_face = profile_numbers()
     n1, n2, n3 = w.grid.n1, w.grid.n2, w.grid.n3
@@ -397,6 +401,17 @@ def main(argv=None):
             fms = a.elapsed_time(b)
             forms[name] = {"value": ncell * args.steps / (fms * 1e-3) / 1e6, "unit": "Mcell-updates/s",
                            "ms_per_step": fms / args.steps}
+            # roofline of the fused stage kernel (HBM): algorithmic bytes per cell of one stage =
+            # primitives in + state in + state and primitives out (+ U^n in for the second stage)
+            fk = sf.time_kernels(2)
+            if fk.get("fused_1", 0.0) > 0.0:
+                su, sw = (4, 4) if pr == ic.ICARUS_FP32 else (8, 4)
+                b1, b2 = 8 * (sw + su + su + sw), 8 * (sw + su + su + su + sw)
+                ach = (b1 + b2) * ncell / ((fk["fused_1"] + fk["fused_2"]) * 1e-3) / 1e9
+                forms[name]["roofline"] = {"kernel": "k_fused_stage", "bound": "hbm", "achieved": ach,
+                                           "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                                           "bytes_per_cell_stage": [b1, b2], "kernel_ms": fk,
+                                           "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
             sf.close()
         if args.batch_members > 0:
             forms["batched_ensemble"] = run_batched(ic, torch, args)

@@ -60,6 +60,7 @@ typedef struct {
     double gamma, omega_si, omega, gm;
     double cfl, divb_coef, rho_floor, p_floor;
     int limiter, flux, gravity, divb;
+    int init_vphi;   /* initial v_phi: 0 at rest in the co-rotating frame, 1 inertially radial */
     double t0, p0, b0;       /* code-unit scales */
     double *U, *U0, *U1, *L, *W, *F[3], *divB, *Ufix;
     double t;
@@ -325,6 +326,15 @@ static void fill_side(orc_t *o, double *U, int d, int side, double tau)
                     continue;
                 }
                 copy_cell(o, U, cell_id(o, d, gi, a, b), cell_id(o, d, src, a, b), flip);
+                if (d == 0 && side == 1 && bc == BC_CONT && o->geom == GEOM_SPH) {
+                    /* outer radius: B_r continues as r^-2 (the radial flux r^2 B_r is what is
+                     * copied), so the ghost layer adds no divergence; e follows the change of B^2 */
+                    long id = cell_id(o, d, gi, a, b);
+                    double f = (ctr(o, 0, src) / ctr(o, 0, gi)) * (ctr(o, 0, src) / ctr(o, 0, gi));
+                    double bs = U[B1 * o->nt + id], bg = bs * f;
+                    U[EN * o->nt + id] += 0.5 * (bg * bg - bs * bs);
+                    U[B1 * o->nt + id] = bg;
+                }
             }
 }
 
@@ -567,7 +577,7 @@ orc_t *orc_create(const int *ig, const double *dg, double gamma, double omega_si
     o->omega_si = omega_si;
     o->omega = omega_si * o->t0;
     o->cfl = od[0]; o->divb_coef = od[1]; o->rho_floor = od[2]; o->p_floor = od[3];
-    o->limiter = oi[0]; o->flux = oi[1]; o->gravity = oi[2]; o->divb = oi[3];
+    o->limiter = oi[0]; o->flux = oi[1]; o->gravity = oi[2]; o->divb = oi[3]; o->init_vphi = oi[4];
     o->gm = O_GM / (O_AU * O_V0 * O_V0);
     if (o->geom == GEOM_CART) { o->omega = 0.0; o->gravity = 0; }
     size_t sz = sizeof(double) * NV * o->nt;
@@ -620,10 +630,11 @@ int orc_set_boundary(orc_t *o, int n_maps, const double *t_si, const double *map
     return 0;
 }
 
-/* initial state (Sect. 2.1): the boundary map at the current time, extended radially as a Parker
- * wind: v_r const, n ~ r^-2, p ~ r^-2gamma, B_r ~ r^-2, B_phi = -B_r Omega r sin(theta) / v_r; the
- * flow is radial in the inertial frame, so in the co-rotating frame v_phi = -Omega r sin(theta)
- * (velocity parallel to the spiral field, no electric field in the rotating frame) */
+/* initial state (Sect. 2.1): the boundary map at the current time, extended radially by the
+ * expansion laws v_r const, n ~ r^-2, p ~ r^-2gamma, B_r ~ r^-2, with the spiral B_phi = -B_r Omega
+ * r sin(theta) / v_r and v_theta = B_theta = 0. v_phi (the paper names no value): 0 in the
+ * co-rotating frame (init_vphi = 0), or the inertially radial flow seen from the rotating frame,
+ * v_phi = -Omega r sin(theta), parallel to the spiral field (init_vphi = 1) */
 int orc_init_state(orc_t *o)
 {
     if (o->geom != GEOM_SPH || o->n_maps < 1) return -1;
@@ -638,7 +649,7 @@ int orc_init_state(orc_t *o)
                 double w[NV], u[NV];
                 w[0] = b[1] * x * x;
                 w[1] = b[0]; w[2] = 0.0;
-                w[3] = -o->omega * r * sin(th);   /* inertially radial (Parker) flow seen co-rotating */
+                w[3] = o->init_vphi ? -o->omega * r * sin(th) : 0.0;
                 w[4] = b[2] * pow(x, 2.0 * o->gamma);
                 w[5] = b[3] * x * x; w[6] = 0.0;
                 w[7] = -w[5] * o->omega * r * sin(th) / w[1];

@@ -195,19 +195,21 @@ __global__ void __launch_bounds__(BATCH_THREADS, sizeof(TW) == 4 ? 3 : 2) k_batc
                 m = next_member(off, A.n, it, m);
                 const Member &M = A.m[m];
                 const long long c = (it - off[m]) * BATCH_THREADS + tid;
-                double smax = 0.0;
-                if (c < (long long)M.P.n1 * M.P.n2 * M.P.n3) {
+                const bool valid = c < (long long)M.P.n1 * M.P.n2 * M.P.n3;
+                TW wo[NV];
+                if (valid) {
                     if (stage == 1)
                         update_cell<1, TS, TW>(M.P, (const TS *)M.U, (const TW *)M.W, (TS *)M.U1, (TW *)M.W1,
                                                (const TW *)M.F1, (const TW *)M.F2, (const TW *)M.F3,
-                                               (const TW *)M.divB, c);
+                                               (const TW *)M.divB, c, wo);
                     else
-                        smax = update_cell<2, TS, TW>(M.P, (const TS *)M.U1, (const TW *)M.W1, (TS *)M.U, (TW *)M.W,
-                                                      (const TW *)M.F1, (const TW *)M.F2, (const TW *)M.F3,
-                                                      (const TW *)M.divB, c);
+                        update_cell<2, TS, TW>(M.P, (const TS *)M.U1, (const TW *)M.W1, (TS *)M.U, (TW *)M.W,
+                                               (const TW *)M.F1, (const TW *)M.F2, (const TW *)M.F3,
+                                               (const TW *)M.divB, c, wo);
                 }
                 if (stage == 2) {
-                    smax = block_max(smax);
+                    const int ci = valid ? (int)(c % M.P.n1) : 0, cj = valid ? (int)((c / M.P.n1) % M.P.n2) : 0;
+                    const double smax = cfl_block_speed<TW>(M.P, wo, ci + NG, cj + NG, valid);
                     if (tid == 0) atomicMax(&M.P.sc->smax_bits, (unsigned long long)__double_as_longlong(smax));
                 }
             }

@@ -162,24 +162,41 @@ int build_metrics(icarus_ctx *c)
             col[per + j * g.n3 + k] = sin(th) * sin(ph);
             col[2 * per + j * g.n3 + k] = cos(th);
         }
+    std::vector<double> ldx2((size_t)p1 * p2);
+    for (int j = 0; j < p2; ++j)
+        for (int i = 0; i < p1; ++i) {
+            const double w1 = iw1[i], w2 = ih2[i] * (1.0 / d2), w3 = ih2[i] * is3[j] * (1.0 / d3);
+            ldx2[(size_t)j * p1 + i] = 1.0 / (w1 * w1 + w2 * w2 + w3 * w3);
+        }
     push(x1c); push(a1); push(iv1); push(q1); push(gp1); push(iw1); push(ih2); push(ig1); push(gmr2);
     push(x2c); push(a2); push(iv2); push(q2); push(gq2); push(sn); push(cs); push(ct); push(is3); push(ig2);
-    push(x3c); push(ig3); push(col);
+    push(x3c); push(ig3); push(col); push(ldx2);
     c->metric = (double *)dalloc(c, buf.size() * sizeof(double));
     if (!c->metric) return fail(ICARUS_ENOMEM, "metric allocation failed");
     CK(cudaMemcpyAsync(c->metric, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    const double *b = c->metric;
+    // the same tables rounded to float, for the single-precision arithmetic
+    std::vector<float> fbuf(buf.begin(), buf.end());
+    float *mfb = (float *)dalloc(c, fbuf.size() * sizeof(float));
+    if (!mfb) return fail(ICARUS_ENOMEM, "metric allocation failed");
+    CK(cudaMemcpyAsync(mfb, fbuf.data(), fbuf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    auto bind = [&](auto &m, const auto *b) {
+        int q = 0;
+        m.x1c = b + off[q++]; m.a1 = b + off[q++]; m.iv1 = b + off[q++]; m.q1 = b + off[q++]; m.gp1 = b + off[q++];
+        m.iw1 = b + off[q++]; m.ih2 = b + off[q++]; m.ig1 = b + off[q++]; m.gm_r2 = b + off[q++];
+        m.x2c = b + off[q++]; m.a2 = b + off[q++]; m.iv2 = b + off[q++]; m.q2 = b + off[q++]; m.gq2 = b + off[q++];
+        m.sn = b + off[q++]; m.cs = b + off[q++]; m.ct = b + off[q++]; m.is3 = b + off[q++]; m.ig2 = b + off[q++];
+        m.x3c = b + off[q++]; m.ig3 = b + off[q++]; m.colvec = b + off[q++]; m.ldx2 = b + off[q++];
+    };
     Metrics &m = c->P.m;
-    int q = 0;
-    m.x1c = b + off[q++]; m.a1 = b + off[q++]; m.iv1 = b + off[q++]; m.q1 = b + off[q++]; m.gp1 = b + off[q++];
-    m.iw1 = b + off[q++]; m.ih2 = b + off[q++]; m.ig1 = b + off[q++]; m.gm_r2 = b + off[q++];
-    m.x2c = b + off[q++]; m.a2 = b + off[q++]; m.iv2 = b + off[q++]; m.q2 = b + off[q++]; m.gq2 = b + off[q++];
-    m.sn = b + off[q++]; m.cs = b + off[q++]; m.ct = b + off[q++]; m.is3 = b + off[q++]; m.ig2 = b + off[q++];
-    m.x3c = b + off[q++]; m.ig3 = b + off[q++]; m.colvec = b + off[q++];
+    bind(m, (const double *)c->metric);
     m.d2 = d2; m.d3 = d3;
     m.id2 = 1.0 / d2; m.id3 = 1.0 / d3;
-    m.iv3 = sph ? 1.0 / d3 : 1.0 / d3;
+    m.iv3 = 1.0 / d3;
+    MetricsT<float> &mf = c->P.mf;
+    bind(mf, (const float *)mfb);
+    mf.d2 = (float)m.d2; mf.d3 = (float)m.d3; mf.id2 = (float)m.id2; mf.id3 = (float)m.id3; mf.iv3 = (float)m.iv3;
     return ICARUS_OK;
 }
 
@@ -187,6 +204,14 @@ void enqueue_step(icarus_ctx *c)
 {
     const Params &P = c->P;
     cudaStream_t s = c->stream;
+    if (c->ops.fused_stage && !c->opts.unfused) {
+        c->ops.fill_ghosts(P, c->U, c->W, 1, s);
+        c->ops.fused_stage(P, 1, c->U, c->W, c->U1, c->W1, s);
+        c->ops.fill_ghosts(P, c->U1, c->W1, 2, s);
+        c->ops.fused_stage(P, 2, c->U1, c->W1, c->U, c->W, s);
+        if (P.n_probes > 0) c->ops.probe(P, c->W, s);
+        return;
+    }
     // stage 1: U, W at t  ->  U1, W1
     c->ops.fill_ghosts(P, c->U, c->W, 1, s);
     c->ops.fluxes(P, c->W, c->F1, c->F2, c->F3, s);
@@ -202,7 +227,7 @@ void enqueue_step(icarus_ctx *c)
 
 int count_launches(const icarus_ctx *c)
 {
-    int per_stage = 3 + 3 + (c->P.divb == 1 ? 1 : 0) + 1;
+    int per_stage = (c->ops.fused_stage && !c->opts.unfused) ? 3 + 1 : 3 + 3 + (c->P.divb == 1 ? 1 : 0) + 1;
     return 2 * per_stage + (c->P.n_probes > 0 ? 1 : 0);
 }
 
@@ -269,8 +294,9 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     if (rc) return rc;
     if (!(gamma > 1.0)) return fail(ICARUS_EINVAL, "gamma must be > 1");
     if (!(opts->cfl > 0.0 && opts->cfl <= 1.0)) return fail(ICARUS_EINVAL, "cfl must be in (0, 1]");
-    if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 1 || opts->divb < 0 || opts->divb > 1)
-        return fail(ICARUS_EINVAL, "bad limiter / flux / divb option");
+    if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 1 || opts->divb < 0 || opts->divb > 1 ||
+        opts->init_vphi < 0 || opts->init_vphi > 1)
+        return fail(ICARUS_EINVAL, "bad limiter / flux / divb / init_vphi option");
     if (opts->precision < 0 || opts->precision > 2) return fail(ICARUS_EINVAL, "bad precision");
     if (opts->ring_capacity < 1) return fail(ICARUS_EINVAL, "ring_capacity must be >= 1");
     icarus_ctx *c = new icarus_ctx();
@@ -292,6 +318,7 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     P.geom = grid->geometry;
     for (int s = 0; s < 6; ++s) P.bc[s] = grid->bc[s];
     P.limiter = opts->limiter; P.flux = opts->flux; P.gravity = opts->gravity; P.divb = opts->divb;
+    P.init_vphi = opts->init_vphi;
     P.gamma = gamma;
     P.divb_coef = opts->divb_coef; P.rho_floor = opts->rho_floor; P.p_floor = opts->p_floor;
     c->t0 = AU / V0;
@@ -304,6 +331,9 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     P.omega = c->omega_code;
     P.omega_si = grid->geometry == ICARUS_GEOM_SPHERICAL ? omega_rot : 0.0;
     P.t0 = c->t0; P.b0 = c->b0; P.p0 = c->p0;
+    P.ph = PhysT<double>{P.gamma, P.gamma - 1.0, 1.0 / (P.gamma - 1.0), P.omega, P.divb_coef, P.rho_floor, P.p_floor};
+    P.phf = PhysT<float>{(float)P.ph.gamma, (float)P.ph.gm1, (float)P.ph.igm1, (float)P.ph.omega,
+                         (float)P.ph.divb_coef, (float)P.ph.rho_floor, (float)P.ph.p_floor};
     P.ring_cap = opts->ring_capacity;
     rc = build_metrics(c);
     if (rc) { icarus_destroy(c); return rc; }
@@ -317,7 +347,8 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     c->F3 = dalloc(c, NV * (size_t)(P.n3 + 1) * P.n2 * P.n1 * tw);
     c->divB = dalloc(c, nt * tw);
     const long long ncell = (long long)P.n1 * P.n2 * P.n3;
-    const long long nblk = (ncell + 255) / 256;
+    long long nblk = (ncell + 255) / 256;
+    if (c->ops.fused_blocks && (long long)c->ops.fused_blocks(P) > nblk) nblk = c->ops.fused_blocks(P);
     c->partial = (double *)dalloc(c, (size_t)nblk * sizeof(double));
     c->sc = (Scalars *)dalloc(c, sizeof(Scalars));
     c->stage_buf = (double *)dalloc(c, NV * (size_t)ncell * sizeof(double));
@@ -586,7 +617,8 @@ int icarus_time_kernels(icarus_ctx *c, int n_steps, double *ms)
 {
     if (!c || !ms || n_steps < 1) return fail(ICARUS_EINVAL, "bad argument");
     if (!c->have_state) return fail(ICARUS_ESTATE, "no state");
-    const int NCLS = 8;
+    const int NCLS = ICARUS_KERNEL_CLASSES;
+    const bool fused = c->ops.fused_stage && !c->opts.unfused;
     cudaEvent_t ev[2];
     CK(cudaEventCreate(&ev[0]));
     CK(cudaEventCreate(&ev[1]));
@@ -611,6 +643,10 @@ int icarus_time_kernels(icarus_ctx *c, int n_steps, double *ms)
             void *Us = stage == 1 ? c->U : c->U1, *Ws = stage == 1 ? c->W : c->W1;
             void *Uo = stage == 1 ? c->U1 : c->U, *Wo = stage == 1 ? c->W1 : c->W;
             rc |= timed(0, [&] { c->ops.fill_ghosts(P, Us, Ws, stage, s); });
+            if (fused) {
+                rc |= timed(7 + stage, [&] { c->ops.fused_stage(P, stage, Us, Ws, Uo, Wo, s); });
+                continue;
+            }
             rc |= timed(1, [&] { c->ops.flux_dir(P, 0, Ws, c->F1, s); });
             rc |= timed(2, [&] { c->ops.flux_dir(P, 1, Ws, c->F2, s); });
             rc |= timed(3, [&] { c->ops.flux_dir(P, 2, Ws, c->F3, s); });

@@ -17,36 +17,46 @@ namespace icarus {
 
 enum { RHO = 0, M1 = 1, M2 = 2, M3 = 3, EN = 4, B1 = 5, B2 = 6, B3 = 7 };
 
-// per-axis metric arrays (device pointers). Index convention: padded index ip = i + NG.
-struct Metrics {
+// per-axis metric arrays (device pointers) in the arithmetic type R: the double tables are the
+// host's FP64 values, the float tables their roundings (so single-precision kernels never convert
+// on the FP64 pipe). Index convention: padded index ip = i + NG.
+template <typename R> struct MetricsT {
     // r (or x): [p1] unless noted
-    const double *x1c;   // centres
-    const double *a1;    // lower-face area factor, [p1 + 1] (r^2 | 1)
-    const double *iv1;   // 1 / volume factor ((r+^3 - r-^3)/3 | dx)
-    const double *q1;    // (r+^2 - r-^2)/2 / v1  (| 1)
-    const double *gp1;   // (a1[i+1] - a1[i]) / v1 (geometric pressure term in m_r)
-    const double *iw1;   // 1 / radial width
-    const double *ih2;   // 1 / r_c (| 1)
-    const double *ig1;   // 1 / (x1c[i+1] - x1c[i-1])
-    const double *gm_r2; // GM / r_c^2
+    const R *x1c;   // centres
+    const R *a1;    // lower-face area factor, [p1 + 1] (r^2 | 1)
+    const R *iv1;   // 1 / volume factor ((r+^3 - r-^3)/3 | dx)
+    const R *q1;    // (r+^2 - r-^2)/2 / v1  (| 1)
+    const R *gp1;   // (a1[i+1] - a1[i]) / v1 (geometric pressure term in m_r)
+    const R *iw1;   // 1 / radial width
+    const R *ih2;   // 1 / r_c (| 1)
+    const R *ig1;   // 1 / (x1c[i+1] - x1c[i-1])
+    const R *gm_r2; // GM / r_c^2
     // theta (or y): [p2] unless noted
-    const double *x2c;
-    const double *a2;    // lower-face area factor, [p2 + 1] (sin theta- | 1)
-    const double *iv2;   // 1 / (cos theta- - cos theta+ | dy)
-    const double *q2;    // dtheta / v2 (| 1)
-    const double *gq2;   // (a2[j+1] - a2[j]) / v2 (geometric pressure term in m_theta)
-    const double *sn;    // sin theta_c (| 1)
-    const double *cs;    // cos theta_c (| 0)
-    const double *ct;    // cot theta_c (| 0)
-    const double *is3;   // 1 / sin theta_c (| 1)
-    const double *ig2;   // 1 / (x2c[j+1] - x2c[j-1])
+    const R *x2c;
+    const R *a2;    // lower-face area factor, [p2 + 1] (sin theta- | 1)
+    const R *iv2;   // 1 / (cos theta- - cos theta+ | dy)
+    const R *q2;    // dtheta / v2 (| 1)
+    const R *gq2;   // (a2[j+1] - a2[j]) / v2 (geometric pressure term in m_theta)
+    const R *sn;    // sin theta_c (| 1)
+    const R *cs;    // cos theta_c (| 0)
+    const R *ct;    // cot theta_c (| 0)
+    const R *is3;   // 1 / sin theta_c (| 1)
+    const R *ig2;   // 1 / (x2c[j+1] - x2c[j-1])
     // phi (or z): [p3]
-    const double *x3c;
-    const double *ig3;   // 1 / (x3c[k+1] - x3c[k-1])
-    double id2, id3, iv3;  // 1/dtheta, 1/dphi, 1/v3 (1/dphi | 1/dz)
-    double d2, d3;
+    const R *x3c;
+    const R *ig3;   // 1 / (x3c[k+1] - x3c[k-1])
+    R id2, id3, iv3;  // 1/dtheta, 1/dphi, 1/v3 (1/dphi | 1/dz)
+    R d2, d3;
     // CME footprint: unit vector of each boundary column centre, [3][n2][n3]
-    const double *colvec;
+    const R *colvec;
+    // Linde diffusion length^2: 1 / (dr^-2 + (r dtheta)^-2 + (r sin(theta) dphi)^-2), [p2][p1]
+    const R *ldx2;
+};
+using Metrics = MetricsT<double>;
+
+// physics constants in the arithmetic type R
+template <typename R> struct PhysT {
+    R gamma, gm1, igm1, omega, divb_coef, rho_floor, p_floor;   // gm1 = gamma - 1, igm1 = 1 / gm1
 };
 
 struct Scalars {               // device-resident step state
@@ -62,9 +72,12 @@ struct Params {
     int n1, n2, n3, p1, p2, p3;
     long long nt;
     int geom, bc[6];
-    int limiter, flux, gravity, divb;
+    int limiter, flux, gravity, divb, init_vphi;
     double gamma, omega, divb_coef, rho_floor, p_floor;
     Metrics m;
+    MetricsT<float> mf;             // float roundings of m
+    PhysT<double> ph;
+    PhysT<float> phf;
     // boundary driving (code units)
     int n_maps, n_cme;
     const double *t_maps;   // [n_maps]
@@ -78,6 +91,13 @@ struct Params {
     Scalars *sc;
     double *partial;        // [n_blocks] CFL partial maxima (scratch)
 };
+
+template <typename R> __host__ __device__ inline const MetricsT<R> &met(const Params &P);
+template <> __host__ __device__ inline const MetricsT<double> &met<double>(const Params &P) { return P.m; }
+template <> __host__ __device__ inline const MetricsT<float> &met<float>(const Params &P) { return P.mf; }
+template <typename R> __host__ __device__ inline const PhysT<R> &phys(const Params &P);
+template <> __host__ __device__ inline const PhysT<double> &phys<double>(const Params &P) { return P.ph; }
+template <> __host__ __device__ inline const PhysT<float> &phys<float>(const Params &P) { return P.phf; }
 
 __host__ __device__ inline long long cidx(const Params &P, int i, int j, int k)
 {
@@ -167,7 +187,25 @@ __device__ __forceinline__ void riemann(const R *wl, const R *wr, int d, int flu
     R ul[NV], ur[NV];
     prim2cons(wl, ul, igm1);
     prim2cons(wr, ur, igm1);
-    R irl = R(1) / wl[0], irr = R(1) / wr[0];
+    // FP64: 1/rho_L and 1/rho_R from one division, 1 / (rho_L rho_R), while the product stays
+    // well inside the normal range (biased exponent test on its bit pattern); two divisions
+    // otherwise and in single precision (where a division is cheap)
+    R irl, irr;
+    if constexpr (sizeof(R) == 8) {
+        const R q = wl[0] * wr[0];
+        const int ex = (hi_bits(q) >> 20) & 0x7ff;
+        if (ex > 60 && ex < 1990) {
+            const R iq = R(1) / q;
+            irl = wr[0] * iq;
+            irr = wl[0] * iq;
+        } else {
+            irl = R(1) / wl[0];
+            irr = R(1) / wr[0];
+        }
+    } else {
+        irl = R(1) / wl[0];
+        irr = R(1) / wr[0];
+    }
     R cl = fast_speed(wl, irl, d, gamma), cr = fast_speed(wr, irr, d, gamma);
     R fl[NV], fr[NV];
 #pragma unroll

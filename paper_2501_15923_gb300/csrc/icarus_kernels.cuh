@@ -21,20 +21,20 @@ template <typename TS, typename TW> struct Prec {
 // ---------------------------------------------------------------------------------------------
 // primitive recovery of one cell in the precision the mode asks for
 template <typename TS, typename TW>
-__device__ __forceinline__ void recover(const TS *u, TW *w, double gamma, int i)
+__device__ __forceinline__ void recover(const Params &P, const TS *u, TW *w, int i)
 {
     if (Prec<TS, TW>::mixed && i < 4) {
         double ud[NV], wd[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) ud[v] = (double)u[v];
-        cons2prim<double>(ud, wd, gamma - 1.0);
+        cons2prim<double>(ud, wd, P.ph.gm1);
 #pragma unroll
         for (int v = 0; v < NV; ++v) w[v] = (TW)wd[v];
     } else {
         TW uw[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) uw[v] = (TW)u[v];
-        cons2prim<TW>(uw, w, TW(gamma - 1.0));
+        cons2prim<TW>(uw, w, phys<TW>(P).gm1);
     }
 }
 
@@ -130,6 +130,16 @@ __device__ __forceinline__ void bnd1_col(const Params &P, TS *__restrict__ U, TW
             if (bc == 2 && (v == M1 || v == B1)) { uu = -uu; ww = -ww; }
             U[v * nt + cg] = uu;
             W[v * nt + cg] = ww;
+        }
+        if (bc == 1 && P.geom == 0) {
+            // spherical outer radius: B_r continues as r^-2 (r^2 B_r is copied), so the ghost
+            // layer adds no divergence; e follows the change of B^2
+            const double rs = P.m.x1c[src + NG], rg = P.m.x1c[gi + NG];
+            const double f = (rs / rg) * (rs / rg);
+            const double bs = (double)U[B1 * nt + cs], bg = bs * f;
+            U[EN * nt + cg] = (TS)((double)U[EN * nt + cs] + 0.5 * (bg * bg - bs * bs));
+            U[B1 * nt + cg] = (TS)bg;
+            W[B1 * nt + cg] = (TW)((double)W[B1 * nt + cs] * f);
         }
     }
 }
@@ -286,7 +296,7 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
 #pragma unroll
             for (int v = 0; v < NV; ++v) { wl[v] = sW[v * sz + pl]; wr[v] = wc[v]; }
         }
-        riemann<TW>(wl, wr, D, P.flux, TW(P.gamma), TW(1.0 / (P.gamma - 1.0)), f);
+        riemann<TW>(wl, wr, D, P.flux, phys<TW>(P).gamma, phys<TW>(P).igm1, f);
         long long fi, fs;
         if (D == 0) { fi = ((long long)k * P.n2 + j) * (P.n1 + 1) + s; fs = (long long)P.n3 * P.n2 * (P.n1 + 1); }
         else if (D == 1) { fi = ((long long)k * (P.n2 + 1) + s) * P.n1 + i; fs = (long long)P.n3 * (P.n2 + 1) * P.n1; }
@@ -329,14 +339,14 @@ __device__ __forceinline__ void divb_cell(const Params &P, const TW *__restrict_
     long long r = tid / e1;
     int j = (int)(r % e2) - 1;
     int k = (int)(r / e2) - 1;
-    const Metrics &m = P.m;
+    const MetricsT<TW> &m = met<TW>(P);
     const long long nt = P.nt, c = cidx(P, i, j, k);
     const int ip = i + NG, jp = j + NG;
     const TW *b1 = W + 5 * nt, *b2 = W + 6 * nt, *b3 = W + 7 * nt;
     const long long s2 = P.p1, s3 = (long long)P.p1 * P.p2;
-    TW d1 = (TW(m.a1[ip + 1]) * (b1[c] + b1[c + 1]) - TW(m.a1[ip]) * (b1[c - 1] + b1[c])) * TW(m.iv1[ip]);
-    TW d2 = (TW(m.a2[jp + 1]) * (b2[c] + b2[c + s2]) - TW(m.a2[jp]) * (b2[c - s2] + b2[c])) * TW(m.q1[ip] * m.iv2[jp]);
-    TW d3 = (b3[c + s3] - b3[c - s3]) * TW(m.q1[ip] * m.q2[jp] * m.iv3);
+    TW d1 = (m.a1[ip + 1] * (b1[c] + b1[c + 1]) - m.a1[ip] * (b1[c - 1] + b1[c])) * m.iv1[ip];
+    TW d2 = (m.a2[jp + 1] * (b2[c] + b2[c + s2]) - m.a2[jp] * (b2[c - s2] + b2[c])) * (m.q1[ip] * m.iv2[jp]);
+    TW d3 = (b3[c + s3] - b3[c - s3]) * (m.q1[ip] * m.q2[jp] * m.iv3);
     divB[c] = TW(0.5) * (d1 + d2 + d3);
 }
 
@@ -401,13 +411,82 @@ __device__ __forceinline__ void finish_dt(Params &P, double smax_block, int adva
 template <typename TW>
 __device__ __forceinline__ double cell_speed(const Params &P, const TW *w, int ip, int jp)
 {
-    const Metrics &m = P.m;
+    const MetricsT<TW> &m = met<TW>(P);
     TW irho = TW(1) / w[0];
-    TW g = TW(P.gamma);
-    TW s1 = (rabs(w[1]) + fast_speed<TW>(w, irho, 0, g)) * TW(m.iw1[ip]);
-    TW s2 = (rabs(w[2]) + fast_speed<TW>(w, irho, 1, g)) * TW(m.ih2[ip] * m.id2);
-    TW s3 = (rabs(w[3]) + fast_speed<TW>(w, irho, 2, g)) * TW(m.ih2[ip] * m.is3[jp] * m.id3);
+    TW g = phys<TW>(P).gamma;
+    TW s1 = (rabs(w[1]) + fast_speed<TW>(w, irho, 0, g)) * m.iw1[ip];
+    TW s2 = (rabs(w[2]) + fast_speed<TW>(w, irho, 1, g)) * (m.ih2[ip] * m.id2);
+    TW s3 = (rabs(w[3]) + fast_speed<TW>(w, irho, 2, g)) * (m.ih2[ip] * m.is3[jp] * m.id3);
     return (double)(s1 + s2 + s3);
+}
+
+// double -> float by truncating the bit pattern, on the integer pipe (the FP64 pipe, which also
+// carries conversions, is the scarce one): relative error below 2^-23 for 2^-126 <= |x| < 2^128,
+// 0 below that range, +-FLT_MAX above it and for non-finite x
+__device__ __forceinline__ float trunc_f(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int ax = hi & 0x7fffffff;
+    const unsigned sign = (unsigned)hi & 0x80000000u;
+    if (ax < 0x38100000) return 0.f;
+    if (ax >= 0x47f00000) return __uint_as_float(sign | 0x7f7fffffu);
+    return __uint_as_float(sign | ((unsigned)(ax - 0x38000000) << 3) | (lo >> 29));
+}
+
+// single-precision estimate of cell_speed from FP64 primitives. Its relative error stays below
+// 1e-3: the fast-speed discriminant s^2 - 4 a^2 b_d^2 (s = a^2 + b^2) can cancel completely, so its
+// absolute error is about 10 x 2^-24 s^2 (the roundings of s, s^2 and the product), which puts an
+// error of at most sqrt(10 x 2^-24) / 2 = 4e-4 of s into c_f^2 >= s / 2, i.e. 4e-4 relative in c_f;
+// the truncations add < 1e-6
+__device__ __forceinline__ float cell_speed_est(const Params &P, const double *wd, int ip, int jp)
+{
+    const MetricsT<float> &m = P.mf;
+    float w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = trunc_f(wd[v]);
+    const float irho = 1.f / w[0], g = P.phf.gamma, ih = m.ih2[ip];
+    const float s1 = (fabsf(w[1]) + fast_speed<float>(w, irho, 0, g)) * m.iw1[ip];
+    const float s2 = (fabsf(w[2]) + fast_speed<float>(w, irho, 1, g)) * (ih * m.id2);
+    const float s3 = (fabsf(w[3]) + fast_speed<float>(w, irho, 2, g)) * (ih * m.is3[jp] * m.id3);
+    return s1 + s2 + s3;
+}
+
+// block-wide max of a float, returned to every thread
+__device__ __forceinline__ float block_max_all(float v)
+{
+    __shared__ float redf[33];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) redf[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < nw ? redf[lane] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) redf[32] = v;
+    }
+    __syncthreads();
+    return redf[32];
+}
+
+// block maximum of the CFL signal speed (valid in thread 0; every thread of the block calls it).
+// FP64: the single-precision estimate of every cell selects the cells within 1 % of the block's
+// largest estimate, and only those evaluate the exact FP64 speed. With estimate errors below 1e-3
+// the cell of the exact maximum always passes (its estimate is >= (1 - 1e-3) / (1 + 1e-3) of the
+// largest), so the result is the exact FP64 maximum, as if every cell had been evaluated
+template <typename TW>
+__device__ __forceinline__ double cfl_block_speed(const Params &P, const TW *wo, int ip, int jp, bool valid)
+{
+    if constexpr (sizeof(TW) == 4) {
+        return block_max(valid ? cell_speed<TW>(P, wo, ip, jp) : 0.0);
+    } else {
+        const float e = valid ? cell_speed_est(P, wo, ip, jp) : 0.f;
+        const float top = block_max_all(e);
+        return block_max(valid && e >= top * 0.99f ? cell_speed<TW>(P, wo, ip, jp) : 0.0);
+    }
 }
 
 template <typename TW>
@@ -440,9 +519,9 @@ __global__ void __launch_bounds__(256) k_cfl(Params P, const TW *__restrict__ W)
 // area / volume factors of the flux divergence of cell (i, j, k)
 template <typename TW> struct DivFactors {
     TW am, ap, iv, bm, bp, jv, kv;
-    __device__ __forceinline__ DivFactors(const Metrics &m, int ip, int jp)
-        : am(TW(m.a1[ip])), ap(TW(m.a1[ip + 1])), iv(TW(m.iv1[ip])), bm(TW(m.a2[jp])), bp(TW(m.a2[jp + 1])),
-          jv(TW(m.q1[ip] * m.iv2[jp])), kv(TW(m.q1[ip] * m.q2[jp] * m.iv3)) {}
+    __device__ __forceinline__ DivFactors(const MetricsT<TW> &m, int ip, int jp)
+        : am(m.a1[ip]), ap(m.a1[ip + 1]), iv(m.iv1[ip]), bm(m.a2[jp]), bp(m.a2[jp + 1]),
+          jv(m.q1[ip] * m.iv2[jp]), kv(m.q1[ip] * m.q2[jp] * m.iv3) {}
     // -(1/V) sum_d (A+ F+ - A- F-) of one field
     __device__ __forceinline__ TW div(TW fr0, TW fr1, TW ft0, TW ft1, TW fp0, TW fp1) const
     {
@@ -457,21 +536,22 @@ template <typename TW> struct DivFactors {
 // per field, out: the full residual) and div B at its six neighbours; returns the cell's CFL
 // signal speed after a second stage (0 otherwise)
 template <int STAGE, typename TS, typename TW>
-__device__ __forceinline__ double update_core(const Params &P, int i, int j, int k, const TW *w, TW *L,
-                                              const TW *dbn, const TS *__restrict__ Us, TS *Uo, TW *__restrict__ Wo)
+__device__ __forceinline__ void update_core(const Params &P, int i, int j, int k, const TW *w, TW *L, const TW *dbn,
+                                            const TS *__restrict__ Us, TS *Uo, TW *__restrict__ Wo, TW *wo)
 {
     const int ip = i + NG, jp = j + NG;
-    const Metrics &m = P.m;
+    const MetricsT<TW> &m = met<TW>(P);
+    const PhysT<TW> &ph = phys<TW>(P);
     const long long nt = P.nt, c = cidx(P, i, j, k);
     const double dt = P.sc->dt;
     if (P.geom == 0) {
         const TW rho = w[0], vr = w[1], vt = w[2], vp = w[3];
         const TW br = w[5], bt = w[6], bp = w[7];
-        const TW ir = TW(m.ih2[ip]), cot = TW(m.ct[jp]);
+        const TW ir = m.ih2[ip], cot = m.ct[jp];
         const TW pt = w[4] + TW(0.5) * (br * br + bt * bt + bp * bp);
         // geometric terms of the spherical divergence; p_tot through face-area differences
-        L[M1] += pt * TW(m.gp1[ip]) + (rho * (vt * vt + vp * vp) - (bt * bt + bp * bp)) * ir;
-        L[M2] += pt * TW(m.q1[ip] * m.gq2[jp]) + (-(rho * vr * vt - br * bt) + cot * (rho * vp * vp - bp * bp)) * ir;
+        L[M1] += pt * m.gp1[ip] + (rho * (vt * vt + vp * vp) - (bt * bt + bp * bp)) * ir;
+        L[M2] += pt * (m.q1[ip] * m.gq2[jp]) + (-(rho * vr * vt - br * bt) + cot * (rho * vp * vp - bp * bp)) * ir;
         L[M3] -= ((rho * vp * vr - bp * br) + cot * (rho * vp * vt - bp * bt)) * ir;
         L[B2] += (vr * bt - vt * br) * ir;
         L[B3] += ((vr * bp - vp * br) + cot * (vt * bp - vp * bt)) * ir;
@@ -479,7 +559,7 @@ __device__ __forceinline__ double update_core(const Params &P, int i, int j, int
             // co-rotating frame, Omega along the polar axis: centrifugal rho Omega^2 r sin(th)
             // (sin th, cos th, 0), Coriolis 2 rho Omega (v_phi sin th, v_phi cos th,
             // -(v_r sin th + v_th cos th)), work of the centrifugal force in e
-            const TW Om = TW(P.omega), sn = TW(m.sn[jp]), cs = TW(m.cs[jp]), rc = TW(m.x1c[ip]);
+            const TW Om = ph.omega, sn = m.sn[jp], cs = m.cs[jp], rc = m.x1c[ip];
             const TW cen = rho * Om * Om * rc * sn;
             const TW vpar = vr * sn + vt * cs;
             L[M1] += cen * sn + TW(2) * rho * Om * vp * sn;
@@ -488,7 +568,7 @@ __device__ __forceinline__ double update_core(const Params &P, int i, int j, int
             L[EN] += cen * vpar;
         }
         if (P.gravity) {
-            const TW g = TW(m.gm_r2[ip]);
+            const TW g = m.gm_r2[ip];
             L[M1] -= rho * g;
             L[EN] -= rho * vr * g;
         }
@@ -497,11 +577,10 @@ __device__ __forceinline__ double update_core(const Params &P, int i, int j, int
     // dbn = div B at (i-1, i+1, j-1, j+1, k-1, k+1)
     TW lb[3] = {TW(0), TW(0), TW(0)};
     if (P.divb == 1 && dt > 0.0) {
-        const TW iw1 = TW(m.iw1[ip]), iw2 = TW(m.ih2[ip] * m.id2), iw3 = TW(m.ih2[ip] * m.is3[jp] * m.id3);
-        const TW coef = TW(P.divb_coef) / (iw1 * iw1 + iw2 * iw2 + iw3 * iw3);
-        lb[0] = coef * (dbn[1] - dbn[0]) * TW(m.ig1[ip]);
-        lb[1] = coef * (dbn[3] - dbn[2]) * TW(m.ih2[ip] * m.ig2[jp]);
-        lb[2] = coef * (dbn[5] - dbn[4]) * TW(m.ih2[ip] * m.is3[jp] * m.ig3[k + NG]);
+        const TW coef = ph.divb_coef * m.ldx2[(long long)jp * P.p1 + ip];
+        lb[0] = coef * (dbn[1] - dbn[0]) * m.ig1[ip];
+        lb[1] = coef * (dbn[3] - dbn[2]) * (m.ih2[ip] * m.ig2[jp]);
+        lb[2] = coef * (dbn[5] - dbn[4]) * (m.ih2[ip] * m.is3[jp] * m.ig3[k + NG]);
     }
     TS uo[NV];
     const TS dts = (TS)dt;
@@ -521,16 +600,16 @@ __device__ __forceinline__ double update_core(const Params &P, int i, int j, int
     for (int v = 0; v < NV; ++v) bad |= (hi_bits(uo[v]) & (sizeof(TS) == 8 ? 0x7ff00000 : 0x7f800000)) ==
                                         (sizeof(TS) == 8 ? 0x7ff00000 : 0x7f800000);   // inf or NaN
     if (bad) atomicOr(&P.sc->status, 1);
-    TW wo[NV];
     int hits = 0;
-    if (uo[RHO] < (TS)P.rho_floor) { uo[RHO] = (TS)P.rho_floor; ++hits; }
-    recover<TS, TW>(uo, wo, P.gamma, i);
-    if (wo[4] < TW(P.p_floor)) {
+    const PhysT<TS> &phs = phys<TS>(P);
+    if (uo[RHO] < phs.rho_floor) { uo[RHO] = phs.rho_floor; ++hits; }
+    recover<TS, TW>(P, uo, wo, i);
+    if (wo[4] < ph.p_floor) {
         // reset e so that p = p_floor, keeping rho, m, B
         TS ke = TS(0.5) * (uo[M1] * uo[M1] + uo[M2] * uo[M2] + uo[M3] * uo[M3]) / uo[RHO];
         TS me = TS(0.5) * (uo[B1] * uo[B1] + uo[B2] * uo[B2] + uo[B3] * uo[B3]);
-        uo[EN] = (TS)P.p_floor / (TS)(P.gamma - 1.0) + ke + me;
-        wo[4] = TW(P.p_floor);
+        uo[EN] = phs.p_floor * phs.igm1 + ke + me;
+        wo[4] = ph.p_floor;
         ++hits;
     }
     if (hits) atomicAdd(&P.sc->floor_hits, (unsigned long long)hits);
@@ -539,15 +618,14 @@ __device__ __forceinline__ double update_core(const Params &P, int i, int j, int
         Uo[v * nt + c] = uo[v];
         Wo[v * nt + c] = wo[v];
     }
-    return STAGE == 2 ? cell_speed<TW>(P, wo, ip, jp) : 0.0;
 }
 
 // the update of cell number tid (r fastest) with fluxes and div B read from their global arrays
 template <int STAGE, typename TS, typename TW>
-__device__ __forceinline__ double update_cell(const Params &P, const TS *__restrict__ Us, const TW *__restrict__ Ws,
-                                              TS *Uo, TW *__restrict__ Wo, const TW *__restrict__ F1,
-                                              const TW *__restrict__ F2, const TW *__restrict__ F3,
-                                              const TW *__restrict__ divB, long long tid)
+__device__ __forceinline__ void update_cell(const Params &P, const TS *__restrict__ Us, const TW *__restrict__ Ws,
+                                            TS *Uo, TW *__restrict__ Wo, const TW *__restrict__ F1,
+                                            const TW *__restrict__ F2, const TW *__restrict__ F3,
+                                            const TW *__restrict__ divB, long long tid, TW *wo)
 {
     const int i = (int)(tid % P.n1);
     const long long r_ = tid / P.n1;
@@ -558,7 +636,7 @@ __device__ __forceinline__ double update_cell(const Params &P, const TS *__restr
     const long long s2 = (long long)P.n3 * (P.n2 + 1) * P.n1, f2 = ((long long)k * (P.n2 + 1) + j) * P.n1 + i;
     const long long s3 = (long long)(P.n3 + 1) * P.n2 * P.n1, f3 = ((long long)k * P.n2 + j) * P.n1 + i;
     const long long o3 = (long long)P.n2 * P.n1;
-    const DivFactors<TW> dv(P.m, i + NG, j + NG);
+    const DivFactors<TW> dv(met<TW>(P), i + NG, j + NG);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         w[v] = Ws[v * nt + c];
@@ -571,7 +649,7 @@ __device__ __forceinline__ double update_cell(const Params &P, const TS *__restr
         dbn[2] = divB[c - q2]; dbn[3] = divB[c + q2];
         dbn[4] = divB[c - q3]; dbn[5] = divB[c + q3];
     }
-    return update_core<STAGE, TS, TW>(P, i, j, k, w, L, dbn, Us, Uo, Wo);
+    update_core<STAGE, TS, TW>(P, i, j, k, w, L, dbn, Us, Uo, Wo, wo);
 }
 
 template <int STAGE, typename TS, typename TW>
@@ -581,12 +659,12 @@ k_update(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo,
          const TW *__restrict__ divB)
 {
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double smax = 0.0;
-    if (tid < (long long)P.n1 * P.n2 * P.n3)
-        smax = update_cell<STAGE, TS, TW>(P, Us, Ws, Uo, Wo, F1, F2, F3, divB, tid);
+    const bool valid = tid < (long long)P.n1 * P.n2 * P.n3;
+    TW wo[NV];
+    if (valid) update_cell<STAGE, TS, TW>(P, Us, Ws, Uo, Wo, F1, F2, F3, divB, tid, wo);
     if (STAGE == 2) {
-        smax = block_max(smax);
-        finish_dt(P, smax, 1);
+        const int i = valid ? (int)(tid % P.n1) : 0, j = valid ? (int)((tid / P.n1) % P.n2) : 0;
+        finish_dt(P, cfl_block_speed<TW>(P, wo, i + NG, j + NG, valid), 1);
     }
 }
 
@@ -603,7 +681,7 @@ __global__ void k_prims(Params P, const TS *__restrict__ U, TW *__restrict__ W)
 #pragma unroll
     for (int v = 0; v < NV; ++v) u[v] = U[v * P.nt + c];
     if (u[RHO] == TS(0)) return;      // untouched ghost corner before the first fill
-    recover<TS, TW>(u, w, P.gamma, i < 0 ? 0 : i);
+    recover<TS, TW>(P, u, w, i < 0 ? 0 : i);
 #pragma unroll
     for (int v = 0; v < NV; ++v) W[v * P.nt + c] = w[v];
 }
@@ -641,7 +719,7 @@ __global__ void k_init_state(Params P, TS *__restrict__ U, TW *__restrict__ W, d
     double wd[NV], ud[NV];
     wd[0] = b[1] * x2;
     wd[1] = b[0]; wd[2] = 0.0;
-    wd[3] = -P.omega * r * P.m.sn[j + NG];   // inertially radial flow, seen from the rotating frame
+    wd[3] = P.init_vphi ? -P.omega * r * P.m.sn[j + NG] : 0.0;   // at rest co-rotating, or radial inertial flow
     wd[4] = b[2] * pow(x, 2.0 * P.gamma);
     wd[5] = b[3] * x2; wd[6] = 0.0;
     wd[7] = -wd[5] * P.omega * r * P.m.sn[j + NG] / wd[1];
@@ -650,7 +728,7 @@ __global__ void k_init_state(Params P, TS *__restrict__ U, TW *__restrict__ W, d
     TS us[NV];
     TW ws[NV];
     for (int v = 0; v < NV; ++v) us[v] = (TS)ud[v];
-    recover<TS, TW>(us, ws, P.gamma, i);
+    recover<TS, TW>(P, us, ws, i);
     for (int v = 0; v < NV; ++v) {
         U[v * P.nt + c] = us[v];
         W[v * P.nt + c] = ws[v];
@@ -875,6 +953,8 @@ template <typename TS, typename TW> struct Launch {
         o.init_state = init_state;
         o.pack = pack;
         o.unpack = unpack;
+        o.fused_stage = nullptr;
+        o.fused_blocks = nullptr;
         o.ts_size = sizeof(TS);
         o.tw_size = sizeof(TW);
         return o;

@@ -18,6 +18,9 @@ struct Ops {
     void (*init_state)(const Params &, void *U, void *W, double r_in, cudaStream_t);
     void (*pack)(const Params &, const void *U, double *out, cudaStream_t);
     void (*unpack)(const Params &, void *U, const double *in, cudaStream_t);
+    // one whole stage (fluxes, div B, update) in a single kernel; null where not available
+    void (*fused_stage)(const Params &, int stage, const void *Us, const void *Ws, void *Uo, void *Wo, cudaStream_t);
+    unsigned int (*fused_blocks)(const Params &);
     size_t ts_size, tw_size;
 };
 int report_error(int code, const char *msg);

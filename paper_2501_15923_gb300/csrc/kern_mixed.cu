@@ -1,5 +1,13 @@
-// kern_mixed.cu -- instantiation of the hot-path kernels for the mixed precision mode
-#include "icarus_kernels.cuh"
+// kern_mixed.cu -- instantiation of the hot-path kernels for the mixed precision mode, with the
+// fused single-kernel stage (single-precision arithmetic)
+#include "icarus_fused.cuh"
 namespace icarus {
-Ops ops_mixed() { return Launch<double, float>::make(); }
+Ops ops_mixed()
+{
+    Ops o = Launch<double, float>::make();
+    FusedLaunch<double>::prepare();
+    o.fused_stage = FusedLaunch<double>::stage;
+    o.fused_blocks = FusedLaunch<double>::blocks;
+    return o;
+}
 }  // namespace icarus

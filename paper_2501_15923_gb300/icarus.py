@@ -43,7 +43,8 @@ class icarus_options(C.Structure):
     _fields_ = [("cfl", C.c_double), ("limiter", C.c_int), ("flux", C.c_int), ("gravity", C.c_int),
                 ("divb", C.c_int), ("divb_coef", C.c_double), ("rho_floor", C.c_double),
                 ("p_floor", C.c_double), ("precision", C.c_int), ("ring_capacity", C.c_int),
-                ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+                ("unfused", C.c_int), ("init_vphi", C.c_int)]
 
 
 _lib = None
@@ -143,8 +144,11 @@ def make_grid(g: I.Grid) -> icarus_grid:
                        g.x3min, g.x3max, (C.c_int * 6)(*g.bc))
 
 
-def make_options(o: I.Options, precision=ICARUS_FP64, ring=4096, stream=None, allocator=None) -> icarus_options:
+def make_options(o: I.Options, precision=ICARUS_FP64, ring=4096, stream=None, allocator=None,
+                 unfused=False) -> icarus_options:
     opt = icarus_options()
+    opt.unfused = int(bool(unfused))
+    opt.init_vphi = int(o.init_vphi)
     opt.cfl, opt.limiter, opt.flux, opt.gravity, opt.divb = o.cfl, o.limiter, o.flux, o.gravity, o.divb
     opt.divb_coef, opt.rho_floor, opt.p_floor = o.divb_coef, o.rho_floor, o.p_floor
     opt.precision, opt.ring_capacity = precision, ring
@@ -243,11 +247,12 @@ def icarus_get_stream(ctx) -> int:
     return int(load().icarus_get_stream(ctx) or 0)
 
 
-KERNEL_CLASSES = ("ghost_fill", "flux_r", "flux_theta", "flux_phi", "divb", "update_1", "update_2", "probe")
+KERNEL_CLASSES = ("ghost_fill", "flux_r", "flux_theta", "flux_phi", "divb", "update_1", "update_2", "probe",
+                  "fused_1", "fused_2")
 
 
 def icarus_time_kernels(ctx, n_steps: int) -> dict:
-    ms = np.zeros(8)
+    ms = np.zeros(len(KERNEL_CLASSES))
     _check(load().icarus_time_kernels(ctx, int(n_steps), _ptr(ms)))
     return dict(zip(KERNEL_CLASSES, ms.tolist()))
 
@@ -264,12 +269,12 @@ class Solver:
     """One solver context on the current CUDA device, memory from torch's caching allocator."""
 
     def __init__(self, grid: I.Grid, gamma: float, omega: float, opts: I.Options, precision=ICARUS_FP64,
-                 ring=4096, device="cuda"):
+                 ring=4096, device="cuda", unfused=False):
         import torch
         self.torch = torch
         self.grid, self.precision = grid, precision
         self._alloc = _TorchAllocator(torch.device(device))
-        self._opts = make_options(opts, precision, ring, None, self._alloc)
+        self._opts = make_options(opts, precision, ring, None, self._alloc, unfused)
         self._grid = make_grid(grid)
         self.ctx = icarus_init(self._grid, gamma, omega, self._opts)
         self.shape = (8, grid.n3, grid.n2, grid.n1)
@@ -321,8 +326,8 @@ class Solver:
         return icarus_launches_per_step(self.ctx)
 
 
-def from_workload(w: I.Workload, precision=ICARUS_FP64, ring=4096) -> Solver:
-    s = Solver(w.grid, w.gamma, w.omega, w.opts, precision, ring)
+def from_workload(w: I.Workload, precision=ICARUS_FP64, ring=4096, unfused=False) -> Solver:
+    s = Solver(w.grid, w.gamma, w.omega, w.opts, precision, ring, unfused=unfused)
     s.set_boundary(w.t_maps, w.maps, w.cmes)
     return s
 

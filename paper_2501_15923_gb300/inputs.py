@@ -45,6 +45,7 @@ GEOM_SPHERICAL, GEOM_CARTESIAN = 0, 1
 LIM_MINMOD, LIM_VANLEER, LIM_MC = 0, 1, 2
 FLUX_TVDLF, FLUX_HLL = 0, 1
 DIVB_NONE, DIVB_LINDE = 0, 1
+IC_COROTATING, IC_INERTIAL_RADIAL = 0, 1     # initial v_phi: at rest co-rotating / radial inertial flow
 
 
 class SplitMix64:
@@ -112,6 +113,7 @@ class Options:
     divb_coef: float = 0.8
     rho_floor: float = 1e-6               # code units (n in cm^-3)
     p_floor: float = 1e-9                 # code units (p / (m_p 1e6 m^-3 (100 km/s)^2))
+    init_vphi: int = IC_COROTATING        # initial v_phi: IC_COROTATING (0) or IC_INERTIAL_RADIAL
 
 
 @dataclass

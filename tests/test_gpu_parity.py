@@ -62,8 +62,10 @@ def assert_step(gpu, orc, U, t, tol=TOL, dt_cap=0.0):
 
 
 # ---------------------------------------------------------------------------------------------
-def test_initial_state_matches(ic):
+@pytest.mark.parametrize("init_vphi", [I.IC_COROTATING, I.IC_INERTIAL_RADIAL])
+def test_initial_state_matches(ic, init_vphi):
     w = I.config0()
+    w.opts.init_vphi = init_vphi
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     Ug, _ = gpu.get_state()
     Uo, _ = orc.get_state()

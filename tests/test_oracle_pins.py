@@ -494,8 +494,43 @@ def test_P8_ghost_layers_same_value_and_asymm():
         assert np.allclose(Wp[f, 2:-2, 2:-2, 0], -Wp[f, 2:-2, 2:-2, 3], atol=1e-13)
 
 
-def test_IC_radial_expansion():
+def test_P8_outer_radius_continues_radial_flux():
+    """Outer-r `cont`: every variable is copied into both ghost layers except B_r, which continues
+    as r^-2. A radial field B_r = C(theta, phi) / r^2 then has (face-average) div B at the last
+    cell of the size of the interior's second-order truncation, not B_r / r as a plain copy gives,
+    and the ghost pressure, density and velocity equal the last cell's."""
+    n1 = 32
+    g = sph_grid(n1, 6, 8, bc=(C, C, C, C, P, P), r=(0.1, 2.0))
+    o = Oracle(g, 1.5, 0.0, opts())
+    rc, tc = centres(g, 0), centres(g, 1)
+    rng = np.random.default_rng(4)
+    W = np.zeros((8, 8, 6, n1))
+    W[0] = 1.0 + rng.random(W.shape[1:])
+    W[1] = 4.0 + rng.random(W.shape[1:])
+    W[3] = 0.3 * rng.standard_normal(W.shape[1:])
+    W[4] = 0.5 + rng.random(W.shape[1:])
+    amp = 1.0 + rng.random((8, 6, 1))
+    W[5] = amp / rc[None, None, 2:-2] ** 2
+    W[7] = 0.2 * rng.standard_normal((1,) + W.shape[2:])     # no phi dependence: no phi term in div B
+    o.set_state(cons_from_prim(W, 1.5), 0.0)
+    o.fill_ghosts(0.0)
+    Wp = prim_from_cons(o.get_state_padded(), 1.5)
+    last = n1 + 1                       # padded index of the last interior cell
+    for gidx in (last + 1, last + 2):
+        r2 = (rc[gidx] / rc[last]) ** 2
+        assert np.allclose(Wp[5, 2:-2, 2:-2, gidx] * r2, Wp[5, 2:-2, 2:-2, last], rtol=1e-14)
+        for f in (0, 1, 2, 3, 4, 6, 7):
+            assert np.allclose(Wp[f, 2:-2, 2:-2, gidx], Wp[f, 2:-2, 2:-2, last], rtol=1e-12, atol=1e-14)
+    db = np.abs(o.divb()) * rc[None, None, 2:-2] / np.abs(W[5])
+    dr_r = (2.0 / 0.1) ** (1.0 / n1) - 1.0
+    assert db[:, :, -1].max() < 2 * dr_r ** 2          # a plain copy gives ~1 here
+    assert db[:, :, -1].max() < 4 * db[:, :, -4].max() + 1e-14
+
+
+@pytest.mark.parametrize("init_vphi", [I.IC_COROTATING, I.IC_INERTIAL_RADIAL])
+def test_IC_radial_expansion(init_vphi):
     w = I.config0()
+    w.opts.init_vphi = init_vphi
     from oracle.oracle import from_workload
     o = from_workload(w)
     U, _ = o.get_state()
@@ -513,11 +548,14 @@ def test_IC_radial_expansion():
     assert np.allclose(W[5], br, rtol=1e-12)
     bphi = -br * sc["omega"] * rc[None, None, :] * np.sin(tc)[None, :, None] / vr
     assert np.allclose(W[7], bphi, rtol=1e-12)
-    # inertially radial flow: v_phi = -Omega r sin(theta) in the co-rotating frame, so the velocity
-    # is parallel to the spiral field (v_phi / v_r = B_phi / B_r) and the rotating-frame E vanishes
-    vphi = -sc["omega"] * rc[None, None, :] * np.sin(tc)[None, :, None] * np.ones_like(W[3])
-    assert np.allclose(W[3], vphi, rtol=1e-12)
-    assert np.allclose(W[3] * W[5], W[1] * W[7], rtol=1e-10, atol=1e-12)
+    if init_vphi == I.IC_COROTATING:
+        assert np.all(W[3] == 0)
+    else:
+        # inertially radial flow: v_phi = -Omega r sin(theta) in the co-rotating frame, so the
+        # velocity is parallel to the spiral field (v_phi / v_r = B_phi / B_r): no rotating-frame E
+        vphi = -sc["omega"] * rc[None, None, :] * np.sin(tc)[None, :, None] * np.ones_like(W[3])
+        assert np.allclose(W[3], vphi, rtol=1e-12)
+        assert np.allclose(W[3] * W[5], W[1] * W[7], rtol=1e-10, atol=1e-12)
     assert np.all(W[2] == 0) and np.all(W[6] == 0)
 
 
