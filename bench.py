@@ -401,17 +401,24 @@ def main(argv=None):
             fms = a.elapsed_time(b)
             forms[name] = {"value": ncell * args.steps / (fms * 1e-3) / 1e6, "unit": "Mcell-updates/s",
                            "ms_per_step": fms / args.steps}
-            # roofline of the fused stage kernel (HBM): algorithmic bytes per cell of one stage =
-            # primitives in + state in + state and primitives out (+ U^n in for the second stage)
+            # HBM roofline of this form's dominant kernel, from per-launch event times and the
+            # algorithmic bytes of one launch (each value read or written once): flux kernels read
+            # the primitives (8 x sw per cell) and write the fluxes (8 x sw per face); the update
+            # reads W, U, the six face fluxes (each face shared by two cells) and div B and writes
+            # U and W, plus U^n in the second stage
             fk = sf.time_kernels(2)
-            if fk.get("fused_1", 0.0) > 0.0:
-                su, sw = (4, 4) if pr == ic.ICARUS_FP32 else (8, 4)
-                b1, b2 = 8 * (sw + su + su + sw), 8 * (sw + su + su + su + sw)
-                ach = (b1 + b2) * ncell / ((fk["fused_1"] + fk["fused_2"]) * 1e-3) / 1e9
-                forms[name]["roofline"] = {"kernel": "k_fused_stage", "bound": "hbm", "achieved": ach,
-                                           "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                                           "bytes_per_cell_stage": [b1, b2], "kernel_ms": fk,
-                                           "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+            su, sw = (4, 4) if pr == ic.ICARUS_FP32 else (8, 4)
+            n1, n2, n3 = w.grid.n1, w.grid.n2, w.grid.n3
+            faces = {"flux_r": (n1 + 1) * n2 * n3, "flux_theta": n1 * (n2 + 1) * n3, "flux_phi": n1 * n2 * (n3 + 1)}
+            kbytes = {k: 8 * sw * (ncell + f) for k, f in faces.items()}
+            kbytes["update_1"] = ncell * (8 * sw + 8 * su + 3 * 8 * sw + sw + 8 * su + 8 * sw)
+            kbytes["update_2"] = kbytes["update_1"] + ncell * 8 * su
+            per_step = {k: fk[k] * (1 if k.startswith("update") else 2) for k in kbytes}
+            dk = max(per_step, key=per_step.get)
+            ach = kbytes[dk] / (fk[dk] * 1e-3) / 1e9
+            forms[name]["roofline"] = {"kernel": dk, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                                       "unit": "GB/s", "frac": ach / hbm_peak, "algorithmic_bytes": kbytes[dk],
+                                       "kernel_ms": fk, "peak_source": "measured (hbm_gbs)"}
             sf.close()
         if args.batch_members > 0:
             forms["batched_ensemble"] = run_batched(ic, torch, args)

@@ -91,8 +91,8 @@ typedef struct {
     icarus_alloc_fn alloc; /* device allocator (NULL: cudaMalloc); must return 256-B aligned */
     icarus_free_fn free;   /* matching free (NULL: cudaFree) */
     void *alloc_user;      /* passed to alloc / free */
-    int unfused;           /* 1: separate flux / div-B / update kernels even where one fused stage
-                              kernel exists (the FP32 and MIXED forms fuse by default) */
+    int fused;             /* 1: one fused stage kernel (fluxes, div B, update) instead of the separate
+                              kernels, FP32 and MIXED only (slower on GB300; see the design notes) */
     int init_vphi;         /* initial state's v_phi (Sect. 2.1 names none): ICARUS_IC_COROTATING
                               (0: at rest in the co-rotating frame) or ICARUS_IC_INERTIAL_RADIAL
                               (1: v_phi = -Omega r sin(theta), the inertially radial flow, parallel
@@ -179,7 +179,7 @@ void *icarus_get_stream(icarus_ctx *ctx);
  * launch of each kernel class: ms[ICARUS_KERNEL_CLASSES] = (ghost fill (3 kernels), flux r,
  * flux theta, flux phi, div B, update stage 1, update stage 2, probes, fused stage 1, fused
  * stage 2); a class the context does not launch reads 0 (the fused stage kernel replaces the
- * flux, div-B and update kernels of the FP32 and MIXED forms unless options.unfused is set). The
+ * flux, div-B and update kernels of the FP32 and MIXED forms when options.fused is set). The
  * steps advance the solution like icarus_step. Synchronous. */
 #define ICARUS_KERNEL_CLASSES 10
 int icarus_time_kernels(icarus_ctx *ctx, int n_steps, double *ms);

@@ -23,9 +23,17 @@ def _deps():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "icarus.h")]
 
 
+# translation units whose arithmetic is single precision (the FP32 and MIXED forms): IEEE-rounded
+# single-precision division and square root are replaced by the hardware approximations (a few
+# ulp) and float denormals flush to zero; double-precision code is unaffected by these flags
+SINGLE = {"kern_fp32.cu", "kern_mixed.cu", "batch_fp32.cu", "batch_mixed.cu"}
+SINGLE_FLAGS = ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]
+
+
 def _compile(src, verbose):
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [NVCC, "-c", src, "-o", obj] + ARCH + FLAGS + (["-Xptxas", "-v"] if verbose else [])
+    extra = SINGLE_FLAGS if os.path.basename(src) in SINGLE else []
+    cmd = [NVCC, "-c", src, "-o", obj] + ARCH + FLAGS + extra + (["-Xptxas", "-v"] if verbose else [])
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

@@ -204,7 +204,7 @@ void enqueue_step(icarus_ctx *c)
 {
     const Params &P = c->P;
     cudaStream_t s = c->stream;
-    if (c->ops.fused_stage && !c->opts.unfused) {
+    if (c->ops.fused_stage && c->opts.fused) {
         c->ops.fill_ghosts(P, c->U, c->W, 1, s);
         c->ops.fused_stage(P, 1, c->U, c->W, c->U1, c->W1, s);
         c->ops.fill_ghosts(P, c->U1, c->W1, 2, s);
@@ -227,7 +227,7 @@ void enqueue_step(icarus_ctx *c)
 
 int count_launches(const icarus_ctx *c)
 {
-    int per_stage = (c->ops.fused_stage && !c->opts.unfused) ? 3 + 1 : 3 + 3 + (c->P.divb == 1 ? 1 : 0) + 1;
+    int per_stage = (c->ops.fused_stage && c->opts.fused) ? 3 + 1 : 3 + 3 + (c->P.divb == 1 ? 1 : 0) + 1;
     return 2 * per_stage + (c->P.n_probes > 0 ? 1 : 0);
 }
 
@@ -618,7 +618,7 @@ int icarus_time_kernels(icarus_ctx *c, int n_steps, double *ms)
     if (!c || !ms || n_steps < 1) return fail(ICARUS_EINVAL, "bad argument");
     if (!c->have_state) return fail(ICARUS_ESTATE, "no state");
     const int NCLS = ICARUS_KERNEL_CLASSES;
-    const bool fused = c->ops.fused_stage && !c->opts.unfused;
+    const bool fused = c->ops.fused_stage && c->opts.fused;
     cudaEvent_t ev[2];
     CK(cudaEventCreate(&ev[0]));
     CK(cudaEventCreate(&ev[1]));

@@ -583,15 +583,28 @@ __device__ __forceinline__ void update_core(const Params &P, int i, int j, int k
         lb[2] = coef * (dbn[5] - dbn[4]) * (m.ih2[ip] * m.is3[jp] * m.ig3[k + NG]);
     }
     TS uo[NV];
-    const TS dts = (TS)dt;
+    if constexpr (Prec<TS, TW>::mixed) {
+        // MIXED: the increment dt L + (Linde term) is formed in single precision like the fluxes it
+        // comes from, and accumulated onto the FP64 state with one conversion per field
+        const TW dtw = TW(dt);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        TW inc = v >= B1 ? lb[v - B1] : (v == EN ? w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2] : TW(0));
-        if (STAGE == 1) {
-            uo[v] = Us[v * nt + c] + dts * (TS)L[v] + (TS)inc;
-        } else {
-            TS un = Uo[v * nt + c];     // U^n (updated in place)
-            uo[v] = TS(0.5) * un + TS(0.5) * (Us[v * nt + c] + dts * (TS)L[v] + (TS)inc);
+        for (int v = 0; v < NV; ++v) {
+            const TW inc = v >= B1 ? lb[v - B1] : (v == EN ? w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2] : TW(0));
+            const TW d = dtw * L[v] + inc;
+            if (STAGE == 1) uo[v] = Us[v * nt + c] + (TS)d;
+            else uo[v] = TS(0.5) * (Uo[v * nt + c] + Us[v * nt + c]) + (TS)(TW(0.5) * d);   // U^n in place
+        }
+    } else {
+        const TS dts = (TS)dt;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            TW inc = v >= B1 ? lb[v - B1] : (v == EN ? w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2] : TW(0));
+            if (STAGE == 1) {
+                uo[v] = Us[v * nt + c] + dts * (TS)L[v] + (TS)inc;
+            } else {
+                TS un = Uo[v * nt + c];     // U^n (updated in place)
+                uo[v] = TS(0.5) * un + TS(0.5) * (Us[v * nt + c] + dts * (TS)L[v] + (TS)inc);
+            }
         }
     }
     // non-finite check and floors

@@ -44,7 +44,7 @@ class icarus_options(C.Structure):
                 ("divb", C.c_int), ("divb_coef", C.c_double), ("rho_floor", C.c_double),
                 ("p_floor", C.c_double), ("precision", C.c_int), ("ring_capacity", C.c_int),
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("unfused", C.c_int), ("init_vphi", C.c_int)]
+                ("fused", C.c_int), ("init_vphi", C.c_int)]
 
 
 _lib = None
@@ -145,9 +145,9 @@ def make_grid(g: I.Grid) -> icarus_grid:
 
 
 def make_options(o: I.Options, precision=ICARUS_FP64, ring=4096, stream=None, allocator=None,
-                 unfused=False) -> icarus_options:
+                 fused=False) -> icarus_options:
     opt = icarus_options()
-    opt.unfused = int(bool(unfused))
+    opt.fused = int(bool(fused))
     opt.init_vphi = int(o.init_vphi)
     opt.cfl, opt.limiter, opt.flux, opt.gravity, opt.divb = o.cfl, o.limiter, o.flux, o.gravity, o.divb
     opt.divb_coef, opt.rho_floor, opt.p_floor = o.divb_coef, o.rho_floor, o.p_floor
@@ -269,12 +269,12 @@ class Solver:
     """One solver context on the current CUDA device, memory from torch's caching allocator."""
 
     def __init__(self, grid: I.Grid, gamma: float, omega: float, opts: I.Options, precision=ICARUS_FP64,
-                 ring=4096, device="cuda", unfused=False):
+                 ring=4096, device="cuda", fused=False):
         import torch
         self.torch = torch
         self.grid, self.precision = grid, precision
         self._alloc = _TorchAllocator(torch.device(device))
-        self._opts = make_options(opts, precision, ring, None, self._alloc, unfused)
+        self._opts = make_options(opts, precision, ring, None, self._alloc, fused)
         self._grid = make_grid(grid)
         self.ctx = icarus_init(self._grid, gamma, omega, self._opts)
         self.shape = (8, grid.n3, grid.n2, grid.n1)
@@ -326,8 +326,8 @@ class Solver:
         return icarus_launches_per_step(self.ctx)
 
 
-def from_workload(w: I.Workload, precision=ICARUS_FP64, ring=4096, unfused=False) -> Solver:
-    s = Solver(w.grid, w.gamma, w.omega, w.opts, precision, ring, unfused=unfused)
+def from_workload(w: I.Workload, precision=ICARUS_FP64, ring=4096, fused=False) -> Solver:
+    s = Solver(w.grid, w.gamma, w.omega, w.opts, precision, ring, fused=fused)
     s.set_boundary(w.t_maps, w.maps, w.cmes)
     return s
 

@@ -1,5 +1,5 @@
-"""The fused one-kernel stage of the single-precision forms (FP32 state, MIXED) against the
-separate flux / div-B / update kernels and against the FP64 oracle.
+"""The fused one-kernel stage of the single-precision forms (FP32 state, MIXED; options.fused)
+against the separate flux / div-B / update kernels and against the FP64 oracle.
 
 Both GPU paths compute the same face states, Riemann fluxes, div B and update in single precision
 (Sect. 2.1 scheme); they may differ only by the order in which the compiler contracts products into
@@ -64,7 +64,7 @@ def compare_paths(ic, make, U, t, prec, orc=None, steps=1):
 def test_fused_stage_grids(ic, prec, n):
     """Ragged tiles in r and theta, a phi chunk that is cut short (80 = 5 x 16), tiny grids."""
     w = I.config1(grid=I.Grid(*n))
-    make = lambda p, unf: ic.from_workload(w, precision=p, unfused=unf)
+    make = lambda p, unf: ic.from_workload(w, precision=p, fused=not unf)
     s = make(prec, False)
     U, t = s.get_state()
     s.close()
@@ -80,7 +80,7 @@ def test_fused_stage_grids(ic, prec, n):
 def test_fused_stage_options_perturbed(ic, prec, lim, flux, divb, grav):
     w = I.config0()
     w.opts = I.Options(limiter=lim, flux=flux, divb=divb, gravity=grav)
-    make = lambda p, unf: ic.from_workload(w, precision=p, unfused=unf)
+    make = lambda p, unf: ic.from_workload(w, precision=p, fused=not unf)
     s = make(prec, False)
     U, _ = s.get_state()
     s.close()
@@ -98,7 +98,7 @@ def test_fused_stage_options_perturbed(ic, prec, lim, flux, divb, grav):
 def test_fused_stage_twenty_steps_with_cme(ic, prec):
     """Twenty consecutive steps through the CME insertion window on a reduced grid."""
     w = I.config1(grid=I.Grid(48, 12, 24))
-    make = lambda p, unf: ic.from_workload(w, precision=p, unfused=unf)
+    make = lambda p, unf: ic.from_workload(w, precision=p, fused=not unf)
     s = make(prec, False)
     U, _ = s.get_state()
     s.close()
@@ -117,7 +117,7 @@ def test_fused_stage_cartesian_and_reflecting(ic, prec):
     W[1:4] = 0.3 * rng.standard_normal((3,) + W.shape[1:])
     W[4] = 1.0 + 0.2 * rng.random(W.shape[1:])
     W[5:8] = 0.5 * rng.standard_normal((3,) + W.shape[1:])
-    make = lambda p, unf: ic.Solver(g, 5 / 3, 0.0, o, precision=p, unfused=unf)
+    make = lambda p, unf: ic.Solver(g, 5 / 3, 0.0, o, precision=p, fused=not unf)
     compare_paths(ic, make, cons_from_prim(W, 5 / 3), 0.0, prec, Oracle(g, 5 / 3, 0.0, o))
     g = sph_grid(20, 10, 16, bc=(I.BC_REFLECT,) * 4 + (I.BC_PERIODIC,) * 2, r=(0.3, 1.0))
     o = I.Options(gravity=0)
@@ -126,5 +126,5 @@ def test_fused_stage_cartesian_and_reflecting(ic, prec):
     W[1:4] = 0.2 * rng.standard_normal((3,) + W.shape[1:])
     W[4] = 2.0 + rng.random(W.shape[1:])
     W[5:8] = 0.4 * rng.standard_normal((3,) + W.shape[1:])
-    make = lambda p, unf: ic.Solver(g, 1.5, I.OMEGA_SUN, o, precision=p, unfused=unf)
+    make = lambda p, unf: ic.Solver(g, 1.5, I.OMEGA_SUN, o, precision=p, fused=not unf)
     compare_paths(ic, make, cons_from_prim(W, 1.5), 0.0, prec, Oracle(g, 1.5, I.OMEGA_SUN, o))
