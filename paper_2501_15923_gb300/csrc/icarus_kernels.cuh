@@ -42,12 +42,15 @@ __device__ __forceinline__ void recover(const Params &P, const TS *u, TW *w, int
 // ghost fill along r: inner side driven by the maps (+ CME) or a plain rule, outer side a plain
 // rule. One thread per interior (j, k) column.
 template <typename TS, typename TW>
-__device__ __forceinline__ void bnd1_col(const Params &P, TS *__restrict__ U, TW *__restrict__ W, int stage, int j, int k)
+__device__ __forceinline__ void bnd1_col(const Params &P, TS *__restrict__ U, TW *__restrict__ W, int stage, int j, int k,
+                                         int task = -1)
 {
     const long long nt = P.nt;
     // inner face
     int bc = P.bc[0];
-    if (bc == 3) {
+    if (task >= NG) {
+        // outer-side layer only
+    } else if (bc == 3) {
         double tau = P.sc->t;
         if (stage == 2) tau = __dadd_rn(tau, P.sc->dt);
         // time bracket (clamped outside the table)
@@ -86,6 +89,7 @@ __device__ __forceinline__ void bnd1_col(const Params &P, TS *__restrict__ U, TW
         const double igm1 = 1.0 / (P.gamma - 1.0);
 #pragma unroll
         for (int g = 1; g <= NG; ++g) {
+            if (task >= 0 && task != g - 1) continue;
             long long cm_ = cidx(P, g - 1, j, k);
             long long cg = cidx(P, -g, j, k);
             double wg[NV], ug[NV];
@@ -104,6 +108,7 @@ __device__ __forceinline__ void bnd1_col(const Params &P, TS *__restrict__ U, TW
     } else {
 #pragma unroll
         for (int g = 1; g <= NG; ++g) {
+            if (task >= 0 && task != g - 1) continue;
             int src = bc == 1 ? 0 : (bc == 2 ? g - 1 : ((-g % P.n1) + P.n1) % P.n1);
             long long cs = cidx(P, src, j, k), cg = cidx(P, -g, j, k);
 #pragma unroll
@@ -120,6 +125,7 @@ __device__ __forceinline__ void bnd1_col(const Params &P, TS *__restrict__ U, TW
     bc = P.bc[1];
 #pragma unroll
     for (int g = 1; g <= NG; ++g) {
+        if (task >= 0 && task != NG + g - 1) continue;
         int gi = P.n1 - 1 + g;
         int src = bc == 1 ? P.n1 - 1 : (bc == 2 ? P.n1 - g : (gi % P.n1));
         long long cs = cidx(P, src, j, k), cg = cidx(P, gi, j, k);
@@ -150,13 +156,14 @@ __global__ void k_bnd1(Params P, TS *__restrict__ U, TW *__restrict__ W, int sta
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int k = blockIdx.y;
     if (j >= P.n2 || k >= P.n3) return;
-    bnd1_col<TS, TW>(P, U, W, stage, j, k);
+    bnd1_col<TS, TW>(P, U, W, stage, j, k, threadIdx.y);     // threadIdx.y: one of the 2 x NG layers
 }
 
 // ghost fill along theta (D = 1) or phi (D = 2) by copy / reflection / periodic images.
 // D = 1 covers every r (ghosts included) and interior phi; D = 2 covers everything.
 template <int D, typename TS, typename TW>
-__device__ __forceinline__ void bnd23_cell(const Params &P, TS *__restrict__ U, TW *__restrict__ W, int ip, int o)
+__device__ __forceinline__ void bnd23_cell(const Params &P, TS *__restrict__ U, TW *__restrict__ W, int ip, int o,
+                                           int task = -1)
 {
     int i = ip - NG;
     const int n = D == 1 ? P.n2 : P.n3;
@@ -166,6 +173,7 @@ __device__ __forceinline__ void bnd23_cell(const Params &P, TS *__restrict__ U, 
         int bc = P.bc[2 * D + side];
 #pragma unroll
         for (int g = 1; g <= NG; ++g) {
+            if (task >= 0 && task != side * NG + g - 1) continue;
             int gi = side == 0 ? -g : n - 1 + g;
             int src;
             if (bc == 1) src = side == 0 ? 0 : n - 1;
@@ -194,7 +202,7 @@ __global__ void k_bnd23(Params P, TS *__restrict__ U, TW *__restrict__ W)
     if (ip >= P.p1) return;
     if (D == 1 && o >= P.n3) return;
     if (D == 2 && o >= P.p2) return;
-    bnd23_cell<D, TS, TW>(P, U, W, ip, o);
+    bnd23_cell<D, TS, TW>(P, U, W, ip, o, threadIdx.y);       // threadIdx.y: one of the 2 x NG layers
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -407,9 +415,9 @@ __device__ __forceinline__ void finish_dt(Params &P, double smax_block, int adva
     }
 }
 
-// CFL signal speed of one cell: sum_d (|v_d| + c_f,d) / dx_d
+// CFL signal speed of one cell: sum_d (|v_d| + c_f,d) / dx_d, in the arithmetic type TW
 template <typename TW>
-__device__ __forceinline__ double cell_speed(const Params &P, const TW *w, int ip, int jp)
+__device__ __forceinline__ TW cell_speed_t(const Params &P, const TW *w, int ip, int jp)
 {
     const MetricsT<TW> &m = met<TW>(P);
     TW irho = TW(1) / w[0];
@@ -417,7 +425,13 @@ __device__ __forceinline__ double cell_speed(const Params &P, const TW *w, int i
     TW s1 = (rabs(w[1]) + fast_speed<TW>(w, irho, 0, g)) * m.iw1[ip];
     TW s2 = (rabs(w[2]) + fast_speed<TW>(w, irho, 1, g)) * (m.ih2[ip] * m.id2);
     TW s3 = (rabs(w[3]) + fast_speed<TW>(w, irho, 2, g)) * (m.ih2[ip] * m.is3[jp] * m.id3);
-    return (double)(s1 + s2 + s3);
+    return s1 + s2 + s3;
+}
+
+template <typename TW>
+__device__ __forceinline__ double cell_speed(const Params &P, const TW *w, int ip, int jp)
+{
+    return (double)cell_speed_t<TW>(P, w, ip, jp);
 }
 
 // double -> float by truncating the bit pattern, on the integer pipe (the FP64 pipe, which also
@@ -481,7 +495,8 @@ template <typename TW>
 __device__ __forceinline__ double cfl_block_speed(const Params &P, const TW *wo, int ip, int jp, bool valid)
 {
     if constexpr (sizeof(TW) == 4) {
-        return block_max(valid ? cell_speed<TW>(P, wo, ip, jp) : 0.0);
+        // single precision: reduce the float speeds, convert the block maximum once
+        return (double)block_max_all(valid ? cell_speed_t<TW>(P, wo, ip, jp) : 0.f);
     } else {
         const float e = valid ? cell_speed_est(P, wo, ip, jp) : 0.f;
         const float top = block_max_all(e);
@@ -891,9 +906,10 @@ template <typename TS, typename TW> struct Launch {
     {
         TS *u = (TS *)U;
         TW *w = (TW *)W;
-        k_bnd1<TS, TW><<<dim3(cdiv(P.n2, 64), P.n3), 64, 0, s>>>(P, u, w, stage);
-        k_bnd23<1, TS, TW><<<dim3(cdiv(P.p1, 64), P.n3), 64, 0, s>>>(P, u, w);
-        k_bnd23<2, TS, TW><<<dim3(cdiv(P.p1, 64), P.p2), 64, 0, s>>>(P, u, w);
+        const dim3 blk(64, 2 * NG);
+        k_bnd1<TS, TW><<<dim3(cdiv(P.n2, 64), P.n3), blk, 0, s>>>(P, u, w, stage);
+        k_bnd23<1, TS, TW><<<dim3(cdiv(P.p1, 64), P.n3), blk, 0, s>>>(P, u, w);
+        k_bnd23<2, TS, TW><<<dim3(cdiv(P.p1, 64), P.p2), blk, 0, s>>>(P, u, w);
     }
     static void flux_dir(const Params &P, int dir, const void *W, void *F, cudaStream_t s)
     {
