@@ -122,14 +122,16 @@ class Clocks:
 
 
 def kernel_source_hash():
-    """Hash of the sources the FP64 flux kernels are compiled from (device code and its
-    instantiation); the Ops table assignments at the end of the kernel header are excluded."""
+    """Hash of the sources the FP64 flux kernels are compiled from: the physics header, the flux
+    section of the kernel header (flux_tile .. k_flux) and the FP64 instantiation."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2501_15923_gb300", "csrc")
     for f in ("icarus_internal.cuh", "icarus_kernels.cuh", "kern_fp64.cu"):
         txt = open(os.path.join(csrc, f), "rb").read()
         if f == "icarus_kernels.cuh":
-            txt = txt.split(b"static Ops make()")[0]
+            a = txt.index(b"__device__ __forceinline__ void flux_tile(")
+            b = txt.index(b"// div B at every cell")
+            txt = txt[a:b]
         h.update(txt)
     return h.hexdigest()[:16]
 
