@@ -640,7 +640,14 @@ __device__ __forceinline__ void update_core(const Params &P, int i, int j, int k
         wo[4] = ph.p_floor;
         ++hits;
     }
-    if (hits) atomicAdd(&P.sc->floor_hits, (unsigned long long)hits);
+    if (hits) {
+        // one atomic per warp: the threads of the warp that hit a floor sum their counts first
+        // (in a long run a large part of the grid can sit at the pressure floor, and one counter
+        // taking an atomic from every such cell each stage serialises the update)
+        const unsigned act = __activemask();
+        const unsigned tot = __reduce_add_sync(act, (unsigned)hits);
+        if ((int)(threadIdx.x & 31) == __ffs(act) - 1) atomicAdd(&P.sc->floor_hits, (unsigned long long)tot);
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         Uo[v * nt + c] = uo[v];

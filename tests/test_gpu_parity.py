@@ -98,7 +98,12 @@ def test_options_perturbed_state(ic, lim, flux, divb, grav):
     Up = I.perturbed_state(U.shape, 11, U, 2e-2)
     Up[2] += 0.05 * np.abs(U[1]).max() * I.perturbed_state(U.shape[1:], 12, np.ones(U.shape[1:]), 1.0)
     Up[6] += 0.05 * np.abs(U[5]).max() * I.perturbed_state(U.shape[1:], 13, np.ones(U.shape[1:]), 1.0)
+    f0 = gpu.status()[1]
     assert_step(gpu, orc, Up, 0.01)
+    # this state has cells with negative pressure: the floors fire, and the counts (density and
+    # pressure resets over both stages, decided in FP64 on both sides) agree exactly
+    assert orc.floor_hits > 0
+    assert gpu.status()[1] - f0 == orc.floor_hits
     gpu.close()
 
 
