@@ -160,6 +160,35 @@ __device__ __forceinline__ bool is_zero(double x) { return ((__double2hiint(x) &
 __device__ __forceinline__ bool is_zero(float x) { return (__float_as_int(x) & 0x7fffffff) == 0; }
 __device__ __forceinline__ unsigned long long abs_bits(double x) { return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull; }
 __device__ __forceinline__ unsigned int abs_bits(float x) { return (unsigned int)__float_as_int(x) & 0x7fffffffu; }
+// binary32 <-> binary64 conversions on the integer pipe (on GB300 the FP64 pipe, which executes
+// the hardware conversions, runs at 1/64 of the FP32 rate). widen: exact for normal numbers and
+// zeros; subnormal inputs (absent under flush-to-zero arithmetic) give a signed zero; inf and NaN
+// keep their class.
+__device__ __forceinline__ double widen_f2d(float x)
+{
+    const unsigned b = __float_as_uint(x), sign = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+    unsigned lo = m << 29;
+    if (e == 0u) { hi = sign; lo = 0u; }
+    if (e == 0xffu) hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
+    return __hiloint2double((int)hi, (int)lo);
+}
+// narrow: IEEE round-to-nearest-even from the bit pattern (the 29 dropped mantissa bits decide;
+// a carry out of the mantissa moves into the exponent and, at the top, to infinity); results
+// below the normal range flush to a signed zero, as flush-to-zero arithmetic does
+__device__ __forceinline__ float narrow_d2f(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u, ax = hi & 0x7fffffffu;
+    const unsigned base = ((ax - 0x38000000u) << 3) | (lo >> 29);
+    const unsigned r = lo & 0x1fffffffu;
+    const unsigned up = (r > 0x10000000u || (r == 0x10000000u && (base & 1u))) ? 1u : 0u;
+    unsigned bits = sign | (base + up);
+    if (ax < 0x38100000u) bits = sign;
+    if (ax >= 0x47f00000u) bits = sign | 0x7f800000u | ((ax > 0x7ff00000u || (ax == 0x7ff00000u && lo)) ? 0x400000u : 0u);
+    return __uint_as_float(bits);
+}
+
 // x <= 0 (for non-NaN x)
 template <typename R> __device__ __forceinline__ bool not_positive(R x) { return hi_bits(x) < 0 || is_zero(x); }
 

@@ -33,7 +33,10 @@ __device__ __forceinline__ void recover(const Params &P, const TS *u, TW *w, int
     } else {
         TW uw[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) uw[v] = (TW)u[v];
+        for (int v = 0; v < NV; ++v) {
+            if constexpr (Prec<TS, TW>::mixed) uw[v] = narrow_d2f(u[v]);
+            else uw[v] = (TW)u[v];
+        }
         cons2prim<TW>(uw, w, phys<TW>(P).gm1);
     }
 }
@@ -600,14 +603,14 @@ __device__ __forceinline__ void update_core(const Params &P, int i, int j, int k
     TS uo[NV];
     if constexpr (Prec<TS, TW>::mixed) {
         // MIXED: the increment dt L + (Linde term) is formed in single precision like the fluxes it
-        // comes from, and accumulated onto the FP64 state with one conversion per field
-        const TW dtw = TW(dt);
+        // comes from, and accumulated onto the FP64 state with one exact widening per field
+        const TW dtw = narrow_d2f(dt);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const TW inc = v >= B1 ? lb[v - B1] : (v == EN ? w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2] : TW(0));
             const TW d = dtw * L[v] + inc;
-            if (STAGE == 1) uo[v] = Us[v * nt + c] + (TS)d;
-            else uo[v] = TS(0.5) * (Uo[v * nt + c] + Us[v * nt + c]) + (TS)(TW(0.5) * d);   // U^n in place
+            if (STAGE == 1) uo[v] = Us[v * nt + c] + widen_f2d(d);
+            else uo[v] = TS(0.5) * (Uo[v * nt + c] + Us[v * nt + c]) + widen_f2d(TW(0.5) * d);   // U^n in place
         }
     } else {
         const TS dts = (TS)dt;
