@@ -160,13 +160,14 @@ def profile_numbers():
 
 
 # ---------------------------------------------------------------------------------------------
-def cpu_oracle_rate(w, steps: int, max_seconds: float = 30.0):
-    """Time the FP64 oracle as it stands on the host cores (OpenMP, all cores)."""
+def cpu_oracle_rate(w, steps: int, max_seconds: float = 30.0, min_seconds: float = 12.0):
+    """Time the FP64 oracle as it stands on the host cores (OpenMP, all cores): at least `steps`
+    full steps, continued until about min_seconds of CPU work, never beyond max_seconds."""
     from oracle.oracle import from_workload as ofw
     o = ofw(w)
     t0 = time.perf_counter()
     n = 0
-    while n < steps:
+    while n < steps or time.perf_counter() - t0 < min_seconds:
         o.step()
         n += 1
         if time.perf_counter() - t0 > max_seconds:
