@@ -1,0 +1,92 @@
+"""Argument checking of the C ABI (host logic, no GPU): every rejected call returns its error code
+and message before any CUDA call, so these run on a machine without a GPU.
+
+Covers the degenerate inputs: empty grids, grids whose padded size overflows the 32-bit cell
+index, colatitude ranges whose ghost cells reach a pole, boundary codes on the wrong face, bad
+physics and numerics options, NULL contexts and negative step counts."""
+import ctypes as C
+import math
+
+import pytest
+
+from paper_2501_15923_gb300 import inputs as I
+
+EINVAL = -1
+
+
+@pytest.fixture(scope="module")
+def ic():
+    from paper_2501_15923_gb300 import build
+    build.build()
+    from paper_2501_15923_gb300 import icarus
+    return icarus
+
+
+def init_rc(ic, grid, gamma=1.5, opts=None, precision=0):
+    lib = ic.load()
+    o = ic.make_options(opts or I.Options(), precision)
+    ctx = C.c_void_p()
+    rc = lib.icarus_init(C.byref(ic.make_grid(grid)), gamma, 0.0, C.byref(o), C.byref(ctx))
+    return rc, lib.icarus_last_error().decode(), ctx
+
+
+def sph(n1=8, n2=12, n3=8, **kw):
+    g = I.Grid(n1, n2, n3)
+    for k, v in kw.items():
+        setattr(g, k, v)
+    return g
+
+
+@pytest.mark.parametrize("grid,msg", [
+    (sph(0, 12, 8), "cell counts"),
+    (sph(8, 0, 8), "cell counts"),
+    (sph(8, 12, 0), "cell counts"),
+    (sph(2000, 2000, 1000), "too large"),
+    (sph(geometry=7), "geometry"),
+    (sph(x1min=2.0, x1max=1.0), "empty coordinate range"),
+    (sph(x1min=0.0), "r_in"),
+    (sph(x2min=0.05, x2max=math.pi - 0.05), "colatitude"),
+])
+def test_bad_grids_rejected(ic, grid, msg):
+    rc, err, ctx = init_rc(ic, grid)
+    assert rc == EINVAL and msg in err, (rc, err)
+    assert not ctx.value
+
+
+def test_bad_boundary_codes_rejected(ic):
+    g = sph()
+    g.bc = (I.BC_DRIVEN, I.BC_DRIVEN, I.BC_CONT, I.BC_CONT, I.BC_PERIODIC, I.BC_PERIODIC)
+    rc, err, _ = init_rc(ic, g)
+    assert rc == EINVAL and "DRIVEN" in err
+    g.bc = (I.BC_DRIVEN, I.BC_CONT, I.BC_CONT, I.BC_CONT, 9, I.BC_PERIODIC)
+    rc, err, _ = init_rc(ic, g)
+    assert rc == EINVAL and "boundary code" in err
+    g = sph(n3=1)
+    g.bc = (I.BC_DRIVEN, I.BC_CONT, I.BC_CONT, I.BC_CONT, I.BC_REFLECT, I.BC_REFLECT)
+    rc, err, _ = init_rc(ic, g)
+    assert rc == EINVAL and "REFLECT" in err
+
+
+@pytest.mark.parametrize("gamma,opts,precision,msg", [
+    (1.0, I.Options(), 0, "gamma"),
+    (1.5, I.Options(cfl=0.0), 0, "cfl"),
+    (1.5, I.Options(cfl=1.5), 0, "cfl"),
+    (1.5, I.Options(limiter=3), 0, "limiter"),
+    (1.5, I.Options(flux=2), 0, "flux"),
+    (1.5, I.Options(divb=2), 0, "divb"),
+    (1.5, I.Options(init_vphi=2), 0, "init_vphi"),
+    (1.5, I.Options(), 3, "precision"),
+])
+def test_bad_options_rejected(ic, gamma, opts, precision, msg):
+    rc, err, _ = init_rc(ic, sph(), gamma, opts, precision)
+    assert rc == EINVAL and msg in err, (rc, err)
+
+
+def test_null_context_and_negative_counts(ic):
+    lib = ic.load()
+    assert lib.icarus_step(None, 1) == EINVAL
+    assert lib.icarus_set_boundary(None, 1, None, None, 0, None) == EINVAL
+    assert lib.icarus_sample(None, 1, 1, None, None, 1, None) == EINVAL
+    o = ic.make_options(I.Options())
+    assert lib.icarus_init(None, 1.5, 0.0, C.byref(o), None) == EINVAL
+    assert "NULL" in lib.icarus_last_error().decode()
