@@ -21,6 +21,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -160,10 +161,23 @@ def profile_numbers():
 
 
 # ---------------------------------------------------------------------------------------------
-def cpu_oracle_rate(w, steps: int, max_seconds: float = 30.0, min_seconds: float = 12.0):
-    """Time the FP64 oracle as it stands on the host cores (OpenMP, all cores): at least `steps`
-    full steps, continued until about min_seconds of CPU work, never beyond max_seconds."""
-    from oracle.oracle import from_workload as ofw
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
+def cpu_oracle_rate(w, steps: int, max_seconds: float = 30.0, min_seconds: float = 12.0, threads: int = 0):
+    """Time the FP64 oracle as it stands on the host cores (OpenMP; all cores, or `threads`): at
+    least `steps` full steps, continued until about min_seconds of CPU work, never beyond
+    max_seconds. Returns (Mcell-updates/s, steps, seconds, threads used)."""
+    from oracle.oracle import from_workload as ofw, set_threads
+    used = set_threads(threads if threads > 0 else (os.cpu_count() or 1))
     o = ofw(w)
     t0 = time.perf_counter()
     n = 0
@@ -173,7 +187,7 @@ def cpu_oracle_rate(w, steps: int, max_seconds: float = 30.0, min_seconds: float
         if time.perf_counter() - t0 > max_seconds:
             break
     el = time.perf_counter() - t0
-    return w.grid.ncell * n / el / 1e6, n, el
+    return w.grid.ncell * n / el / 1e6, n, el, used
 
 
 def run_reference(args):
@@ -187,7 +201,8 @@ def run_reference(args):
     w = workload(args.grid)
     cores = os.cpu_count()
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-    from oracle.oracle import from_workload as ofw
+    from oracle.oracle import from_workload as ofw, set_threads
+    cores = set_threads(cores)
     o = ofw(w)
     for _ in range(args.warmup):
         o.step()
@@ -436,9 +451,12 @@ def main(argv=None):
             "clocks": clocks, "roofline": roof, "e2e": e2e, "floor_hits": floor_hits,
             "gpu_launches": s.launches_per_step * args.steps, "forms": forms}
     if rank == 0 and not args.no_cpu and world == 1:
-        v, n, el = cpu_oracle_rate(w, steps=3, max_seconds=25.0)
-        line["cpu_baseline"] = {"value": v, "unit": "Mcell-updates/s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"{n} full steps of {w.name} ({el:.1f} s, OpenMP)"}
+        v, n, el, used = cpu_oracle_rate(w, steps=3, max_seconds=25.0)
+        v1, n1, el1, _ = cpu_oracle_rate(w, steps=1, max_seconds=20.0, min_seconds=8.0, threads=1)
+        line["cpu_baseline"] = {"value": v, "unit": "Mcell-updates/s", "cores": used, "kind": "oracle",
+                                "cpu_model": cpu_model(),
+                                "sample": f"{n} full steps of {w.name} ({el:.1f} s, OpenMP on {used} threads)",
+                                "single_thread": {"value": v1, "sample": f"{n1} full steps ({el1:.1f} s, 1 thread)"}}
     s.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

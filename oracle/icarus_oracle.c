@@ -27,6 +27,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---- constants (SI) ------------------------------------------------------------------------ */
 #define O_AU 1.495978707e11
@@ -851,4 +854,23 @@ void orc_sample(const orc_t *o, int n_probes, int n_knots, const double *traj, d
         q[9] = bmag * o->b0;
         q[10] = i; q[11] = j; q[12] = k;
     }
+}
+
+/* threads the oracle's OpenMP loops use (timing on the host cores; no effect on the results) */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

@@ -26,6 +26,8 @@ def lib():
         sig = {
             "orc_create": (P, [P, P, D, D, P, P]),
             "orc_destroy": (None, [P]),
+            "orc_set_threads": (None, [I]),
+            "orc_max_threads": (I, []),
             "orc_set_boundary": (I, [P, I, P, P, I, P]),
             "orc_init_state": (I, [P]),
             "orc_set_state": (None, [P, P, D]),
@@ -230,3 +232,10 @@ def restrict(Uf, vol_f):
     Uc = np.empty((8, f3 // 2, f2 // 2, f1 // 2))
     lib().orc_restrict(_ptr(Uf), _ptr(vol_f), _ptr(Uc), f1 // 2, f2 // 2, f3 // 2)
     return Uc
+
+
+def set_threads(n: int) -> int:
+    """Number of host threads the oracle's OpenMP loops use (for timing only); returns the new
+    maximum."""
+    lib().orc_set_threads(int(n))
+    return int(lib().orc_max_threads())
