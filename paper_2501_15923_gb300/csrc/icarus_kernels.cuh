@@ -551,16 +551,16 @@ template <typename TW> struct DivFactors {
 };
 
 // the update of one interior cell (i, j, k) from its primitives w, the flux divergence L (in:
-// per field, out: the full residual) and div B at its six neighbours; returns the cell's CFL
-// signal speed after a second stage (0 otherwise)
-template <int STAGE, typename TS, typename TW>
-__device__ __forceinline__ void update_core(const Params &P, int i, int j, int k, const TW *w, TW *L, const TW *dbn,
-                                            const TS *__restrict__ Us, TS *Uo, TW *__restrict__ Wo, TW *wo)
+// per field, out: the full residual), div B at its six neighbours, its stage-start state us(v)
+// and (second stage) U^n un(v) (accessors, so that loads sit where they are used): the new state
+// uo and primitives wo (floors applied and counted)
+template <int STAGE, typename TS, typename TW, typename LS, typename LN>
+__device__ __forceinline__ void update_math(const Params &P, int i, int j, int k, const TW *w, TW *L, const TW *dbn,
+                                            LS us, LN un, TS *uo, TW *wo)
 {
     const int ip = i + NG, jp = j + NG;
     const MetricsT<TW> &m = met<TW>(P);
     const PhysT<TW> &ph = phys<TW>(P);
-    const long long nt = P.nt, c = cidx(P, i, j, k);
     const double dt = P.sc->dt;
     if (P.geom == 0) {
         const TW rho = w[0], vr = w[1], vt = w[2], vp = w[3];
@@ -600,7 +600,6 @@ __device__ __forceinline__ void update_core(const Params &P, int i, int j, int k
         lb[1] = coef * (dbn[3] - dbn[2]) * (m.ih2[ip] * m.ig2[jp]);
         lb[2] = coef * (dbn[5] - dbn[4]) * (m.ih2[ip] * m.is3[jp] * m.ig3[k + NG]);
     }
-    TS uo[NV];
     if constexpr (Prec<TS, TW>::mixed) {
         // MIXED: the increment dt L + (Linde term) is formed in single precision like the fluxes it
         // comes from, and accumulated onto the FP64 state with one exact widening per field
@@ -609,20 +608,16 @@ __device__ __forceinline__ void update_core(const Params &P, int i, int j, int k
         for (int v = 0; v < NV; ++v) {
             const TW inc = v >= B1 ? lb[v - B1] : (v == EN ? w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2] : TW(0));
             const TW d = dtw * L[v] + inc;
-            if (STAGE == 1) uo[v] = Us[v * nt + c] + widen_f2d(d);
-            else uo[v] = TS(0.5) * (Uo[v * nt + c] + Us[v * nt + c]) + widen_f2d(TW(0.5) * d);   // U^n in place
+            if (STAGE == 1) uo[v] = us(v) + widen_f2d(d);
+            else uo[v] = TS(0.5) * (un(v) + us(v)) + widen_f2d(TW(0.5) * d);
         }
     } else {
         const TS dts = (TS)dt;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             TW inc = v >= B1 ? lb[v - B1] : (v == EN ? w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2] : TW(0));
-            if (STAGE == 1) {
-                uo[v] = Us[v * nt + c] + dts * (TS)L[v] + (TS)inc;
-            } else {
-                TS un = Uo[v * nt + c];     // U^n (updated in place)
-                uo[v] = TS(0.5) * un + TS(0.5) * (Us[v * nt + c] + dts * (TS)L[v] + (TS)inc);
-            }
+            if (STAGE == 1) uo[v] = us(v) + dts * (TS)L[v] + (TS)inc;
+            else uo[v] = TS(0.5) * un(v) + TS(0.5) * (us(v) + dts * (TS)L[v] + (TS)inc);
         }
     }
     // non-finite check and floors
@@ -651,6 +646,18 @@ __device__ __forceinline__ void update_core(const Params &P, int i, int j, int k
         const unsigned tot = __reduce_add_sync(act, (unsigned)hits);
         if ((int)(threadIdx.x & 31) == __ffs(act) - 1) atomicAdd(&P.sc->floor_hits, (unsigned long long)tot);
     }
+}
+
+// update_math of cell (i, j, k) with its state read from and written to the global arrays (U^n is
+// updated in place in the second stage)
+template <int STAGE, typename TS, typename TW>
+__device__ __forceinline__ void update_core(const Params &P, int i, int j, int k, const TW *w, TW *L, const TW *dbn,
+                                            const TS *__restrict__ Us, TS *Uo, TW *__restrict__ Wo, TW *wo)
+{
+    const long long nt = P.nt, c = cidx(P, i, j, k);
+    TS uo[NV];
+    update_math<STAGE, TS, TW>(P, i, j, k, w, L, dbn, [&](int v) { return Us[v * nt + c]; },
+                               [&](int v) { return Uo[v * nt + c]; }, uo, wo);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         Uo[v * nt + c] = uo[v];
@@ -703,6 +710,88 @@ k_update(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo,
     if (STAGE == 2) {
         const int i = valid ? (int)(tid % P.n1) : 0, j = valid ? (int)((tid / P.n1) % P.n2) : 0;
         finish_dt(P, cfl_block_speed<TW>(P, wo, i + NG, j + NG, valid), 1);
+    }
+}
+
+// single-precision primitives (FP32 and MIXED forms), n1 even: one thread updates the two cells
+// (i, i+1), i even, of a radial row with two-element vector loads and stores (every array offset
+// of such a pair is even: p1, n1, the field strides and the base addresses are), which halves the
+// memory instructions of this latency-bound kernel; the arithmetic is update_math per cell
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using t = float2; };
+template <> struct Vec2<double> { using t = double2; };
+
+template <int STAGE, typename TS, typename TW>
+__global__ void __launch_bounds__(256, 2)
+k_update_pair(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo, TW *__restrict__ Wo,
+              const TW *__restrict__ F1, const TW *__restrict__ F2, const TW *__restrict__ F3,
+              const TW *__restrict__ divB)
+{
+    using S2 = typename Vec2<TS>::t;
+    using W2 = typename Vec2<TW>::t;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int h = P.n1 / 2;
+    const bool valid = tid < (long long)h * P.n2 * P.n3;
+    TW wo[2][NV];
+    int i = 0, j = 0;
+    if (valid) {
+        i = 2 * (int)(tid % h);
+        const long long r_ = tid / h;
+        j = (int)(r_ % P.n2);
+        const int k = (int)(r_ / P.n2);
+        const long long nt = P.nt, c = cidx(P, i, j, k);
+        const long long s1 = (long long)P.n3 * P.n2 * (P.n1 + 1), f1 = ((long long)k * P.n2 + j) * (P.n1 + 1) + i;
+        const long long s2 = (long long)P.n3 * (P.n2 + 1) * P.n1, f2 = ((long long)k * (P.n2 + 1) + j) * P.n1 + i;
+        const long long s3 = (long long)(P.n3 + 1) * P.n2 * P.n1, f3 = ((long long)k * P.n2 + j) * P.n1 + i;
+        const long long o3 = (long long)P.n2 * P.n1;
+        const DivFactors<TW> dv0(met<TW>(P), i + NG, j + NG), dv1(met<TW>(P), i + 1 + NG, j + NG);
+        TW w[2][NV], L[2][NV], dbn[2][6];
+        TS us[2][NV], un[2][NV], uo[2][NV];
+        (void)us; (void)un;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const W2 wv = *reinterpret_cast<const W2 *>(Ws + v * nt + c);
+            w[0][v] = wv.x; w[1][v] = wv.y;
+            const TW a0 = F1[v * s1 + f1], a1 = F1[v * s1 + f1 + 1], a2 = F1[v * s1 + f1 + 2];
+            const W2 b0 = *reinterpret_cast<const W2 *>(F2 + v * s2 + f2);
+            const W2 b1 = *reinterpret_cast<const W2 *>(F2 + v * s2 + f2 + P.n1);
+            const W2 e0 = *reinterpret_cast<const W2 *>(F3 + v * s3 + f3);
+            const W2 e1 = *reinterpret_cast<const W2 *>(F3 + v * s3 + f3 + o3);
+            L[0][v] = dv0.div(a0, a1, b0.x, b1.x, e0.x, e1.x);
+            L[1][v] = dv1.div(a1, a2, b0.y, b1.y, e0.y, e1.y);
+            const S2 u2 = *reinterpret_cast<const S2 *>(Us + v * nt + c);
+            us[0][v] = u2.x; us[1][v] = u2.y;
+            if (STAGE == 2) {
+                const S2 n2 = *reinterpret_cast<const S2 *>(Uo + v * nt + c);
+                un[0][v] = n2.x; un[1][v] = n2.y;
+            } else {
+                un[0][v] = un[1][v] = TS(0);
+            }
+        }
+        if (P.divb == 1) {
+            const long long q2 = P.p1, q3 = (long long)P.p1 * P.p2;
+            const W2 d0 = *reinterpret_cast<const W2 *>(divB + c);
+            const W2 dm2 = *reinterpret_cast<const W2 *>(divB + c - q2), dp2 = *reinterpret_cast<const W2 *>(divB + c + q2);
+            const W2 dm3 = *reinterpret_cast<const W2 *>(divB + c - q3), dp3 = *reinterpret_cast<const W2 *>(divB + c + q3);
+            dbn[0][0] = divB[c - 1]; dbn[0][1] = d0.y; dbn[0][2] = dm2.x; dbn[0][3] = dp2.x; dbn[0][4] = dm3.x; dbn[0][5] = dp3.x;
+            dbn[1][0] = d0.x; dbn[1][1] = divB[c + 2]; dbn[1][2] = dm2.y; dbn[1][3] = dp2.y; dbn[1][4] = dm3.y; dbn[1][5] = dp3.y;
+        }
+        update_math<STAGE, TS, TW>(P, i, j, k, w[0], L[0], dbn[0], [&](int v) { return us[0][v]; },
+                                   [&](int v) { return un[0][v]; }, uo[0], wo[0]);
+        update_math<STAGE, TS, TW>(P, i + 1, j, k, w[1], L[1], dbn[1], [&](int v) { return us[1][v]; },
+                                   [&](int v) { return un[1][v]; }, uo[1], wo[1]);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            S2 u2; u2.x = uo[0][v]; u2.y = uo[1][v];
+            *reinterpret_cast<S2 *>(Uo + v * nt + c) = u2;
+            W2 w2; w2.x = wo[0][v]; w2.y = wo[1][v];
+            *reinterpret_cast<W2 *>(Wo + v * nt + c) = w2;
+        }
+    }
+    if (STAGE == 2) {
+        TW sp = TW(0);
+        if (valid) sp = fmaxf(cell_speed_t<TW>(P, wo[0], i + NG, j + NG), cell_speed_t<TW>(P, wo[1], i + 1 + NG, j + NG));
+        finish_dt(P, (double)block_max_all(sp), 1);
     }
 }
 
@@ -943,6 +1032,16 @@ template <typename TS, typename TW> struct Launch {
                        const void *F1, const void *F2, const void *F3, const void *D, cudaStream_t s)
     {
         long long n = (long long)P.n1 * P.n2 * P.n3;
+        if constexpr (sizeof(TW) == 4) if (P.n1 % 2 == 0) {
+            const long long np = n / 2;
+            if (stage == 1)
+                k_update_pair<1, TS, TW><<<cdiv(np, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo,
+                    (TW *)Wo, (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
+            else
+                k_update_pair<2, TS, TW><<<cdiv(np, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo,
+                    (TW *)Wo, (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
+            return;
+        }
         if (stage == 1)
             k_update<1, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo, (TW *)Wo,
                 (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
