@@ -713,10 +713,11 @@ k_update(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo,
     }
 }
 
-// single-precision primitives (FP32 and MIXED forms), n1 even: one thread updates the two cells
-// (i, i+1), i even, of a radial row with two-element vector loads and stores (every array offset
-// of such a pair is even: p1, n1, the field strides and the base addresses are), which halves the
-// memory instructions of this latency-bound kernel; the arithmetic is update_math per cell
+// FP32 form, n1 even: one thread updates the two cells (i, i+1), i even, of a radial row with
+// two-element vector loads and stores (every array offset of such a pair is even: p1, n1, the
+// field strides and the base addresses are), which halves the memory instructions of this
+// latency-bound kernel; the arithmetic is update_math per cell. (Measured on the MIXED form it was
+// slower than one cell per thread: its FP64 state doubles the registers a pair needs.)
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using t = float2; };
 template <> struct Vec2<double> { using t = double2; };
@@ -1032,7 +1033,7 @@ template <typename TS, typename TW> struct Launch {
                        const void *F1, const void *F2, const void *F3, const void *D, cudaStream_t s)
     {
         long long n = (long long)P.n1 * P.n2 * P.n3;
-        if constexpr (sizeof(TW) == 4) if (P.n1 % 2 == 0) {
+        if constexpr (sizeof(TS) == 4 && sizeof(TW) == 4) if (P.n1 % 2 == 0) {
             const long long np = n / 2;
             if (stage == 1)
                 k_update_pair<1, TS, TW><<<cdiv(np, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo,
