@@ -97,10 +97,18 @@ typedef struct {
                               (0: at rest in the co-rotating frame) or ICARUS_IC_INERTIAL_RADIAL
                               (1: v_phi = -Omega r sin(theta), the inertially radial flow, parallel
                               to the spiral field) */
+    int cme_model;         /* cone CME at the inner boundary (Sect. 3.2): ICARUS_CME_WINDOW (0): the cone
+                              of the half-width over [t_on, t_on + duration); ICARUS_CME_SPHERE (1): a
+                              spherical cloud of radius r_in sin(half-width) moving out along the
+                              axis at the CME speed, its leading point at r_in at t_on; the footprint
+                              is the part of the r_in sphere inside the cloud, for 2 R / speed (the
+                              duration entry is not used) */
 } icarus_options;
 
 #define ICARUS_IC_COROTATING 0
 #define ICARUS_IC_INERTIAL_RADIAL 1
+#define ICARUS_CME_WINDOW 0
+#define ICARUS_CME_SPHERE 1
 
 typedef struct icarus_ctx icarus_ctx;
 

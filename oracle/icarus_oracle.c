@@ -64,6 +64,7 @@ typedef struct {
     double cfl, divb_coef, rho_floor, p_floor;
     int limiter, flux, gravity, divb;
     int init_vphi;   /* initial v_phi: 0 at rest in the co-rotating frame, 1 inertially radial */
+    int cme_model;   /* 0: cone footprint over a fixed window; 1: spherical cloud crossing r_in */
     double t0, p0, b0;       /* code-unit scales */
     double *U, *U0, *U1, *L, *W, *F[3], *divB, *Ufix;
     double t;
@@ -259,9 +260,14 @@ static void map_value(const orc_t *o, double tau, int j, int k, double *out5)
     }
 }
 
-/* cone CME (Sect. 3.2): a boundary column lies in the cone when the angle between its centre
- * direction and the CME axis is at most the half-width; the test compares the dot product of
- * the two unit vectors with cos(half-width). Later CMEs override earlier ones. */
+/* cone CME (Sect. 3.2): a boundary column lies in the CME when the angle alpha between its
+ * centre direction and the CME axis is small enough; the test compares the dot product of the two
+ * unit vectors, cos(alpha), with a threshold. Model 0: the cone of the half-width omega over the
+ * window [t_on, t_on + duration): threshold cos(omega). Model 1: a spherical cloud of radius
+ * R = r_in sin(omega) whose centre moves out along the axis at the CME speed v, its leading point
+ * reaching r_in at t_on (centre distance d = r_in - R + v (tau - t_on)); a column at r_in is inside
+ * while |r_in e - d a| <= R, i.e. cos(alpha) >= (r_in^2 + d^2 - R^2) / (2 r_in d), for
+ * tau in [t_on, t_on + 2 R / v) (the duration entry is not used). Later CMEs override earlier ones. */
 static int cme_hit(const orc_t *o, double tau, int j, int k, double *out5)
 {
     int hit = 0;
@@ -269,11 +275,19 @@ static int cme_hit(const orc_t *o, double tau, int j, int k, double *out5)
     double ex = sin(th) * cos(ph), ey = sin(th) * sin(ph), ez = cos(th);
     for (int c = 0; c < o->n_cme; c++) {
         const double *q = o->cme + 8 * c;
-        if (!(tau >= q[0] && tau < q[0] + q[1])) continue;
+        double thr = cos(q[4]);
+        if (o->cme_model == 1) {
+            double rb = o->xmin[0], R = rb * sin(q[4]);
+            if (!(tau >= q[0] && tau < q[0] + 2.0 * R / q[5])) continue;
+            double d = (rb - R) + q[5] * (tau - q[0]);
+            thr = (rb * rb + d * d - R * R) / (2.0 * rb * d);
+        } else if (!(tau >= q[0] && tau < q[0] + q[1])) {
+            continue;
+        }
         double lat = q[2], lon = q[3];
         double ax = cos(lat) * cos(lon), ay = cos(lat) * sin(lon), az = sin(lat);
         double dot = ex * ax + ey * ay + ez * az;
-        if (dot >= cos(q[4])) {
+        if (dot >= thr) {
             out5[0] = q[6];   /* rho (code) */
             out5[1] = q[5];   /* v_r */
             out5[2] = q[7];   /* p */
@@ -581,6 +595,7 @@ orc_t *orc_create(const int *ig, const double *dg, double gamma, double omega_si
     o->omega = omega_si * o->t0;
     o->cfl = od[0]; o->divb_coef = od[1]; o->rho_floor = od[2]; o->p_floor = od[3];
     o->limiter = oi[0]; o->flux = oi[1]; o->gravity = oi[2]; o->divb = oi[3]; o->init_vphi = oi[4];
+    o->cme_model = oi[5];
     o->gm = O_GM / (O_AU * O_V0 * O_V0);
     if (o->geom == GEOM_CART) { o->omega = 0.0; o->gravity = 0; }
     size_t sz = sizeof(double) * NV * o->nt;

@@ -76,7 +76,8 @@ class Oracle:
         ig = np.array([grid.n1, grid.n2, grid.n3, grid.geometry, grid.stretch, *grid.bc], dtype=np.int32)
         dg = np.array([grid.x1min, grid.x1max, grid.x2min, grid.x2max, grid.x3min, grid.x3max])
         od = np.array([opts.cfl, opts.divb_coef, opts.rho_floor, opts.p_floor])
-        oi = np.array([opts.limiter, opts.flux, opts.gravity, opts.divb, opts.init_vphi], dtype=np.int32)
+        oi = np.array([opts.limiter, opts.flux, opts.gravity, opts.divb, opts.init_vphi, opts.cme_model],
+                      dtype=np.int32)
         self.h = lib().orc_create(_ptr(ig), _ptr(dg), gamma, omega, _ptr(od), _ptr(oi))
         self.shape = (NV, grid.n3, grid.n2, grid.n1)
         self.pshape = (NV, grid.n3 + 2 * NG, grid.n2 + 2 * NG, grid.n1 + 2 * NG)

@@ -295,8 +295,8 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     if (!(gamma > 1.0)) return fail(ICARUS_EINVAL, "gamma must be > 1");
     if (!(opts->cfl > 0.0 && opts->cfl <= 1.0)) return fail(ICARUS_EINVAL, "cfl must be in (0, 1]");
     if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 1 || opts->divb < 0 || opts->divb > 1 ||
-        opts->init_vphi < 0 || opts->init_vphi > 1)
-        return fail(ICARUS_EINVAL, "bad limiter / flux / divb / init_vphi option");
+        opts->init_vphi < 0 || opts->init_vphi > 1 || opts->cme_model < 0 || opts->cme_model > 1)
+        return fail(ICARUS_EINVAL, "bad limiter / flux / divb / init_vphi / cme_model option");
     if (opts->precision < 0 || opts->precision > 2) return fail(ICARUS_EINVAL, "bad precision");
     if (opts->ring_capacity < 1) return fail(ICARUS_EINVAL, "ring_capacity must be >= 1");
     icarus_ctx *c = new icarus_ctx();
@@ -319,6 +319,8 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     for (int s = 0; s < 6; ++s) P.bc[s] = grid->bc[s];
     P.limiter = opts->limiter; P.flux = opts->flux; P.gravity = opts->gravity; P.divb = opts->divb;
     P.init_vphi = opts->init_vphi;
+    P.cme_model = opts->cme_model;
+    P.r_in = grid->x1min;
     P.gamma = gamma;
     P.divb_coef = opts->divb_coef; P.rho_floor = opts->rho_floor; P.p_floor = opts->p_floor;
     c->t0 = AU / V0;
@@ -393,10 +395,10 @@ int icarus_set_boundary(icarus_ctx *c, int n_maps, const double *t_maps, const d
             dst[4 * per + q] = src[4 * per + q] / c->b0;
         }
     }
-    std::vector<double> hc(9 * (size_t)(n_cme > 0 ? n_cme : 1));
+    std::vector<double> hc(10 * (size_t)(n_cme > 0 ? n_cme : 1));
     for (int q = 0; q < n_cme; ++q) {
         const double *s = cmes + 8 * q;
-        double *d = hc.data() + 9 * q;
+        double *d = hc.data() + 10 * q;
         d[0] = s[0] / c->t0;
         d[1] = s[1] / c->t0;
         d[2] = cos(s[2]) * cos(s[3]);
@@ -406,6 +408,9 @@ int icarus_set_boundary(icarus_ctx *c, int n_maps, const double *t_maps, const d
         d[6] = s[5] / V0;
         d[7] = s[6] / N0;
         d[8] = 2.0 * s[6] * KB * s[7] / c->p0;
+        // spherical cloud: radius in AU, and the crossing time 2 R / v as the window length
+        d[9] = c->grid.x1min * sin(s[4]);
+        if (c->P.cme_model == ICARUS_CME_SPHERE) d[1] = 2.0 * d[9] / d[6];
     }
     CK(cudaStreamSynchronize(c->stream));
     if (hm.size() > c->maps_cap) {

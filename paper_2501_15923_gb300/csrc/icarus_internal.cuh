@@ -72,8 +72,9 @@ struct Params {
     int n1, n2, n3, p1, p2, p3;
     long long nt;
     int geom, bc[6];
-    int limiter, flux, gravity, divb, init_vphi;
+    int limiter, flux, gravity, divb, init_vphi, cme_model;
     double gamma, omega, divb_coef, rho_floor, p_floor;
+    double r_in;                    // inner radius (AU; x1min of the grid)
     Metrics m;
     MetricsT<float> mf;             // float roundings of m
     PhysT<double> ph;
@@ -82,7 +83,7 @@ struct Params {
     int n_maps, n_cme;
     const double *t_maps;   // [n_maps]
     const double *maps;     // [n_maps][5][n2][n3] (v_r, rho, p, B_r, B_phi)
-    const double *cme;      // [n_cme][8] (t_on, dur, ax, ay, az, cos_hw, v_r, rho) + p in [n_cme] extra
+    const double *cme;      // [n_cme][10] (t_on, dur, ax, ay, az, cos_hw, v_r, rho, p, R = r_in sin(hw))
     // probes
     int n_probes, n_knots, ring_cap;
     const double *traj;     // [P][K][4] SI

@@ -83,11 +83,20 @@ __device__ __forceinline__ void bnd1_col(const Params &P, TS *__restrict__ U, TW
         }
         // cone CME: footprint by the dot product of unit vectors against cos(half-width)
         for (int c = 0; c < P.n_cme; ++c) {
-            const double *cm = P.cme + 9 * c;
+            const double *cm = P.cme + 10 * c;
             if (!(tau >= cm[0] && tau < __dadd_rn(cm[0], cm[1]))) continue;
+            double thr = cm[5];
+            if (P.cme_model == 1) {
+                // spherical cloud: centre at d = r_in - R + v (tau - t_on) on the axis; a column
+                // at r_in is inside while cos(alpha) >= (r_in^2 + d^2 - R^2) / (2 r_in d)
+                const double r0 = P.r_in, R = cm[9];
+                const double d = __dadd_rn(__dsub_rn(r0, R), __dmul_rn(cm[6], __dsub_rn(tau, cm[0])));
+                thr = __ddiv_rn(__dsub_rn(__dadd_rn(__dmul_rn(r0, r0), __dmul_rn(d, d)), __dmul_rn(R, R)),
+                                __dmul_rn(__dmul_rn(2.0, r0), d));
+            }
             double ex = P.m.colvec[col], ey = P.m.colvec[per + col], ez = P.m.colvec[2 * per + col];
             double dot = __dadd_rn(__dadd_rn(__dmul_rn(ex, cm[2]), __dmul_rn(ey, cm[3])), __dmul_rn(ez, cm[4]));
-            if (dot >= cm[5]) { q[0] = cm[7]; q[1] = cm[6]; q[2] = cm[8]; }
+            if (dot >= thr) { q[0] = cm[7]; q[1] = cm[6]; q[2] = cm[8]; }
         }
         const double igm1 = 1.0 / (P.gamma - 1.0);
 #pragma unroll

@@ -44,7 +44,7 @@ class icarus_options(C.Structure):
                 ("divb", C.c_int), ("divb_coef", C.c_double), ("rho_floor", C.c_double),
                 ("p_floor", C.c_double), ("precision", C.c_int), ("ring_capacity", C.c_int),
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("fused", C.c_int), ("init_vphi", C.c_int)]
+                ("fused", C.c_int), ("init_vphi", C.c_int), ("cme_model", C.c_int)]
 
 
 _lib = None
@@ -149,6 +149,7 @@ def make_options(o: I.Options, precision=ICARUS_FP64, ring=4096, stream=None, al
     opt = icarus_options()
     opt.fused = int(bool(fused))
     opt.init_vphi = int(o.init_vphi)
+    opt.cme_model = int(o.cme_model)
     opt.cfl, opt.limiter, opt.flux, opt.gravity, opt.divb = o.cfl, o.limiter, o.flux, o.gravity, o.divb
     opt.divb_coef, opt.rho_floor, opt.p_floor = o.divb_coef, o.rho_floor, o.p_floor
     opt.precision, opt.ring_capacity = precision, ring

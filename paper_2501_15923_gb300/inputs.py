@@ -46,6 +46,7 @@ LIM_MINMOD, LIM_VANLEER, LIM_MC = 0, 1, 2
 FLUX_TVDLF, FLUX_HLL = 0, 1
 DIVB_NONE, DIVB_LINDE = 0, 1
 IC_COROTATING, IC_INERTIAL_RADIAL = 0, 1     # initial v_phi: at rest co-rotating / radial inertial flow
+CME_WINDOW, CME_SPHERE = 0, 1                # cone footprint over a fixed window / spherical cloud crossing
 
 
 class SplitMix64:
@@ -114,6 +115,7 @@ class Options:
     rho_floor: float = 1e-6               # code units (n in cm^-3)
     p_floor: float = 1e-9                 # code units (p / (m_p 1e6 m^-3 (100 km/s)^2))
     init_vphi: int = IC_COROTATING        # initial v_phi: IC_COROTATING (0) or IC_INERTIAL_RADIAL
+    cme_model: int = CME_WINDOW           # CME_WINDOW (0) or CME_SPHERE (1)
 
 
 @dataclass

@@ -75,6 +75,7 @@ def test_bad_boundary_codes_rejected(ic):
     (1.5, I.Options(flux=2), 0, "flux"),
     (1.5, I.Options(divb=2), 0, "divb"),
     (1.5, I.Options(init_vphi=2), 0, "init_vphi"),
+    (1.5, I.Options(cme_model=2), 0, "cme_model"),
     (1.5, I.Options(), 3, "precision"),
 ])
 def test_bad_options_rejected(ic, gamma, opts, precision, msg):

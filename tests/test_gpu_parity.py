@@ -129,6 +129,27 @@ def test_dynamic_maps_and_cme_window(ic):
     gpu.close()
 
 
+def test_sphere_cme_crossing(ic):
+    """Spherical-cloud CME option: steps while the cloud crosses the inner boundary (footprint
+    growing, full, shrinking) and one after it has passed; the footprint is decided by the same
+    FP64 operations on both sides, so the boundary ghosts agree exactly."""
+    g = I.Grid(48, 12, 24)
+    w = I.config1(grid=g)
+    w.opts.cme_model = I.CME_SPHERE
+    gpu, orc = ic.from_workload(w), oracle_workload(w)
+    sc = orc.scales()
+    U, _ = gpu.get_state()
+    t_on = w.cmes[0, 0] / sc["t0"]
+    cross = 2.0 * g.x1min * math.sin(w.cmes[0, 4]) / (w.cmes[0, 5] / 1e5)
+    for f in (0.2, 0.37, 0.8, 1.3):
+        assert_step(gpu, orc, U, t_on + f * cross)
+    _, hit = orc.boundary_values(t_on + 0.37 * cross)
+    assert hit.sum() > 0
+    _, hit = orc.boundary_values(t_on + 1.01 * cross)
+    assert hit.sum() == 0
+    gpu.close()
+
+
 def test_ragged_grid_sizes(ic):
     """Sizes that are not multiples of any block edge (ragged tails in every kernel)."""
     for n in ((37, 9, 7), (129, 17, 33), (2, 10, 3)):

@@ -625,6 +625,52 @@ def test_P9_phi_wrap_and_corotation():
         assert abs(q[1] / 1e6 - expect) < 1e-9
 
 
+def test_P10_sphere_cme_footprint_brute_force():
+    """Spherical-cloud CME (cme_model 1): the footprint at r_in is the set of boundary column
+    centres inside the moving sphere, checked by Cartesian distances to the sphere centre
+    (independent of the oracle's cos(alpha) threshold); it grows from nothing to the full cone
+    of the half-width (reached when the centre is at r_in cos(omega)) and shrinks back, over the
+    crossing time 2 R / v with R = r_in sin(omega); the duration entry plays no part."""
+    g = sph_grid(8, 24, 48, bc=(D, C, C, C, P, P))
+    o = Oracle(g, 1.5, 0.0, opts(cme_model=I.CME_SPHERE))
+    mp = np.ones((1, 5, 24, 48))
+    hw, v, t_on = math.radians(30.0), 1.2e6, 3600.0
+    cme = np.array([[t_on, 123.0, math.radians(10.0), math.radians(200.0), hw, v, 1e9, 8e5]])
+    o.set_boundary(np.zeros(1), mp, cme)
+    sc = o.scales()
+    t0 = sc["t0"]
+    rb = g.x1min                                   # AU
+    R = rb * math.sin(hw)
+    v_au = v / 1.495978707e11                      # AU per second
+    tc, pc = centres(g, 1)[2:-2], centres(g, 2)[2:-2]
+    TH, PH = np.meshgrid(tc, pc, indexing="ij")
+    X = rb * np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)])
+    lat, lon = cme[0, 2], cme[0, 3]
+    ax = np.array([math.cos(lat) * math.cos(lon), math.cos(lat) * math.sin(lon), math.sin(lat)])
+    cross = 2 * R / v_au                           # s
+    counts = []
+    for f in (0.02, 0.1, 0.366, 0.7, 0.95):
+        tt = t_on + f * cross
+        d = rb - R + v_au * (tt - t_on)
+        dist2 = ((X - d * ax[:, None, None]) ** 2).sum(0)
+        inside = dist2 <= R * R
+        assert np.all(np.abs(dist2 - R * R) > 1e-12 * R * R)       # no centre on the surface
+        _, hit = o.boundary_values(tt / t0)
+        assert np.array_equal(hit.astype(bool), inside), f
+        counts.append(int(inside.sum()))
+    assert counts[0] < counts[1] < counts[2] and counts[2] > counts[3] > counts[4], counts
+    # at d = r_in cos(omega) the footprint is the full cone: the window model's set
+    ow = Oracle(g, 1.5, 0.0, opts())
+    ow.set_boundary(np.zeros(1), mp, np.array([[t_on, 8 * 3600.0, lat, lon, hw, v, 1e9, 8e5]]))
+    t_full = t_on + (rb * math.cos(hw) - (rb - R)) / v_au
+    _, hs = o.boundary_values(t_full / t0)
+    _, hw_ = ow.boundary_values(t_full / t0)
+    assert abs(int(hs.sum()) - int(hw_.sum())) <= 2 and hs.sum() > 10
+    for tt in (0.0, t_on - 1.0, t_on + cross + 1.0, t_on + 8 * 3600.0):
+        _, hit = o.boundary_values(tt / t0)
+        assert hit.sum() == 0
+
+
 def test_P10_cme_footprint_brute_force():
     g = sph_grid(8, 24, 48, bc=(D, C, C, C, P, P))
     o = Oracle(g, 1.5, 0.0, opts())
