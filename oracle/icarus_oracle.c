@@ -48,7 +48,7 @@ enum { RHO = 0, M1 = 1, M2 = 2, M3 = 3, EN = 4, B1 = 5, B2 = 6, B3 = 7, NV = 8 }
 enum { BC_PERIODIC = 0, BC_CONT = 1, BC_REFLECT = 2, BC_DRIVEN = 3, BC_FIXED = 4 };
 enum { GEOM_SPH = 0, GEOM_CART = 1 };
 enum { LIM_MINMOD = 0, LIM_VANLEER = 1, LIM_MC = 2 };
-enum { FLUX_TVDLF = 0, FLUX_HLL = 1 };
+enum { FLUX_TVDLF = 0, FLUX_HLL = 1, FLUX_HLLD = 2 };
 enum { DIVB_NONE = 0, DIVB_LINDE = 1 };
 
 #define NG 2
@@ -190,10 +190,91 @@ static double limit(int lim, double a, double b)
     return a > 0.0 ? m : -m;
 }
 
+/* HLLD (Miyoshi & Kusano 2005): four intermediate states separated by the entropy wave S_M and
+ * the rotational waves S*_L, S*_R inside the fast waves S_L = min(u_L, u_R) - max(c_fL, c_fR),
+ * S_R = max(u_L, u_R) + max(c_fL, c_fR). The normal field in the intermediate states is the mean
+ * of the two face states. Where rho (S - u)(S - S_M) - B_n^2 vanishes (degenerate fast / Alfven
+ * waves), the star state keeps the outer tangential velocity and field. */
+static void hlld(const orc_t *o, const double *wl, const double *wr, int d, double *f)
+{
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    double ul[NV], ur[NV], fl[NV], fr[NV];
+    prim2cons(o, wl, ul);
+    prim2cons(o, wr, ur);
+    phys_flux(o, wl, ul, d, fl);
+    phys_flux(o, wr, ur, d, fr);
+    const double cl = fast_speed(o, wl, d), cr = fast_speed(o, wr, d);
+    const double uL = wl[1 + d], uR = wr[1 + d];
+    const double cmax = fmax(cl, cr);
+    const double SL = fmin(uL, uR) - cmax, SR = fmax(uL, uR) + cmax;
+    if (SL > 0.0) { for (int v = 0; v < NV; v++) f[v] = fl[v]; return; }
+    if (SR < 0.0) { for (int v = 0; v < NV; v++) f[v] = fr[v]; return; }
+    const double bn = 0.5 * (wl[5 + d] + wr[5 + d]);
+    const double ptL = wl[4] + 0.5 * (wl[5] * wl[5] + wl[6] * wl[6] + wl[7] * wl[7]);
+    const double ptR = wr[4] + 0.5 * (wr[5] * wr[5] + wr[6] * wr[6] + wr[7] * wr[7]);
+    const double aL = (SL - uL) * wl[0], aR = (SR - uR) * wr[0];       /* mass fluxes relative to S */
+    const double SM = (aR * uR - aL * uL - ptR + ptL) / (aR - aL);
+    const double pts = (aR * ptL - aL * ptR + aL * aR * (uR - uL)) / (aR - aL);
+    /* star states: index 0 left, 1 right */
+    double us[2][NV], vt[2][2], bt[2][2], rs[2];
+    for (int s = 0; s < 2; s++) {
+        const double *w = s ? wr : wl, *u = s ? ur : ul;
+        const double S = s ? SR : SL, a = s ? aR : aL, un = w[1 + d], pt = s ? ptR : ptL;
+        const double rho = a / (S - SM);
+        const double den = a * (S - SM) - bn * bn;
+        const double scale = a * (S - un) + bn * bn;
+        double vy = w[1 + t1], vz = w[1 + t2], by = w[5 + t1], bz = w[5 + t2];
+        if (fabs(den) > 1e-12 * scale) {
+            const double cv = bn * (SM - un) / den, cb = (a * (S - un) - bn * bn) / den;
+            vy = w[1 + t1] - by * cv; vz = w[1 + t2] - bz * cv;
+            by = w[5 + t1] * cb; bz = w[5 + t2] * cb;
+        }
+        const double vb = w[1] * w[5] + w[2] * w[6] + w[3] * w[7];
+        const double vbs = SM * bn + vy * by + vz * bz;
+        const double e = ((S - un) * u[EN] - pt * un + pts * SM + bn * (vb - vbs)) / (S - SM);
+        rs[s] = rho;
+        vt[s][0] = vy; vt[s][1] = vz; bt[s][0] = by; bt[s][1] = bz;
+        us[s][RHO] = rho;
+        us[s][M1 + d] = rho * SM; us[s][M1 + t1] = rho * vy; us[s][M1 + t2] = rho * vz;
+        us[s][EN] = e;
+        us[s][B1 + d] = bn; us[s][B1 + t1] = by; us[s][B1 + t2] = bz;
+    }
+    const double sqL = sqrt(rs[0]), sqR = sqrt(rs[1]);
+    const double SsL = SM - fabs(bn) / sqL, SsR = SM + fabs(bn) / sqR;
+    if (SsL >= 0.0) {                               /* F*_L */
+        for (int v = 0; v < NV; v++) f[v] = fl[v] + SL * (us[0][v] - ul[v]);
+        return;
+    }
+    if (SsR <= 0.0) {                               /* F*_R */
+        for (int v = 0; v < NV; v++) f[v] = fr[v] + SR * (us[1][v] - ur[v]);
+        return;
+    }
+    /* double-star states (shared tangential velocity and field) */
+    const double sg = bn > 0.0 ? 1.0 : (bn < 0.0 ? -1.0 : 0.0), isum = 1.0 / (sqL + sqR);
+    double vss[2], bss[2];
+    for (int c = 0; c < 2; c++) {
+        vss[c] = (sqL * vt[0][c] + sqR * vt[1][c] + (bt[1][c] - bt[0][c]) * sg) * isum;
+        bss[c] = (sqL * bt[1][c] + sqR * bt[0][c] + sqL * sqR * (vt[1][c] - vt[0][c]) * sg) * isum;
+    }
+    const double vbss = SM * bn + vss[0] * bss[0] + vss[1] * bss[1];
+    const int s = SM >= 0.0 ? 0 : 1;                /* side of the entropy wave */
+    const double sq = s ? sqR : sqL, Ss = s ? SsR : SsL, S = s ? SR : SL;
+    const double *uo = s ? ur : ul, *fo = s ? fr : fl;
+    const double vbs = SM * bn + vt[s][0] * bt[s][0] + vt[s][1] * bt[s][1];
+    double uss[NV];
+    uss[RHO] = rs[s];
+    uss[M1 + d] = rs[s] * SM; uss[M1 + t1] = rs[s] * vss[0]; uss[M1 + t2] = rs[s] * vss[1];
+    uss[EN] = us[s][EN] + (s ? 1.0 : -1.0) * sq * (vbs - vbss) * sg;
+    uss[B1 + d] = bn; uss[B1 + t1] = bss[0]; uss[B1 + t2] = bss[1];
+    for (int v = 0; v < NV; v++) f[v] = fo[v] + S * (us[s][v] - uo[v]) + Ss * (uss[v] - us[s][v]);
+}
+
 /* TVDLF: F = (F_L + F_R)/2 - c_max (U_R - U_L)/2, c_max = max(|v_n| + c_f) over L and R.
- * HLL:   F = (s_R F_L - s_L F_R + s_L s_R (U_R - U_L)) / (s_R - s_L), upwinded outside the fan. */
+ * HLL:   F = (s_R F_L - s_L F_R + s_L s_R (U_R - U_L)) / (s_R - s_L), upwinded outside the fan.
+ * HLLD:  see hlld(). */
 static void riemann(const orc_t *o, const double *wl, const double *wr, int d, double *f)
 {
+    if (o->flux == FLUX_HLLD) { hlld(o, wl, wr, d, f); return; }
     double ul[NV], ur[NV], fl[NV], fr[NV];
     prim2cons(o, wl, ul);
     prim2cons(o, wr, ur);
@@ -889,3 +970,11 @@ int orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* the face flux of the configured Riemann solver for primitive face states wl, wr (code units)
+ * normal to direction d (test access to one face) */
+void orc_riemann(const orc_t *o, const double *wl, const double *wr, int d, double *f)
+{
+    riemann(o, wl, wr, d, f);
+}
+

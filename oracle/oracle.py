@@ -27,6 +27,7 @@ def lib():
             "orc_create": (P, [P, P, D, D, P, P]),
             "orc_destroy": (None, [P]),
             "orc_set_threads": (None, [I]),
+            "orc_riemann": (None, [P, P, P, I, P]),
             "orc_max_threads": (I, []),
             "orc_set_boundary": (I, [P, I, P, P, I, P]),
             "orc_init_state": (I, [P]),
@@ -156,6 +157,13 @@ class Oracle:
         hit = np.empty((g.n2, g.n3), dtype=np.int32)
         lib().orc_boundary_values(self.h, float(tau), _ptr(out), _ptr(hit))
         return out, hit
+
+    def riemann(self, wl, wr, d: int) -> np.ndarray:
+        """Face flux of the configured Riemann solver for primitive states wl, wr (code units)."""
+        f = np.empty(8)
+        a, b = _c(wl), _c(wr)
+        lib().orc_riemann(self.h, _ptr(a), _ptr(b), int(d), _ptr(f))
+        return f
 
     @property
     def floor_hits(self) -> int:

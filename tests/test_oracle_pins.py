@@ -179,7 +179,7 @@ def shock_tube(n, d, flux, lim, wl, wr, b=(0.0, 0.0, 0.0), gamma=1.4, t_end=0.2)
 
 
 @pytest.mark.parametrize("d", [0, 1, 2])
-@pytest.mark.parametrize("flux", [I.FLUX_TVDLF, I.FLUX_HLL])
+@pytest.mark.parametrize("flux", [I.FLUX_TVDLF, I.FLUX_HLL, I.FLUX_HLLD])
 def test_P3_sod_against_exact_riemann(d, flux):
     wl, wr = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
     errs = []
@@ -192,6 +192,125 @@ def test_P3_sod_against_exact_riemann(d, flux):
     errs = np.array(errs)
     assert errs[1, 0] < (0.012 if flux == I.FLUX_TVDLF else 0.009), errs
     assert np.all(errs[1] < errs[0] * 0.8), errs   # converging (first order at discontinuities)
+
+
+def _one_step_1d(W, gamma, flux, n):
+    g = cart_grid(n, 1, 1, L=(1.0, 1e3, 1e3), bc=(C, C, P, P, P, P))
+    o = Oracle(g, gamma, 0.0, opts(divb=I.DIVB_NONE, flux=flux, cfl=0.5))
+    U = cons_from_prim(W, gamma).reshape(8, 1, 1, n)
+    o.set_state(U)
+    o.step()
+    return U, o.get_state()[0]
+
+
+@pytest.mark.parametrize("flux,exact_kept", [(I.FLUX_HLLD, True), (I.FLUX_HLL, False)])
+def test_P3b_hlld_keeps_stationary_contact(flux, exact_kept):
+    """A stationary contact with a normal field (density jump only; u, v_t, p, B continuous) is an
+    exact discontinuous solution; HLLD reproduces it to round-off, HLL smears it."""
+    n = 64
+    x = (np.arange(n) + 0.5) / n
+    W = np.zeros((8, n))
+    W[0] = np.where(x < 0.5, 1.0, 0.2)
+    W[4] = 1.0
+    W[5], W[6], W[7] = 0.8, 0.5, -0.3
+    U0, U1 = _one_step_1d(W, 5 / 3, flux, n)
+    d = np.abs(U1 - U0).max() / np.abs(U0).max()
+    if exact_kept:
+        assert d < 1e-13, d
+    else:
+        assert d > 1e-3, d
+
+
+@pytest.mark.parametrize("flux,exact_kept", [(I.FLUX_HLLD, True), (I.FLUX_HLL, False)])
+def test_P3b_hlld_keeps_stationary_rotational_discontinuity(flux, exact_kept):
+    """A stationary rotational discontinuity, built from the Rankine-Hugoniot conditions with zero
+    speed: rho, p, u = -B_n / sqrt(rho), B_n and |B_t| continuous, B_t rotates by 90 degrees and
+    v_t = v0 - B_t / sqrt(rho) (so [rho u v_t - B_n B_t] = [u B_t - B_n v_t] = 0 and the energy flux
+    matches). HLLD resolves it to round-off; HLL smears it."""
+    n = 64
+    x = (np.arange(n) + 0.5) / n
+    rho, bn = 1.3, 0.9
+    sq = np.sqrt(rho)
+    by = np.where(x < 0.5, 0.7, 0.0)
+    bz = np.where(x < 0.5, 0.0, 0.7)
+    v0 = (0.2, -0.1)
+    W = np.zeros((8, n))
+    W[0], W[4], W[5] = rho, 0.6, bn
+    W[1] = -bn / sq
+    W[6], W[7] = by, bz
+    W[2], W[3] = v0[0] - by / sq, v0[1] - bz / sq
+    U0, U1 = _one_step_1d(W, 5 / 3, flux, n)
+    d = np.abs(U1 - U0).max() / np.abs(U0).max()
+    if exact_kept:
+        assert d < 1e-12, d
+    else:
+        assert d > 1e-3, d
+
+
+def _face_state(d, rho, un, vt, p, bn, bt):
+    """Primitive state with normal direction d: (n, t1, t2) components mapped cyclically."""
+    w = np.zeros(8)
+    w[0], w[4] = rho, p
+    w[1 + d], w[1 + (d + 1) % 3], w[1 + (d + 2) % 3] = un, vt[0], vt[1]
+    w[5 + d], w[5 + (d + 1) % 3], w[5 + (d + 2) % 3] = bn, bt[0], bt[1]
+    return w
+
+
+@pytest.mark.parametrize("d", [0, 2])
+def test_P3c_hlld_face_flux_exact_for_moving_contacts_and_rotations(d):
+    """HLLD is exact for isolated contacts and rotational discontinuities at any speed: the face
+    flux equals the flux of the state the exact solution has at the face (x / t = 0), which is the
+    solver's own flux of that state on both sides (consistency). Moving rotational discontinuities
+    put the face inside the double-star states (between S_M and S*_R, or S*_L and S_M), so every
+    intermediate-state formula enters; HLL is not exact for either wave."""
+    g = cart_grid(4, 4, 4)
+    hd = Oracle(g, 5 / 3, 0.0, opts(flux=I.FLUX_HLLD))
+    hl = Oracle(g, 5 / 3, 0.0, opts(flux=I.FLUX_HLL))
+    bt, vt = (0.5, -0.3), (0.1, -0.2)
+    cases = []
+    # contacts with a normal field, moving right (face sees the left state) and left
+    for u in (0.4, -0.4):
+        wa = _face_state(d, 1.0, u, vt, 0.7, 0.8, bt)
+        wb = _face_state(d, 0.3, u, vt, 0.7, 0.8, bt)
+        cases.append((wa, wb, wa if u > 0 else wb))
+    # rotational discontinuities: B_t turns by 90 degrees at constant |B_t|; right-going
+    # (speed u + B_n / sqrt(rho) > 0 with u < 0, v_t = v0 - B_t / sqrt(rho)) and left-going
+    # (speed u - B_n / sqrt(rho) < 0 with u > 0, v_t = v0 + B_t / sqrt(rho)), from the
+    # Rankine-Hugoniot conditions
+    rho, bn, p, v0 = 1.3, 0.9, 0.6, np.array([0.2, -0.1])
+    sq = math.sqrt(rho)
+    ba, bb = np.array([0.7, 0.0]), np.array([0.0, 0.7])
+    for u, sgn in ((-0.3, -1.0), (0.3, 1.0)):
+        wa = _face_state(d, rho, u, v0 + sgn * ba / sq, p, bn, ba)
+        wb = _face_state(d, rho, u, v0 + sgn * bb / sq, p, bn, bb)
+        cases.append((wa, wb, wa if u < 0 else wb))
+    # contact and rotational discontinuity together, densities differing: a | contact (u) | c |
+    # RD (u + B_n / sqrt(rho_b)) | b with u < 0 < the RD speed; the face sits in state c, which
+    # has the density of b and the tangential velocity and field of a (and the mirror image: RD
+    # going left on the left of a contact moving right). The double-star weights of the two
+    # densities enter here.
+    ra, rb_ = 1.6, 0.5
+    u = -0.25
+    va = v0.copy()
+    vb = va - (bb - ba) / math.sqrt(rb_)
+    wa = _face_state(d, ra, u, va, p, bn, ba)
+    wb = _face_state(d, rb_, u, vb, p, bn, bb)
+    cases.append((wa, wb, _face_state(d, rb_, u, va, p, bn, ba)))
+    u = 0.25
+    vb = v0.copy()
+    va = vb - (bb - ba) / math.sqrt(ra)
+    wa = _face_state(d, ra, u, va, p, bn, ba)
+    wb = _face_state(d, rb_, u, vb, p, bn, bb)
+    cases.append((wa, wb, _face_state(d, ra, u, vb, p, bn, bb)))
+    for wa, wb, wexact in cases:
+        f = hd.riemann(wa, wb, d)
+        fe = hd.riemann(wexact, wexact, d)
+        assert np.allclose(f, fe, rtol=0, atol=1e-13 * np.abs(fe).max()), (f, fe)
+        fh = hl.riemann(wa, wb, d)
+        assert np.abs(fh - fe).max() > 1e-3 * np.abs(fe).max()
+    # consistency of HLLD and HLL with the physical flux on equal states
+    w = _face_state(d, 1.1, 0.3, vt, 0.8, 0.6, bt)
+    assert np.allclose(hd.riemann(w, w, d), hl.riemann(w, w, d), rtol=1e-15, atol=1e-15)
 
 
 def test_P3_sod_star_state():
@@ -234,7 +353,7 @@ def test_P3_brio_wu_invariants():
 
 
 # ---------------------------------------------------------------------------------------------
-def wave_error(n, d, mode, lim, gamma=5.0 / 3.0, eps=1e-6):
+def wave_error(n, d, mode, lim, gamma=5.0 / 3.0, eps=1e-6, flux=0):
     """Linear MHD eigenmode along direction d: L1 error after one wave period."""
     # background flow 0.25 along the wave so that no mode (entropy included) stands still
     w0 = np.array([1.0, 0.25, 0.0, 0.0, 1.0 / gamma, 1.0, math.sqrt(2.0), 0.5])
@@ -245,7 +364,7 @@ def wave_error(n, d, mode, lim, gamma=5.0 / 3.0, eps=1e-6):
     nn = [1, 1, 1]
     nn[d] = n
     g = cart_grid(*nn, L=L)
-    o = Oracle(g, gamma, 0.0, opts(divb=I.DIVB_NONE, limiter=lim, cfl=0.8))
+    o = Oracle(g, gamma, 0.0, opts(divb=I.DIVB_NONE, limiter=lim, cfl=0.8, flux=flux))
     x = (np.arange(n) + 0.5) / n
     avg = math.sin(math.pi / n) / (math.pi / n)           # cell average of cos(2 pi x)
     pert = np.outer(Rv[:, mode], np.cos(2 * np.pi * x) * avg) * eps
@@ -277,6 +396,19 @@ def test_P4_linear_waves_second_order(d, mode, lim):
     term changes the propagation speed or shape and the error stays O(1)."""
     e1 = wave_error(64, d, mode, lim)
     e2 = wave_error(128, d, mode, lim)
+    order = math.log2(e1 / e2)
+    assert order > 1.8, (e1, e2, order)
+    assert e2 < 0.02, e2
+
+
+@pytest.mark.parametrize("d", [0, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 6])
+def test_P4_linear_waves_second_order_hlld(d, mode):
+    """The same eigenmodes with the HLLD flux: every intermediate state (star and double-star,
+    the Alfven mode passes through the double-star states) enters, so a wrong term in any of them
+    spoils the propagation or the order."""
+    e1 = wave_error(64, d, mode, I.LIM_MC, flux=I.FLUX_HLLD)
+    e2 = wave_error(128, d, mode, I.LIM_MC, flux=I.FLUX_HLLD)
     order = math.log2(e1 / e2)
     assert order > 1.8, (e1, e2, order)
     assert e2 < 0.02, e2
