@@ -294,10 +294,12 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     if (rc) return rc;
     if (!(gamma > 1.0)) return fail(ICARUS_EINVAL, "gamma must be > 1");
     if (!(opts->cfl > 0.0 && opts->cfl <= 1.0)) return fail(ICARUS_EINVAL, "cfl must be in (0, 1]");
-    if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 1 || opts->divb < 0 || opts->divb > 1 ||
+    if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 2 || opts->divb < 0 || opts->divb > 1 ||
         opts->init_vphi < 0 || opts->init_vphi > 1 || opts->cme_model < 0 || opts->cme_model > 1)
         return fail(ICARUS_EINVAL, "bad limiter / flux / divb / init_vphi / cme_model option");
     if (opts->precision < 0 || opts->precision > 2) return fail(ICARUS_EINVAL, "bad precision");
+    if (opts->fused && opts->flux == ICARUS_FLUX_HLLD)
+        return fail(ICARUS_EINVAL, "the fused stage kernel supports the TVDLF and HLL fluxes only");
     if (opts->ring_capacity < 1) return fail(ICARUS_EINVAL, "ring_capacity must be >= 1");
     icarus_ctx *c = new icarus_ctx();
     c->grid = *grid;

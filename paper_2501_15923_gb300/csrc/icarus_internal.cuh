@@ -209,9 +209,99 @@ template <typename R> __device__ __forceinline__ R limiter(int lim, R a, R b)
     return hi_bits(a) >= 0 ? m : -m;
 }
 
-// Riemann flux across a face normal to d from left / right primitive states.
-// TVDLF: (F_L + F_R)/2 - c_max (U_R - U_L)/2; HLL with signal speeds from the fast speeds.
+// HLLD (Miyoshi & Kusano 2005): intermediate states separated by the entropy wave S_M and the
+// rotational waves S*_L, S*_R inside S_L = min(u_L, u_R) - max(c_fL, c_fR), S_R = max(u_L, u_R) +
+// max(c_fL, c_fR); the normal field of the intermediate states is the mean of the two faces'; a
+// degenerate star state (rho (S - u)(S - S_M) - B_n^2 vanishing) keeps the outer tangential
+// velocity and field. ul, ur, fl, fr: conserved states and physical fluxes of the face states.
 template <typename R>
+__device__ __forceinline__ void hlld(const R *wl, const R *wr, const R *ul, const R *ur, const R *fl, const R *fr,
+                                     R cl, R cr, int d, R *f)
+{
+    const int t1 = d == 0 ? 1 : (d == 1 ? 2 : 0), t2 = d == 0 ? 2 : (d == 1 ? 0 : 1);
+    const R uL = wl[1 + d], uR = wr[1 + d];
+    const R cmax = rmax(cl, cr);
+    const R SL = rmin(uL, uR) - cmax, SR = rmax(uL, uR) + cmax;
+    if (SL > R(0)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) f[v] = fl[v];
+        return;
+    }
+    if (SR < R(0)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) f[v] = fr[v];
+        return;
+    }
+    const R bn = R(0.5) * (wl[5 + d] + wr[5 + d]);
+    const R ptL = wl[4] + R(0.5) * (wl[5] * wl[5] + wl[6] * wl[6] + wl[7] * wl[7]);
+    const R ptR = wr[4] + R(0.5) * (wr[5] * wr[5] + wr[6] * wr[6] + wr[7] * wr[7]);
+    const R aL = (SL - uL) * wl[0], aR = (SR - uR) * wr[0];
+    const R SM = (aR * uR - aL * uL - ptR + ptL) / (aR - aL);
+    const R pts = (aR * ptL - aL * ptR + aL * aR * (uR - uL)) / (aR - aL);
+    R us[2][NV], vt[2][2], bt[2][2], rs[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const R *w = s ? wr : wl, *u = s ? ur : ul;
+        const R S = s ? SR : SL, a = s ? aR : aL, un = w[1 + d], pt = s ? ptR : ptL;
+        const R rho = a / (S - SM);
+        const R den = a * (S - SM) - bn * bn;
+        const R scale = a * (S - un) + bn * bn;
+        R vy = w[1 + t1], vz = w[1 + t2], by = w[5 + t1], bz = w[5 + t2];
+        if (rabs(den) > R(1e-12) * scale) {
+            const R cv = bn * (SM - un) / den, cb = (a * (S - un) - bn * bn) / den;
+            vy = w[1 + t1] - by * cv; vz = w[1 + t2] - bz * cv;
+            by = w[5 + t1] * cb; bz = w[5 + t2] * cb;
+        }
+        const R vb = w[1] * w[5] + w[2] * w[6] + w[3] * w[7];
+        const R vbs = SM * bn + vy * by + vz * bz;
+        const R e = ((S - un) * u[EN] - pt * un + pts * SM + bn * (vb - vbs)) / (S - SM);
+        rs[s] = rho;
+        vt[s][0] = vy; vt[s][1] = vz; bt[s][0] = by; bt[s][1] = bz;
+        us[s][RHO] = rho;
+        us[s][M1 + d] = rho * SM; us[s][M1 + t1] = rho * vy; us[s][M1 + t2] = rho * vz;
+        us[s][EN] = e;
+        us[s][B1 + d] = bn; us[s][B1 + t1] = by; us[s][B1 + t2] = bz;
+    }
+    const R sqL = sqrt(rs[0]), sqR = sqrt(rs[1]);
+    const R SsL = SM - rabs(bn) / sqL, SsR = SM + rabs(bn) / sqR;
+    if (SsL >= R(0)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) f[v] = fl[v] + SL * (us[0][v] - ul[v]);
+        return;
+    }
+    if (SsR <= R(0)) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) f[v] = fr[v] + SR * (us[1][v] - ur[v]);
+        return;
+    }
+    const R sg = bn > R(0) ? R(1) : (bn < R(0) ? R(-1) : R(0)), isum = R(1) / (sqL + sqR);
+    R vss[2], bss[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        vss[c] = (sqL * vt[0][c] + sqR * vt[1][c] + (bt[1][c] - bt[0][c]) * sg) * isum;
+        bss[c] = (sqL * bt[1][c] + sqR * bt[0][c] + sqL * sqR * (vt[1][c] - vt[0][c]) * sg) * isum;
+    }
+    const R vbss = SM * bn + vss[0] * bss[0] + vss[1] * bss[1];
+    const bool s = SM < R(0);                       // side of the entropy wave (selects, no indexing)
+    const R sq = s ? sqR : sqL, Ss = s ? SsR : SsL, S = s ? SR : SL, rS = s ? rs[1] : rs[0];
+    const R vbs = SM * bn + (s ? vt[1][0] * bt[1][0] + vt[1][1] * bt[1][1] : vt[0][0] * bt[0][0] + vt[0][1] * bt[0][1]);
+    R uss[NV];
+    uss[RHO] = rS;
+    uss[M1 + d] = rS * SM; uss[M1 + t1] = rS * vss[0]; uss[M1 + t2] = rS * vss[1];
+    uss[EN] = (s ? us[1][EN] : us[0][EN]) + (s ? R(1) : R(-1)) * sq * (vbs - vbss) * sg;
+    uss[B1 + d] = bn; uss[B1 + t1] = bss[0]; uss[B1 + t2] = bss[1];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const R uo = s ? ur[v] : ul[v], fo = s ? fr[v] : fl[v], u1 = s ? us[1][v] : us[0][v];
+        f[v] = fo + S * (u1 - uo) + Ss * (uss[v] - u1);
+    }
+}
+
+// Riemann flux across a face normal to d from left / right primitive states.
+// TVDLF: (F_L + F_R)/2 - c_max (U_R - U_L)/2; HLL with signal speeds from the fast speeds (flux
+// chosen at run time); HLLD when HD (a separate instantiation, so that the larger solver does not
+// weigh on the registers of the other two)
+template <typename R, bool HD = false>
 __device__ __forceinline__ void riemann(const R *wl, const R *wr, int d, int flux, R gamma, R igm1, R *f)
 {
     R ul[NV], ur[NV];
@@ -257,7 +347,10 @@ __device__ __forceinline__ void riemann(const R *wl, const R *wr, int d, int flu
         ff[B2] = vn * w[6] - bn * w[2];
         ff[B3] = vn * w[7] - bn * w[3];
     }
-    if (flux == 0) {
+    if constexpr (HD) {
+        (void)flux;
+        hlld<R>(wl, wr, ul, ur, fl, fr, cl, cr, d, f);
+    } else if (flux == 0) {
         R c = rmax(rabs(wl[1 + d]) + cl, rabs(wr[1 + d]) + cr);
 #pragma unroll
         for (int v = 0; v < NV; ++v) f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * c * (ur[v] - ul[v]);

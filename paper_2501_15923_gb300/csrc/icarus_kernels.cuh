@@ -224,7 +224,7 @@ __global__ void k_bnd23(Params P, TS *__restrict__ U, TW *__restrict__ W)
 // A tile is BX x BY threads; along D it covers S - 1 faces (S = BX for D = 0, BY otherwise).
 // D = 0: faces f0 .. f0+BX-2 of BY consecutive (j) rows; D = 1, 2: BY-1 faces along D for BX
 // consecutive r. Must be called by every thread of the block (it synchronises the block).
-template <int D, int BX, int BY, typename TW>
+template <int D, int BX, int BY, typename TW, bool HD = false>
 __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict__ W, TW *__restrict__ F,
                                           int bx, int by, int bz, int tx, int ty, TW *sW, TW *sP)
 {
@@ -316,7 +316,7 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
 #pragma unroll
             for (int v = 0; v < NV; ++v) { wl[v] = sW[v * sz + pl]; wr[v] = wc[v]; }
         }
-        riemann<TW>(wl, wr, D, P.flux, phys<TW>(P).gamma, phys<TW>(P).igm1, f);
+        riemann<TW, HD>(wl, wr, D, P.flux, phys<TW>(P).gamma, phys<TW>(P).igm1, f);
         long long fi, fs;
         if (D == 0) { fi = ((long long)k * P.n2 + j) * (P.n1 + 1) + s; fs = (long long)P.n3 * P.n2 * (P.n1 + 1); }
         else if (D == 1) { fi = ((long long)k * (P.n2 + 1) + s) * P.n1 + i; fs = (long long)P.n3 * (P.n2 + 1) * P.n1; }
@@ -339,14 +339,14 @@ template <int D> struct FluxShape {
     static constexpr int BY = D == 0 ? 1 : 16;
 };
 
-template <int D, typename TW>
+template <int D, typename TW, bool HD = false>
 __global__ void __launch_bounds__(FluxShape<D>::BX * FluxShape<D>::BY)
 k_flux(Params P, const TW *__restrict__ W, TW *__restrict__ F)
 {
     constexpr int BX = FluxShape<D>::BX, BY = FluxShape<D>::BY;
     __shared__ TW sW[NV * BY * BX];
     __shared__ TW sP[NV * BY * BX];
-    flux_tile<D, BX, BY, TW>(P, W, F, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, sW, sP);
+    flux_tile<D, BX, BY, TW, HD>(P, W, F, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, sW, sP);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1020,12 +1020,16 @@ template <typename TS, typename TW> struct Launch {
         k_bnd23<1, TS, TW><<<dim3(cdiv(P.p1, 64), P.n3), blk, 0, s>>>(P, u, w);
         k_bnd23<2, TS, TW><<<dim3(cdiv(P.p1, 64), P.p2), blk, 0, s>>>(P, u, w);
     }
+    template <bool HD> static void flux_dir_t(const Params &P, int dir, const TW *w, TW *F, cudaStream_t s)
+    {
+        if (dir == 0) k_flux<0, TW, HD><<<dim3(cdiv(P.n1 + 1, 127), P.n2, P.n3), dim3(128, 1), 0, s>>>(P, w, F);
+        else if (dir == 1) k_flux<1, TW, HD><<<dim3(cdiv(P.n1, 16), cdiv(P.n2 + 1, 15), P.n3), dim3(16, 16), 0, s>>>(P, w, F);
+        else k_flux<2, TW, HD><<<dim3(cdiv(P.n1, 16), cdiv(P.n3 + 1, 15), P.n2), dim3(16, 16), 0, s>>>(P, w, F);
+    }
     static void flux_dir(const Params &P, int dir, const void *W, void *F, cudaStream_t s)
     {
-        const TW *w = (const TW *)W;
-        if (dir == 0) k_flux<0, TW><<<dim3(cdiv(P.n1 + 1, 127), P.n2, P.n3), dim3(128, 1), 0, s>>>(P, w, (TW *)F);
-        else if (dir == 1) k_flux<1, TW><<<dim3(cdiv(P.n1, 16), cdiv(P.n2 + 1, 15), P.n3), dim3(16, 16), 0, s>>>(P, w, (TW *)F);
-        else k_flux<2, TW><<<dim3(cdiv(P.n1, 16), cdiv(P.n3 + 1, 15), P.n2), dim3(16, 16), 0, s>>>(P, w, (TW *)F);
+        if (P.flux == 2) flux_dir_t<true>(P, dir, (const TW *)W, (TW *)F, s);
+        else flux_dir_t<false>(P, dir, (const TW *)W, (TW *)F, s);
     }
     static void fluxes(const Params &P, const void *W, void *F1, void *F2, void *F3, cudaStream_t s)
     {

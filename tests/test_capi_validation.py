@@ -72,7 +72,7 @@ def test_bad_boundary_codes_rejected(ic):
     (1.5, I.Options(cfl=0.0), 0, "cfl"),
     (1.5, I.Options(cfl=1.5), 0, "cfl"),
     (1.5, I.Options(limiter=3), 0, "limiter"),
-    (1.5, I.Options(flux=2), 0, "flux"),
+    (1.5, I.Options(flux=3), 0, "flux"),
     (1.5, I.Options(divb=2), 0, "divb"),
     (1.5, I.Options(init_vphi=2), 0, "init_vphi"),
     (1.5, I.Options(cme_model=2), 0, "cme_model"),
@@ -81,6 +81,14 @@ def test_bad_boundary_codes_rejected(ic):
 def test_bad_options_rejected(ic, gamma, opts, precision, msg):
     rc, err, _ = init_rc(ic, sph(), gamma, opts, precision)
     assert rc == EINVAL and msg in err, (rc, err)
+
+
+def test_fused_stage_rejects_hlld(ic):
+    lib = ic.load()
+    o = ic.make_options(I.Options(flux=I.FLUX_HLLD), 1, fused=True)
+    ctx = C.c_void_p()
+    rc = lib.icarus_init(C.byref(ic.make_grid(sph())), 1.5, 0.0, C.byref(o), C.byref(ctx))
+    assert rc == EINVAL and "fused" in lib.icarus_last_error().decode()
 
 
 def test_null_context_and_negative_counts(ic):

@@ -10,7 +10,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle.oracle import Oracle, cons_from_prim
+from oracle.oracle import Oracle, cons_from_prim, prim_from_cons
 from oracle.oracle import from_workload as oracle_workload
 from paper_2501_15923_gb300 import inputs as I
 
@@ -104,6 +104,26 @@ def test_options_perturbed_state(ic, lim, flux, divb, grav):
     # pressure resets over both stages, decided in FP64 on both sides) agree exactly
     assert orc.floor_hits > 0
     assert gpu.status()[1] - f0 == orc.floor_hits
+    gpu.close()
+
+
+@pytest.mark.parametrize("lim,divb,grav", [(I.LIM_VANLEER, I.DIVB_LINDE, 1), (I.LIM_MC, I.DIVB_NONE, 0)])
+def test_hlld_perturbed_state(ic, lim, divb, grav):
+    """HLLD flux (its own kernel instantiation) on a perturbed config-0 state. The perturbation is
+    made in primitive variables so that the pressure stays positive: HLLD's intermediate states
+    have no meaning for negative pressures (the oracle's step turns non-finite there too)."""
+    w = I.config0()
+    w.opts = I.Options(limiter=lim, flux=I.FLUX_HLLD, divb=divb, gravity=grav)
+    gpu, orc = ic.from_workload(w), oracle_workload(w)
+    U, _ = gpu.get_state()
+    W = prim_from_cons(U, w.gamma)
+    Wp = I.perturbed_state(W.shape, 11, W, 2e-2)
+    noise = lambda seed: I.perturbed_state(W.shape[1:], seed, np.ones(W.shape[1:]), 1.0) - 1.0
+    Wp[2] += 0.1 * np.abs(W[1]) * noise(12)
+    Wp[6] += 0.1 * np.sqrt((W[5:8] ** 2).sum(0)) * noise(13)
+    U1, t1 = assert_step(gpu, orc, cons_from_prim(Wp, w.gamma), 0.01)
+    for _ in range(4):
+        U1, t1 = assert_step(gpu, orc, U1, t1)
     gpu.close()
 
 
