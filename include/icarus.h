@@ -55,6 +55,8 @@ enum {
 enum { ICARUS_BC_PERIODIC = 0, ICARUS_BC_CONT = 1, ICARUS_BC_REFLECT = 2, ICARUS_BC_DRIVEN = 3 };
 enum { ICARUS_GEOM_SPHERICAL = 0, ICARUS_GEOM_CARTESIAN = 1 };
 enum { ICARUS_LIM_MINMOD = 0, ICARUS_LIM_VANLEER = 1, ICARUS_LIM_MC = 2 };
+/* face fluxes: TVDLF (Rusanov), HLL, HLLD (Miyoshi & Kusano 2005; not in the fused stage or the
+ * batched form) */
 enum { ICARUS_FLUX_TVDLF = 0, ICARUS_FLUX_HLL = 1, ICARUS_FLUX_HLLD = 2 };
 enum { ICARUS_DIVB_NONE = 0, ICARUS_DIVB_LINDE = 1 };
 /* FP64: everything in double. FP32: state and arithmetic in float. MIXED: state, update
