@@ -162,11 +162,11 @@ def current_sheet_map(theta_c: np.ndarray, phi_c: np.ndarray, tilt: float, phase
     return np.stack([vr, n, p, br, bphi]).astype(np.float64)
 
 
-def tilt_walk(rng: SplitMix64, n_maps: int, tilt0: float) -> list:
-    """Tilt sequence a_{k+1} = clamp(a_k + U(-5, 5) deg, 0, 90 deg)."""
+def tilt_walk(rng: SplitMix64, n_maps: int, tilt0: float, step_deg: float = 5.0) -> list:
+    """Tilt sequence a_{k+1} = clamp(a_k + U(-step, step) deg, 0, 90 deg) (step 5 deg by default)."""
     tilts = [tilt0]
     for _ in range(n_maps - 1):
-        a = tilts[-1] + math.radians(rng.uniform(-5.0, 5.0))
+        a = tilts[-1] + math.radians(rng.uniform(-step_deg, step_deg))
         tilts.append(min(max(a, 0.0), math.radians(90.0)))
     return tilts
 
@@ -251,6 +251,27 @@ def config1(seed: int = 1, grid: Grid | None = None, days: float = 10.0, n_scale
                              math.radians(30.0), 1.2e6, 1000e6, 8e5)])
     return Workload("cfg1_512x64x128_dynamic_cme", g, Options(), 1.5, OMEGA_SUN, t_maps, maps, cmes,
                     traj, t_end=days * DAY, meta={"phase": phase, "tilts": tilts})
+
+
+def paper2019(seed: int = 7, days: float = 42.0, n_maps: int = 454, cadence_h: float = 2.0,
+              grid: Grid | None = None) -> Workload:
+    """Stand-in for the paper's 2019 dynamic run (Sect. 4): a uniform 600 x 64 x 192 grid over
+    0.1-2 AU, 454 synthetic maps at a 2 h cadence (the current-sheet recipe of the production
+    workload, tilt random-walking by U(-1.5, 1.5) deg per map, about +-5 deg per day), no CME,
+    two probes on circular orbits (1 AU at latitude 0, and 0.96 AU 40 deg behind in longitude),
+    42 simulated days (the maps stop after 37.8 d and the last one is held)."""
+    g = grid or Grid(600, 64, 192, stretch=0)
+    rng = SplitMix64(seed)
+    phase = 2.0 * math.pi * rng.uniform()
+    tilts = tilt_walk(rng, n_maps, math.radians(15.0), step_deg=1.5)
+    th, ph = g.theta_centres(), g.phi_centres()
+    maps = np.stack([current_sheet_map(th, ph, a, phase, OMEGA_SUN, g.x1min) for a in tilts])
+    t_maps = np.arange(n_maps) * cadence_h * 3600.0
+    t_knots = np.arange(0.0, (days + 1.0) * DAY + 1.0, 3600.0)
+    traj = np.stack([circular_orbit(t_knots, 1.0, 0.0, 0.0, 365.25),
+                     circular_orbit(t_knots, 0.96, 0.0, -40.0, 346.0)])
+    return Workload(f"paper2019_{g.n1}x{g.n2}x{g.n3}_dynamic", g, Options(), 1.5, OMEGA_SUN, t_maps, maps,
+                    np.zeros((0, 8)), traj, t_end=days * DAY, meta={"phase": phase, "tilts": tilts})
 
 
 def ensemble(seed: int = 3, n_members: int = 64, nr_set=(128, 256, 384, 512), nth_range=(32, 64),

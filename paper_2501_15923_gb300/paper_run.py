@@ -1,0 +1,78 @@
+"""The paper-shaped long run (orchestration only): the 2019 dynamic-boundary case at its grid and
+map cadence (inputs.paper2019: uniform 600 x 64 x 192, 454 maps at 2 h, 42 simulated days), in
+FP64 and in the MIXED form, with wall-clock times, throughput, floor counts and the MIXED form's
+errors against FP64 along the probe series and on the grid at the end.
+
+The paper ran this case on 216 CPU cores in 57 min (Sect. 4, Table 1); that figure is context.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import icarus as ic
+from . import inputs as I
+from .precision import derived, probe_errors, rel_errors
+
+
+def run(days: float = 42.0, forms=("fp64", "mixed"), chunk: int = 500, ring: int = 1 << 16, log=None):
+    import torch
+    w = I.paper2019(days=days)
+    prec = {"fp64": ic.ICARUS_FP64, "mixed": ic.ICARUS_MIXED, "fp32": ic.ICARUS_FP32}
+    res, states, series = {"workload": w.name, "cells": w.grid.ncell, "maps": int(len(w.t_maps)),
+                           "days": days}, {}, {}
+    for name in forms:
+        s = ic.from_workload(w, precision=prec[name], ring=ring)
+        s.sample(w.traj, cap=1)
+        t_end = days * I.DAY / s.scales()["t0"]
+        s.set_stop_time(t_end)
+        recs = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while True:
+            t, dt = s.time()
+            if t >= t_end * (1 - 1e-15) or dt <= 0.0:
+                break
+            s.step(chunk)
+            rec, n = s.sample(None, cap=ring)
+            recs.append(rec[:n])
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        rc, floors = s.status()
+        series[name] = np.concatenate(recs)
+        steps = len(series[name]) - 1
+        U, t = s.get_state()
+        states[name] = derived(U, w.gamma)
+        res[name] = {"seconds": secs, "steps": steps, "status": rc, "floor_hits": floors,
+                     "mean_dt_s": days * I.DAY / max(steps, 1),
+                     "mcell_updates_per_s": w.grid.ncell * steps / secs / 1e6,
+                     "t_days": t * s.scales()["t0"] / I.DAY}
+        if log:
+            log(f"{name}: {res[name]}")
+        s.close()
+    if "fp64" in forms:
+        for name in forms:
+            if name == "fp64":
+                continue
+            res[name]["grid_error_vs_fp64"] = rel_errors(states["fp64"], states[name])
+            res[name]["probe_error_vs_fp64"] = probe_errors(series["fp64"], series[name])
+            res[name]["speedup_vs_fp64"] = res[name]["mcell_updates_per_s"] / res["fp64"]["mcell_updates_per_s"]
+    return res
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--days", type=float, default=42.0)
+    p.add_argument("--forms", default="fp64,mixed")
+    a = p.parse_args(argv)
+    import torch
+    torch.cuda.set_device(0)
+    res = run(a.days, tuple(a.forms.split(",")), log=lambda s: print(s, flush=True))
+    print(json.dumps(res, default=float))
+
+
+if __name__ == "__main__":
+    main()

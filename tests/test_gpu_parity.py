@@ -170,6 +170,18 @@ def test_sphere_cme_crossing(ic):
     gpu.close()
 
 
+def test_uniform_radial_grid_two_hour_maps(ic):
+    """The paper-shaped 2019 drivers (uniform radial spacing, maps every 2 h) on a reduced grid:
+    steps between maps and across a map time."""
+    w = I.paper2019(grid=I.Grid(60, 16, 48, stretch=0))
+    gpu, orc = ic.from_workload(w), oracle_workload(w)
+    sc = orc.scales()
+    U, _ = gpu.get_state()
+    for t in (3.3 * 3600.0 / sc["t0"], (2 * 7200.0 - 1.0) / sc["t0"]):
+        assert_step(gpu, orc, U, t)
+    gpu.close()
+
+
 def test_ragged_grid_sizes(ic):
     """Sizes that are not multiples of any block edge (ragged tails in every kernel)."""
     for n in ((37, 9, 7), (129, 17, 33), (2, 10, 3)):

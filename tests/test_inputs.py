@@ -56,3 +56,16 @@ def test_ensemble_members():
         c = m.cmes[0]
         assert 600e3 <= c[5] <= 2000e3 and math.radians(15) <= c[4] <= math.radians(45)
         assert abs(c[2]) <= math.radians(20) and 0 <= c[0] <= 2 * I.DAY
+
+
+def test_paper2019_shape_and_cadence():
+    w = I.paper2019()
+    assert (w.grid.n1, w.grid.n2, w.grid.n3, w.grid.stretch) == (600, 64, 192, 0)
+    assert w.maps.shape == (454, 5, 64, 192) and len(w.cmes) == 0
+    assert np.allclose(np.diff(w.t_maps), 7200.0)
+    tilts = np.array(w.meta["tilts"])
+    assert np.all(np.abs(np.diff(tilts)) <= np.radians(1.5) + 1e-12)
+    assert w.traj.shape[0] == 2 and w.traj[0, -1, 0] >= 42 * I.DAY
+    w2 = I.paper2019()
+    assert np.array_equal(w.maps, w2.maps)
+
