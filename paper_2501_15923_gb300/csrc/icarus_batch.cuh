@@ -97,7 +97,7 @@ __device__ __forceinline__ int next_member(const long long *off, int n, long lon
 }
 
 template <typename TS, typename TW>
-__global__ void __launch_bounds__(BATCH_THREADS, sizeof(TW) == 4 ? 3 : 2) k_batch_step(BatchArgs A)
+__global__ void __launch_bounds__(BATCH_THREADS, sizeof(TW) == 4 ? 4 : 2) k_batch_step(BatchArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TW *smem = reinterpret_cast<TW *>(smem_raw);
