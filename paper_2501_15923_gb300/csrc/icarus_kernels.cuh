@@ -707,10 +707,10 @@ __device__ __forceinline__ void update_cell(const Params &P, const TS *__restric
 }
 
 template <int STAGE, typename TS, typename TW>
-__global__ void __launch_bounds__(256)
-k_update(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo, TW *__restrict__ Wo,
-         const TW *__restrict__ F1, const TW *__restrict__ F2, const TW *__restrict__ F3,
-         const TW *__restrict__ divB)
+__device__ __forceinline__ void update_kernel_body(Params &P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo,
+                                                   TW *__restrict__ Wo, const TW *__restrict__ F1,
+                                                   const TW *__restrict__ F2, const TW *__restrict__ F3,
+                                                   const TW *__restrict__ divB)
 {
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = tid < (long long)P.n1 * P.n2 * P.n3;
@@ -720,6 +720,26 @@ k_update(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo,
         const int i = valid ? (int)(tid % P.n1) : 0, j = valid ? (int)((tid / P.n1) % P.n2) : 0;
         finish_dt(P, cfl_block_speed<TW>(P, wo, i + NG, j + NG, valid), 1);
     }
+}
+
+template <int STAGE, typename TS, typename TW>
+__global__ void __launch_bounds__(256)
+k_update(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo, TW *__restrict__ Wo,
+         const TW *__restrict__ F1, const TW *__restrict__ F2, const TW *__restrict__ F3,
+         const TW *__restrict__ divB)
+{
+    update_kernel_body<STAGE, TS, TW>(P, Us, Ws, Uo, Wo, F1, F2, F3, divB);
+}
+
+// the same update with at most 48 registers (5 blocks of 256 per SM): measured faster for the
+// second MIXED stage, whose register demand otherwise limits it to 3 blocks
+template <int STAGE, typename TS, typename TW>
+__global__ void __launch_bounds__(256, 5)
+k_update_capped(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo, TW *__restrict__ Wo,
+                const TW *__restrict__ F1, const TW *__restrict__ F2, const TW *__restrict__ F3,
+                const TW *__restrict__ divB)
+{
+    update_kernel_body<STAGE, TS, TW>(P, Us, Ws, Uo, Wo, F1, F2, F3, divB);
 }
 
 // FP32 form, n1 even: one thread updates the two cells (i, i+1), i even, of a radial row with
@@ -1059,6 +1079,9 @@ template <typename TS, typename TW> struct Launch {
         if (stage == 1)
             k_update<1, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo, (TW *)Wo,
                 (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
+        else if constexpr (Prec<TS, TW>::mixed)
+            k_update_capped<2, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo,
+                (TW *)Wo, (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
         else
             k_update<2, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo, (TW *)Wo,
                 (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
