@@ -67,6 +67,8 @@ typedef struct {
     int cme_model;   /* 0: cone footprint over a fixed window; 1: spherical cloud crossing r_in */
     double t0, p0, b0;       /* code-unit scales */
     double *U, *U0, *U1, *L, *W, *F[3], *divB, *Ufix;
+    int tracer;                     /* CME tracer on: T = rho c, c = 1 in inserted CME plasma */
+    double *T, *T0, *T1, *LT, *C;   /* padded: rho c now / at the step start / stage 1, residual, c */
     double t;
     int n_maps; double *tm; double *maps;      /* code units, [n_maps][5][n2][n3] */
     int n_cme; double *cme;                    /* code units, [n_cme][8] */
@@ -677,6 +679,7 @@ orc_t *orc_create(const int *ig, const double *dg, double gamma, double omega_si
     o->cfl = od[0]; o->divb_coef = od[1]; o->rho_floor = od[2]; o->p_floor = od[3];
     o->limiter = oi[0]; o->flux = oi[1]; o->gravity = oi[2]; o->divb = oi[3]; o->init_vphi = oi[4];
     o->cme_model = oi[5];
+    o->tracer = oi[6];
     o->gm = O_GM / (O_AU * O_V0 * O_V0);
     if (o->geom == GEOM_CART) { o->omega = 0.0; o->gravity = 0; }
     size_t sz = sizeof(double) * NV * o->nt;
@@ -684,6 +687,9 @@ orc_t *orc_create(const int *ig, const double *dg, double gamma, double omega_si
     o->L = (double *)calloc(1, sz); o->W = (double *)calloc(1, sz); o->Ufix = (double *)calloc(1, sz);
     for (int d = 0; d < 3; d++) o->F[d] = (double *)calloc(1, sz);
     o->divB = (double *)calloc(1, sizeof(double) * o->nt);
+    o->T = (double *)calloc(1, sizeof(double) * o->nt); o->T0 = (double *)calloc(1, sizeof(double) * o->nt);
+    o->T1 = (double *)calloc(1, sizeof(double) * o->nt); o->LT = (double *)calloc(1, sizeof(double) * o->nt);
+    o->C = (double *)calloc(1, sizeof(double) * o->nt);
     return o;
 }
 
@@ -692,6 +698,7 @@ void orc_destroy(orc_t *o)
     if (!o) return;
     for (int d = 0; d < 3; d++) { free(o->e[d]); free(o->c[d]); free(o->F[d]); }
     free(o->U); free(o->U0); free(o->U1); free(o->L); free(o->W); free(o->Ufix); free(o->divB);
+    free(o->T); free(o->T0); free(o->T1); free(o->LT); free(o->C);
     free(o->tm); free(o->maps); free(o->cme);
     free(o);
 }
@@ -797,6 +804,96 @@ double orc_cfl_dt(orc_t *o) { return cfl_dt(o, o->U); }
 
 /* one SSP-RK2 step: U1 = U + dt L(U, t); U <- U/2 + (U1 + dt L(U1, t + dt))/2; floors after each
  * stage; dt = CFL bound, capped by dt_max when dt_max > 0. Returns dt, or -1 on non-finite state */
+/* ---- CME tracer (a passive scalar c carried by the plasma; rho c is conserved) --------------
+ * The paper marks inserted CME plasma with a tracer. Boundary: c = 1 in the ghost columns inside
+ * the CME footprint while it is inserted, 0 elsewhere on the driven face; c is copied like the
+ * other variables on every other face. Face flux: F_rho times the limited linear reconstruction
+ * of c on the upwind side of the mass flux (the same limiter as the MHD variables), so that c = 1
+ * everywhere moves rho c exactly like rho. After each stage rho c is clipped to [0, rho]. */
+static void tracer_fill_side(orc_t *o, double *T, const double *U, int d, int side, double tau)
+{
+    int bc = o->bc[2 * d + side];
+    int n = o->n[d];
+    int a_lo = -NG, a_hi = o->n[(d + 1) % 3] + NG, b_lo = -NG, b_hi = o->n[(d + 2) % 3] + NG;
+    if (d == 0) { a_lo = 0; a_hi = o->n[1]; b_lo = 0; b_hi = o->n[2]; }
+    if (d == 1) { a_lo = 0; a_hi = o->n[2]; b_lo = -NG; b_hi = o->n[0] + NG; }
+    if (bc == BC_DRIVEN) {
+        for (int k = 0; k < o->n[2]; k++)
+            for (int j = 0; j < o->n[1]; j++) {
+                double q[5] = {0, 0, 0, 0, 0};
+                int hit = cme_hit(o, tau, j, k, q);
+                for (int g = 1; g <= NG; g++) {
+                    long id = IDX(o, -g, j, k);
+                    T[id] = hit ? U[RHO * o->nt + id] : 0.0;
+                }
+            }
+        return;
+    }
+    for (int b = b_lo; b < b_hi; b++)
+        for (int a = a_lo; a < a_hi; a++)
+            for (int g = 1; g <= NG; g++) {
+                int gi = side == 0 ? -g : n - 1 + g;
+                int src;
+                if (bc == BC_CONT) src = side == 0 ? 0 : n - 1;
+                else if (bc == BC_REFLECT) src = side == 0 ? g - 1 : n - g;
+                else if (bc == BC_PERIODIC) src = ((gi % n) + n) % n;
+                else src = gi;   /* FIXED: keep */
+                T[cell_id(o, d, gi, a, b)] = T[cell_id(o, d, src, a, b)];
+            }
+}
+
+static void tracer_fill(orc_t *o, double *T, const double *U, double tau)
+{
+    for (int d = 0; d < 3; d++)
+        for (int side = 0; side < 2; side++) tracer_fill_side(o, T, U, d, side, tau);
+}
+
+/* residual of rho c, with the mass fluxes of the residual just evaluated for U (o->F) */
+static void tracer_residual(orc_t *o, const double *T, const double *U)
+{
+#pragma omp parallel for
+    for (long id = 0; id < o->nt; id++) {
+        double rho = U[RHO * o->nt + id];
+        o->C[id] = rho != 0.0 ? T[id] / rho : 0.0;
+    }
+    const int sh[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+#pragma omp parallel for collapse(2)
+    for (int k = 0; k < o->n[2]; k++)
+        for (int j = 0; j < o->n[1]; j++)
+            for (int i = 0; i < o->n[0]; i++) {
+                long id = IDX(o, i, j, k);
+                double V = volume(o, i, j, k), l = 0.0;
+                for (int d = 0; d < 3; d++) {
+                    double ft[2];
+                    for (int s = 0; s < 2; s++) {      /* lower (s = 0) and upper face along d */
+                        int b[3] = {i + s * sh[d][0], j + s * sh[d][1], k + s * sh[d][2]};
+                        long ib = IDX(o, b[0], b[1], b[2]);
+                        long st = d == 0 ? 1 : (d == 1 ? o->p[0] : (long)o->p[0] * o->p[1]);
+                        double cm2 = o->C[ib - 2 * st], cm1 = o->C[ib - st], c0 = o->C[ib], cp1 = o->C[ib + st];
+                        double cl = cm1 + 0.5 * limit(o->limiter, cm1 - cm2, c0 - cm1);
+                        double cr = c0 - 0.5 * limit(o->limiter, c0 - cm1, cp1 - c0);
+                        double fr = o->F[d][RHO * o->nt + ib];
+                        ft[s] = fr * (fr >= 0.0 ? cl : cr);
+                    }
+                    double am = area(o, d, i, j, k);
+                    double ap = area(o, d, i + sh[d][0], j + sh[d][1], k + sh[d][2]);
+                    l -= (ap * ft[1] - am * ft[0]) / V;
+                }
+                o->LT[id] = l;
+            }
+}
+
+static void tracer_clip(orc_t *o, double *T, const double *U)
+{
+    for (int k = 0; k < o->n[2]; k++)
+        for (int j = 0; j < o->n[1]; j++)
+            for (int i = 0; i < o->n[0]; i++) {
+                long id = IDX(o, i, j, k);
+                double rho = U[RHO * o->nt + id];
+                T[id] = fmin(fmax(T[id], 0.0), rho);
+            }
+}
+
 double orc_step(orc_t *o, double dt_max)
 {
     double dt = cfl_dt(o, o->U);
@@ -805,6 +902,18 @@ double orc_step(orc_t *o, double dt_max)
     memcpy(o->U0, o->U, sizeof(double) * tot);
     fill_ghosts(o, o->U, o->t);
     residual(o, o->U, dt);
+    if (o->tracer) {
+        memcpy(o->T0, o->T, sizeof(double) * o->nt);
+        tracer_fill(o, o->T, o->U, o->t);
+        tracer_residual(o, o->T, o->U);
+        memcpy(o->T1, o->T, sizeof(double) * o->nt);
+        for (int k = 0; k < o->n[2]; k++)
+            for (int j = 0; j < o->n[1]; j++)
+                for (int i = 0; i < o->n[0]; i++) {
+                    long id = IDX(o, i, j, k);
+                    o->T1[id] = o->T0[id] + dt * o->LT[id];
+                }
+    }
     memcpy(o->U1, o->U, sizeof(double) * tot);
     for (int v = 0; v < NV; v++)
         for (int k = 0; k < o->n[2]; k++)
@@ -814,8 +923,19 @@ double orc_step(orc_t *o, double dt_max)
                     o->U1[id] = o->U0[id] + dt * o->L[id];
                 }
     apply_floors(o, o->U1);
+    if (o->tracer) tracer_clip(o, o->T1, o->U1);
     fill_ghosts(o, o->U1, o->t + dt);
     residual(o, o->U1, dt);
+    if (o->tracer) {
+        tracer_fill(o, o->T1, o->U1, o->t + dt);
+        tracer_residual(o, o->T1, o->U1);
+        for (int k = 0; k < o->n[2]; k++)
+            for (int j = 0; j < o->n[1]; j++)
+                for (int i = 0; i < o->n[0]; i++) {
+                    long id = IDX(o, i, j, k);
+                    o->T[id] = 0.5 * o->T0[id] + 0.5 * (o->T1[id] + dt * o->LT[id]);
+                }
+    }
     for (int v = 0; v < NV; v++)
         for (int k = 0; k < o->n[2]; k++)
             for (int j = 0; j < o->n[1]; j++)
@@ -824,8 +944,30 @@ double orc_step(orc_t *o, double dt_max)
                     o->U[id] = 0.5 * o->U0[id] + 0.5 * (o->U1[id] + dt * o->L[id]);
                 }
     apply_floors(o, o->U);
+    if (o->tracer) tracer_clip(o, o->T, o->U);
     o->t = o->t + dt;
     return o->status ? -1.0 : dt;
+}
+
+/* tracer values c of the interior cells, [n3][n2][n1]: set (rho c from the current rho) / get */
+void orc_set_tracer(orc_t *o, const double *c)
+{
+    for (int k = 0; k < o->n[2]; k++)
+        for (int j = 0; j < o->n[1]; j++)
+            for (int i = 0; i < o->n[0]; i++) {
+                long id = IDX(o, i, j, k);
+                o->T[id] = o->U[RHO * o->nt + id] * c[((long)k * o->n[1] + j) * o->n[0] + i];
+            }
+}
+
+void orc_get_tracer(const orc_t *o, double *c)
+{
+    for (int k = 0; k < o->n[2]; k++)
+        for (int j = 0; j < o->n[1]; j++)
+            for (int i = 0; i < o->n[0]; i++) {
+                long id = IDX(o, i, j, k);
+                c[((long)k * o->n[1] + j) * o->n[0] + i] = o->T[id] / o->U[RHO * o->nt + id];
+            }
 }
 
 /* residual L(U) at the current state and time (ghosts filled at tau), interior [8][n3][n2][n1] */

@@ -28,6 +28,8 @@ def lib():
             "orc_destroy": (None, [P]),
             "orc_set_threads": (None, [I]),
             "orc_riemann": (None, [P, P, P, I, P]),
+            "orc_set_tracer": (None, [P, P]),
+            "orc_get_tracer": (None, [P, P]),
             "orc_max_threads": (I, []),
             "orc_set_boundary": (I, [P, I, P, P, I, P]),
             "orc_init_state": (I, [P]),
@@ -77,8 +79,8 @@ class Oracle:
         ig = np.array([grid.n1, grid.n2, grid.n3, grid.geometry, grid.stretch, *grid.bc], dtype=np.int32)
         dg = np.array([grid.x1min, grid.x1max, grid.x2min, grid.x2max, grid.x3min, grid.x3max])
         od = np.array([opts.cfl, opts.divb_coef, opts.rho_floor, opts.p_floor])
-        oi = np.array([opts.limiter, opts.flux, opts.gravity, opts.divb, opts.init_vphi, opts.cme_model],
-                      dtype=np.int32)
+        oi = np.array([opts.limiter, opts.flux, opts.gravity, opts.divb, opts.init_vphi, opts.cme_model,
+                       opts.tracer], dtype=np.int32)
         self.h = lib().orc_create(_ptr(ig), _ptr(dg), gamma, omega, _ptr(od), _ptr(oi))
         self.shape = (NV, grid.n3, grid.n2, grid.n1)
         self.pshape = (NV, grid.n3 + 2 * NG, grid.n2 + 2 * NG, grid.n1 + 2 * NG)
@@ -157,6 +159,17 @@ class Oracle:
         hit = np.empty((g.n2, g.n3), dtype=np.int32)
         lib().orc_boundary_values(self.h, float(tau), _ptr(out), _ptr(hit))
         return out, hit
+
+    def set_tracer(self, c):
+        """CME tracer values c of the interior cells [n3][n2][n1] (rho c from the current rho)."""
+        a = _c(c)
+        assert a.shape == self.shape[1:]
+        lib().orc_set_tracer(self.h, _ptr(a))
+
+    def get_tracer(self) -> np.ndarray:
+        out = np.empty(self.shape[1:])
+        lib().orc_get_tracer(self.h, _ptr(out))
+        return out
 
     def riemann(self, wl, wr, d: int) -> np.ndarray:
         """Face flux of the configured Riemann solver for primitive states wl, wr (code units)."""

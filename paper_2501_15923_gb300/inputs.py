@@ -116,6 +116,7 @@ class Options:
     p_floor: float = 1e-9                 # code units (p / (m_p 1e6 m^-3 (100 km/s)^2))
     init_vphi: int = IC_COROTATING        # initial v_phi: IC_COROTATING (0) or IC_INERTIAL_RADIAL
     cme_model: int = CME_WINDOW           # CME_WINDOW (0) or CME_SPHERE (1)
+    tracer: int = 0                       # 1: carry the CME tracer c (passive, rho c conserved)
 
 
 @dataclass

@@ -826,3 +826,90 @@ def test_P10_cme_footprint_brute_force():
     for tt in (0.0, 3599.0, 9 * 3600.0, 20 * 3600.0):
         _, hit = o.boundary_values(tt / t0)
         assert hit.sum() == 0
+
+
+# ---------------------------------------------------------------------------------------------
+def _tracer_box(n=24, seed=3, flow=0.3):
+    g = cart_grid(n, n, n)
+    o = Oracle(g, 5 / 3, 0.0, opts(divb=I.DIVB_LINDE, tracer=1))
+    rng = np.random.default_rng(seed)
+    W = np.zeros((8, n, n, n))
+    W[0] = 1.0 + 0.3 * rng.random(W.shape[1:])
+    W[1:4] = flow * rng.standard_normal((3,) + W.shape[1:])
+    W[4] = 1.0 + 0.2 * rng.random(W.shape[1:])
+    W[5:8] = 0.4 * rng.standard_normal((3,) + W.shape[1:])
+    o.set_state(cons_from_prim(W, 5 / 3), 0.0)
+    return o, rng
+
+
+def test_tracer_uniform_is_kept_exactly():
+    """c = 1 everywhere: the tracer flux is the mass flux times 1, so rho c follows rho to the last
+    bit and c stays exactly 1 (periodic box, random flow and field, Linde on)."""
+    o, _ = _tracer_box()
+    o.set_tracer(np.ones(o.shape[1:]))
+    for _ in range(3):
+        o.step()
+    assert np.all(o.get_tracer() == 1.0)
+
+
+def test_tracer_conserved_and_bounded():
+    """Random c in [0, 1] in a periodic Cartesian box: the total of rho c is conserved to round-off
+    and c stays within [0, 1]."""
+    o, rng = _tracer_box(seed=5)
+    c0 = rng.random(o.shape[1:])
+    o.set_tracer(c0)
+    U0, _ = o.get_state()
+    m0 = (U0[0] * c0).sum()
+    for _ in range(4):
+        o.step()
+    U, _ = o.get_state()
+    c = o.get_tracer()
+    assert abs((U[0] * c).sum() - m0) <= 1e-12 * m0
+    assert c.min() >= 0.0 and c.max() <= 1.0
+
+
+def test_tracer_advection_second_order():
+    """A smooth tracer profile carried once around a periodic box by a uniform flow returns with a
+    second-order error (64 -> 128 cells)."""
+    errs = []
+    for n in (64, 128):
+        g = cart_grid(n, 1, 1, L=(1.0, 1e3, 1e3))
+        o = Oracle(g, 5 / 3, 0.0, opts(divb=I.DIVB_NONE, tracer=1, cfl=0.8))
+        W = np.zeros((8, 1, 1, n))
+        W[0], W[1], W[4] = 1.0, 1.0, 1.0
+        o.set_state(cons_from_prim(W, 5 / 3), 0.0)
+        x = (np.arange(n) + 0.5) / n
+        avg = math.sin(math.pi / n) / (math.pi / n)
+        c0 = 0.5 + 0.4 * np.sin(2 * np.pi * x) * avg
+        o.set_tracer(c0.reshape(1, 1, n))
+        run_to(o, 1.0)
+        errs.append(np.abs(o.get_tracer().ravel() - c0).mean())
+    assert math.log2(errs[0] / errs[1]) > 1.8, errs
+    assert errs[1] < 2e-3, errs
+
+
+def test_tracer_marks_inserted_cme_plasma():
+    """During the CME window the driven face sets c = 1 in the footprint columns and 0 elsewhere:
+    after one step from c = 0 the first radial cell carries tracer in the footprint, and none in
+    columns five or more cells away from it."""
+    from oracle.oracle import from_workload
+    w = I.config1(grid=I.Grid(24, 16, 32))
+    w.opts.tracer = 1
+    o = from_workload(w)
+    t = (w.cmes[0, 0] + 1800.0) / o.scales()["t0"]
+    U, _ = o.get_state()
+    o.set_state(U, t)
+    o.set_tracer(np.zeros(o.shape[1:]))
+    _, hit = o.boundary_values(t)
+    o.step()
+    c = o.get_tracer()[:, :, 0].T                 # [n2][n3] first radial cell
+    hit = hit.astype(bool)
+    assert hit.sum() > 0 and np.all(c[hit] > 0.1)
+    far = np.ones_like(hit)
+    jj, kk = np.nonzero(hit)
+    for j, k in zip(jj, kk):
+        for dj in range(-4, 5):
+            for dk in range(-4, 5):
+                if 0 <= j + dj < hit.shape[0]:
+                    far[j + dj, (k + dk) % hit.shape[1]] = False
+    assert far.sum() > 0 and np.all(c[far] == 0.0)
