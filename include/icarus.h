@@ -105,6 +105,11 @@ typedef struct {
                               axis at the CME speed, its leading point at r_in at t_on; the footprint
                               is the part of the r_in sphere inside the cloud, for 2 R / speed (the
                               duration entry is not used) */
+    int tracer;            /* 1: carry the CME tracer c (Sect. 3.2 marks inserted CME plasma): rho c is
+                              conserved, moved by the mass flux with the limited upwind c, c = 1 on
+                              the driven face inside the CME footprint and 0 outside, rho c clipped
+                              to [0, rho] after each stage; starts at c = 0 (icarus_set_tracer).
+                              Not with the fused stage kernel or the batched form. */
 } icarus_options;
 
 #define ICARUS_IC_COROTATING 0
@@ -160,6 +165,13 @@ int icarus_get_state(icarus_ctx *ctx, double *U, double *t);
 /* Replace the interior state (code units, double) and the time (code units); recomputes dt.
  * Synchronous. Enables stepping without boundary maps when no face is DRIVEN. */
 int icarus_set_state(icarus_ctx *ctx, const double *U, double t);
+
+/* CME tracer (options.tracer = 1): set c of the interior cells from HOST doubles [n3][n2][n1]
+ * (rho c = rho * c with the current rho), or copy c = rho c / rho back to the host. Synchronous.
+ * EINVAL without the tracer option, ESTATE before a state exists. icarus_set_state keeps rho c
+ * (so c changes with rho). */
+int icarus_set_tracer(icarus_ctx *ctx, const double *c);
+int icarus_get_tracer(icarus_ctx *ctx, double *c);
 
 /* Copy the interior state into a DEVICE buffer U_dev [8][n3][n2][n1] (double, code units).
  * Synchronous. */

@@ -212,22 +212,28 @@ void enqueue_step(icarus_ctx *c)
         if (P.n_probes > 0) c->ops.probe(P, c->W, s);
         return;
     }
-    // stage 1: U, W at t  ->  U1, W1
+    // stage 1: U, W at t  ->  U1, W1 (tracer: rho c in T, c in C  ->  T1, C1, with the stage's mass fluxes)
+    const bool tr = c->opts.tracer != 0;
     c->ops.fill_ghosts(P, c->U, c->W, 1, s);
+    if (tr) c->ops.tracer_ghost(P, c->C, 1, s);
     c->ops.fluxes(P, c->W, c->F1, c->F2, c->F3, s);
     if (P.divb == 1) c->ops.divb(P, c->W, c->divB, s);
     c->ops.update(P, 1, c->U, c->W, c->U1, c->W1, c->F1, c->F2, c->F3, c->divB, s);
+    if (tr) c->ops.tracer_update(P, 1, c->C, c->F1, c->F2, c->F3, c->T, c->T1, c->U1, c->C1, s);
     // stage 2: U1, W1 at t + dt  ->  U, W (in place), next dt, t += dt
     c->ops.fill_ghosts(P, c->U1, c->W1, 2, s);
+    if (tr) c->ops.tracer_ghost(P, c->C1, 2, s);
     c->ops.fluxes(P, c->W1, c->F1, c->F2, c->F3, s);
     if (P.divb == 1) c->ops.divb(P, c->W1, c->divB, s);
     c->ops.update(P, 2, c->U1, c->W1, c->U, c->W, c->F1, c->F2, c->F3, c->divB, s);
+    if (tr) c->ops.tracer_update(P, 2, c->C1, c->F1, c->F2, c->F3, c->T1, c->T, c->U, c->C, s);
     if (P.n_probes > 0) c->ops.probe(P, c->W, s);
 }
 
 int count_launches(const icarus_ctx *c)
 {
-    int per_stage = (c->ops.fused_stage && c->opts.fused) ? 3 + 1 : 3 + 3 + (c->P.divb == 1 ? 1 : 0) + 1;
+    int per_stage = (c->ops.fused_stage && c->opts.fused) ? 3 + 1
+                  : 3 + 3 + (c->P.divb == 1 ? 1 : 0) + 1 + (c->opts.tracer ? 2 : 0);
     return 2 * per_stage + (c->P.n_probes > 0 ? 1 : 0);
 }
 
@@ -295,11 +301,13 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     if (!(gamma > 1.0)) return fail(ICARUS_EINVAL, "gamma must be > 1");
     if (!(opts->cfl > 0.0 && opts->cfl <= 1.0)) return fail(ICARUS_EINVAL, "cfl must be in (0, 1]");
     if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 2 || opts->divb < 0 || opts->divb > 1 ||
-        opts->init_vphi < 0 || opts->init_vphi > 1 || opts->cme_model < 0 || opts->cme_model > 1)
-        return fail(ICARUS_EINVAL, "bad limiter / flux / divb / init_vphi / cme_model option");
+        opts->init_vphi < 0 || opts->init_vphi > 1 || opts->cme_model < 0 || opts->cme_model > 1 ||
+        opts->tracer < 0 || opts->tracer > 1)
+        return fail(ICARUS_EINVAL, "bad limiter / flux / divb / init_vphi / cme_model / tracer option");
     if (opts->precision < 0 || opts->precision > 2) return fail(ICARUS_EINVAL, "bad precision");
     if (opts->fused && opts->flux == ICARUS_FLUX_HLLD)
         return fail(ICARUS_EINVAL, "the fused stage kernel supports the TVDLF and HLL fluxes only");
+    if (opts->fused && opts->tracer) return fail(ICARUS_EINVAL, "the fused stage kernel carries no CME tracer");
     if (opts->ring_capacity < 1) return fail(ICARUS_EINVAL, "ring_capacity must be >= 1");
     icarus_ctx *c = new icarus_ctx();
     c->grid = *grid;
@@ -356,6 +364,20 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     c->partial = (double *)dalloc(c, (size_t)nblk * sizeof(double));
     c->sc = (Scalars *)dalloc(c, sizeof(Scalars));
     c->stage_buf = (double *)dalloc(c, NV * (size_t)ncell * sizeof(double));
+    if (opts->tracer) {
+        c->T = dalloc(c, nt * ts);
+        c->T1 = dalloc(c, nt * ts);
+        c->C = dalloc(c, nt * tw);
+        c->C1 = dalloc(c, nt * tw);
+        if (!c->T || !c->T1 || !c->C || !c->C1) {
+            icarus_destroy(c);
+            return fail(ICARUS_ENOMEM, "device allocation failed");
+        }
+        CK(cudaMemsetAsync(c->T, 0, nt * ts, c->stream));
+        CK(cudaMemsetAsync(c->T1, 0, nt * ts, c->stream));
+        CK(cudaMemsetAsync(c->C, 0, nt * tw, c->stream));
+        CK(cudaMemsetAsync(c->C1, 0, nt * tw, c->stream));
+    }
     if (!c->U || !c->U1 || !c->W || !c->W1 || !c->F1 || !c->F2 || !c->F3 || !c->divB || !c->partial || !c->sc || !c->stage_buf) {
         icarus_destroy(c);
         return fail(ICARUS_ENOMEM, "device allocation failed");
@@ -553,12 +575,40 @@ int icarus_set_state(icarus_ctx *c, const double *U, double t)
     s.status = 0;
     s.done = 0;
     CK(cudaMemcpyAsync(c->sc, &s, sizeof s, cudaMemcpyHostToDevice, c->stream));
+    if (c->opts.tracer) c->ops.tracer_set(P, nullptr, c->U, c->T, c->C, c->stream);   // keep rho c, c = rho c / rho
     c->have_state = true;
     if (c->grid.bc[0] == ICARUS_BC_DRIVEN && !c->have_boundary) {
         CK(cudaStreamSynchronize(c->stream));
         return ICARUS_OK;   // dt is computed once the maps arrive
     }
     return first_dt(c);
+}
+
+int icarus_set_tracer(icarus_ctx *c, const double *cin)
+{
+    if (!c || !cin) return fail(ICARUS_EINVAL, "NULL argument");
+    if (!c->opts.tracer) return fail(ICARUS_EINVAL, "the context carries no tracer (options.tracer = 0)");
+    if (!c->have_state) return fail(ICARUS_ESTATE, "no state yet: set_state or set_boundary first");
+    const size_t n = (size_t)c->P.n1 * c->P.n2 * c->P.n3;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(c->stage_buf, cin, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    c->ops.tracer_set(c->P, c->stage_buf, c->U, c->T, c->C, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return ICARUS_OK;
+}
+
+int icarus_get_tracer(icarus_ctx *c, double *cout)
+{
+    if (!c || !cout) return fail(ICARUS_EINVAL, "NULL argument");
+    if (!c->opts.tracer) return fail(ICARUS_EINVAL, "the context carries no tracer (options.tracer = 0)");
+    if (!c->have_state) return fail(ICARUS_ESTATE, "no state yet: set_state or set_boundary first");
+    const size_t n = (size_t)c->P.n1 * c->P.n2 * c->P.n3;
+    c->ops.tracer_get(c->P, c->T, c->U, c->stage_buf, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(cout, c->stage_buf, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ICARUS_OK;
 }
 
 int icarus_copy_state(icarus_ctx *c, double *U_dev)

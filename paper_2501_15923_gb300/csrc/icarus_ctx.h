@@ -17,6 +17,7 @@ struct icarus_ctx {
     std::vector<void *> allocs;
     void *U = nullptr, *U1 = nullptr, *W = nullptr, *W1 = nullptr;
     void *F1 = nullptr, *F2 = nullptr, *F3 = nullptr, *divB = nullptr;
+    void *T = nullptr, *T1 = nullptr, *C = nullptr, *C1 = nullptr;   // CME tracer: rho c (state type), c
     double *metric = nullptr, *partial = nullptr, *stage_buf = nullptr;
     icarus::Scalars *sc = nullptr;
     double *maps = nullptr, *tmaps = nullptr, *cme = nullptr, *traj = nullptr, *ring = nullptr;

@@ -66,6 +66,7 @@ struct Scalars {               // device-resident step state
     int status;                     // bit 0: non-finite state
     unsigned long long floor_hits;
     long long ring_head;            // probe records written so far
+    double dt_step;                 // dt of the step just completed (set when t advances)
 };
 
 struct Params {

@@ -42,6 +42,34 @@ __device__ __forceinline__ void recover(const Params &P, const TS *u, TW *w, int
 }
 
 // ---------------------------------------------------------------------------------------------
+// cone CME at the inner boundary column (j, k) at time tau: when the column is inside a CME
+// footprint, q (rho, v_r, p, ...) takes the CME values (later CMEs override earlier ones); returns
+// whether it is inside any. The footprint: dot product of unit vectors against cos(half-width),
+// or (spherical cloud) against the crossing threshold.
+__device__ __forceinline__ bool cme_column(const Params &P, double tau, int j, int k, double *q)
+{
+    const long long per = (long long)P.n2 * P.n3, col = (long long)j * P.n3 + k;
+    bool hit = false;
+    for (int c = 0; c < P.n_cme; ++c) {
+        const double *cm = P.cme + 10 * c;
+        if (!(tau >= cm[0] && tau < __dadd_rn(cm[0], cm[1]))) continue;
+        double thr = cm[5];
+        if (P.cme_model == 1) {
+            // spherical cloud: centre at d = r_in - R + v (tau - t_on) on the axis; a column
+            // at r_in is inside while cos(alpha) >= (r_in^2 + d^2 - R^2) / (2 r_in d)
+            const double r0 = P.r_in, R = cm[9];
+            const double d = __dadd_rn(__dsub_rn(r0, R), __dmul_rn(cm[6], __dsub_rn(tau, cm[0])));
+            thr = __ddiv_rn(__dsub_rn(__dadd_rn(__dmul_rn(r0, r0), __dmul_rn(d, d)), __dmul_rn(R, R)),
+                            __dmul_rn(__dmul_rn(2.0, r0), d));
+        }
+        double ex = P.m.colvec[col], ey = P.m.colvec[per + col], ez = P.m.colvec[2 * per + col];
+        double dot = __dadd_rn(__dadd_rn(__dmul_rn(ex, cm[2]), __dmul_rn(ey, cm[3])), __dmul_rn(ez, cm[4]));
+        if (dot >= thr) { q[0] = cm[7]; q[1] = cm[6]; q[2] = cm[8]; hit = true; }
+    }
+    return hit;
+}
+
+// ---------------------------------------------------------------------------------------------
 // ghost fill along r: inner side driven by the maps (+ CME) or a plain rule, outer side a plain
 // rule. One thread per interior (j, k) column.
 template <typename TS, typename TW>
@@ -81,23 +109,7 @@ __device__ __forceinline__ void bnd1_col(const Params &P, TS *__restrict__ U, TW
             double b = P.maps[((long long)m1 * 5 + ord[f]) * per + col];
             q[f] = __dadd_rn(__dmul_rn(__dsub_rn(1.0, w), a), __dmul_rn(w, b));
         }
-        // cone CME: footprint by the dot product of unit vectors against cos(half-width)
-        for (int c = 0; c < P.n_cme; ++c) {
-            const double *cm = P.cme + 10 * c;
-            if (!(tau >= cm[0] && tau < __dadd_rn(cm[0], cm[1]))) continue;
-            double thr = cm[5];
-            if (P.cme_model == 1) {
-                // spherical cloud: centre at d = r_in - R + v (tau - t_on) on the axis; a column
-                // at r_in is inside while cos(alpha) >= (r_in^2 + d^2 - R^2) / (2 r_in d)
-                const double r0 = P.r_in, R = cm[9];
-                const double d = __dadd_rn(__dsub_rn(r0, R), __dmul_rn(cm[6], __dsub_rn(tau, cm[0])));
-                thr = __ddiv_rn(__dsub_rn(__dadd_rn(__dmul_rn(r0, r0), __dmul_rn(d, d)), __dmul_rn(R, R)),
-                                __dmul_rn(__dmul_rn(2.0, r0), d));
-            }
-            double ex = P.m.colvec[col], ey = P.m.colvec[per + col], ez = P.m.colvec[2 * per + col];
-            double dot = __dadd_rn(__dadd_rn(__dmul_rn(ex, cm[2]), __dmul_rn(ey, cm[3])), __dmul_rn(ez, cm[4]));
-            if (dot >= thr) { q[0] = cm[7]; q[1] = cm[6]; q[2] = cm[8]; }
-        }
+        cme_column(P, tau, j, k, q);
         const double igm1 = 1.0 / (P.gamma - 1.0);
 #pragma unroll
         for (int g = 1; g <= NG; ++g) {
@@ -421,6 +433,7 @@ __device__ __forceinline__ void finish_dt(Params &P, double smax_block, int adva
         double dt = sc->cfl / v;
         if (sc->t_stop > 0.0) dt = fmin(dt, fmax(__dsub_rn(sc->t_stop, t), 0.0));
         if (!(v > 0.0)) dt = 0.0;
+        if (advance_t) sc->dt_step = sc->dt;
         sc->t = t;
         sc->dt = dt;
         sc->done = 0;
@@ -826,6 +839,120 @@ k_update_pair(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS
 }
 
 // ---------------------------------------------------------------------------------------------
+// CME tracer: a passive scalar c marking inserted CME plasma; rho c is conserved and carried by
+// the mass flux with the limited linear reconstruction of c on the upwind side (so c = 1 moves
+// exactly like rho); after each stage rho c is clipped to [0, rho].
+// Ghost values of c for the cells the tracer stencil reads: the ghost layers along one direction
+// at interior indices of the other two (its face fluxes never reach a corner). The driven face
+// sets c = 1 in the CME footprint and 0 elsewhere; every other face copies like the MHD state.
+template <typename TW>
+__global__ void k_tracer_ghost(Params P, TW *__restrict__ C, int stage)
+{
+    const long long nr = 2LL * NG * P.n2 * P.n3, nth = 2LL * NG * P.n1 * P.n3, nph = 2LL * NG * P.n1 * P.n2;
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nr + nth + nph) return;
+    int D = 0;
+    if (q >= nr) { q -= nr; D = 1; if (q >= nth) { q -= nth; D = 2; } }
+    const int g = (int)(q % NG) + 1;
+    long long r = q / NG;
+    const int side = (int)(r % 2);
+    r /= 2;
+    const int n = D == 0 ? P.n1 : (D == 1 ? P.n2 : P.n3);
+    const int na = D == 0 ? P.n2 : P.n1;                 // first of the two other indices
+    const int a = (int)(r % na), b = (int)(r / na);
+    const int gi = side == 0 ? -g : n - 1 + g;
+    const int bc = P.bc[2 * D + side];
+    auto at = [&](int s) -> long long {
+        return D == 0 ? cidx(P, s, a, b) : (D == 1 ? cidx(P, a, s, b) : cidx(P, a, b, s));
+    };
+    if (bc == 3) {                                      // driven (inner radial face)
+        double tau = P.sc->t;
+        if (stage == 2) tau = __dadd_rn(tau, P.sc->dt);
+        double qq[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        C[at(gi)] = cme_column(P, tau, a, b, qq) ? TW(1) : TW(0);
+        return;
+    }
+    // continuation (1), mirror (2), periodic (0)
+    const int src = bc == 1 ? (side == 0 ? 0 : n - 1) : (bc == 2 ? (side == 0 ? g - 1 : n - g) : ((gi % n) + n) % n);
+    C[at(gi)] = C[at(src)];
+}
+
+template <int STAGE, typename TS, typename TW>
+__global__ void __launch_bounds__(256)
+k_tracer_update(Params P, const TW *__restrict__ C, const TW *__restrict__ F1, const TW *__restrict__ F2,
+                const TW *__restrict__ F3, const TS *__restrict__ Ts, TS *To, const TS *__restrict__ Unew,
+                TW *__restrict__ Cout)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)P.n1 * P.n2 * P.n3) return;
+    const int i = (int)(tid % P.n1);
+    const long long r_ = tid / P.n1;
+    const int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
+    const long long c = cidx(P, i, j, k);
+    const long long f1 = ((long long)k * P.n2 + j) * (P.n1 + 1) + i;
+    const long long f2 = ((long long)k * (P.n2 + 1) + j) * P.n1 + i;
+    const long long f3 = ((long long)k * P.n2 + j) * P.n1 + i;
+    const long long o3 = (long long)P.n2 * P.n1;
+    const long long st[3] = {1, P.p1, (long long)P.p1 * P.p2};
+    // tracer flux through the lower face of the cell at padded offset cb along d, with mass flux fr
+    auto face = [&](int d, long long cb, TW fr) -> TW {
+        const TW cm2 = C[cb - 2 * st[d]], cm1 = C[cb - st[d]], c0 = C[cb], cp1 = C[cb + st[d]];
+        const TW cl = cm1 + TW(0.5) * limiter<TW>(P.limiter, cm1 - cm2, c0 - cm1);
+        const TW cr = c0 - TW(0.5) * limiter<TW>(P.limiter, c0 - cm1, cp1 - c0);
+        return fr * (fr >= TW(0) ? cl : cr);
+    };
+    // density (field 0) fluxes: F1 [faces r], F2 [faces theta], F3 [faces phi]
+    const TW r0 = face(0, c, F1[f1]), r1 = face(0, c + 1, F1[f1 + 1]);
+    const TW t0 = face(1, c, F2[f2]), t1 = face(1, c + st[1], F2[f2 + P.n1]);
+    const TW p0 = face(2, c, F3[f3]), p1 = face(2, c + st[2], F3[f3 + o3]);
+    const DivFactors<TW> dv(met<TW>(P), i + NG, j + NG);
+    const TW L = dv.div(r0, r1, t0, t1, p0, p1);
+    const long long nt = P.nt;
+    const double dt = STAGE == 1 ? P.sc->dt : P.sc->dt_step;   // the second stage's update has advanced t, dt
+    TS to;
+    if constexpr (Prec<TS, TW>::mixed) {
+        const TW d = narrow_d2f(dt) * L + TW(0);
+        if (STAGE == 1) to = Ts[c] + widen_f2d(d);
+        else to = TS(0.5) * (To[c] + Ts[c]) + widen_f2d(TW(0.5) * d);
+    } else {
+        const TS dts = (TS)dt;
+        if (STAGE == 1) to = Ts[c] + dts * (TS)L + (TS)TW(0);
+        else to = TS(0.5) * To[c] + TS(0.5) * (Ts[c] + dts * (TS)L + (TS)TW(0));
+    }
+    const TS rho = Unew[RHO * nt + c];
+    to = to < TS(0) ? TS(0) : (to > rho ? rho : to);
+    To[c] = to;
+    Cout[c] = (TW)(to / rho);
+}
+
+// rho c = rho * c_in from the current rho (c_in NULL: keep rho c); c = rho c / rho
+template <typename TS, typename TW>
+__global__ void k_tracer_set(Params P, const double *__restrict__ cin, const TS *__restrict__ U, TS *T, TW *C)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)P.n1 * P.n2 * P.n3) return;
+    const int i = (int)(tid % P.n1);
+    const long long r_ = tid / P.n1;
+    const int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
+    const long long c = cidx(P, i, j, k);
+    const TS rho = U[RHO * P.nt + c];
+    if (cin) T[c] = (TS)((double)rho * cin[tid]);
+    C[c] = (TW)(T[c] / rho);
+}
+
+template <typename TS>
+__global__ void k_tracer_get(Params P, const TS *__restrict__ T, const TS *__restrict__ U, double *out)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)P.n1 * P.n2 * P.n3) return;
+    const int i = (int)(tid % P.n1);
+    const long long r_ = tid / P.n1;
+    const int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
+    const long long c = cidx(P, i, j, k);
+    out[tid] = (double)T[c] / (double)U[RHO * P.nt + c];
+}
+
+// ---------------------------------------------------------------------------------------------
 // primitives of every padded cell (after a state upload)
 template <typename TS, typename TW>
 __global__ void k_prims(Params P, const TS *__restrict__ U, TW *__restrict__ W)
@@ -1114,6 +1241,32 @@ template <typename TS, typename TW> struct Launch {
         long long n = (long long)P.n1 * P.n2 * P.n3 * NV;
         k_unpack<TS><<<cdiv(n, 256), 256, 0, s>>>(P, (TS *)U, in);
     }
+    static void tracer_ghost(const Params &P, void *C, int stage, cudaStream_t s)
+    {
+        const long long n = 2LL * NG * ((long long)P.n2 * P.n3 + (long long)P.n1 * P.n3 + (long long)P.n1 * P.n2);
+        k_tracer_ghost<TW><<<cdiv(n, 256), 256, 0, s>>>(P, (TW *)C, stage);
+    }
+    static void tracer_update(const Params &P, int stage, const void *C, const void *F1, const void *F2, const void *F3,
+                              const void *Ts, void *To, const void *Unew, void *Cout, cudaStream_t s)
+    {
+        const long long n = (long long)P.n1 * P.n2 * P.n3;
+        if (stage == 1)
+            k_tracer_update<1, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TW *)C, (const TW *)F1, (const TW *)F2,
+                (const TW *)F3, (const TS *)Ts, (TS *)To, (const TS *)Unew, (TW *)Cout);
+        else
+            k_tracer_update<2, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TW *)C, (const TW *)F1, (const TW *)F2,
+                (const TW *)F3, (const TS *)Ts, (TS *)To, (const TS *)Unew, (TW *)Cout);
+    }
+    static void tracer_set(const Params &P, const double *cin, const void *U, void *T, void *C, cudaStream_t s)
+    {
+        const long long n = (long long)P.n1 * P.n2 * P.n3;
+        k_tracer_set<TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, cin, (const TS *)U, (TS *)T, (TW *)C);
+    }
+    static void tracer_get(const Params &P, const void *T, const void *U, double *out, cudaStream_t s)
+    {
+        const long long n = (long long)P.n1 * P.n2 * P.n3;
+        k_tracer_get<TS><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)T, (const TS *)U, out);
+    }
     static Ops make()
     {
         Ops o;
@@ -1130,6 +1283,10 @@ template <typename TS, typename TW> struct Launch {
         o.unpack = unpack;
         o.fused_stage = nullptr;
         o.fused_blocks = nullptr;
+        o.tracer_ghost = tracer_ghost;
+        o.tracer_update = tracer_update;
+        o.tracer_set = tracer_set;
+        o.tracer_get = tracer_get;
         o.ts_size = sizeof(TS);
         o.tw_size = sizeof(TW);
         return o;

@@ -21,6 +21,13 @@ struct Ops {
     // one whole stage (fluxes, div B, update) in a single kernel; null where not available
     void (*fused_stage)(const Params &, int stage, const void *Us, const void *Ws, void *Uo, void *Wo, cudaStream_t);
     unsigned int (*fused_blocks)(const Params &);
+    // CME tracer: ghost values of c at the stage time; the stage update of rho c (after update);
+    // c of the interior from / to host-layout doubles [n3][n2][n1] (staged on the device)
+    void (*tracer_ghost)(const Params &, void *C, int stage, cudaStream_t);
+    void (*tracer_update)(const Params &, int stage, const void *C, const void *F1, const void *F2, const void *F3,
+                          const void *Ts, void *To, const void *Unew, void *Cout, cudaStream_t);
+    void (*tracer_set)(const Params &, const double *c, const void *U, void *T, void *C, cudaStream_t);
+    void (*tracer_get)(const Params &, const void *T, const void *U, double *c, cudaStream_t);
     size_t ts_size, tw_size;
 };
 int report_error(int code, const char *msg);

@@ -44,7 +44,8 @@ class icarus_options(C.Structure):
                 ("divb", C.c_int), ("divb_coef", C.c_double), ("rho_floor", C.c_double),
                 ("p_floor", C.c_double), ("precision", C.c_int), ("ring_capacity", C.c_int),
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("fused", C.c_int), ("init_vphi", C.c_int), ("cme_model", C.c_int)]
+                ("fused", C.c_int), ("init_vphi", C.c_int), ("cme_model", C.c_int),
+                ("tracer", C.c_int)]
 
 
 _lib = None
@@ -60,6 +61,8 @@ SIGNATURES = {
     "icarus_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double]),
     "icarus_set_stop_time": (C.c_int, [C.c_void_p, C.c_double]),
     "icarus_copy_state": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "icarus_set_tracer": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "icarus_get_tracer": (C.c_int, [C.c_void_p, C.c_void_p]),
     "icarus_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "icarus_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
     "icarus_scales": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -150,6 +153,7 @@ def make_options(o: I.Options, precision=ICARUS_FP64, ring=4096, stream=None, al
     opt.fused = int(bool(fused))
     opt.init_vphi = int(o.init_vphi)
     opt.cme_model = int(o.cme_model)
+    opt.tracer = int(o.tracer)
     opt.cfl, opt.limiter, opt.flux, opt.gravity, opt.divb = o.cfl, o.limiter, o.flux, o.gravity, o.divb
     opt.divb_coef, opt.rho_floor, opt.p_floor = o.divb_coef, o.rho_floor, o.p_floor
     opt.precision, opt.ring_capacity = precision, ring
@@ -212,6 +216,17 @@ def icarus_get_state(ctx, shape):
 def icarus_set_state(ctx, U, t=0.0):
     U = _f64(U)
     _check(load().icarus_set_state(ctx, _ptr(U), float(t)))
+
+
+def icarus_set_tracer(ctx, c):
+    c = _f64(c)
+    _check(load().icarus_set_tracer(ctx, _ptr(c)))
+
+
+def icarus_get_tracer(ctx, shape):
+    c = np.empty(shape)
+    _check(load().icarus_get_tracer(ctx, _ptr(c)))
+    return c
 
 
 def icarus_copy_state(ctx, U_dev_ptr):
@@ -306,6 +321,13 @@ class Solver:
 
     def set_state(self, U, t=0.0):
         icarus_set_state(self.ctx, U, t)
+
+    def set_tracer(self, c):
+        """CME tracer c of the interior cells [n3][n2][n1] (rho c from the current rho)."""
+        icarus_set_tracer(self.ctx, c)
+
+    def get_tracer(self):
+        return icarus_get_tracer(self.ctx, self.shape[1:])
 
     def set_stop_time(self, t_stop):
         icarus_set_stop_time(self.ctx, t_stop)

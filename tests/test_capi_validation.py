@@ -76,6 +76,7 @@ def test_bad_boundary_codes_rejected(ic):
     (1.5, I.Options(divb=2), 0, "divb"),
     (1.5, I.Options(init_vphi=2), 0, "init_vphi"),
     (1.5, I.Options(cme_model=2), 0, "cme_model"),
+    (1.5, I.Options(tracer=2), 0, "tracer"),
     (1.5, I.Options(), 3, "precision"),
 ])
 def test_bad_options_rejected(ic, gamma, opts, precision, msg):
@@ -89,6 +90,14 @@ def test_fused_stage_rejects_hlld(ic):
     ctx = C.c_void_p()
     rc = lib.icarus_init(C.byref(ic.make_grid(sph())), 1.5, 0.0, C.byref(o), C.byref(ctx))
     assert rc == EINVAL and "fused" in lib.icarus_last_error().decode()
+
+
+def test_fused_stage_rejects_tracer(ic):
+    lib = ic.load()
+    o = ic.make_options(I.Options(tracer=1), 2, fused=True)
+    ctx = C.c_void_p()
+    rc = lib.icarus_init(C.byref(ic.make_grid(sph())), 1.5, 0.0, C.byref(o), C.byref(ctx))
+    assert rc == EINVAL and "tracer" in lib.icarus_last_error().decode()
 
 
 def test_null_context_and_negative_counts(ic):
