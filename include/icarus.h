@@ -73,6 +73,11 @@ typedef struct {
     double x2min, x2max;   /* colatitude range in rad (spherical; inside (0, pi)) */
     double x3min, x3max;   /* longitude range in rad, co-rotating frame (spherical) */
     int bc[6];             /* ICARUS_BC_* for (1-, 1+, 2-, 2+, 3-, 3+); DRIVEN only at 1- */
+    int band_refine;       /* static refinement band (a fixed stand-in for the adaptive refinement
+                              of Sect. 2): > 1 makes the radial cells band_refine times narrower
+                              in [band_lo, band_hi] (in ln r when stretched) than outside, with n1
+                              cells in all; 0 or 1: no band; at most 64 */
+    double band_lo, band_hi;   /* the band, x1min < band_lo < band_hi < x1max (AU) */
 } icarus_grid;
 
 typedef void *(*icarus_alloc_fn)(size_t bytes, void *user);

@@ -56,6 +56,8 @@ enum { DIVB_NONE = 0, DIVB_LINDE = 1 };
 typedef struct {
     int n[3], geom, stretch, bc[6];
     double xmin[3], xmax[3];
+    int band_refine;                /* > 1: radial cells band_refine times narrower in [band_lo, band_hi] */
+    double band_lo, band_hi;
     int p[3];
     long nt;                 /* padded cells */
     double *e[3];            /* edges, e[d][i+NG] = lower edge of cell i, i in [-NG, n+NG] */
@@ -79,8 +81,32 @@ typedef struct {
 #define IDX(o, i, j, k) ((((long)(k) + NG) * (o)->p[1] + ((j) + NG)) * (o)->p[0] + ((i) + NG))
 
 /* ---- grid --------------------------------------------------------------------------------- */
+/* Static refinement band (a fixed substitute for the paper's adaptive refinement, Sect. 2): in the
+ * radial coordinate x (ln r on a stretched spherical grid, r or x otherwise) the cells are
+ * band_refine times narrower inside [x(band_lo), x(band_hi)] than outside, with n1 cells over the
+ * whole range: edge i sits where the cell-count density, 1 outside and band_refine inside,
+ * integrates to i / n1 of its total. Ghost edges continue the outside spacing. */
+static double band_edge(const orc_t *o, int i)
+{
+    const int lg = o->geom == GEOM_SPH && o->stretch;
+    const double f = o->band_refine;
+    const double X0 = lg ? log(o->xmin[0]) : o->xmin[0], X1 = lg ? log(o->xmax[0]) : o->xmax[0];
+    const double A = lg ? log(o->band_lo) : o->band_lo, B = lg ? log(o->band_hi) : o->band_hi;
+    if (i == 0) return o->xmin[0];
+    if (i == o->n[0]) return o->xmax[0];
+    const double total = (X1 - X0) + (f - 1.0) * (B - A);       /* integral of the density */
+    const double s = total * i / o->n[0];
+    const double sA = A - X0, sB = sA + f * (B - A);              /* the band's start and end in s */
+    double x;
+    if (s <= sA) x = X0 + s;
+    else if (s <= sB) x = A + (s - sA) / f;
+    else x = B + (s - sB);
+    return lg ? exp(x) : x;
+}
+
 static double edge_pos(const orc_t *o, int d, int i)
 {
+    if (d == 0 && o->band_refine > 1) return band_edge(o, i);
     if (o->geom == GEOM_SPH && d == 0 && o->stretch)
         return o->xmin[0] * pow(o->xmax[0] / o->xmin[0], (double)i / o->n[0]);
     return o->xmin[d] + i * ((o->xmax[d] - o->xmin[d]) / o->n[d]);
@@ -661,6 +687,7 @@ orc_t *orc_create(const int *ig, const double *dg, double gamma, double omega_si
     for (int d = 0; d < 3; d++) { o->n[d] = ig[d]; o->xmin[d] = dg[2 * d]; o->xmax[d] = dg[2 * d + 1]; }
     o->geom = ig[3]; o->stretch = ig[4];
     for (int s = 0; s < 6; s++) o->bc[s] = ig[5 + s];
+    o->band_refine = ig[11]; o->band_lo = dg[6]; o->band_hi = dg[7];
     for (int d = 0; d < 3; d++) o->p[d] = o->n[d] + 2 * NG;
     o->nt = (long)o->p[0] * o->p[1] * o->p[2];
     for (int d = 0; d < 3; d++) {
@@ -801,6 +828,12 @@ void orc_get_state_padded(const orc_t *o, double *Up) { memcpy(Up, o->U, sizeof(
 void orc_fill_ghosts(orc_t *o, double tau) { fill_ghosts(o, o->U, tau); }
 
 double orc_cfl_dt(orc_t *o) { return cfl_dt(o, o->U); }
+
+/* the n + 1 interior edges of direction d */
+void orc_edges(const orc_t *o, int d, double *out)
+{
+    for (int i = 0; i <= o->n[d]; i++) out[i] = o->e[d][i + NG];
+}
 
 /* one SSP-RK2 step: U1 = U + dt L(U, t); U <- U/2 + (U1 + dt L(U1, t + dt))/2; floors after each
  * stage; dt = CFL bound, capped by dt_max when dt_max > 0. Returns dt, or -1 on non-finite state */

@@ -44,6 +44,7 @@ def lib():
             "orc_divb": (None, [P, P]),
             "orc_volumes": (None, [P, P]),
             "orc_centres": (None, [P, I, P]),
+            "orc_edges": (None, [P, I, P]),
             "orc_boundary_values": (None, [P, D, P, P]),
             "orc_floor_hits": (L, [P]),
             "orc_time": (D, [P]),
@@ -76,8 +77,10 @@ class Oracle:
 
     def __init__(self, grid, gamma: float, omega: float, opts):
         self.grid, self.opts = grid, opts
-        ig = np.array([grid.n1, grid.n2, grid.n3, grid.geometry, grid.stretch, *grid.bc], dtype=np.int32)
-        dg = np.array([grid.x1min, grid.x1max, grid.x2min, grid.x2max, grid.x3min, grid.x3max])
+        ig = np.array([grid.n1, grid.n2, grid.n3, grid.geometry, grid.stretch, *grid.bc, grid.band_refine],
+                      dtype=np.int32)
+        dg = np.array([grid.x1min, grid.x1max, grid.x2min, grid.x2max, grid.x3min, grid.x3max,
+                       grid.band_lo, grid.band_hi])
         od = np.array([opts.cfl, opts.divb_coef, opts.rho_floor, opts.p_floor])
         oi = np.array([opts.limiter, opts.flux, opts.gravity, opts.divb, opts.init_vphi, opts.cme_model,
                        opts.tracer], dtype=np.int32)
@@ -151,6 +154,13 @@ class Oracle:
         n = (self.grid.n1, self.grid.n2, self.grid.n3)[d]
         out = np.empty(n + 2 * NG)
         lib().orc_centres(self.h, d, _ptr(out))
+        return out
+
+    def edges(self, d):
+        """The n + 1 interior cell edges of direction d."""
+        n = (self.grid.n1, self.grid.n2, self.grid.n3)[d]
+        out = np.empty(n + 1)
+        lib().orc_edges(self.h, d, _ptr(out))
         return out
 
     def boundary_values(self, tau):

@@ -82,9 +82,27 @@ void drop_graph(icarus_ctx *c)
     c->p_version++;
 }
 
+// radial edge i of a grid with a refined band: in the coordinate u (ln r when stretched, else r)
+// the cell density is band_refine inside the band and 1 outside, and edge i is where its integral
+// from the inner edge reaches i / n1 of the total (ghost edges continue the outer spacing)
+double band_edge(const icarus_grid &g, int i)
+{
+    if (i == 0) return g.x1min;
+    if (i == g.n1) return g.x1max;
+    const bool lg = g.geometry == ICARUS_GEOM_SPHERICAL && g.stretch;
+    auto u = [lg](double r) { return lg ? log(r) : r; };
+    const double f = (double)g.band_refine;
+    const double u0 = u(g.x1min), ua = u(g.band_lo), ub = u(g.band_hi), u1 = u(g.x1max);
+    const double s = ((u1 - u0) + (f - 1.0) * (ub - ua)) * i / g.n1;   // density integral up to edge i
+    const double s_in = ua - u0, s_out = s_in + f * (ub - ua);         // ... at the band's two ends
+    const double x = s <= s_in ? u0 + s : (s <= s_out ? ua + (s - s_in) / f : ub + (s - s_out));
+    return lg ? exp(x) : x;
+}
+
 // edges of direction d at padded edge index e (cell i has lower edge i, i in [-2, n+2])
 double edge(const icarus_grid &g, int d, int i)
 {
+    if (d == 0 && g.band_refine > 1) return band_edge(g, i);
     const int n = d == 0 ? g.n1 : (d == 1 ? g.n2 : g.n3);
     const double lo = d == 0 ? g.x1min : (d == 1 ? g.x2min : g.x3min);
     const double hi = d == 0 ? g.x1max : (d == 1 ? g.x2max : g.x3max);
@@ -270,6 +288,9 @@ int check_grid(const icarus_grid *g)
         return fail(ICARUS_EINVAL, "unknown geometry %d", g->geometry);
     if (!(g->x1max > g->x1min) || !(g->x2max > g->x2min) || !(g->x3max > g->x3min))
         return fail(ICARUS_EINVAL, "empty coordinate range");
+    if (g->band_refine < 0 || g->band_refine > 64) return fail(ICARUS_EINVAL, "band_refine must be in [0, 64]");
+    if (g->band_refine > 1 && !(g->x1min < g->band_lo && g->band_lo < g->band_hi && g->band_hi < g->x1max))
+        return fail(ICARUS_EINVAL, "the refined band must lie strictly inside (x1min, x1max)");
     if (g->geometry == ICARUS_GEOM_SPHERICAL) {
         if (!(g->x1min > 0)) return fail(ICARUS_EINVAL, "r_in must be > 0");
         double d2 = (g->x2max - g->x2min) / g->n2;

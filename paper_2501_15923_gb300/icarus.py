@@ -32,7 +32,8 @@ class IcarusError(RuntimeError):
 class icarus_grid(C.Structure):
     _fields_ = [("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int), ("geometry", C.c_int), ("stretch", C.c_int),
                 ("x1min", C.c_double), ("x1max", C.c_double), ("x2min", C.c_double), ("x2max", C.c_double),
-                ("x3min", C.c_double), ("x3max", C.c_double), ("bc", C.c_int * 6)]
+                ("x3min", C.c_double), ("x3max", C.c_double), ("bc", C.c_int * 6), ("band_refine", C.c_int),
+                ("band_lo", C.c_double), ("band_hi", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -144,7 +145,7 @@ class _TorchAllocator:
 
 def make_grid(g: I.Grid) -> icarus_grid:
     return icarus_grid(g.n1, g.n2, g.n3, g.geometry, g.stretch, g.x1min, g.x1max, g.x2min, g.x2max,
-                       g.x3min, g.x3max, (C.c_int * 6)(*g.bc))
+                       g.x3min, g.x3max, (C.c_int * 6)(*g.bc), g.band_refine, g.band_lo, g.band_hi)
 
 
 def make_options(o: I.Options, precision=ICARUS_FP64, ring=4096, stream=None, allocator=None,

@@ -89,6 +89,9 @@ class Grid:
     x3min: float = 0.0                    # spherical: longitude in the co-rotating frame, rad
     x3max: float = 2.0 * math.pi
     bc: tuple = (BC_DRIVEN, BC_CONT, BC_CONT, BC_CONT, BC_PERIODIC, BC_PERIODIC)
+    band_refine: int = 1                  # > 1: radial cells this many times narrower in the band
+    band_lo: float = 0.0                  # the refined radial band [band_lo, band_hi] (AU)
+    band_hi: float = 0.0
 
     @property
     def ncell(self) -> int:

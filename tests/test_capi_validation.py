@@ -46,6 +46,11 @@ def sph(n1=8, n2=12, n3=8, **kw):
     (sph(x1min=2.0, x1max=1.0), "empty coordinate range"),
     (sph(x1min=0.0), "r_in"),
     (sph(x2min=0.05, x2max=math.pi - 0.05), "colatitude"),
+    (sph(band_refine=65, band_lo=0.5, band_hi=1.0), "band_refine"),
+    (sph(band_refine=-1), "band_refine"),
+    (sph(band_refine=4, band_lo=0.05, band_hi=1.0), "band"),
+    (sph(band_refine=4, band_lo=1.0, band_hi=0.5), "band"),
+    (sph(band_refine=4, band_lo=1.0, band_hi=2.0), "band"),
 ])
 def test_bad_grids_rejected(ic, grid, msg):
     rc, err, ctx = init_rc(ic, grid)

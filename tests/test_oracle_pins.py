@@ -913,3 +913,61 @@ def test_tracer_marks_inserted_cme_plasma():
                 if 0 <= j + dj < hit.shape[0]:
                     far[j + dj, (k + dk) % hit.shape[1]] = False
     assert far.sum() > 0 and np.all(c[far] == 0.0)
+
+
+# ---------------------------------------------------------------------------------------------
+# P11: static refinement band. In the radial coordinate u (ln r on a stretched grid, r on a
+# uniform one) the cell density is band_refine inside [band_lo, band_hi] and 1 outside, and all
+# n1 cells hold the same amount of it. Checked here by interval overlaps of each cell with the band
+# (not by inverting the density): every cell, the two that straddle the band's ends included,
+# holds the same count; the outer edges are exact; the ghost cells continue the outer spacing.
+def band_counts(u_edges, ua, ub, f):
+    lo, hi = u_edges[:-1], u_edges[1:]
+    inside = np.clip(np.minimum(hi, ub) - np.maximum(lo, ua), 0.0, None)
+    return (hi - lo - inside) + f * inside
+
+
+@pytest.mark.parametrize("stretch,f,band", [(1, 4, (0.8, 1.2)), (0, 2, (0.35, 0.9)), (1, 7, (0.15, 0.2)),
+                                            (0, 3, (1.05, 1.95))])
+def test_P11_band_edges_hold_equal_counts(stretch, f, band):
+    g = I.Grid(53, 4, 4, stretch=stretch, band_refine=f, band_lo=band[0], band_hi=band[1])
+    o = Oracle(g, 1.5, 0.0, I.Options())
+    e = o.edges(0)
+    assert e[0] == g.x1min and e[-1] == g.x1max and np.all(np.diff(e) > 0)
+    u = np.log if stretch else (lambda x: x)
+    cnt = band_counts(u(e), u(band[0]), u(band[1]), f)
+    np.testing.assert_allclose(cnt, cnt.mean(), rtol=1e-12)
+    total = (u(g.x1max) - u(g.x1min)) + (f - 1) * (u(band[1]) - u(band[0]))
+    assert abs(cnt.mean() * g.n1 - total) <= 1e-12 * total
+    # cells wholly inside are f times narrower (in u) than cells wholly outside
+    w = np.diff(u(e))
+    ins = (e[:-1] >= band[0]) & (e[1:] <= band[1])
+    assert ins.sum() >= 2
+    np.testing.assert_allclose(w[ins] * f, w[~ins & ((e[1:] <= band[0]) | (e[:-1] >= band[1]))].max(), rtol=1e-12)
+    # ghost cells continue the outside spacing: their edges, recovered from the centres (the
+    # arithmetic mean of a cell's two edges), sit one and two outside widths beyond each end
+    cg, w_out = o.centres(0), cnt.mean()
+    lo1 = 2 * cg[1] - e[0]                          # edge between cells -2 and -1
+    lo2 = 2 * cg[0] - lo1                           # lower edge of cell -2
+    hi1 = 2 * cg[-2] - e[-1]                        # edge between cells n1 and n1 + 1
+    hi2 = 2 * cg[-1] - hi1
+    for d in (u(e[0]) - u(lo1), u(lo1) - u(lo2), u(hi1) - u(e[-1]), u(hi2) - u(hi1)):
+        assert abs(d - w_out) <= 1e-9 * w_out, (d, w_out)
+
+
+def test_P11_band_uniform_rest_preserved():
+    """P1 on a banded stretched grid (band 0.4-0.8 of a 0.1-2 shell, refine 4): the face-area
+    pressure terms balance cell by cell at any spacing."""
+    g = sph_grid(40, 8, 12, bc=(R, C, R, R, P, P))
+    g.band_refine, g.band_lo, g.band_hi = 4, 0.4, 0.8
+    o = Oracle(g, 1.5, 0.0, opts(gravity=0, divb=I.DIVB_NONE))
+    assert np.diff(np.log(o.edges(0))).min() < 0.3 * np.diff(np.log(o.edges(0))).max()
+    W = np.zeros((8, g.n3, g.n2, g.n1))
+    W[0], W[4] = 2.0, 3.0
+    U0 = cons_from_prim(W, 1.5)
+    o.set_state(U0)
+    for _ in range(50):
+        o.step()
+    U, _ = o.get_state()
+    assert np.max(np.abs(U[0] - 2.0)) < 1e-13 * 2.0
+    assert np.max(np.abs(U[1:4])) < 1e-12
