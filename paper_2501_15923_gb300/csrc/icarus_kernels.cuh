@@ -877,29 +877,40 @@ __global__ void k_tracer_ghost(Params P, TW *__restrict__ C, int stage)
     C[at(gi)] = C[at(src)];
 }
 
+// limited slope of the tracer: van Leer branches around its division (c is zero, and its slopes
+// vanish, in most of the domain); the other limiters as for the MHD variables
+template <typename TW> __device__ __forceinline__ TW tracer_slope(int lim, TW a, TW b)
+{
+    if (lim != 1) return limiter<TW>(lim, a, b);
+    if ((a > TW(0) && b > TW(0)) || (a < TW(0) && b < TW(0))) return TW(2) * a * b / (a + b);
+    return TW(0);
+}
+
 template <int STAGE, typename TS, typename TW>
 __global__ void __launch_bounds__(256)
 k_tracer_update(Params P, const TW *__restrict__ C, const TW *__restrict__ F1, const TW *__restrict__ F2,
                 const TW *__restrict__ F3, const TS *__restrict__ Ts, TS *To, const TS *__restrict__ Unew,
                 TW *__restrict__ Cout)
 {
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (long long)P.n1 * P.n2 * P.n3) return;
-    const int i = (int)(tid % P.n1);
-    const long long r_ = tid / P.n1;
-    const int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
+    const unsigned int tid = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^31
+    if (tid >= (unsigned int)(P.n1 * P.n2 * P.n3)) return;
+    const int i = (int)(tid % (unsigned int)P.n1);
+    const unsigned int r_ = tid / (unsigned int)P.n1;
+    const int j = (int)(r_ % (unsigned int)P.n2), k = (int)(r_ / (unsigned int)P.n2);
     const long long c = cidx(P, i, j, k);
     const long long f1 = ((long long)k * P.n2 + j) * (P.n1 + 1) + i;
     const long long f2 = ((long long)k * (P.n2 + 1) + j) * P.n1 + i;
     const long long f3 = ((long long)k * P.n2 + j) * P.n1 + i;
     const long long o3 = (long long)P.n2 * P.n1;
     const long long st[3] = {1, P.p1, (long long)P.p1 * P.p2};
-    // tracer flux through the lower face of the cell at padded offset cb along d, with mass flux fr
+    // tracer flux through the lower face of the cell at padded offset cb along d, with mass flux
+    // fr: fr times the limited linear reconstruction of c on the upwind side (only that side)
     auto face = [&](int d, long long cb, TW fr) -> TW {
-        const TW cm2 = C[cb - 2 * st[d]], cm1 = C[cb - st[d]], c0 = C[cb], cp1 = C[cb + st[d]];
-        const TW cl = cm1 + TW(0.5) * limiter<TW>(P.limiter, cm1 - cm2, c0 - cm1);
-        const TW cr = c0 - TW(0.5) * limiter<TW>(P.limiter, c0 - cm1, cp1 - c0);
-        return fr * (fr >= TW(0) ? cl : cr);
+        const TW cm1 = C[cb - st[d]], c0 = C[cb];
+        TW cu;
+        if (fr >= TW(0)) cu = cm1 + TW(0.5) * tracer_slope<TW>(P.limiter, cm1 - C[cb - 2 * st[d]], c0 - cm1);
+        else cu = c0 - TW(0.5) * tracer_slope<TW>(P.limiter, c0 - cm1, C[cb + st[d]] - c0);
+        return fr * cu;
     };
     // density (field 0) fluxes: F1 [faces r], F2 [faces theta], F3 [faces phi]
     const TW r0 = face(0, c, F1[f1]), r1 = face(0, c + 1, F1[f1 + 1]);

@@ -278,6 +278,47 @@ def paper2019(seed: int = 7, days: float = 42.0, n_maps: int = 454, cadence_h: f
                     np.zeros((0, 8)), traj, t_end=days * DAY, meta={"phase": phase, "tilts": tilts})
 
 
+# The five eruptions of the paper's June-July 2015 case (Sect. 4, Table 2): time at 0.1 AU,
+# latitude and longitude (HEEQ, deg), half-width (deg), speed (km/s).
+PAPER2015_START = "2015-06-10T01:14"
+PAPER2015_CMES = (("2015-06-18T20:00", 11.0, -50.0, 45.0, 1000.0),
+                  ("2015-06-19T14:59", -33.0, 9.0, 54.0, 603.0),
+                  ("2015-06-21T05:01", 7.0, -8.0, 47.0, 1250.0),
+                  ("2015-06-22T21:10", 14.0, 3.0, 45.0, 1155.0),
+                  ("2015-06-25T10:51", 23.0, 46.0, 41.0, 1450.0))
+
+
+def paper2015(seed: int = 11, days: float = 29.875, cadence_h: float = 2.0, grid: Grid | None = None) -> Workload:
+    """Stand-in for the paper's June-July 2015 dynamic case with five CMEs (Sect. 4): a uniform
+    600 x 64 x 192 grid over 0.1-2 AU from 2015-06-10 01:14 for 29.875 days (to 2015-07-09 22:14:
+    8 d relaxation, 7 d of CME insertion, the rest propagation); synthetic maps every 2 h from the
+    production recipe (the paper's cadence for this case is not stated; its 2019 case used 2 h);
+    the five cone CMEs of Table 2 at their times, latitudes, longitudes relative to Earth's,
+    half-widths and speeds, with the production workload's density (1000 cm^-3) and temperature
+    (0.8 MK), which the table does not give, inserted as spherical clouds; the CME tracer on; one
+    probe at Earth (1 AU, latitude 0)."""
+    from datetime import datetime
+    g = grid or Grid(600, 64, 192, stretch=0)
+    rng = SplitMix64(seed)
+    phase = 2.0 * math.pi * rng.uniform()
+    n_maps = int(math.ceil(days * 24.0 / cadence_h)) + 1
+    tilts = tilt_walk(rng, n_maps, math.radians(15.0), step_deg=1.5)
+    th, ph = g.theta_centres(), g.phi_centres()
+    maps = np.stack([current_sheet_map(th, ph, a, phase, OMEGA_SUN, g.x1min) for a in tilts])
+    t_maps = np.arange(n_maps) * cadence_h * 3600.0
+    t_knots = np.arange(0.0, (days + 1.0) * DAY + 1.0, 3600.0)
+    earth = circular_orbit(t_knots, 1.0, 0.0, 0.0, 365.25)
+    t0 = datetime.fromisoformat(PAPER2015_START)
+    cmes = []
+    for when, lat, lon, hw, v in PAPER2015_CMES:
+        t_on = (datetime.fromisoformat(when) - t0).total_seconds()
+        lon_c = (lon_corot(earth, t_on, OMEGA_SUN) + math.radians(lon)) % (2.0 * math.pi)
+        cmes.append(cme_row(t_on, 8 * 3600.0, math.radians(lat), lon_c, math.radians(hw), v * 1e3, 1000e6, 8e5))
+    o = Options(cme_model=CME_SPHERE, tracer=1)
+    return Workload(f"paper2015_{g.n1}x{g.n2}x{g.n3}_dynamic_5cme", g, o, 1.5, OMEGA_SUN, t_maps, maps,
+                    np.array(cmes), earth[None].copy(), t_end=days * DAY, meta={"phase": phase, "tilts": tilts})
+
+
 def ensemble(seed: int = 3, n_members: int = 64, nr_set=(128, 256, 384, 512), nth_range=(32, 64),
              nph_range=(64, 128), days: float = 10.0) -> list:
     """Cone-CME ensemble: speed U(600, 2000) km/s, half-width U(15, 45) deg, direction within

@@ -69,3 +69,23 @@ def test_paper2019_shape_and_cadence():
     w2 = I.paper2019()
     assert np.array_equal(w.maps, w2.maps)
 
+
+
+def test_paper2015_five_cmes_of_the_table():
+    """The 2015 case: the CME onsets are the table's 0.1 AU times counted from 2015-06-10 01:14
+    (8.782, 9.573, 11.158, 12.831, 15.401 d), speeds and half-widths as printed, longitudes
+    relative to Earth's co-rotating longitude at onset; maps every 2 h cover the 29.875 days."""
+    w = I.paper2015()
+    assert (w.grid.n1, w.grid.n2, w.grid.n3, w.grid.stretch) == (600, 64, 192, 0)
+    assert w.cmes.shape == (5, 8)
+    np.testing.assert_allclose(w.cmes[:, 0] / I.DAY, [8 + 18 / 24 + 46 / 1440, 9 + 13 / 24 + 45 / 1440,
+                                                      11 + 3 / 24 + 47 / 1440, 12 + 19 / 24 + 56 / 1440,
+                                                      15 + 9 / 24 + 37 / 1440], rtol=1e-12)
+    np.testing.assert_allclose(w.cmes[:, 5], [1.0e6, 6.03e5, 1.25e6, 1.155e6, 1.45e6])
+    np.testing.assert_allclose(np.degrees(w.cmes[:, 4]), [45, 54, 47, 45, 41])
+    np.testing.assert_allclose(np.degrees(w.cmes[:, 2]), [11, -33, 7, 14, 23])
+    for row, lon in zip(w.cmes, (-50, 9, -8, 3, 46)):
+        d = (row[3] - I.lon_corot(w.traj[0], row[0], I.OMEGA_SUN) - np.radians(lon)) % (2 * np.pi)
+        assert min(d, 2 * np.pi - d) < 1e-12
+    assert w.t_maps[-1] >= w.t_end and np.allclose(np.diff(w.t_maps), 7200.0)
+    assert w.opts.tracer == 1 and w.opts.cme_model == I.CME_SPHERE
