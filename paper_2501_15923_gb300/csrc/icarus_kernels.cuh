@@ -933,7 +933,8 @@ k_tracer_update(Params P, const TW *__restrict__ C, const TW *__restrict__ F1, c
     const TS rho = Unew[RHO * nt + c];
     to = to < TS(0) ? TS(0) : (to > rho ? rho : to);
     To[c] = to;
-    Cout[c] = (TW)(to / rho);
+    if constexpr (Prec<TS, TW>::mixed) Cout[c] = narrow_d2f(to) / narrow_d2f(rho);   // c in single precision
+    else Cout[c] = (TW)(to / rho);
 }
 
 // rho c = rho * c_in from the current rho (c_in NULL: keep rho c); c = rho c / rho

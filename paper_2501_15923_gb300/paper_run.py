@@ -21,7 +21,14 @@ import numpy as np
 
 from . import icarus as ic
 from . import inputs as I
-from .precision import derived, probe_errors, rel_errors
+from .precision import advance, advancing_steps, derived, probe_errors, rel_errors
+
+
+SNAPSHOTS_2015 = (9.0, 10.3, 11.5)     # days: the paper's equatorial-plane snapshots of the CME case
+
+
+def tracer_stats(c: np.ndarray) -> dict:
+    return {"max": float(c.max()), "cells_above_0.5": int((c > 0.5).sum()), "cells_above_0.01": int((c > 0.01).sum())}
 
 
 def run(days: float | None = None, forms=("fp64", "mixed"), chunk: int = 500, ring: int = 1 << 16, log=None,
@@ -29,39 +36,35 @@ def run(days: float | None = None, forms=("fp64", "mixed"), chunk: int = 500, ri
     import torch
     w = I.paper2019(days=days or 42.0) if case == "2019" else I.paper2015(days=days or 29.875)
     days = w.t_end / I.DAY
+    snaps = [d for d in SNAPSHOTS_2015 if d < days] if w.opts.tracer else []
     prec = {"fp64": ic.ICARUS_FP64, "mixed": ic.ICARUS_MIXED, "fp32": ic.ICARUS_FP32}
-    res, states, series = {"workload": w.name, "cells": w.grid.ncell, "maps": int(len(w.t_maps)),
-                           "days": days}, {}, {}
+    res, states, series, tracers = {"workload": w.name, "cells": w.grid.ncell, "maps": int(len(w.t_maps)),
+                                    "days": days}, {}, {}, {}
     for name in forms:
         s = ic.from_workload(w, precision=prec[name], ring=ring)
         s.sample(w.traj, cap=1)
-        t_end = days * I.DAY / s.scales()["t0"]
-        s.set_stop_time(t_end)
-        recs = []
+        t0u = s.scales()["t0"]
+        recs, tracers[name] = [], []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        while True:
-            t, dt = s.time()
-            if t >= t_end * (1 - 1e-15) or dt <= 0.0:
-                break
-            s.step(chunk)
-            rec, n = s.sample(None, cap=ring)
-            recs.append(rec[:n])
+        for d in snaps + [days]:
+            s.set_stop_time(d * I.DAY / t0u)
+            advance(s, d * I.DAY / t0u, chunk, ring, recs)
+            if w.opts.tracer:
+                tracers[name].append((d, s.get_tracer()))
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
         rc, floors = s.status()
         series[name] = np.concatenate(recs)
-        steps = len(series[name]) - 1
+        steps = advancing_steps(series[name])
         U, t = s.get_state()
         states[name] = derived(U, w.gamma)
-        if w.opts.tracer:
-            c = s.get_tracer()
-            res.setdefault("tracer", {})[name] = {"max": float(c.max()), "cells_above_0.5": int((c > 0.5).sum()),
-                                                  "cells_above_0.01": int((c > 0.01).sum())}
         res[name] = {"seconds": secs, "steps": steps, "status": rc, "floor_hits": floors,
                      "mean_dt_s": days * I.DAY / max(steps, 1),
                      "mcell_updates_per_s": w.grid.ncell * steps / secs / 1e6,
-                     "t_days": t * s.scales()["t0"] / I.DAY}
+                     "t_days": t * t0u / I.DAY}
+        if w.opts.tracer:
+            res[name]["tracer"] = {f"{d:g}d": tracer_stats(c) for d, c in tracers[name]}
         if log:
             log(f"{name}: {res[name]}")
         s.close()
@@ -72,6 +75,11 @@ def run(days: float | None = None, forms=("fp64", "mixed"), chunk: int = 500, ri
             res[name]["grid_error_vs_fp64"] = rel_errors(states["fp64"], states[name])
             res[name]["probe_error_vs_fp64"] = probe_errors(series["fp64"], series[name])
             res[name]["speedup_vs_fp64"] = res[name]["mcell_updates_per_s"] / res["fp64"]["mcell_updates_per_s"]
+            if w.opts.tracer:
+                res[name]["tracer_vs_fp64"] = {
+                    f"{d:g}d": {"max_abs": float(np.abs(c - cf).max()),
+                                "cells_above_0.5_differ": int(((c > 0.5) != (cf > 0.5)).sum())}
+                    for (d, c), (_, cf) in zip(tracers[name], tracers["fp64"])}
     return res
 
 

@@ -24,6 +24,7 @@ import numpy as np
 
 from . import icarus as ic
 from . import inputs as I
+from .precision import advance, advancing_steps
 
 
 def band_cells(n1, x1min, x1max, lo, hi, f):
@@ -69,17 +70,11 @@ def run(n1=256, n2=32, n3=64, f=4, days=None, precision="fp64", chunk=500, ring=
         recs = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        while True:
-            t, dt = s.time()
-            if t >= te * (1 - 1e-15) or dt <= 0.0:
-                break
-            s.step(chunk)
-            rec, n = s.sample(None, cap=ring)
-            recs.append(rec[:n])
+        advance(s, te, chunk, ring, recs)
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
         series[name] = np.concatenate(recs)
-        steps = len(series[name]) - 1
+        steps = advancing_steps(series[name])
         rc, floors = s.status()
         res[name] = {"n1": g.n1, "cells": g.ncell, "steps": steps, "seconds": secs, "status": rc,
                      "cell_updates": g.ncell * steps, "mcell_updates_per_s": g.ncell * steps / secs / 1e6}
