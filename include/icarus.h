@@ -49,7 +49,7 @@ enum {
     ICARUS_ENOMEM = -3,      /* device allocation failed */
     ICARUS_ECUDA = -4,       /* a CUDA runtime call failed */
     ICARUS_ENONFINITE = -5,  /* the solution became non-finite (sticky) */
-    ICARUS_ETIMEOUT = -6     /* a bounded device wait gave up (batched form) */
+    ICARUS_ETIMEOUT = -6     /* a bounded device wait gave up (batched form, tensor-core closure) */
 };
 
 enum { ICARUS_BC_PERIODIC = 0, ICARUS_BC_CONT = 1, ICARUS_BC_REFLECT = 2, ICARUS_BC_DRIVEN = 3 };

@@ -4,9 +4,11 @@
 // restricted fine solution; trained on the GPU by the kernels below.
 //
 // Every convolution runs on the tensor cores as an implicit GEMM with BF16 operands and FP32
-// accumulation (mma.sync m16n8k16): forward (rows = voxels, K = 27 taps x C_in), data gradient
-// (rows = padded voxels, K = 27 x C_out, transposed weights), weight gradient (rows = C_out,
-// columns = C_in, K = voxels, split over blocks and summed with atomics). Activations are stored
+// accumulation: the forward (rows = voxels, K = 27 taps x C_in) on the 5th-generation tensor
+// cores (tcgen05.mma, accumulators in tensor memory, operands staged in shared memory); the data
+// gradient (rows = padded voxels, K = 27 x C_out, transposed weights) and the weight gradient
+// (rows = C_out, columns = C_in, K = voxels, split over blocks and summed with atomics) with
+// mma.sync m16n8k16. Activations are stored
 // channels-last on a grid padded by one ghost layer; a pad kernel fills the ghosts (replicate /
 // circular) and a fold kernel adds ghost gradients back to the cells they copy (the adjoint).
 // Channel counts are padded to multiples of 16 (layer 0 input 8 -> 16 zero channels, layer 3
@@ -77,83 +79,232 @@ __device__ __forceinline__ void mma16816(float *d, const uint32_t *a, uint32_t b
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// ---- forward: y = act(conv(P(x)) + b) -----------------------------------------------------------
-// block = 4 warps, 128 voxels (each warp 2 m16 row tiles); all O output channels per block.
-// out_pad (bf16, padded, may be null) receives act(y); out_f (fp32 [N][O], may be null) too.
-template <int C, int O, int ACT>
-__global__ void __launch_bounds__(128) k_conv_fwd(Geo g, const bf16 *__restrict__ in, const bf16 *__restrict__ w,
-                                                  const float *__restrict__ b, bf16 *out_pad, float *out_f)
+// ---- forward on the 5th-generation tensor cores (tcgen05, accumulators in tensor memory) ---------
+// The same y = act(conv(P(x)) + b) as an implicit GEMM D[128 voxels][O] = sum over the 27 taps and
+// the input channels, one tcgen05.mma (M = 128, N = O, K = 16, BF16 in, FP32 accumulate) per tap
+// and 16 channels, issued by one thread, accumulated in tensor memory (32 columns).
+// A tile is 128 consecutive voxels along r at fixed (j, k). Shared memory holds the nine r-lines
+// (j + d2, k + d3) of the padded input around it, with one halo voxel on each side (130 rows), in
+// the no-swizzle K-major operand layout: a row is 16 bytes (8 channels), rows of one channel group
+// are consecutive ([line][group][row][8 channels]), so 8-row core matrices are 128 bytes apart
+// (stride offset) and channel groups ROWS x 16 bytes apart (leading offset). The operand of tap
+// (d1, d2, d3) is then line (d2, d3) started d1 + 1 rows in: a 16-byte shift of the descriptor's
+// start address, no re-staging per tap. The weights of all taps are staged once per block in the
+// same layout ([tap][group][o][8]). Persistent blocks (one per SM: 206 KB of shared memory at
+// C = O = 32) loop over tiles; while the tensor core works on tile n, the threads copy tile n + 1
+// into the other buffer (cp.async, zero fill beyond the grid's ghost layer), then read D
+// (tcgen05.ld), add the bias, apply the ReLU and store. Waits on the MMA completion barrier are
+// bounded: on expiry the block records the failure in tc_status and stops.
+__device__ int tc_status;
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 2, tig = lane & 3;
-    const long long v0 = (long long)blockIdx.x * 128 + warp * 32;
-    long long pb[2][2];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            long long v = v0 + mt * 16 + grp + 8 * h;
-            pb[mt][h] = pidx_of_voxel(g, v < g.N ? v : 0);
-        }
-    float acc[2][O / 8][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < O / 8; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
-    for (int t = 0; t < 27; ++t) {
-        const long long off = tap_off(g, t);
-#pragma unroll
-        for (int ks = 0; ks < C / 16; ++ks) {
-            uint32_t a[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const bf16 *r0 = in + (pb[mt][0] + off) * C + ks * 16 + tig * 2;
-                const bf16 *r1 = in + (pb[mt][1] + off) * C + ks * 16 + tig * 2;
-                a[mt][0] = ld32(r0);
-                a[mt][1] = ld32(r1);
-                a[mt][2] = ld32(r0 + 8);
-                a[mt][3] = ld32(r1 + 8);
-            }
-#pragma unroll
-            for (int nt = 0; nt < O / 8; ++nt) {
-                const bf16 *wb = w + ((long long)(nt * 8 + grp) * 27 + t) * C + ks * 16 + tig * 2;
-                const uint32_t b0 = ld32(wb), b1 = ld32(wb + 8);
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], a[mt], b0, b1);
-            }
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr(dst)), "l"(src), "r"(bytes) : "memory");
+}
+
+// shared-memory matrix descriptor: no swizzle, start / leading / stride byte offsets in 16-byte units
+__device__ __forceinline__ uint64_t umma_desc(uint32_t start, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((start & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, N = O, M = 128
+template <int O> __device__ __forceinline__ uint32_t umma_idesc()
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(O >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int C> __host__ __device__ constexpr int tc_a_bytes() { return 9 * (C / 8) * 130 * 16; }
+template <int C, int O> __host__ __device__ constexpr int tc_b_bytes() { return 27 * (C / 8) * O * 16; }
+// (+ 1 KB of slack after the weights)
+template <int C, int O> __host__ __device__ constexpr int tc_smem_bytes() { return 128 + tc_b_bytes<C, O>() + 2 * tc_a_bytes<C>() + 1024; }
+
+template <int C>
+__device__ __forceinline__ void tc_stage_tile(const Geo &g, const bf16 *__restrict__ in, long long tile, int tpl,
+                                              unsigned char *dst)
+{
+    constexpr int G = C / 8, ROWS = 130;
+    const long long line = tile / tpl;
+    const int i0 = (int)(tile % tpl) * 128;
+    const int j = (int)(line % g.n2), k = (int)(line / g.n2);
+    // line by line; a warp copies 32 / G consecutive rows, all G groups of each: each group's rows
+    // land as one contiguous run of shared memory, the warp reads 32 / G whole voxels
+    constexpr int RW = 32 / G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int grp = lane / RW, rl = lane % RW;
+    const int last = g.n1 + 1 - i0;                    // rows 0 .. last hold voxels -1 .. n1
+#pragma unroll 1
+    for (int L = 0; L < 9; ++L) {
+        const bf16 *line_src = in + pidx(g, i0 - 1, j + L % 3 - 1, k + L / 3 - 1) * C + grp * 8;
+        unsigned char *line_dst = dst + (L * G + grp) * ROWS * 16;
+        for (int row = warp * RW + rl; row < ROWS; row += nw * RW) {
+            const bool ok = row <= last;
+            cp_async16(line_dst + row * 16, ok ? line_src + (long long)row * C : in, ok ? 16 : 0);
         }
     }
+}
+
+template <int C, int O, int ACT>
+__global__ void __launch_bounds__(256, 1) k_conv_fwd_tc(Geo g, const bf16 *__restrict__ in, const bf16 *__restrict__ w,
+                                                        const float *__restrict__ b, bf16 *out_pad, float *out_f)
+{
+    constexpr int G = C / 8, ROWS = 130, H = O / 2;
+    extern __shared__ __align__(128) unsigned char smem[];
+    // [barrier, tensor-memory address, flag | 128 B][A tile, buffer 0][A tile, buffer 1][weights]
+    unsigned char *sA[2] = {smem + 128, smem + 128 + tc_a_bytes<C>()};
+    unsigned char *sB = smem + 128 + 2 * tc_a_bytes<C>();
+    const uint32_t bar = saddr(smem), slot = saddr(smem + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tpl = (g.n1 + 127) / 128;
+    const long long ntiles = (long long)tpl * g.n2 * g.n3;
+
+    for (int q = tid; q < 27 * G * O; q += blockDim.x) {     // weights: q = (t * G + grp) * O + o
+        const int o = q % O, tg = q / O, grp = tg % G, t = tg / G;
+        cp_async16(sB + q * 16, w + ((long long)o * 27 + t) * C + grp * 8, 16);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(slot) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    long long tile = blockIdx.x;
+    if (tile < ntiles) tc_stage_tile<C>(g, in, tile, tpl, sA[0]);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(smem + 8);
+    const uint32_t idesc = umma_idesc<O>();
+    uint32_t parity = 0;
+    int buf = 0;
+    for (; tile < ntiles; tile += gridDim.x) {
+        if (tid == 0) {
+            // base descriptors; each operand's start moves by a compile-time number of 16-byte
+            // units (the start field is the low 14 bits and never carries: addresses < 256 KB)
+            const uint64_t dA = umma_desc(saddr(sA[buf]), ROWS * 16, 128), dB = umma_desc(saddr(sB), O * 16, 128);
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+            for (int t = 0; t < 27; ++t) {
+                const int d1 = t % 3, L = t / 3;             // L = (d3 + 1) * 3 + (d2 + 1)
 #pragma unroll
-        for (int nt = 0; nt < O / 8; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int h = e >> 1, col = nt * 8 + tig * 2 + (e & 1);
-                const long long v = v0 + mt * 16 + grp + 8 * h;
-                if (v >= g.N) continue;
-                float val = acc[mt][nt][e] + b[col];
-                if (ACT) val = fmaxf(val, 0.f);
-                if (out_pad) out_pad[pb[mt][h] * O + col] = __float2bfloat16_rn(val);
-                if (out_f) out_f[v * O + col] = val;
+                for (int ks = 0; ks < C / 16; ++ks) {
+                    const uint64_t ad = dA + (uint64_t)((L * G + 2 * ks) * ROWS + d1);
+                    const uint64_t bd = dB + (uint64_t)((t * G + 2 * ks) * O);
+                    const uint32_t acc = (t | ks) ? 1u : 0u;
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+                                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                 : "memory");
+                }
             }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                         : "memory");
+        }
+        const long long nxt = tile + gridDim.x;
+        if (nxt < ntiles) tc_stage_tile<C>(g, in, nxt, tpl, sA[buf ^ 1]);
+        if (tid == 0) *reinterpret_cast<volatile int *>(smem + 12) = mbar_wait(bar, parity) ? 1 : 0;
+        parity ^= 1;
+        __syncthreads();                                      // the MMAs of this tile are complete
+        if (*reinterpret_cast<volatile int *>(smem + 12) == 0) {   // they never completed: give up
+            if (tid == 0) atomicExch(&tc_status, 1);
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // D rows 32 (warp % 4) .. + 31 (tensor-memory lanes), columns (warp / 4) * O/2 .. + O/2
+        uint32_t r[H];
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * H);
+        if constexpr (H == 16) {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15])
+                         : "r"(ta));
+        } else {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(ta));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        {
+            const long long line = tile / tpl;
+            const int i = (int)(tile % tpl) * 128 + 32 * (warp & 3) + lane;
+            if (i < g.n1) {
+                const int j = (int)(line % g.n2), k = (int)(line / g.n2), c0 = (warp >> 2) * H;
+                float v[H];
+#pragma unroll
+                for (int e = 0; e < H; ++e) {
+                    v[e] = __uint_as_float(r[e]) + b[c0 + e];
+                    if (ACT) v[e] = fmaxf(v[e], 0.f);
+                }
+                if (out_pad) {
+                    uint32_t pk[H / 2];
+#pragma unroll
+                    for (int e = 0; e < H / 2; ++e)
+                        pk[e] = pack2(__float2bfloat16_rn(v[2 * e]), __float2bfloat16_rn(v[2 * e + 1]));
+                    uint4 *dst = reinterpret_cast<uint4 *>(out_pad + pidx(g, i, j, k) * O + c0);
+#pragma unroll
+                    for (int e = 0; e < H / 8; ++e) dst[e] = make_uint4(pk[4 * e], pk[4 * e + 1], pk[4 * e + 2], pk[4 * e + 3]);
+                }
+                if (out_f) {
+                    float4 *dst = reinterpret_cast<float4 *>(out_f + (((long long)k * g.n2 + j) * g.n1 + i) * O + c0);
+#pragma unroll
+                    for (int e = 0; e < H / 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+                }
+            }
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        buf ^= 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem) : "memory");
 }
 
 // ---- padding and its adjoint ------------------------------------------------------------------
 template <typename T>
 __global__ void k_pad_fill(Geo g, T *buf, int C)
 {
-    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= g.NP) return;
-    int ip = (int)(q % g.q1);
-    long long r = q / g.q1;
-    int jp = (int)(r % g.q2), kp = (int)(r / g.q2);
-    int i = ip - 1, j = jp - 1, k = kp - 1;
+    const unsigned int q = blockIdx.x * blockDim.x + threadIdx.x;     // padded cells < 2^31
+    if (q >= (unsigned int)g.NP) return;
+    const unsigned int r = q / (unsigned int)g.q1;
+    const int i = (int)(q % (unsigned int)g.q1) - 1, j = (int)(r % (unsigned int)g.q2) - 1,
+              k = (int)(r / (unsigned int)g.q2) - 1;
     if (i >= 0 && i < g.n1 && j >= 0 && j < g.n2 && k >= 0 && k < g.n3) return;
-    int si = min(max(i, 0), g.n1 - 1), sj = min(max(j, 0), g.n2 - 1), sk = (k + g.n3) % g.n3;
-    long long src = pidx(g, si, sj, sk);
-    for (int c = 0; c < C; ++c) buf[q * C + c] = buf[src * C + c];
+    const int si = min(max(i, 0), g.n1 - 1), sj = min(max(j, 0), g.n2 - 1), sk = (k + g.n3) % g.n3;
+    const long long src = pidx(g, si, sj, sk);
+    if ((C * sizeof(T)) % 16 == 0) {                  // whole cells in 16-byte pieces
+        const uint4 *s = reinterpret_cast<const uint4 *>(buf + src * C);
+        uint4 *d = reinterpret_cast<uint4 *>(buf + (long long)q * C);
+        for (int c = 0; c < (int)(C * sizeof(T) / 16); ++c) d[c] = s[c];
+    } else {
+        for (int c = 0; c < C; ++c) buf[(long long)q * C + c] = buf[src * C + c];
+    }
 }
 
 // add every ghost cell's gradient to the interior cell it copies (in place, interior = result)
@@ -355,15 +506,23 @@ __global__ void __launch_bounds__(128) k_conv_dgrad(Geo g, const bf16 *__restric
 __global__ void k_norm_in(Geo g, const double *__restrict__ U, const double *__restrict__ mean,
                           const double *__restrict__ scale, bf16 *x)
 {
-    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= g.N) return;
-    const int i = (int)(v % g.n1);
-    const long long q = pidx_of_voxel(g, v);
-    for (int c = 0; c < 16; ++c) {
-        float val = 0.f;
-        if (c < NV) val = (float)((U[c * g.N + v] - mean[c * g.n1 + i]) / scale[c * g.n1 + i]);
-        x[q * 16 + c] = __float2bfloat16_rn(val);
+    const unsigned int v = blockIdx.x * blockDim.x + threadIdx.x;     // voxels < 2^31
+    if (v >= (unsigned int)g.N) return;
+    const unsigned int r = v / (unsigned int)g.n1;
+    const int i = (int)(v % (unsigned int)g.n1), j = (int)(r % (unsigned int)g.n2), k = (int)(r / (unsigned int)g.n2);
+    // (U - mean) in double, the division by the scale in single precision (the result is BF16)
+    uint32_t pk[8];
+#pragma unroll
+    for (int c = 0; c < NV; c += 2) {
+        const float a = (float)(U[c * g.N + v] - mean[c * g.n1 + i]) / (float)scale[c * g.n1 + i];
+        const float b = (float)(U[(c + 1) * g.N + v] - mean[(c + 1) * g.n1 + i]) / (float)scale[(c + 1) * g.n1 + i];
+        pk[c / 2] = pack2(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
     }
+#pragma unroll
+    for (int c = 4; c < 8; ++c) pk[c] = 0u;            // channels 8 .. 15 are zero padding
+    uint4 *d = reinterpret_cast<uint4 *>(x + pidx(g, i, j, k) * 16);
+    d[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    d[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
 }
 
 // loss = mean over voxels and the 8 fields of (y - dU / oscale)^2; dy = its gradient
@@ -466,12 +625,39 @@ unsigned int ccdiv(long long a, long long b) { return (unsigned int)((a + b - 1)
 // layer shapes (C_in padded, C_out padded, real C_in, real C_out)
 const int LC[4] = {16, 32, 32, 32}, LO[4] = {32, 32, 32, 16}, RC[4] = {8, 32, 32, 32}, RO[4] = {32, 32, 32, 8};
 
+// persistent tcgen05 forward: one block per SM (at most one per tile)
+template <int C, int O, int ACT>
+void launch_fwd_tc(Geo g, const bf16 *in, const bf16 *w, const float *b, bf16 *out_pad, float *out_f, cudaStream_t s)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_conv_fwd_tc<C, O, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes<C, O>());
+    }
+    const long long tiles = (long long)((g.n1 + 127) / 128) * g.n2 * g.n3;
+    const unsigned int nb = (unsigned int)(tiles < sms ? tiles : sms);
+    k_conv_fwd_tc<C, O, ACT><<<nb, 256, tc_smem_bytes<C, O>(), s>>>(g, in, w, b, out_pad, out_f);
+}
+
+// a tcgen05 forward block whose MMA completion wait expired (read and cleared; call after a sync)
+bool tc_timed_out()
+{
+    int v = 0;
+    cudaMemcpyFromSymbol(&v, tc_status, sizeof v);
+    if (v) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(tc_status, &zero, sizeof zero);
+    }
+    return v != 0;
+}
+
 void launch_fwd(int l, Geo g, const bf16 *in, const bf16 *w, const float *b, bf16 *out_pad, float *out_f, cudaStream_t s)
 {
-    const unsigned int nb = ccdiv(g.N, 128);
-    if (l == 0) k_conv_fwd<16, 32, 1><<<nb, 128, 0, s>>>(g, in, w, b, out_pad, out_f);
-    else if (l < 3) k_conv_fwd<32, 32, 1><<<nb, 128, 0, s>>>(g, in, w, b, out_pad, out_f);
-    else k_conv_fwd<32, 16, 0><<<nb, 128, 0, s>>>(g, in, w, b, out_pad, out_f);
+    if (l == 0) launch_fwd_tc<16, 32, 1>(g, in, w, b, out_pad, out_f, s);
+    else if (l < 3) launch_fwd_tc<32, 32, 1>(g, in, w, b, out_pad, out_f, s);
+    else launch_fwd_tc<32, 16, 0>(g, in, w, b, out_pad, out_f, s);
 }
 
 void launch_wgrad(int l, Geo g, const bf16 *dpre, const bf16 *in, float *dw, cudaStream_t s)
@@ -691,6 +877,7 @@ int icarus_closure_train_step(icarus_closure *c, const double *U_in, const doubl
     if (loss) {
         CCK(cudaMemcpyAsync(loss, c->loss, 8, cudaMemcpyDeviceToHost, s));
         CCK(cudaStreamSynchronize(s));
+        if (tc_timed_out()) return report_error(ICARUS_ETIMEOUT, "tensor-core forward: MMA completion wait expired");
     }
     CCK(cudaGetLastError());
     return ICARUS_OK;
@@ -830,6 +1017,7 @@ int icarus_conv3d_layer(int n1, int n2, int n3, int C, int O, int act, const flo
         k_pad_fold<<<ccdiv(gg.NP, 256), 256>>>(gg, dinf, C);
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) rc = report_error(ICARUS_ECUDA, cudaGetErrorString(e));
+        else if (tc_timed_out()) rc = report_error(ICARUS_ETIMEOUT, "tensor-core forward: MMA completion wait expired");
         if (!rc) {
             cudaMemcpy(y, yf, gg.N * O * 4, cudaMemcpyDeviceToHost);
             cudaMemcpy(dw, dwf, O * 27 * C * 4, cudaMemcpyDeviceToHost);

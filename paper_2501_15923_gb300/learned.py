@@ -231,6 +231,42 @@ def pair_gain(net, pairs: PairSet, indices):
     return math.sqrt(num / max(den, 1e-300))
 
 
+FLOPS_PER_VOXEL = 2 * 27 * (8 * 32 + 32 * 32 + 32 * 32 + 32 * 8)   # forward of the unpadded network
+
+
+def time_network(shape=(256, 32, 64), reps: int = 20, seed: int = 5):
+    """CUDA-event time of one prediction (forward + normalisation) and of one training step on a
+    coarse grid of the given shape, random weights and inputs; with the tensor-core rate of the
+    forward from the network's algorithmic flops."""
+    import torch
+    n1, n2, n3 = shape
+    net = ic.Closure(n1, n2, n3, seed=seed, stream=torch.cuda.current_stream().cuda_stream)
+    net.set_norm(np.zeros(8), np.ones(8), np.ones(8))
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    U = torch.randn((8, n3, n2, n1), dtype=torch.float64, device="cuda", generator=g)
+    dU = torch.randn((8, n3, n2, n1), dtype=torch.float64, device="cuda", generator=g) * 0.01
+    out = torch.empty_like(U)
+    res = {}
+    for name, fn in (("predict", lambda: net.predict(U.data_ptr(), out.data_ptr())),
+                     ("train_step", lambda: net.train_step(U.data_ptr(), dU.data_ptr(), 1e-4))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name + "_ms"] = e0.elapsed_time(e1) / reps
+    vox = n1 * n2 * n3
+    res["predict_tflops"] = FLOPS_PER_VOXEL * vox / (res["predict_ms"] * 1e-3) / 1e12
+    res["train_step_tflops"] = 3 * FLOPS_PER_VOXEL * vox / (res["train_step_ms"] * 1e-3) / 1e12
+    res["shape"] = list(shape)
+    net.close()
+    return res
+
+
 def main(argv=None):
     """Full pipeline at production size: pairs, training, held-out evaluation; prints JSON."""
     import argparse
@@ -244,9 +280,13 @@ def main(argv=None):
     p.add_argument("--lr", type=float, default=1e-3)
     p.add_argument("--eval-window", type=float, default=1.0)
     p.add_argument("--fine", default="512x64x128")
+    p.add_argument("--time-only", action="store_true", help="only time the network kernels on the coarse grid")
     a = p.parse_args(argv)
     fine = tuple(int(x) for x in a.fine.split("x"))
     torch.cuda.set_device(0)
+    if a.time_only:
+        print(json.dumps(time_network((fine[0] // 2, fine[1] // 2, fine[2] // 2))))
+        return
     log = lambda s: print(s, flush=True)
     t0 = time.perf_counter()
     pairs = generate_pairs(range(100, 100 + a.seeds), a.windows, a.spinup, fine=fine, log=log)

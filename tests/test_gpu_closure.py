@@ -32,7 +32,8 @@ def bf16(a):
 
 
 @pytest.mark.parametrize("C,Oc,act,shape", [(16, 32, 1, (11, 6, 5)), (32, 32, 1, (9, 7, 4)), (32, 16, 0, (13, 5, 6)),
-                                            (32, 32, 1, (40, 12, 10))])
+                                            (32, 32, 1, (40, 12, 10)), (32, 32, 1, (150, 5, 3)),
+                                            (16, 32, 1, (256, 3, 2)), (32, 16, 0, (129, 4, 3))])
 def test_layer_forward_and_gradients_match_oracle(ic, C, Oc, act, shape):
     n1, n2, n3 = shape
     rng = np.random.default_rng(C * 100 + Oc + n1)
