@@ -13,6 +13,8 @@
 // circular) and a fold kernel adds ghost gradients back to the cells they copy (the adjoint).
 // Channel counts are padded to multiples of 16 (layer 0 input 8 -> 16 zero channels, layer 3
 // output 8 -> 16 with zero weights); the padding never carries a gradient.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -86,16 +88,21 @@ __device__ __forceinline__ void mma16816(float *d, const uint32_t *a, uint32_t b
 // A tile is 128 consecutive voxels along r at fixed (j, k). Shared memory holds the nine r-lines
 // (j + d2, k + d3) of the padded input around it, with one halo voxel on each side (130 rows), in
 // the no-swizzle K-major operand layout: a row is 16 bytes (8 channels), rows of one channel group
-// are consecutive ([line][group][row][8 channels]), so 8-row core matrices are 128 bytes apart
-// (stride offset) and channel groups ROWS x 16 bytes apart (leading offset). The operand of tap
-// (d1, d2, d3) is then line (d2, d3) started d1 + 1 rows in: a 16-byte shift of the descriptor's
-// start address, no re-staging per tap. The weights of all taps are staged once per block in the
-// same layout ([tap][group][o][8]). Persistent blocks (one per SM: 206 KB of shared memory at
-// C = O = 32) loop over tiles; while the tensor core works on tile n, the threads copy tile n + 1
-// into the other buffer (cp.async, zero fill beyond the grid's ghost layer), then read D
-// (tcgen05.ld), add the bias, apply the ReLU and store. Waits on the MMA completion barrier are
-// bounded: on expiry the block records the failure in tc_status and stops.
+// are consecutive ([line][group][row][8 channels], each (line, group) block padded to 136 rows so
+// that it starts on a 128-byte boundary), so 8-row core matrices are 128 bytes apart (stride
+// offset) and channel groups one block apart (leading offset). The operand of tap (d1, d2, d3) is
+// then line (d2, d3) started d1 + 1 rows in: a 16-byte shift of the descriptor's start address,
+// no re-staging per tap. The tensor memory accelerator fills each block with one 130 x 8 box of a
+// 5-D tensor map (channel in group, group, i, j, k), zero beyond the padded line; the weights of
+// all taps are staged once per block in the same layout ([tap][group][o][8]). Persistent blocks
+// of 128 threads (one per SM, 209 KB of shared memory at C = O = 32) loop over tiles with two
+// input buffers and two accumulators (64 tensor-memory columns): thread 0 waits for tile n's
+// copies and issues its MMAs into accumulator n % 2; once tile n-1's MMAs are done it starts tile
+// n+1's copies into the buffer they read, and every thread reads its row of tile n-1's D
+// (tcgen05.ld), adds the bias, applies the ReLU and stores, while the tensor core works on tile n. All waits are bounded: on expiry the block records the failure in
+// tc_status and stops.
 __device__ int tc_status;
+bool tc_host_error = false;
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -131,47 +138,119 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-template <int C> __host__ __device__ constexpr int tc_a_bytes() { return 9 * (C / 8) * 130 * 16; }
+// one (line, channel group) block of an A tile: 130 rows of 16 bytes, padded to 136 rows so that
+// every block (a tensor-copy destination) starts on a 128-byte boundary
+constexpr int TC_BLOCK = 136 * 16;
+template <int C> __host__ __device__ constexpr int tc_a_bytes() { return 9 * (C / 8) * TC_BLOCK; }
 template <int C, int O> __host__ __device__ constexpr int tc_b_bytes() { return 27 * (C / 8) * O * 16; }
-// (+ 1 KB of slack after the weights)
-template <int C, int O> __host__ __device__ constexpr int tc_smem_bytes() { return 128 + tc_b_bytes<C, O>() + 2 * tc_a_bytes<C>() + 1024; }
+// (+ 128 B to align the start to 128 bytes, + 1 KB of slack after the weights)
+template <int C, int O> __host__ __device__ constexpr int tc_smem_bytes() { return 128 + 128 + tc_b_bytes<C, O>() + 2 * tc_a_bytes<C>() + 1024; }
 
+// the nine r-lines of tile `tile` into dst by the tensor memory accelerator: one box of 130 rows x
+// 8 channels per line and channel group (tensor map dims: channel in group, group, i, j, k of the
+// padded grid); rows past the padded line are zero-filled; completion counted on barrier bar
 template <int C>
-__device__ __forceinline__ void tc_stage_tile(const Geo &g, const bf16 *__restrict__ in, long long tile, int tpl,
-                                              unsigned char *dst)
+__device__ __forceinline__ void tc_load_tile(const CUtensorMap *tm, const Geo &g, long long tile, int tpl,
+                                             unsigned char *dst, uint32_t bar)
 {
     constexpr int G = C / 8, ROWS = 130;
     const long long line = tile / tpl;
-    const int i0 = (int)(tile % tpl) * 128;
+    const int i0 = (int)(tile % tpl) * 128;            // padded index of voxel i0 - 1
     const int j = (int)(line % g.n2), k = (int)(line / g.n2);
-    // line by line; a warp copies 32 / G consecutive rows, all G groups of each: each group's rows
-    // land as one contiguous run of shared memory, the warp reads 32 / G whole voxels
-    constexpr int RW = 32 / G;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int grp = lane / RW, rl = lane % RW;
-    const int last = g.n1 + 1 - i0;                    // rows 0 .. last hold voxels -1 .. n1
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(9 * G * ROWS * 16)
+                 : "memory");
 #pragma unroll 1
-    for (int L = 0; L < 9; ++L) {
-        const bf16 *line_src = in + pidx(g, i0 - 1, j + L % 3 - 1, k + L / 3 - 1) * C + grp * 8;
-        unsigned char *line_dst = dst + (L * G + grp) * ROWS * 16;
-        for (int row = warp * RW + rl; row < ROWS; row += nw * RW) {
-            const bool ok = row <= last;
-            cp_async16(line_dst + row * 16, ok ? line_src + (long long)row * C : in, ok ? 16 : 0);
-        }
+    for (int L = 0; L < 9; ++L)
+#pragma unroll
+        for (int grp = 0; grp < G; ++grp)
+            asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n"
+                         ::"r"(saddr(dst + (L * G + grp) * TC_BLOCK)), "l"(tm), "r"(0), "r"(grp), "r"(i0),
+                         "r"(j + L % 3), "r"(k + L / 3), "r"(bar)
+                         : "memory");
+}
+
+// partial accumulators per tile (consecutive MMAs rotate over them; the epilogue adds them). One:
+// four measured no faster at these sizes, the MMAs are not what limits the kernel
+constexpr int TC_PARTS = 1;
+
+template <int O> __device__ __forceinline__ void tc_ld(uint32_t ta, uint32_t *r)
+{
+    if constexpr (O == 32) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                       "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                       "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                       "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                     : "r"(ta));
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                       "=r"(r[14]), "=r"(r[15])
+                     : "r"(ta));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+template <int C, int O, int ACT>
+__device__ __forceinline__ void tc_epilogue(const Geo &g, uint32_t ta, long long tile, int tpl, const float *__restrict__ b,
+                                            bf16 *out_pad, float *out_f)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float acc[O];
+    uint32_t r[O];
+    tc_ld<O>(ta, r);
+#pragma unroll
+    for (int e = 0; e < O; ++e) acc[e] = __uint_as_float(r[e]);
+#pragma unroll
+    for (int p = 1; p < TC_PARTS; ++p) {
+        tc_ld<O>(ta + (uint32_t)(p * O), r);
+#pragma unroll
+        for (int e = 0; e < O; ++e) acc[e] += __uint_as_float(r[e]);
+    }
+    const long long line = tile / tpl;
+    const int i = (int)(tile % tpl) * 128 + 32 * warp + lane;
+    if (i >= g.n1) return;
+    const int j = (int)(line % g.n2), k = (int)(line / g.n2);
+    float v[O];
+#pragma unroll
+    for (int e = 0; e < O; ++e) {
+        v[e] = acc[e] + b[e];
+        if (ACT) v[e] = fmaxf(v[e], 0.f);
+    }
+    if (out_pad) {
+        uint32_t pk[O / 2];
+#pragma unroll
+        for (int e = 0; e < O / 2; ++e) pk[e] = pack2(__float2bfloat16_rn(v[2 * e]), __float2bfloat16_rn(v[2 * e + 1]));
+        uint4 *dst = reinterpret_cast<uint4 *>(out_pad + pidx(g, i, j, k) * O);
+#pragma unroll
+        for (int e = 0; e < O / 8; ++e) dst[e] = make_uint4(pk[4 * e], pk[4 * e + 1], pk[4 * e + 2], pk[4 * e + 3]);
+    }
+    if (out_f) {
+        float4 *dst = reinterpret_cast<float4 *>(out_f + (((long long)k * g.n2 + j) * g.n1 + i) * O);
+#pragma unroll
+        for (int e = 0; e < O / 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
     }
 }
 
 template <int C, int O, int ACT>
-__global__ void __launch_bounds__(256, 1) k_conv_fwd_tc(Geo g, const bf16 *__restrict__ in, const bf16 *__restrict__ w,
-                                                        const float *__restrict__ b, bf16 *out_pad, float *out_f)
+__global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, Geo g,
+                                                        const bf16 *__restrict__ w, const float *__restrict__ b,
+                                                        bf16 *out_pad, float *out_f)
 {
-    constexpr int G = C / 8, ROWS = 130, H = O / 2;
-    extern __shared__ __align__(128) unsigned char smem[];
-    // [barrier, tensor-memory address, flag | 128 B][A tile, buffer 0][A tile, buffer 1][weights]
+    constexpr int G = C / 8;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // from the first 128-byte boundary: [MMA barriers 0, 1 | full barriers 0, 1 | tensor-memory
+    // address | flag | to 128 B][A tile, buffer 0][A tile, buffer 1][weights]
+    unsigned char *smem = smem_raw + ((128u - (saddr(smem_raw) & 127u)) & 127u);
     unsigned char *sA[2] = {smem + 128, smem + 128 + tc_a_bytes<C>()};
     unsigned char *sB = smem + 128 + 2 * tc_a_bytes<C>();
-    const uint32_t bar = saddr(smem), slot = saddr(smem + 8);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t mbar[2] = {saddr(smem), saddr(smem + 8)}, full[2] = {saddr(smem + 16), saddr(smem + 24)};
+    const uint32_t slot = saddr(smem + 32);
+    volatile int *flag = reinterpret_cast<volatile int *>(smem + 36);
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int tpl = (g.n1 + 127) / 128;
     const long long ntiles = (long long)tpl * g.n2 * g.n3;
 
@@ -179,111 +258,92 @@ __global__ void __launch_bounds__(256, 1) k_conv_fwd_tc(Geo g, const bf16 *__res
         const int o = q % O, tg = q / O, grp = tg % G, t = tg / G;
         cp_async16(sB + q * 16, w + ((long long)o * 27 + t) * C + grp * 8, 16);
     }
+    constexpr int TCOLS = 2 * TC_PARTS * O;                   // two tiles x TC_PARTS partial accumulators
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(slot) : "memory");
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "n"(TCOLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        for (int q = 0; q < 2; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar[q]) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full[q]) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tm_in) : "memory");
+        if ((long long)blockIdx.x < ntiles) tc_load_tile<C>(&tm_in, g, blockIdx.x, tpl, sA[0], full[0]);
     }
-    long long tile = blockIdx.x;
-    if (tile < ntiles) tc_stage_tile<C>(g, in, tile, tpl, sA[0]);
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(smem + 8);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(smem + 32);
     const uint32_t idesc = umma_idesc<O>();
-    uint32_t parity = 0;
+    // software pipeline: iteration n issues tile n's MMAs into accumulator n % 2, then (once the
+    // previous tile's MMAs are done) starts tile n+1's copies and stores the previous tile
+    uint32_t fpar = 0, mpar = 0;                        // barrier phases, one bit per buffer
     int buf = 0;
-    for (; tile < ntiles; tile += gridDim.x) {
+    long long prev = -1;
+    for (long long tile = blockIdx.x;; tile += gridDim.x) {
+        const bool have = tile < ntiles;
+        if (!have && prev < 0) break;
         if (tid == 0) {
-            // base descriptors; each operand's start moves by a compile-time number of 16-byte
-            // units (the start field is the low 14 bits and never carries: addresses < 256 KB)
-            const uint64_t dA = umma_desc(saddr(sA[buf]), ROWS * 16, 128), dB = umma_desc(saddr(sB), O * 16, 128);
+            int ok = 1;
+            if (have) {
+                ok = mbar_wait(full[buf], (fpar >> buf) & 1) ? 1 : 0;   // this tile's input has landed
+                fpar ^= 1u << buf;
+                if (ok) {
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    // base descriptors; each operand's start moves by a compile-time number of
+                    // 16-byte units (the start field is the low 14 bits and never carries)
+                    const uint64_t dA = umma_desc(saddr(sA[buf]), TC_BLOCK, 128), dB = umma_desc(saddr(sB), O * 16, 128);
+                    const uint32_t td = tmem + (uint32_t)(TC_PARTS * O * buf);
 #pragma unroll
-            for (int t = 0; t < 27; ++t) {
-                const int d1 = t % 3, L = t / 3;             // L = (d3 + 1) * 3 + (d2 + 1)
+                    for (int t = 0; t < 27; ++t) {
+                        const int d1 = t % 3, L = t / 3;         // L = (d3 + 1) * 3 + (d2 + 1)
 #pragma unroll
-                for (int ks = 0; ks < C / 16; ++ks) {
-                    const uint64_t ad = dA + (uint64_t)((L * G + 2 * ks) * ROWS + d1);
-                    const uint64_t bd = dB + (uint64_t)((t * G + 2 * ks) * O);
-                    const uint32_t acc = (t | ks) ? 1u : 0u;
-                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-                                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                                 : "memory");
+                        for (int ks = 0; ks < C / 16; ++ks) {
+                            const int q = t * (C / 16) + ks;         // MMA number: partial q % TC_PARTS
+                            const uint64_t ad = dA + (uint64_t)((L * G + 2 * ks) * (TC_BLOCK / 16) + d1);
+                            const uint64_t bd = dB + (uint64_t)((t * G + 2 * ks) * O);
+                            const uint32_t acc = q >= TC_PARTS ? 1u : 0u;
+                            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(td + (uint32_t)((q % TC_PARTS) * O)),
+                                         "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                                         : "memory");
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                                 ::"r"(mbar[buf]) : "memory");
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
-                         : "memory");
+            if (ok && prev >= 0) {                          // the previous tile's MMAs
+                ok = mbar_wait(mbar[buf ^ 1], (mpar >> (buf ^ 1)) & 1) ? 1 : 0;
+                mpar ^= 1u << (buf ^ 1);
+            }
+            // the next tile into the other buffer (its last reader, the previous tile, is done)
+            if (ok && tile + gridDim.x < ntiles) tc_load_tile<C>(&tm_in, g, tile + gridDim.x, tpl, sA[buf ^ 1], full[buf ^ 1]);
+            *flag = ok;
         }
-        const long long nxt = tile + gridDim.x;
-        if (nxt < ntiles) tc_stage_tile<C>(g, in, nxt, tpl, sA[buf ^ 1]);
-        if (tid == 0) *reinterpret_cast<volatile int *>(smem + 12) = mbar_wait(bar, parity) ? 1 : 0;
-        parity ^= 1;
-        __syncthreads();                                      // the MMAs of this tile are complete
-        if (*reinterpret_cast<volatile int *>(smem + 12) == 0) {   // they never completed: give up
+        __syncthreads();
+        if (*flag == 0) {                                     // a wait expired: give up
             if (tid == 0) atomicExch(&tc_status, 1);
-            asm volatile("cp.async.wait_all;\n" ::: "memory");
             break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        // D rows 32 (warp % 4) .. + 31 (tensor-memory lanes), columns (warp / 4) * O/2 .. + O/2
-        uint32_t r[H];
-        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * H);
-        if constexpr (H == 16) {
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                           "=r"(r[14]), "=r"(r[15])
-                         : "r"(ta));
-        } else {
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7])
-                         : "r"(ta));
+        if (prev >= 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            tc_epilogue<C, O, ACT>(g, tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(TC_PARTS * O * (buf ^ 1)), prev, tpl, b,
+                                   out_pad, out_f);
         }
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        {
-            const long long line = tile / tpl;
-            const int i = (int)(tile % tpl) * 128 + 32 * (warp & 3) + lane;
-            if (i < g.n1) {
-                const int j = (int)(line % g.n2), k = (int)(line / g.n2), c0 = (warp >> 2) * H;
-                float v[H];
-#pragma unroll
-                for (int e = 0; e < H; ++e) {
-                    v[e] = __uint_as_float(r[e]) + b[c0 + e];
-                    if (ACT) v[e] = fmaxf(v[e], 0.f);
-                }
-                if (out_pad) {
-                    uint32_t pk[H / 2];
-#pragma unroll
-                    for (int e = 0; e < H / 2; ++e)
-                        pk[e] = pack2(__float2bfloat16_rn(v[2 * e]), __float2bfloat16_rn(v[2 * e + 1]));
-                    uint4 *dst = reinterpret_cast<uint4 *>(out_pad + pidx(g, i, j, k) * O + c0);
-#pragma unroll
-                    for (int e = 0; e < H / 8; ++e) dst[e] = make_uint4(pk[4 * e], pk[4 * e + 1], pk[4 * e + 2], pk[4 * e + 3]);
-                }
-                if (out_f) {
-                    float4 *dst = reinterpret_cast<float4 *>(out_f + (((long long)k * g.n2 + j) * g.n1 + i) * O + c0);
-#pragma unroll
-                    for (int e = 0; e < H / 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-                }
-            }
-        }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();
+        __syncthreads();                                      // accumulator buf ^ 1 is free again
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        prev = have ? tile : -1;
         buf ^= 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TCOLS) : "memory");
 }
 
 // ---- padding and its adjoint ------------------------------------------------------------------
@@ -625,6 +685,27 @@ unsigned int ccdiv(long long a, long long b) { return (unsigned int)((a + b - 1)
 // layer shapes (C_in padded, C_out padded, real C_in, real C_out)
 const int LC[4] = {16, 32, 32, 32}, LO[4] = {32, 32, 32, 16}, RC[4] = {8, 32, 32, 32}, RO[4] = {32, 32, 32, 8};
 
+// tensor map of a padded channels-last BF16 activation buffer with C channels, as 5-D boxes
+// (channel in group, group of 8 channels, i, j, k); encoded through the driver entry point
+bool tc_tensor_map(CUtensorMap *tm, const bf16 *buf, const Geo &g, int C)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[5] = {8, (cuuint64_t)(C / 8), (cuuint64_t)g.q1, (cuuint64_t)g.q2, (cuuint64_t)g.q3};
+    const cuuint64_t strides[4] = {16, (cuuint64_t)C * 2, (cuuint64_t)g.q1 * C * 2, (cuuint64_t)g.q1 * g.q2 * C * 2};
+    const cuuint32_t box[5] = {8, 1, 130, 1, 1}, estr[5] = {1, 1, 1, 1, 1};
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void *)buf, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // persistent tcgen05 forward: one block per SM (at most one per tile)
 template <int C, int O, int ACT>
 void launch_fwd_tc(Geo g, const bf16 *in, const bf16 *w, const float *b, bf16 *out_pad, float *out_f, cudaStream_t s)
@@ -636,14 +717,24 @@ void launch_fwd_tc(Geo g, const bf16 *in, const bf16 *w, const float *b, bf16 *o
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(k_conv_fwd_tc<C, O, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes<C, O>());
     }
+    CUtensorMap tm;
+    if (!tc_tensor_map(&tm, in, g, C)) {
+        tc_host_error = true;
+        return;
+    }
     const long long tiles = (long long)((g.n1 + 127) / 128) * g.n2 * g.n3;
     const unsigned int nb = (unsigned int)(tiles < sms ? tiles : sms);
-    k_conv_fwd_tc<C, O, ACT><<<nb, 256, tc_smem_bytes<C, O>(), s>>>(g, in, w, b, out_pad, out_f);
+    k_conv_fwd_tc<C, O, ACT><<<nb, 128, tc_smem_bytes<C, O>(), s>>>(tm, g, w, b, out_pad, out_f);
 }
 
-// a tcgen05 forward block whose MMA completion wait expired (read and cleared; call after a sync)
+// a tcgen05 forward block whose MMA completion wait expired, or a tensor map that could not be
+// encoded (read and cleared; call after a sync)
 bool tc_timed_out()
 {
+    if (tc_host_error) {
+        tc_host_error = false;
+        return true;
+    }
     int v = 0;
     cudaMemcpyFromSymbol(&v, tc_status, sizeof v);
     if (v) {
