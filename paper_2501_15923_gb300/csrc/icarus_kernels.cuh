@@ -277,11 +277,14 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
             da[v] = b - a;
             db[v] = e - b;
         }
+        bool half = false;                       // dl holds half the limited slope
         if (P.limiter == 1 && sizeof(TW) == 8) {
             // FP64 van Leer 2ab/(a+b) for the eight fields with ONE division: batch inversion of
             // the eight sums (prefix products, one reciprocal, then peel off; zero sums replaced
             // by 1); the product stays far inside the double range unless all eight sums are
-            // extreme, in which case the eight divisions are done one by one
+            // extreme, in which case the eight divisions are done one by one. dl = ab/(a+b), half
+            // the slope: the factor 2 and the 1/2 of the face extrapolation cancel exactly
+            half = true;
             TW s[NV], pre[NV];
             bool ok[NV];
 #pragma unroll
@@ -300,12 +303,12 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
                 for (int v = NV - 1; v > 0; --v) {
                     const TW iv = inv * pre[v - 1];     // 1 / s[v]
                     inv = inv * s[v];                   // 1 / (s[0] ... s[v-1])
-                    dl[v] = ok[v] ? TW(2) * da[v] * db[v] * iv : TW(0);
+                    dl[v] = ok[v] ? da[v] * db[v] * iv : TW(0);
                 }
-                dl[0] = ok[0] ? TW(2) * da[0] * db[0] * inv : TW(0);
+                dl[0] = ok[0] ? da[0] * db[0] * inv : TW(0);
             } else {
 #pragma unroll
-                for (int v = 0; v < NV; ++v) dl[v] = ok[v] ? TW(2) * da[v] * db[v] / s[v] : TW(0);
+                for (int v = 0; v < NV; ++v) dl[v] = ok[v] ? da[v] * db[v] / s[v] : TW(0);
             }
         } else {
 #pragma unroll
@@ -313,9 +316,10 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            wm[v] = wc[v] - TW(0.5) * dl[v];
+            const TW h = half ? dl[v] : TW(0.5) * dl[v];
+            wm[v] = wc[v] - h;
             sW[v * sz + sl] = wc[v];
-            sP[v * sz + sl] = wc[v] + TW(0.5) * dl[v];
+            sP[v * sz + sl] = wc[v] + h;
         }
     }
     __syncthreads();
