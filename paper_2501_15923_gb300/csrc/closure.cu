@@ -84,23 +84,25 @@ __device__ __forceinline__ void mma16816(float *d, const uint32_t *a, uint32_t b
 // ---- forward on the 5th-generation tensor cores (tcgen05, accumulators in tensor memory) ---------
 // The same y = act(conv(P(x)) + b) as an implicit GEMM D[128 voxels][O] = sum over the 27 taps and
 // the input channels, one tcgen05.mma (M = 128, N = O, K = 16, BF16 in, FP32 accumulate) per tap
-// and 16 channels, issued by one thread, accumulated in tensor memory (32 columns).
-// A tile is 128 consecutive voxels along r at fixed (j, k). Shared memory holds the nine r-lines
-// (j + d2, k + d3) of the padded input around it, with one halo voxel on each side (130 rows), in
-// the no-swizzle K-major operand layout: a row is 16 bytes (8 channels), rows of one channel group
-// are consecutive ([line][group][row][8 channels], each (line, group) block padded to 136 rows so
-// that it starts on a 128-byte boundary), so 8-row core matrices are 128 bytes apart (stride
-// offset) and channel groups one block apart (leading offset). The operand of tap (d1, d2, d3) is
-// then line (d2, d3) started d1 + 1 rows in: a 16-byte shift of the descriptor's start address,
-// no re-staging per tap. The tensor memory accelerator fills each block with one 130 x 8 box of a
-// 5-D tensor map (channel in group, group, i, j, k), zero beyond the padded line; the weights of
-// all taps are staged once per block in the same layout ([tap][group][o][8]). Persistent blocks
-// of 128 threads (one per SM, 209 KB of shared memory at C = O = 32) loop over tiles with two
-// input buffers and two accumulators (64 tensor-memory columns): thread 0 waits for tile n's
-// copies and issues its MMAs into accumulator n % 2; once tile n-1's MMAs are done it starts tile
-// n+1's copies into the buffer they read, and every thread reads its row of tile n-1's D
-// (tcgen05.ld), adds the bias, applies the ReLU and stores, while the tensor core works on tile n. All waits are bounded: on expiry the block records the failure in
-// tc_status and stops.
+// and 16 channels, issued by one thread, accumulated in tensor memory.
+// A tile is 128 consecutive voxels along r at fixed (j, k). Shared memory holds r-lines of the
+// padded input with one halo voxel on each side (130 rows) in the no-swizzle K-major operand
+// layout: a row is 16 bytes (8 channels), rows of one channel group are consecutive
+// ([line][group][row][8 channels], each (line, group) block padded to 136 rows so that it starts
+// on a 128-byte boundary), so 8-row core matrices are 128 bytes apart (stride offset) and channel
+// groups one block apart (leading offset). The operand of tap (d1, d2, d3) is line (d2, d3)
+// started d1 + 1 rows in: a 16-byte shift of the descriptor's start address, no re-staging per
+// tap. A block walks the tiles of one column (i0, j) along k: the three lines (j - 1, j, j + 1) of
+// a padded k index form a plane, a ring of planes holds the three a tile reads and the next ones,
+// so each tile brings in one new plane (three lines instead of nine). The tensor memory
+// accelerator fills each block with one 130 x 8 box of a 5-D tensor map (channel in group, group,
+// i, j, k), zero beyond the padded line; the weights of all taps are staged once per block in the
+// same layout ([tap][group][o][8]). Persistent blocks of 128 threads (one per SM, 208 KB of shared
+// memory at C = O = 32) with two accumulators: thread 0 waits for tile k's newest plane and issues
+// its MMAs into one accumulator; once tile k-1's MMAs are done it starts the copy of a plane
+// several tiles ahead into the slot tile k-1 freed, and every thread reads its row of tile k-1's D
+// (tcgen05.ld), adds the bias, applies the ReLU and stores, while the tensor core works on tile k.
+// All waits are bounded: on expiry the block records the failure in tc_status and stops.
 __device__ int tc_status;
 bool tc_host_error = false;
 
@@ -138,40 +140,39 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-// one (line, channel group) block of an A tile: 130 rows of 16 bytes, padded to 136 rows so that
-// every block (a tensor-copy destination) starts on a 128-byte boundary
+// one (line, channel group) block: 130 rows of 16 bytes, padded to 136 rows so that every block
+// (a tensor-copy destination) starts on a 128-byte boundary; a k-plane is the three lines
+// (j - 1, j, j + 1) of one padded k index; a ring of TC_RING planes holds a tile's three and the
+// next ones in flight
 constexpr int TC_BLOCK = 136 * 16;
-template <int C> __host__ __device__ constexpr int tc_a_bytes() { return 9 * (C / 8) * TC_BLOCK; }
+constexpr int TC_KC = 8;                                     // tiles (k steps) per work item
+constexpr int TC_RING = 6;                                   // k-planes in shared memory
+template <int C> __host__ __device__ constexpr int tc_plane_bytes() { return 3 * (C / 8) * TC_BLOCK; }
 template <int C, int O> __host__ __device__ constexpr int tc_b_bytes() { return 27 * (C / 8) * O * 16; }
-// (+ 128 B to align the start to 128 bytes, + 1 KB of slack after the weights)
-template <int C, int O> __host__ __device__ constexpr int tc_smem_bytes() { return 128 + 128 + tc_b_bytes<C, O>() + 2 * tc_a_bytes<C>() + 1024; }
-
-// the nine r-lines of tile `tile` into dst by the tensor memory accelerator: one box of 130 rows x
-// 8 channels per line and channel group (tensor map dims: channel in group, group, i, j, k of the
-// padded grid); rows past the padded line are zero-filled; completion counted on barrier bar
-template <int C>
-__device__ __forceinline__ void tc_load_tile(const CUtensorMap *tm, const Geo &g, long long tile, int tpl,
-                                             unsigned char *dst, uint32_t bar)
+// (+ 128 B to align the start to 128 bytes, 128 B of barriers, + 1 KB of slack after the weights)
+template <int C, int O> __host__ __device__ constexpr int tc_smem_bytes()
 {
-    constexpr int G = C / 8, ROWS = 130;
-    const long long line = tile / tpl;
-    const int i0 = (int)(tile % tpl) * 128;            // padded index of voxel i0 - 1
-    const int j = (int)(line % g.n2), k = (int)(line / g.n2);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(9 * G * ROWS * 16)
+    return 128 + 128 + TC_RING * tc_plane_bytes<C>() + tc_b_bytes<C, O>() + 1024;
+}
+
+// padded k-plane kp of column (i0, j) into dst by the tensor memory accelerator: per line and
+// channel group one box of 130 rows x 8 channels (tensor map dims: channel in group, group, i, j, k
+// of the padded grid); rows past the padded line are zero-filled; completion counted on bar
+template <int C>
+__device__ __forceinline__ void tc_load_plane(const CUtensorMap *tm, int i0, int j, int kp, unsigned char *dst, uint32_t bar)
+{
+    constexpr int G = C / 8;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(3 * G * 130 * 16)
                  : "memory");
-#pragma unroll 1
-    for (int L = 0; L < 9; ++L)
+#pragma unroll
+    for (int jj = 0; jj < 3; ++jj)
 #pragma unroll
         for (int grp = 0; grp < G; ++grp)
             asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n"
-                         ::"r"(saddr(dst + (L * G + grp) * TC_BLOCK)), "l"(tm), "r"(0), "r"(grp), "r"(i0),
-                         "r"(j + L % 3), "r"(k + L / 3), "r"(bar)
+                         ::"r"(saddr(dst + (jj * G + grp) * TC_BLOCK)), "l"(tm), "r"(0), "r"(grp), "r"(i0),
+                         "r"(j + jj), "r"(kp), "r"(bar)
                          : "memory");
 }
-
-// partial accumulators per tile (consecutive MMAs rotate over them; the epilogue adds them). One:
-// four measured no faster at these sizes, the MMAs are not what limits the kernel
-constexpr int TC_PARTS = 1;
 
 template <int O> __device__ __forceinline__ void tc_ld(uint32_t ta, uint32_t *r)
 {
@@ -194,30 +195,20 @@ template <int O> __device__ __forceinline__ void tc_ld(uint32_t ta, uint32_t *r)
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
+// row 32 warp + lane of tile (i0, j, k): D from tensor memory, bias, ReLU, stores
 template <int C, int O, int ACT>
-__device__ __forceinline__ void tc_epilogue(const Geo &g, uint32_t ta, long long tile, int tpl, const float *__restrict__ b,
+__device__ __forceinline__ void tc_epilogue(const Geo &g, uint32_t ta, int i0, int j, int k, const float *__restrict__ b,
                                             bf16 *out_pad, float *out_f)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float acc[O];
     uint32_t r[O];
     tc_ld<O>(ta, r);
-#pragma unroll
-    for (int e = 0; e < O; ++e) acc[e] = __uint_as_float(r[e]);
-#pragma unroll
-    for (int p = 1; p < TC_PARTS; ++p) {
-        tc_ld<O>(ta + (uint32_t)(p * O), r);
-#pragma unroll
-        for (int e = 0; e < O; ++e) acc[e] += __uint_as_float(r[e]);
-    }
-    const long long line = tile / tpl;
-    const int i = (int)(tile % tpl) * 128 + 32 * warp + lane;
+    const int i = i0 + 32 * warp + lane;
     if (i >= g.n1) return;
-    const int j = (int)(line % g.n2), k = (int)(line / g.n2);
     float v[O];
 #pragma unroll
     for (int e = 0; e < O; ++e) {
-        v[e] = acc[e] + b[e];
+        v[e] = __uint_as_float(r[e]) + b[e];
         if (ACT) v[e] = fmaxf(v[e], 0.f);
     }
     if (out_pad) {
@@ -240,110 +231,120 @@ __global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(const __grid_constant__ 
                                                         const bf16 *__restrict__ w, const float *__restrict__ b,
                                                         bf16 *out_pad, float *out_f)
 {
-    constexpr int G = C / 8;
+    constexpr int G = C / 8, PB = tc_plane_bytes<C>();
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    // from the first 128-byte boundary: [MMA barriers 0, 1 | full barriers 0, 1 | tensor-memory
-    // address | flag | to 128 B][A tile, buffer 0][A tile, buffer 1][weights]
+    // from the first 128-byte boundary: [MMA barriers 0, 1 | plane barriers | tensor-memory
+    // address | flag | to 128 B][k-plane ring][weights]
     unsigned char *smem = smem_raw + ((128u - (saddr(smem_raw) & 127u)) & 127u);
-    unsigned char *sA[2] = {smem + 128, smem + 128 + tc_a_bytes<C>()};
-    unsigned char *sB = smem + 128 + 2 * tc_a_bytes<C>();
-    const uint32_t mbar[2] = {saddr(smem), saddr(smem + 8)}, full[2] = {saddr(smem + 16), saddr(smem + 24)};
-    const uint32_t slot = saddr(smem + 32);
-    volatile int *flag = reinterpret_cast<volatile int *>(smem + 36);
+    unsigned char *sA = smem + 128;
+    unsigned char *sB = sA + TC_RING * PB;
+    const uint32_t mbar0 = saddr(smem), full0 = saddr(smem + 16);   // barrier q at + 8 q
+    const uint32_t slot = saddr(smem + 16 + 8 * TC_RING);
+    volatile int *flag = reinterpret_cast<volatile int *>(smem + 20 + 8 * TC_RING);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int tpl = (g.n1 + 127) / 128;
-    const long long ntiles = (long long)tpl * g.n2 * g.n3;
+    const int tpl = (g.n1 + 127) / 128, ncol = tpl * g.n2, nchunk = (g.n3 + TC_KC - 1) / TC_KC;
+    const int nitems = ncol * nchunk;
 
     for (int q = tid; q < 27 * G * O; q += blockDim.x) {     // weights: q = (t * G + grp) * O + o
         const int o = q % O, tg = q / O, grp = tg % G, t = tg / G;
         cp_async16(sB + q * 16, w + ((long long)o * 27 + t) * C + grp * 8, 16);
     }
-    constexpr int TCOLS = 2 * TC_PARTS * O;                   // two tiles x TC_PARTS partial accumulators
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "n"(TCOLS) : "memory");
+    if (warp == 0) {                                          // two accumulators of O columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "n"(2 * O) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        for (int q = 0; q < 2; ++q) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar[q]) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full[q]) : "memory");
-        }
+        for (int q = 0; q < 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar0 + 8 * q) : "memory");
+        for (int q = 0; q < TC_RING; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full0 + 8 * q) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tm_in) : "memory");
-        if ((long long)blockIdx.x < ntiles) tc_load_tile<C>(&tm_in, g, blockIdx.x, tpl, sA[0], full[0]);
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(smem + 32);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(smem + 16 + 8 * TC_RING);
     const uint32_t idesc = umma_idesc<O>();
-    // software pipeline: iteration n issues tile n's MMAs into accumulator n % 2, then (once the
-    // previous tile's MMAs are done) starts tile n+1's copies and stores the previous tile
-    uint32_t fpar = 0, mpar = 0;                        // barrier phases, one bit per buffer
-    int buf = 0;
-    long long prev = -1;
-    for (long long tile = blockIdx.x;; tile += gridDim.x) {
-        const bool have = tile < ntiles;
-        if (!have && prev < 0) break;
-        if (tid == 0) {
-            int ok = 1;
-            if (have) {
-                ok = mbar_wait(full[buf], (fpar >> buf) & 1) ? 1 : 0;   // this tile's input has landed
-                fpar ^= 1u << buf;
-                if (ok) {
-                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    // base descriptors; each operand's start moves by a compile-time number of
-                    // 16-byte units (the start field is the low 14 bits and never carries)
-                    const uint64_t dA = umma_desc(saddr(sA[buf]), TC_BLOCK, 128), dB = umma_desc(saddr(sB), O * 16, 128);
-                    const uint32_t td = tmem + (uint32_t)(TC_PARTS * O * buf);
-#pragma unroll
-                    for (int t = 0; t < 27; ++t) {
-                        const int d1 = t % 3, L = t / 3;         // L = (d3 + 1) * 3 + (d2 + 1)
-#pragma unroll
-                        for (int ks = 0; ks < C / 16; ++ks) {
-                            const int q = t * (C / 16) + ks;         // MMA number: partial q % TC_PARTS
-                            const uint64_t ad = dA + (uint64_t)((L * G + 2 * ks) * (TC_BLOCK / 16) + d1);
-                            const uint64_t bd = dB + (uint64_t)((t * G + 2 * ks) * O);
-                            const uint32_t acc = q >= TC_PARTS ? 1u : 0u;
-                            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(td + (uint32_t)((q % TC_PARTS) * O)),
-                                         "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                                         : "memory");
-                        }
+    const uint64_t dA = umma_desc(saddr(sA), TC_BLOCK, 128), dB = umma_desc(saddr(sB), O * 16, 128);
+    uint32_t fpar = 0, mpar = 0;                        // barrier phases to wait for, one bit each
+    int acc = 0;                                        // accumulator of the next tile
+    bool failed = false;
+    // a work item: column (i0, j), tiles k0 .. k1 - 1 walked in k; tile k reads padded planes
+    // k, k + 1, k + 2 (ring slot: plane index mod TC_RING); after tile k-1's MMAs, plane
+    // k + TC_RING - 1 goes into the slot plane k - 1 held, TC_RING - 3 tiles ahead of its first
+    // use. Tile k's MMAs overlap tile k-1's stores.
+    for (int item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
+        const int col = item % ncol, chunk = item / ncol;
+        const int i0 = (col % tpl) * 128, j = col / tpl, k0 = chunk * TC_KC;
+        const int k1 = min(k0 + TC_KC, g.n3);
+        if (tid == 0)
+            for (int kp = k0; kp < k0 + TC_RING - 1 && kp <= k1 + 1; ++kp)
+                tc_load_plane<C>(&tm_in, i0, j, kp, sA + (kp % TC_RING) * PB, full0 + 8 * (kp % TC_RING));
+        for (int k = k0; k <= k1; ++k) {                  // k = k1: drain (stores of tile k1 - 1)
+            if (tid == 0) {
+                int ok = 1;
+                if (k < k1) {
+                    for (int kp = (k == k0 ? k : k + 2); kp <= k + 2 && ok; ++kp) {
+                        const int sl = kp % TC_RING;
+                        ok = mbar_wait(full0 + 8 * sl, (fpar >> sl) & 1) ? 1 : 0;
+                        fpar ^= 1u << sl;
                     }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                                 ::"r"(mbar[buf]) : "memory");
+                    if (ok) {
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                        uint64_t pl[3];                       // 16-byte units of planes k, k+1, k+2
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) pl[q] = (uint64_t)(((k + q) % TC_RING) * (PB / 16));
+                        const uint32_t td = tmem + (uint32_t)(O * acc);
+#pragma unroll
+                        for (int t = 0; t < 27; ++t) {
+                            const int d1 = t % 3, d2 = (t / 3) % 3, d3 = t / 9;   // shifts + 1
+#pragma unroll
+                            for (int ks = 0; ks < C / 16; ++ks) {
+                                const uint64_t ad = dA + pl[d3] + (uint64_t)((d2 * G + 2 * ks) * (TC_BLOCK / 16) + d1);
+                                const uint64_t bd = dB + (uint64_t)((t * G + 2 * ks) * O);
+                                const uint32_t en = (t | ks) ? 1u : 0u;
+                                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(td),
+                                             "l"(ad), "l"(bd), "r"(idesc), "r"(en)
+                                             : "memory");
+                            }
+                        }
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                                     ::"r"(mbar0 + 8 * acc) : "memory");
+                    }
                 }
+                if (ok && k > k0) {                       // tile k-1's MMAs
+                    ok = mbar_wait(mbar0 + 8 * (acc ^ 1), (mpar >> (acc ^ 1)) & 1) ? 1 : 0;
+                    mpar ^= 1u << (acc ^ 1);
+                }
+                // plane k + TC_RING - 1 into plane k - 1's slot (free: its last reader, tile k-1, is
+                // done; at k0 that slot was not filled by the opening loads)
+                const int kn = k + TC_RING - 1;
+                if (ok && kn <= k1 + 1)
+                    tc_load_plane<C>(&tm_in, i0, j, kn, sA + (kn % TC_RING) * PB, full0 + 8 * (kn % TC_RING));
+                *flag = ok;
             }
-            if (ok && prev >= 0) {                          // the previous tile's MMAs
-                ok = mbar_wait(mbar[buf ^ 1], (mpar >> (buf ^ 1)) & 1) ? 1 : 0;
-                mpar ^= 1u << (buf ^ 1);
+            __syncthreads();
+            if (*flag == 0) {                             // a wait expired: give up
+                if (tid == 0) atomicExch(&tc_status, 1);
+                failed = true;
+                break;
             }
-            // the next tile into the other buffer (its last reader, the previous tile, is done)
-            if (ok && tile + gridDim.x < ntiles) tc_load_tile<C>(&tm_in, g, tile + gridDim.x, tpl, sA[buf ^ 1], full[buf ^ 1]);
-            *flag = ok;
-        }
-        __syncthreads();
-        if (*flag == 0) {                                     // a wait expired: give up
-            if (tid == 0) atomicExch(&tc_status, 1);
-            break;
-        }
-        if (prev >= 0) {
+            if (k > k0) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                tc_epilogue<C, O, ACT>(g, tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(O * (acc ^ 1)), i0, j, k - 1,
+                                       b, out_pad, out_f);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();                              // accumulator acc ^ 1 is free again
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            tc_epilogue<C, O, ACT>(g, tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(TC_PARTS * O * (buf ^ 1)), prev, tpl, b,
-                                   out_pad, out_f);
+            if (k < k1) acc ^= 1;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();                                      // accumulator buf ^ 1 is free again
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        prev = have ? tile : -1;
-        buf ^= 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TCOLS) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(2 * O) : "memory");
 }
 
 // ---- padding and its adjoint ------------------------------------------------------------------
@@ -722,8 +723,8 @@ void launch_fwd_tc(Geo g, const bf16 *in, const bf16 *w, const float *b, bf16 *o
         tc_host_error = true;
         return;
     }
-    const long long tiles = (long long)((g.n1 + 127) / 128) * g.n2 * g.n3;
-    const unsigned int nb = (unsigned int)(tiles < sms ? tiles : sms);
+    const long long items = (long long)((g.n1 + 127) / 128) * g.n2 * ((g.n3 + TC_KC - 1) / TC_KC);
+    const unsigned int nb = (unsigned int)(items < sms ? items : sms);
     k_conv_fwd_tc<C, O, ACT><<<nb, 128, tc_smem_bytes<C, O>(), s>>>(tm, g, w, b, out_pad, out_f);
 }
 
