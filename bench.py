@@ -68,7 +68,7 @@ def dist_env():
 
 def workload(grid_s: str):
     n1, n2, n3 = (int(x) for x in grid_s.split("x"))
-    return I.config1(grid=I.Grid(n1, n2, n3))
+    return I.dynamic_cme(grid=I.Grid(n1, n2, n3))
 
 
 class Clocks:

@@ -216,7 +216,7 @@ def cme_row(t_on, duration, lat, lon, half_width, speed, n, temp) -> list:
 
 
 # --- workloads -------------------------------------------------------------------------------
-def config0(seed: int = 0, n_steps: int = 200, grid: Grid | None = None) -> Workload:
+def static_sheet(seed: int = 0, n_steps: int = 200, grid: Grid | None = None) -> Workload:
     """60x16x32 stretched grid, static tilted-sheet map (tilt 15 deg, random phase), 200 steps,
     two circular 1 AU probes (latitudes 0 and 7.25 deg, inertial longitudes 0 and 60 deg)."""
     g = grid or Grid(60, 16, 32)
@@ -226,11 +226,11 @@ def config0(seed: int = 0, n_steps: int = 200, grid: Grid | None = None) -> Work
     t_knots = np.arange(0.0, 3.0 * DAY + 1.0, 3600.0)
     traj = np.stack([circular_orbit(t_knots, 1.0, 0.0, 0.0, 365.25),
                      circular_orbit(t_knots, 1.0, 7.25, 60.0, 365.25)])
-    return Workload("cfg0_60x16x32_static", g, Options(), 1.5, OMEGA_SUN, np.zeros(1), m[None].copy(),
+    return Workload("static_sheet_60x16x32", g, Options(), 1.5, OMEGA_SUN, np.zeros(1), m[None].copy(),
                     np.zeros((0, 8)), traj, t_end=0.0, n_steps=n_steps, meta={"phase": phase})
 
 
-def config1(seed: int = 1, grid: Grid | None = None, days: float = 10.0, n_scale: float = 1.0) -> Workload:
+def dynamic_cme(seed: int = 1, grid: Grid | None = None, days: float = 10.0, n_scale: float = 1.0) -> Workload:
     """512x64x128 stretched grid, 10 daily maps with a random-walk tilt, one cone CME
     (1200 km/s, half-width 30 deg, 1000 cm^-3, 0.8 MK, 8 h, onset U(1, 3) d, aimed at probe 1),
     four Keplerian-like probes between 0.7 and 1.5 AU, 10 simulated days."""
@@ -253,7 +253,7 @@ def config1(seed: int = 1, grid: Grid | None = None, days: float = 10.0, n_scale
     t_on = rng.uniform(1.0, 3.0) * DAY
     cmes = np.array([cme_row(t_on, 8 * 3600.0, 0.0, lon_corot(traj[0], t_on, OMEGA_SUN),
                              math.radians(30.0), 1.2e6, 1000e6, 8e5)])
-    return Workload("cfg1_512x64x128_dynamic_cme", g, Options(), 1.5, OMEGA_SUN, t_maps, maps, cmes,
+    return Workload("dynamic_cme_512x64x128", g, Options(), 1.5, OMEGA_SUN, t_maps, maps, cmes,
                     traj, t_end=days * DAY, meta={"phase": phase, "tilts": tilts})
 
 

@@ -69,11 +69,11 @@ class PairSet:
 
 
 def generate_pairs(seeds, windows: int, spinup_days: float, k: int = 10, fine=(512, 64, 128), log=None):
-    """Pairs from fine FP64 runs with config-1 drivers of the given seeds."""
+    """Pairs from fine FP64 runs with production drivers (10 daily maps, one cone CME) of the given seeds."""
     import torch
     pairs = PairSet(torch)
     for seed in seeds:
-        w = I.config1(seed=seed, grid=I.Grid(*fine))
+        w = I.dynamic_cme(seed=seed, grid=I.Grid(*fine))
         wc = coarse_workload(w)
         F = ic.from_workload(w, precision=ic.ICARUS_FP64)
         Cs = ic.from_workload(wc, precision=ic.ICARUS_FP64)
@@ -157,7 +157,7 @@ def evaluate(net, seed: int, spinup_days: float, window_days: float, k: int = 10
              threshold: float = 0.01, log=None):
     """Fine plain solve vs coarse plain solve vs coarse + closure on a held-out seed."""
     import torch
-    w = I.config1(seed=seed, grid=I.Grid(*fine))
+    w = I.dynamic_cme(seed=seed, grid=I.Grid(*fine))
     wc = coarse_workload(w)
     F = ic.from_workload(w, precision=ic.ICARUS_FP64)
     t_start = spinup_days * I.DAY / F.scales()["t0"]

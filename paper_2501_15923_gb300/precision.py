@@ -73,7 +73,7 @@ def advancing_steps(series: np.ndarray) -> int:
 
 def run(days: float, grid=(512, 64, 128), chunk: int = 200, ring: int = 1 << 16, log=None):
     import torch
-    w = I.config1(grid=I.Grid(*grid), days=days)
+    w = I.dynamic_cme(grid=I.Grid(*grid), days=days)
     res, states, series = {}, {}, {}
     for name, prec in (("fp64", ic.ICARUS_FP64), ("mixed", ic.ICARUS_MIXED), ("fp32", ic.ICARUS_FP32)):
         s = ic.from_workload(w, precision=prec, ring=ring)

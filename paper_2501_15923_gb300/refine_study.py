@@ -1,5 +1,5 @@
 """Static refinement band against adaptive refinement's purpose (orchestration only): the
-production drivers (config-1 maps, one cone CME aimed at probe 0) on three radial grids with the
+production drivers (production maps, one cone CME aimed at probe 0) on three radial grids with the
 same 32 x 64 angular grid, stepped from the initial state through the CME's passage at probe 0:
 
   base     n1 cells, stretched;
@@ -47,7 +47,7 @@ def probe0_errors(ref, got, t_lo, t_hi):
 
 def run(n1=256, n2=32, n3=64, f=4, days=None, precision="fp64", chunk=500, ring=1 << 16, log=None):
     import torch
-    w0 = I.config1(grid=I.Grid(n1, n2, n3))
+    w0 = I.dynamic_cme(grid=I.Grid(n1, n2, n3))
     traj = np.asarray(w0.traj)
     r0 = traj[0, :, 1] / I.AU
     lo, hi = float(r0.min()) - 0.15, float(r0.max()) + 0.15
@@ -62,7 +62,7 @@ def run(n1=256, n2=32, n3=64, f=4, days=None, precision="fp64", chunk=500, ring=
            "precision": precision}
     series = {}
     for name, g in grids.items():
-        w = I.config1(grid=g)
+        w = I.dynamic_cme(grid=g)
         s = ic.from_workload(w, precision=prec, ring=ring)
         s.sample(w.traj, cap=1)
         te = t_end / s.scales()["t0"]

@@ -29,7 +29,7 @@ def ic():
 def test_graph_steps_equal_single_steps(ic, prec):
     """step(7) (graph replay, dt kept on the device) against seven step(1) calls, through a CME
     window, with probes registered: identical state, time and probe records."""
-    w = I.config1(grid=I.Grid(64, 16, 32))
+    w = I.dynamic_cme(grid=I.Grid(64, 16, 32))
     a, b = ic.from_workload(w, precision=prec), ic.from_workload(w, precision=prec)
     U, _ = a.get_state()
     t = (w.cmes[0, 0] - 120.0) / a.scales()["t0"]
@@ -49,7 +49,7 @@ def test_graph_steps_equal_single_steps(ic, prec):
 
 
 def test_calls_out_of_order_rejected(ic):
-    w = I.config0()
+    w = I.static_sheet()
     s = ic.Solver(w.grid, w.gamma, w.omega, w.opts)
     with pytest.raises(ic.IcarusError) as e:
         s.step(1)
@@ -63,7 +63,7 @@ def test_calls_out_of_order_rejected(ic):
 @pytest.mark.parametrize("prec", [1, 2])
 def test_full_size_single_precision_forms(ic, prec):
     """512 x 64 x 128, one step from the initial state at a time in the CME window."""
-    w = I.config1()
+    w = I.dynamic_cme()
     gpu, orc = ic.from_workload(w, precision=prec), oracle_workload(w)
     U, _ = gpu.get_state()
     t = (w.cmes[0, 0] + 1800.0) / orc.scales()["t0"]

@@ -27,7 +27,7 @@ def ic():
 @pytest.mark.parametrize("stretch,f,band", [(1, 4, (0.8, 1.2)), (0, 3, (0.5, 1.1))])
 def test_band_step_parity(ic, stretch, f, band):
     g = I.Grid(72, 12, 24, stretch=stretch, band_refine=f, band_lo=band[0], band_hi=band[1])
-    w = I.config1(grid=g)
+    w = I.dynamic_cme(grid=g)
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     sc = orc.scales()
     U, _ = gpu.get_state()
@@ -38,7 +38,7 @@ def test_band_step_parity(ic, stretch, f, band):
 
 def test_band_probe_indices(ic):
     g = I.Grid(72, 12, 24, band_refine=4, band_lo=0.8, band_hi=1.2)
-    w = I.config1(grid=g)
+    w = I.dynamic_cme(grid=g)
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     e = orc.edges(0)
     assert np.diff(np.log(e)).min() < 0.3 * np.diff(np.log(e)).max()     # the band is there

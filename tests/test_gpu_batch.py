@@ -27,7 +27,7 @@ def members():
     shapes = [(40, 10, 16), (64, 12, 24), (33, 9, 20), (96, 16, 32)]
     ws = []
     for q, s in enumerate(shapes):
-        w = I.config1(seed=40 + q, grid=I.Grid(*s))
+        w = I.dynamic_cme(seed=40 + q, grid=I.Grid(*s))
         ws.append(w)
     return ws
 

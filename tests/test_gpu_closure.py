@@ -3,7 +3,10 @@
 Inputs, weights and output gradients are rounded to BF16 first and handed to both sides, so the
 GPU result differs from the oracle only by its FP32 accumulation (relative ~1e-6); the bar is
 2e-5 of each tensor's largest magnitude. This checks the forward pass and the three gradients the
-GPU training uses (data, weight, bias), including the ReLU mask and the padding's adjoint.
+GPU training uses (data, weight, bias), including the ReLU mask and the padding's adjoint. The
+shapes cover the tensor-core forward's tiling: ragged 128-voxel tiles along r, several tiles per
+r-line, columns walked along k in chunks of 8 with a ring of k-planes that wraps (n3 = 9, 19),
+and a single k-plane.
 """
 import numpy as np
 import pytest
@@ -33,7 +36,9 @@ def bf16(a):
 
 @pytest.mark.parametrize("C,Oc,act,shape", [(16, 32, 1, (11, 6, 5)), (32, 32, 1, (9, 7, 4)), (32, 16, 0, (13, 5, 6)),
                                             (32, 32, 1, (40, 12, 10)), (32, 32, 1, (150, 5, 3)),
-                                            (16, 32, 1, (256, 3, 2)), (32, 16, 0, (129, 4, 3))])
+                                            (16, 32, 1, (256, 3, 2)), (32, 16, 0, (129, 4, 3)),
+                                            (32, 32, 1, (140, 3, 19)), (16, 32, 1, (20, 2, 9)),
+                                            (32, 16, 0, (7, 3, 1))])
 def test_layer_forward_and_gradients_match_oracle(ic, C, Oc, act, shape):
     n1, n2, n3 = shape
     rng = np.random.default_rng(C * 100 + Oc + n1)

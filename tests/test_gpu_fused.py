@@ -63,7 +63,7 @@ def compare_paths(ic, make, U, t, prec, orc=None, steps=1):
 @pytest.mark.parametrize("n", [(60, 16, 32), (37, 9, 7), (129, 17, 33), (2, 10, 3), (70, 12, 80)])
 def test_fused_stage_grids(ic, prec, n):
     """Ragged tiles in r and theta, a phi chunk that is cut short (80 = 5 x 16), tiny grids."""
-    w = I.config1(grid=I.Grid(*n))
+    w = I.dynamic_cme(grid=I.Grid(*n))
     make = lambda p, unf: ic.from_workload(w, precision=p, fused=not unf)
     s = make(prec, False)
     U, t = s.get_state()
@@ -78,7 +78,7 @@ def test_fused_stage_grids(ic, prec, n):
     (I.LIM_VANLEER, I.FLUX_HLL, I.DIVB_NONE, 0),
 ])
 def test_fused_stage_options_perturbed(ic, prec, lim, flux, divb, grav):
-    w = I.config0()
+    w = I.static_sheet()
     w.opts = I.Options(limiter=lim, flux=flux, divb=divb, gravity=grav)
     make = lambda p, unf: ic.from_workload(w, precision=p, fused=not unf)
     s = make(prec, False)
@@ -97,7 +97,7 @@ def test_fused_stage_options_perturbed(ic, prec, lim, flux, divb, grav):
 @pytest.mark.parametrize("prec", PRECS)
 def test_fused_stage_twenty_steps_with_cme(ic, prec):
     """Twenty consecutive steps through the CME insertion window on a reduced grid."""
-    w = I.config1(grid=I.Grid(48, 12, 24))
+    w = I.dynamic_cme(grid=I.Grid(48, 12, 24))
     make = lambda p, unf: ic.from_workload(w, precision=p, fused=not unf)
     s = make(prec, False)
     U, _ = s.get_state()

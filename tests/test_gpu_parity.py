@@ -64,7 +64,7 @@ def assert_step(gpu, orc, U, t, tol=TOL, dt_cap=0.0):
 # ---------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("init_vphi", [I.IC_COROTATING, I.IC_INERTIAL_RADIAL])
 def test_initial_state_matches(ic, init_vphi):
-    w = I.config0()
+    w = I.static_sheet()
     w.opts.init_vphi = init_vphi
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     Ug, _ = gpu.get_state()
@@ -73,10 +73,10 @@ def test_initial_state_matches(ic, init_vphi):
     gpu.close()
 
 
-def test_config0_per_step_parity_20_steps(ic):
-    """Twenty consecutive steps of the config-0 workload; at every step the oracle restarts from
+def test_static_sheet_per_step_parity_20_steps(ic):
+    """Twenty consecutive steps of the static-sheet workload (60 x 16 x 32); at every step the oracle restarts from
     the GPU state, so each comparison is one step from an identical state."""
-    w = I.config0()
+    w = I.static_sheet()
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     U, t = gpu.get_state()
     for _ in range(20):
@@ -90,8 +90,8 @@ def test_config0_per_step_parity_20_steps(ic):
     (I.LIM_VANLEER, I.FLUX_HLL, I.DIVB_NONE, 0),
 ])
 def test_options_perturbed_state(ic, lim, flux, divb, grav):
-    """Randomly perturbed config-0 state (every component nonzero, limiter branches mixed)."""
-    w = I.config0()
+    """Randomly perturbed static-sheet state (every component nonzero, limiter branches mixed)."""
+    w = I.static_sheet()
     w.opts = I.Options(limiter=lim, flux=flux, divb=divb, gravity=grav)
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     U, t = gpu.get_state()
@@ -109,10 +109,10 @@ def test_options_perturbed_state(ic, lim, flux, divb, grav):
 
 @pytest.mark.parametrize("lim,divb,grav", [(I.LIM_VANLEER, I.DIVB_LINDE, 1), (I.LIM_MC, I.DIVB_NONE, 0)])
 def test_hlld_perturbed_state(ic, lim, divb, grav):
-    """HLLD flux (its own kernel instantiation) on a perturbed config-0 state. The perturbation is
+    """HLLD flux (its own kernel instantiation) on a perturbed static-sheet state. The perturbation is
     made in primitive variables so that the pressure stays positive: HLLD's intermediate states
     have no meaning for negative pressures (the oracle's step turns non-finite there too)."""
-    w = I.config0()
+    w = I.static_sheet()
     w.opts = I.Options(limiter=lim, flux=I.FLUX_HLLD, divb=divb, gravity=grav)
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     U, _ = gpu.get_state()
@@ -128,10 +128,10 @@ def test_hlld_perturbed_state(ic, lim, divb, grav):
 
 
 def test_dynamic_maps_and_cme_window(ic):
-    """Config-1 drivers on a reduced grid: time between two maps and inside the CME window,
+    """Production drivers (10 daily maps, one cone CME) on a reduced grid: time between two maps and inside the CME window,
     then a step that crosses the end of the window (boundary values change between stages)."""
     g = I.Grid(48, 12, 24)
-    w = I.config1(grid=g)
+    w = I.dynamic_cme(grid=g)
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     sc = orc.scales()
     U, _ = gpu.get_state()
@@ -154,7 +154,7 @@ def test_sphere_cme_crossing(ic):
     growing, full, shrinking) and one after it has passed; the footprint is decided by the same
     FP64 operations on both sides, so the boundary ghosts agree exactly."""
     g = I.Grid(48, 12, 24)
-    w = I.config1(grid=g)
+    w = I.dynamic_cme(grid=g)
     w.opts.cme_model = I.CME_SPHERE
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     sc = orc.scales()
@@ -186,7 +186,7 @@ def test_ragged_grid_sizes(ic):
     """Sizes that are not multiples of any block edge (ragged tails in every kernel)."""
     for n in ((37, 9, 7), (129, 17, 33), (2, 10, 3)):
         g = I.Grid(*n)
-        w = I.config1(grid=g)
+        w = I.dynamic_cme(grid=g)
         gpu, orc = ic.from_workload(w), oracle_workload(w)
         U, t = gpu.get_state()
         for _ in range(2):
@@ -239,7 +239,7 @@ def test_reflecting_shell(ic):
 
 
 def test_stop_time_caps_dt(ic):
-    w = I.config0()
+    w = I.static_sheet()
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     U, t = gpu.get_state()
     _, dt = gpu.time()
@@ -255,7 +255,7 @@ def test_stop_time_caps_dt(ic):
 
 # ---------------------------------------------------------------------------------------------
 def test_probe_parity_indices_exact(ic):
-    w = I.config1(grid=I.Grid(96, 24, 48))
+    w = I.dynamic_cme(grid=I.Grid(96, 24, 48))
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     U, _ = gpu.get_state()
     sc = orc.scales()
@@ -275,7 +275,7 @@ def test_probe_parity_indices_exact(ic):
 
 
 def test_probe_ring_records_every_step(ic):
-    w = I.config0()
+    w = I.static_sheet()
     gpu = ic.from_workload(w)
     gpu.sample(w.traj, cap=1)
     gpu.step(7)
@@ -288,9 +288,9 @@ def test_probe_ring_records_every_step(ic):
 
 
 def test_full_size_one_step_parity(ic):
-    """512 x 64 x 128 (the production-size grid) from the config-1 initial state at a time in the
+    """512 x 64 x 128 (the production-size grid) from the production initial state at a time in the
     CME window: one step compared on the whole grid."""
-    w = I.config1()
+    w = I.dynamic_cme()
     gpu, orc = ic.from_workload(w), oracle_workload(w)
     U, _ = gpu.get_state()
     t = (w.cmes[0, 0] + 1800.0) / orc.scales()["t0"]
@@ -302,7 +302,7 @@ def test_full_size_one_step_parity(ic):
 @pytest.mark.parametrize("prec,tol", [(1, 2e-5), (2, 2e-5)])
 def test_reduced_precision_step(ic, prec, tol):
     """FP32 state and MIXED: one step from the same state within single-precision error."""
-    w = I.config0()
+    w = I.static_sheet()
     gpu, orc = ic.from_workload(w, precision=prec), oracle_workload(w)
     U, t = gpu.get_state()
     gpu.set_state(U, t)

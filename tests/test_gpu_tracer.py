@@ -27,7 +27,7 @@ def ic():
 
 
 def tracer_workload(cme_model):
-    w = I.config1(grid=I.Grid(48, 12, 24))
+    w = I.dynamic_cme(grid=I.Grid(48, 12, 24))
     w.opts.tracer = 1
     w.opts.cme_model = cme_model
     return w
@@ -81,7 +81,7 @@ def test_tracer_round_trip_launches_and_errors(ic):
     c = np.random.default_rng(3).uniform(0.0, 1.0, U.shape[1:])
     gpu.set_tracer(c)
     assert np.abs(gpu.get_tracer() - c).max() <= 1e-15
-    w0 = I.config1(grid=I.Grid(48, 12, 24))
+    w0 = I.dynamic_cme(grid=I.Grid(48, 12, 24))
     plain = ic.from_workload(w0)
     assert gpu.launches_per_step == plain.launches_per_step + 4   # ghost + update per stage
     with pytest.raises(ic.IcarusError) as e:

@@ -21,8 +21,8 @@ def _digest(*arrays):
     return h.hexdigest()[:16]
 
 
-def test_config0_deterministic_and_recipe():
-    a, b = I.config0(), I.config0()
+def test_static_sheet_deterministic_and_recipe():
+    a, b = I.static_sheet(), I.static_sheet()
     assert _digest(a.maps, a.traj) == _digest(b.maps, b.traj)
     m = a.maps[0]
     vr, n, p, br, bphi = m
@@ -36,8 +36,8 @@ def test_config0_deterministic_and_recipe():
     assert (br > 0).any() and (br < 0).any()
 
 
-def test_config1_shapes_and_ranges():
-    w = I.config1(grid=I.Grid(32, 16, 32))
+def test_dynamic_cme_shapes_and_ranges():
+    w = I.dynamic_cme(grid=I.Grid(32, 16, 32))
     assert w.maps.shape == (10, 5, 16, 32) and w.t_maps[-1] == 9 * I.DAY
     tilts = np.array(w.meta["tilts"])
     assert np.all(np.abs(np.diff(tilts)) <= math.radians(5.0) + 1e-12)

@@ -609,7 +609,7 @@ def test_P8_boundary_time_interpolation():
 
 
 def test_P8_ghost_layers_same_value_and_asymm():
-    w = I.config0()
+    w = I.static_sheet()
     from oracle.oracle import from_workload
     o = from_workload(w)
     o.fill_ghosts(0.0)
@@ -661,7 +661,7 @@ def test_P8_outer_radius_continues_radial_flux():
 
 @pytest.mark.parametrize("init_vphi", [I.IC_COROTATING, I.IC_INERTIAL_RADIAL])
 def test_IC_radial_expansion(init_vphi):
-    w = I.config0()
+    w = I.static_sheet()
     w.opts.init_vphi = init_vphi
     from oracle.oracle import from_workload
     o = from_workload(w)
@@ -893,7 +893,7 @@ def test_tracer_marks_inserted_cme_plasma():
     after one step from c = 0 the first radial cell carries tracer in the footprint, and none in
     columns five or more cells away from it."""
     from oracle.oracle import from_workload
-    w = I.config1(grid=I.Grid(24, 16, 32))
+    w = I.dynamic_cme(grid=I.Grid(24, 16, 32))
     w.opts.tracer = 1
     o = from_workload(w)
     t = (w.cmes[0, 0] + 1800.0) / o.scales()["t0"]

@@ -45,7 +45,7 @@ def noalloc_dt(ic, torch, grid_c, gamma, cfl, U):
 @pytest.mark.parametrize("shape", [(64, 16, 32), (512, 64, 128)])
 def test_noalloc_dt_matches_allocating_path_twice(env, shape):
     ic, torch = env
-    w = I.config1(grid=I.Grid(*shape))
+    w = I.dynamic_cme(grid=I.Grid(*shape))
     s = ic.from_workload(w)
     grid_c = ic.make_grid(w.grid)
     U_a, t = s.get_state()
