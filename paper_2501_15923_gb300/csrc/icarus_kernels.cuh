@@ -370,11 +370,11 @@ k_flux(Params P, const TW *__restrict__ W, TW *__restrict__ F)
 template <typename TW>
 __device__ __forceinline__ void divb_cell(const Params &P, const TW *__restrict__ W, TW *__restrict__ divB, long long tid)
 {
-    const int e1 = P.n1 + 2, e2 = P.n2 + 2;
-    int i = (int)(tid % e1) - 1;
-    long long r = tid / e1;
-    int j = (int)(r % e2) - 1;
-    int k = (int)(r / e2) - 1;
+    const unsigned int e1 = P.n1 + 2, e2 = P.n2 + 2, ut = (unsigned int)tid;   // padded cells < 2^31
+    const unsigned int r = ut / e1;
+    const int i = (int)(ut - r * e1) - 1;
+    const int j = (int)(r % e2) - 1;
+    const int k = (int)(r / e2) - 1;
     const MetricsT<TW> &m = met<TW>(P);
     const long long nt = P.nt, c = cidx(P, i, j, k);
     const int ip = i + NG, jp = j + NG;
@@ -782,10 +782,10 @@ k_update_pair(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS
     TW wo[2][NV];
     int i = 0, j = 0;
     if (valid) {
-        i = 2 * (int)(tid % h);
-        const long long r_ = tid / h;
-        j = (int)(r_ % P.n2);
-        const int k = (int)(r_ / P.n2);
+        const unsigned int r_ = (unsigned int)tid / (unsigned int)h;
+        i = 2 * (int)((unsigned int)tid - r_ * (unsigned int)h);
+        j = (int)(r_ % (unsigned int)P.n2);
+        const int k = (int)(r_ / (unsigned int)P.n2);
         const long long nt = P.nt, c = cidx(P, i, j, k);
         const long long s1 = (long long)P.n3 * P.n2 * (P.n1 + 1), f1 = ((long long)k * P.n2 + j) * (P.n1 + 1) + i;
         const long long s2 = (long long)P.n3 * (P.n2 + 1) * P.n1, f2 = ((long long)k * (P.n2 + 1) + j) * P.n1 + i;
