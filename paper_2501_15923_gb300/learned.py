@@ -10,7 +10,7 @@ exactly t0 + T; the target is dU = R(F(t0 + T)) - C10. Consecutive windows of on
 consecutive pairs (the end of one window is the start of the next), after a spin-up from the
 initial state. The network maps the normalised C10 to the normalised dU.
 
-Use. Every k = 10 coarse steps the correction is added to the coarse state. The judge is the
+Use. Every k = 10 coarse steps the correction is added to the coarse state. The reference is the
 plain fine solve: relative L2 errors of v_r, n and |B| at the probes (series interpolated onto a
 common hourly grid) and of the restricted state on the whole grid; if the corrected run's probe
 error exceeds the threshold (1 %), the result falls back to the plain fine solve.
