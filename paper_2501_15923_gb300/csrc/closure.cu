@@ -394,43 +394,84 @@ __global__ void __launch_bounds__(256) k_dpre(Geo g, const float *__restrict__ d
     __shared__ float sdb[O];
     if (threadIdx.x < O) sdb[threadIdx.x] = 0.f;
     __syncthreads();
-    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < g.NP) {
-        int ip = (int)(q % g.q1);
-        long long r = q / g.q1;
-        int jp = (int)(r % g.q2), kp = (int)(r / g.q2);
-        int i = ip - 1, j = jp - 1, k = kp - 1;
-        bool inside = i >= 0 && i < g.n1 && j >= 0 && j < g.n2 && k >= 0 && k < g.n3;
-        for (int o = 0; o < O; ++o) {
-            float d = 0.f;
-            if (inside) {
-                long long s = dout_padded ? q : ((long long)k * g.n2 + j) * g.n1 + i;
-                d = dout[s * O + o];
-                if (act_out && !(__bfloat162float(act_out[q * O + o]) > 0.f)) d = 0.f;
-                d = __bfloat162float(__float2bfloat16_rn(d));
-                atomicAdd(&sdb[o], d);
+    const unsigned int q = blockIdx.x * blockDim.x + threadIdx.x;   // padded cells < 2^31
+    const bool live = q < (unsigned int)g.NP;
+    float d[O];
+#pragma unroll
+    for (int o = 0; o < O; ++o) d[o] = 0.f;
+    if (live) {
+        const unsigned int r = q / (unsigned int)g.q1;
+        const int i = (int)(q - r * (unsigned int)g.q1) - 1, j = (int)(r % (unsigned int)g.q2) - 1,
+                  k = (int)(r / (unsigned int)g.q2) - 1;
+        if (i >= 0 && i < g.n1 && j >= 0 && j < g.n2 && k >= 0 && k < g.n3) {
+            const long long s = dout_padded ? (long long)q : ((long long)k * g.n2 + j) * g.n1 + i;
+            const float4 *src = reinterpret_cast<const float4 *>(dout + s * O);
+#pragma unroll
+            for (int e = 0; e < O / 4; ++e) {
+                const float4 v = src[e];
+                d[4 * e] = v.x; d[4 * e + 1] = v.y; d[4 * e + 2] = v.z; d[4 * e + 3] = v.w;
             }
-            dpre[q * O + o] = __float2bfloat16_rn(d);
+            if (act_out) {
+                const uint4 *am = reinterpret_cast<const uint4 *>(act_out + (long long)q * O);
+#pragma unroll
+                for (int e = 0; e < O / 8; ++e) {
+                    const uint4 a = am[e];
+                    const uint32_t wds[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                    for (int h = 0; h < 8; ++h) {
+                        const float av = __uint_as_float((wds[h >> 1] >> (16 * (h & 1))) << 16);
+                        if (!(av > 0.f)) d[8 * e + h] = 0.f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < O; ++o) d[o] = __bfloat162float(__float2bfloat16_rn(d[o]));
         }
+        uint32_t pk[O / 2];
+#pragma unroll
+        for (int e = 0; e < O / 2; ++e) pk[e] = pack2(__float2bfloat16_rn(d[2 * e]), __float2bfloat16_rn(d[2 * e + 1]));
+        uint4 *dst = reinterpret_cast<uint4 *>(dpre + (long long)q * O);
+#pragma unroll
+        for (int e = 0; e < O / 8; ++e) dst[e] = make_uint4(pk[4 * e], pk[4 * e + 1], pk[4 * e + 2], pk[4 * e + 3]);
+    }
+    // db: warp sums per channel, one shared atomic per warp and channel
+#pragma unroll
+    for (int o = 0; o < O; ++o) {
+        float v = d[o];
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&sdb[o], v);
     }
     __syncthreads();
     if (threadIdx.x < O) atomicAdd(&db[threadIdx.x], sdb[threadIdx.x]);
 }
 
 // ---- weight gradient: dw[o][t][c] += sum_x dpre[x][o] in[x + off_t][c] ----------------------------
-// block = 4 warps over a chunk of voxels; per tap the (O x C) tile is accumulated over the chunk
-// (K = 64 voxels per shared-memory stage) and added to dw with atomics.
+// block = 4 warps over a chunk of TC_WG voxels: the chunk's output gradients (and its voxels'
+// padded indices) are staged in shared memory once; per tap the (O x C) tile is accumulated over
+// the chunk in stages of 64 voxels (the tap's inputs staged with 16-byte loads) and added to dw
+// with atomics.
+constexpr int TC_WG = 512;
 template <int C, int O>
 __global__ void __launch_bounds__(128) k_conv_wgrad(Geo g, const bf16 *__restrict__ dpre, const bf16 *__restrict__ in,
-                                                    float *dw, long long chunk)
+                                                    float *dw)
 {
     constexpr int MT = O / 16, NT = C / 8, TILES = MT * NT, PER = (TILES + 3) / 4;
-    __shared__ __align__(16) bf16 sD[64][O];
+    __shared__ __align__(16) bf16 sD[TC_WG][O];
     __shared__ __align__(16) bf16 sX[64][C];
-    __shared__ long long spb[64];
+    __shared__ long long spb[TC_WG];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 2, tig = lane & 3;
-    const long long vb = (long long)blockIdx.x * chunk;
-    const long long ve = min(g.N, vb + chunk);
+    const long long vb = (long long)blockIdx.x * TC_WG;
+    const int nv = (int)min((long long)TC_WG, g.N - vb);
+    for (int q = threadIdx.x; q < TC_WG; q += blockDim.x) spb[q] = q < nv ? pidx_of_voxel(g, vb + q) : -1;
+    __syncthreads();
+    for (int e = threadIdx.x; e < TC_WG * (O / 8); e += blockDim.x) {      // 16-byte pieces
+        const int row = e / (O / 8), cp = e % (O / 8);
+        const uint4 val = spb[row] >= 0 ? *reinterpret_cast<const uint4 *>(dpre + spb[row] * O + cp * 8) : make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4 *>(&sD[row][cp * 8]) = val;
+    }
+    __syncthreads();
+    const int nstage = (nv + 63) / 64;
     for (int t = 0; t < 27; ++t) {
         const long long off = tap_off(g, t);
         float acc[PER][4];
@@ -438,26 +479,18 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(Geo g, const bf16 *__restric
         for (int p = 0; p < PER; ++p)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[p][e] = 0.f;
-        for (long long sv = vb; sv < ve; sv += 64) {
-            if (threadIdx.x < 64) {
-                long long v = sv + threadIdx.x;
-                spb[threadIdx.x] = v < ve ? pidx_of_voxel(g, v) : -1;
-            }
-            __syncthreads();
-            for (int e = threadIdx.x; e < 64 * (O / 2); e += 128) {
-                int row = e / (O / 2), cp = e % (O / 2);
-                uint32_t val = spb[row] >= 0 ? ld32(dpre + spb[row] * O + cp * 2) : 0u;
-                *reinterpret_cast<uint32_t *>(&sD[row][cp * 2]) = val;
-            }
-            for (int e = threadIdx.x; e < 64 * (C / 2); e += 128) {
-                int row = e / (C / 2), cp = e % (C / 2);
-                uint32_t val = spb[row] >= 0 ? ld32(in + (spb[row] + off) * C + cp * 2) : 0u;
-                *reinterpret_cast<uint32_t *>(&sX[row][cp * 2]) = val;
+        for (int st = 0; st < nstage; ++st) {
+            const int rb = st * 64;
+            for (int e = threadIdx.x; e < 64 * (C / 8); e += blockDim.x) {
+                const int row = e / (C / 8), cp = e % (C / 8);
+                const long long pb = spb[rb + row];
+                const uint4 val = pb >= 0 ? *reinterpret_cast<const uint4 *>(in + (pb + off) * C + cp * 8) : make_uint4(0, 0, 0, 0);
+                *reinterpret_cast<uint4 *>(&sX[row][cp * 8]) = val;
             }
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-                const int k0 = kk * 16 + tig * 2;
+                const int k0 = kk * 16 + tig * 2, kd = rb + k0;
 #pragma unroll
                 for (int p = 0; p < PER; ++p) {
                     const int tile = warp + 4 * p;
@@ -465,10 +498,10 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(Geo g, const bf16 *__restric
                     const int mt = tile / NT, nt = tile % NT;
                     const int o0 = mt * 16 + grp, c0 = nt * 8 + grp;
                     uint32_t a[4];
-                    a[0] = pack2(sD[k0][o0], sD[k0 + 1][o0]);
-                    a[1] = pack2(sD[k0][o0 + 8], sD[k0 + 1][o0 + 8]);
-                    a[2] = pack2(sD[k0 + 8][o0], sD[k0 + 9][o0]);
-                    a[3] = pack2(sD[k0 + 8][o0 + 8], sD[k0 + 9][o0 + 8]);
+                    a[0] = pack2(sD[kd][o0], sD[kd + 1][o0]);
+                    a[1] = pack2(sD[kd][o0 + 8], sD[kd + 1][o0 + 8]);
+                    a[2] = pack2(sD[kd + 8][o0], sD[kd + 9][o0]);
+                    a[3] = pack2(sD[kd + 8][o0 + 8], sD[kd + 9][o0 + 8]);
                     const uint32_t b0 = pack2(sX[k0][c0], sX[k0 + 1][c0]);
                     const uint32_t b1 = pack2(sX[k0 + 8][c0], sX[k0 + 9][c0]);
                     mma16816(acc[p], a, b0, b1);
@@ -591,21 +624,31 @@ __global__ void __launch_bounds__(256) k_mse(Geo g, const float *__restrict__ y,
                                              const double *__restrict__ oscale, float *dy, double *loss)
 {
     __shared__ double red[8];
-    long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned int v = blockIdx.x * blockDim.x + threadIdx.x;   // voxels < 2^31
     double s = 0.0;
-    if (v < g.N) {
-        const int i = (int)(v % g.n1);
-        const double norm = 1.0 / (8.0 * (double)g.N);
-        for (int c = 0; c < 16; ++c) {
-            float d = 0.f;
-            if (c < NV) {
-                double tgt = dU[c * g.N + v] / oscale[c * g.n1 + i];
-                double e = (double)y[v * 16 + c] - tgt;
-                s += e * e * norm;
-                d = (float)(2.0 * e * norm);
+    if (v < (unsigned int)g.N) {
+        const int i = (int)(v % (unsigned int)g.n1);
+        // per element in single precision (the network's own precision), the sum in double
+        const float norm = (float)(1.0 / (8.0 * (double)g.N));
+        const float4 *yv = reinterpret_cast<const float4 *>(y + (long long)v * 16);
+        float4 *dv = reinterpret_cast<float4 *>(dy + (long long)v * 16);
+        float e[NV];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 yy = yv[h];
+            const float ya[4] = {yy.x, yy.y, yy.z, yy.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = 4 * h + q;
+                e[c] = ya[q] - (float)dU[(long long)c * g.N + v] / (float)oscale[c * g.n1 + i];
+                s += (double)(e[c] * e[c]);
             }
-            dy[v * 16 + c] = d;
         }
+        s *= (double)norm;
+        dv[0] = make_float4(2.f * e[0] * norm, 2.f * e[1] * norm, 2.f * e[2] * norm, 2.f * e[3] * norm);
+        dv[1] = make_float4(2.f * e[4] * norm, 2.f * e[5] * norm, 2.f * e[6] * norm, 2.f * e[7] * norm);
+        dv[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dv[3] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -754,11 +797,10 @@ void launch_fwd(int l, Geo g, const bf16 *in, const bf16 *w, const float *b, bf1
 
 void launch_wgrad(int l, Geo g, const bf16 *dpre, const bf16 *in, float *dw, cudaStream_t s)
 {
-    const long long chunk = 2048;
-    const unsigned int nb = ccdiv(g.N, chunk);
-    if (l == 0) k_conv_wgrad<16, 32><<<nb, 128, 0, s>>>(g, dpre, in, dw, chunk);
-    else if (l < 3) k_conv_wgrad<32, 32><<<nb, 128, 0, s>>>(g, dpre, in, dw, chunk);
-    else k_conv_wgrad<32, 16><<<nb, 128, 0, s>>>(g, dpre, in, dw, chunk);
+    const unsigned int nb = ccdiv(g.N, TC_WG);
+    if (l == 0) k_conv_wgrad<16, 32><<<nb, 128, 0, s>>>(g, dpre, in, dw);
+    else if (l < 3) k_conv_wgrad<32, 32><<<nb, 128, 0, s>>>(g, dpre, in, dw);
+    else k_conv_wgrad<32, 16><<<nb, 128, 0, s>>>(g, dpre, in, dw);
 }
 
 void launch_dgrad(int l, Geo g, const bf16 *dpre, const bf16 *wt, float *din, cudaStream_t s)

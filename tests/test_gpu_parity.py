@@ -314,3 +314,20 @@ def test_reduced_precision_step(ic, prec, tol):
     err = field_errors(Ug, Uo)
     assert err.max() <= tol, err
     gpu.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_hlld_single_precision_forms(ic, prec):
+    """HLLD in the FP32-state and MIXED forms: one step on the perturbed static-sheet state of
+    test_hlld_perturbed_state, within the single-precision bar (2e-5 of each field's scale)."""
+    w = I.static_sheet()
+    w.opts = I.Options(flux=I.FLUX_HLLD)
+    gpu, orc = ic.from_workload(w, precision=prec), oracle_workload(w)
+    U, _ = gpu.get_state()
+    W = prim_from_cons(U, w.gamma)
+    Wp = I.perturbed_state(W.shape, 11, W, 2e-2)
+    Ug, Uo, tg, to, _ = step_both(gpu, orc, cons_from_prim(Wp, w.gamma), 0.01)
+    err = field_errors(Ug, Uo)
+    assert err.max() <= 2e-5, err
+    assert abs(tg - to) <= 1e-5 * abs(to - 0.01)
+    gpu.close()
