@@ -450,15 +450,29 @@ __global__ void __launch_bounds__(256) k_dpre(Geo g, const float *__restrict__ d
 // block = 4 warps over a chunk of TC_WG voxels: the chunk's output gradients (and its voxels'
 // padded indices) are staged in shared memory once; per tap the (O x C) tile is accumulated over
 // the chunk in stages of 64 voxels (the tap's inputs staged with 16-byte loads) and added to dw
-// with atomics.
-constexpr int TC_WG = 512;
+// with atomics. Both operands are voxel-major in shared memory (rows padded by 8 elements so that
+// the eight 16-byte rows of a fragment fall in distinct banks) and reach the MMA fragments by
+// transposing ldmatrix loads.
+constexpr int TC_WG = 448;
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t *r, const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(saddr(p)));
+}
+
+__device__ __forceinline__ void ldsm_x2_t(uint32_t *r, const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(saddr(p)));
+}
 template <int C, int O>
 __global__ void __launch_bounds__(128) k_conv_wgrad(Geo g, const bf16 *__restrict__ dpre, const bf16 *__restrict__ in,
                                                     float *dw)
 {
     constexpr int MT = O / 16, NT = C / 8, TILES = MT * NT, PER = (TILES + 3) / 4;
-    __shared__ __align__(16) bf16 sD[TC_WG][O];
-    __shared__ __align__(16) bf16 sX[64][C];
+    __shared__ __align__(16) bf16 sD[TC_WG][O + 8];
+    __shared__ __align__(16) bf16 sX[64][C + 8];
     __shared__ long long spb[TC_WG];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 2, tig = lane & 3;
     const long long vb = (long long)blockIdx.x * TC_WG;
@@ -472,8 +486,9 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(Geo g, const bf16 *__restric
     }
     __syncthreads();
     const int nstage = (nv + 63) / 64;
-    for (int t = 0; t < 27; ++t) {
-        const long long off = tap_off(g, t);
+    for (int tt = 0; tt < 27; ++tt) {
+        const int t = (tt + (int)(blockIdx.x % 27)) % 27;      // blocks start on different taps, so
+        const long long off = tap_off(g, t);                   // their atomics meet fewer addresses
         float acc[PER][4];
 #pragma unroll
         for (int p = 0; p < PER; ++p)
@@ -488,23 +503,19 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(Geo g, const bf16 *__restric
                 *reinterpret_cast<uint4 *>(&sX[row][cp * 8]) = val;
             }
             __syncthreads();
+            const int lr = lane & 7, lj = lane >> 3;          // ldmatrix: row and matrix of this lane
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-                const int k0 = kk * 16 + tig * 2, kd = rb + k0;
 #pragma unroll
                 for (int p = 0; p < PER; ++p) {
                     const int tile = warp + 4 * p;
                     if (tile >= TILES) break;
                     const int mt = tile / NT, nt = tile % NT;
-                    const int o0 = mt * 16 + grp, c0 = nt * 8 + grp;
-                    uint32_t a[4];
-                    a[0] = pack2(sD[kd][o0], sD[kd + 1][o0]);
-                    a[1] = pack2(sD[kd][o0 + 8], sD[kd + 1][o0 + 8]);
-                    a[2] = pack2(sD[kd + 8][o0], sD[kd + 9][o0]);
-                    a[3] = pack2(sD[kd + 8][o0 + 8], sD[kd + 9][o0 + 8]);
-                    const uint32_t b0 = pack2(sX[k0][c0], sX[k0 + 1][c0]);
-                    const uint32_t b1 = pack2(sX[k0 + 8][c0], sX[k0 + 9][c0]);
-                    mma16816(acc[p], a, b0, b1);
+                    // A[o][k] = sD[k][o]: matrices (o 0-7 | 8-15) x (k 0-7 | 8-15); B[k][c] = sX[k][c]
+                    uint32_t a[4], bb[2];
+                    ldsm_x4_t(a, &sD[rb + kk * 16 + lr + (lj >> 1) * 8][mt * 16 + (lj & 1) * 8]);
+                    ldsm_x2_t(bb, &sX[kk * 16 + lr + (lj & 1) * 8][nt * 8]);
+                    mma16816(acc[p], a, bb[0], bb[1]);
                 }
             }
             __syncthreads();
