@@ -4,11 +4,12 @@
 // restricted fine solution; trained on the GPU by the kernels below.
 //
 // Every convolution runs on the tensor cores as an implicit GEMM with BF16 operands and FP32
-// accumulation: the forward (rows = voxels, K = 27 taps x C_in) on the 5th-generation tensor
-// cores (tcgen05.mma, accumulators in tensor memory, operands staged in shared memory); the data
-// gradient (rows = padded voxels, K = 27 x C_out, transposed weights) and the weight gradient
-// (rows = C_out, columns = C_in, K = voxels, split over blocks and summed with atomics) with
-// mma.sync m16n8k16. Activations are stored
+// accumulation: the forward (rows = voxels, K = 27 taps x C_in) and the data gradient (the same
+// convolution over the padded grid with the transposed, tap-reversed weights, rows = padded
+// voxels, K = 27 x C_out) on the 5th-generation tensor cores (tcgen05.mma, accumulators in tensor
+// memory, operands brought into shared memory by the tensor memory accelerator); the weight
+// gradient (rows = C_out, columns = C_in, K = voxels, split over blocks and summed with atomics)
+// with mma.sync m16n8k16 fed by ldmatrix. Activations are stored
 // channels-last on a grid padded by one ghost layer; a pad kernel fills the ghosts (replicate /
 // circular) and a fold kernel adds ghost gradients back to the cells they copy (the adjoint).
 // Channel counts are padded to multiples of 16 (layer 0 input 8 -> 16 zero channels, layer 3
@@ -104,6 +105,7 @@ __device__ __forceinline__ void mma16816(float *d, const uint32_t *a, uint32_t b
 // (tcgen05.ld), adds the bias, applies the ReLU and stores, while the tensor core works on tile k.
 // All waits are bounded: on expiry the block records the failure in tc_status and stops.
 __device__ int tc_status;
+__device__ float tc_zero_bias[32];
 bool tc_host_error = false;
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -159,7 +161,8 @@ template <int C, int O> __host__ __device__ constexpr int tc_smem_bytes()
 // channel group one box of 130 rows x 8 channels (tensor map dims: channel in group, group, i, j, k
 // of the padded grid); rows past the padded line are zero-filled; completion counted on bar
 template <int C>
-__device__ __forceinline__ void tc_load_plane(const CUtensorMap *tm, int i0, int j, int kp, unsigned char *dst, uint32_t bar)
+__device__ __forceinline__ void tc_load_plane(const CUtensorMap *tm, int i0, int j, int kp, int coff, unsigned char *dst,
+                                              uint32_t bar)
 {
     constexpr int G = C / 8;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(3 * G * 130 * 16)
@@ -169,8 +172,8 @@ __device__ __forceinline__ void tc_load_plane(const CUtensorMap *tm, int i0, int
 #pragma unroll
         for (int grp = 0; grp < G; ++grp)
             asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n"
-                         ::"r"(saddr(dst + (jj * G + grp) * TC_BLOCK)), "l"(tm), "r"(0), "r"(grp), "r"(i0),
-                         "r"(j + jj), "r"(kp), "r"(bar)
+                         ::"r"(saddr(dst + (jj * G + grp) * TC_BLOCK)), "l"(tm), "r"(0), "r"(grp), "r"(i0 + coff),
+                         "r"(j + jj + coff), "r"(kp + coff), "r"(bar)
                          : "memory");
 }
 
@@ -229,7 +232,7 @@ __device__ __forceinline__ void tc_epilogue(const Geo &g, uint32_t ta, int i0, i
 template <int C, int O, int ACT>
 __global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, Geo g,
                                                         const bf16 *__restrict__ w, const float *__restrict__ b,
-                                                        bf16 *out_pad, float *out_f)
+                                                        bf16 *out_pad, float *out_f, int coff)
 {
     constexpr int G = C / 8, PB = tc_plane_bytes<C>();
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(const __grid_constant__ 
         const int k1 = min(k0 + TC_KC, g.n3);
         if (tid == 0)
             for (int kp = k0; kp < k0 + TC_RING - 1 && kp <= k1 + 1; ++kp)
-                tc_load_plane<C>(&tm_in, i0, j, kp, sA + (kp % TC_RING) * PB, full0 + 8 * (kp % TC_RING));
+                tc_load_plane<C>(&tm_in, i0, j, kp, coff, sA + (kp % TC_RING) * PB, full0 + 8 * (kp % TC_RING));
         for (int k = k0; k <= k1; ++k) {                  // k = k1: drain (stores of tile k1 - 1)
             if (tid == 0) {
                 int ok = 1;
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(const __grid_constant__ 
                 // done; at k0 that slot was not filled by the opening loads)
                 const int kn = k + TC_RING - 1;
                 if (ok && kn <= k1 + 1)
-                    tc_load_plane<C>(&tm_in, i0, j, kn, sA + (kn % TC_RING) * PB, full0 + 8 * (kn % TC_RING));
+                    tc_load_plane<C>(&tm_in, i0, j, kn, coff, sA + (kn % TC_RING) * PB, full0 + 8 * (kn % TC_RING));
                 *flag = ok;
             }
             __syncthreads();
@@ -534,77 +537,6 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(Geo g, const bf16 *__restric
     }
 }
 
-// ---- data gradient over the padded grid: din[z][c] = sum_{t,o} w[o][t][c] dpre[z - off_t][o] ----
-// wt is the transposed weight copy [C][27][O]; dpre has zero ghosts; sources outside the padded
-// box contribute nothing. The result is folded into the interior by k_pad_fold.
-template <int C, int O>
-__global__ void __launch_bounds__(128) k_conv_dgrad(Geo g, const bf16 *__restrict__ dpre, const bf16 *__restrict__ wt,
-                                                    float *din)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 2, tig = lane & 3;
-    const long long z0 = (long long)blockIdx.x * 128 + warp * 32;
-    int zc[2][2][3];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            long long z = z0 + mt * 16 + grp + 8 * h;
-            if (z >= g.NP) z = 0;
-            zc[mt][h][0] = (int)(z % g.q1);
-            long long r = z / g.q1;
-            zc[mt][h][1] = (int)(r % g.q2);
-            zc[mt][h][2] = (int)(r / g.q2);
-        }
-    float acc[2][C / 8][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < C / 8; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.f;
-    for (int t = 0; t < 27; ++t) {
-        const int d1 = t % 3 - 1, d2 = (t / 3) % 3 - 1, d3 = t / 9 - 1;
-        long long src[2][2];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                int a = zc[mt][h][0] - d1, b = zc[mt][h][1] - d2, c = zc[mt][h][2] - d3;
-                bool ok = a >= 0 && a < g.q1 && b >= 0 && b < g.q2 && c >= 0 && c < g.q3;
-                src[mt][h] = ok ? ((long long)c * g.q2 + b) * g.q1 + a : -1;
-            }
-#pragma unroll
-        for (int ks = 0; ks < O / 16; ++ks) {
-            uint32_t a[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const long long s0 = src[mt][0], s1 = src[mt][1];
-                const int cb = ks * 16 + tig * 2;
-                a[mt][0] = s0 >= 0 ? ld32(dpre + s0 * O + cb) : 0u;
-                a[mt][1] = s1 >= 0 ? ld32(dpre + s1 * O + cb) : 0u;
-                a[mt][2] = s0 >= 0 ? ld32(dpre + s0 * O + cb + 8) : 0u;
-                a[mt][3] = s1 >= 0 ? ld32(dpre + s1 * O + cb + 8) : 0u;
-            }
-#pragma unroll
-            for (int nt = 0; nt < C / 8; ++nt) {
-                const bf16 *wb = wt + ((long long)(nt * 8 + grp) * 27 + t) * O + ks * 16 + tig * 2;
-                const uint32_t b0 = ld32(wb), b1 = ld32(wb + 8);
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], a[mt], b0, b1);
-            }
-        }
-    }
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < C / 8; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const long long z = z0 + mt * 16 + grp + 8 * (e >> 1);
-                if (z >= g.NP) continue;
-                din[z * C + nt * 8 + tig * 2 + (e & 1)] = acc[mt][nt][e];
-            }
-}
 
 // ---- normalisation, loss, correction, optimiser --------------------------------------------------
 // x[z][c] = (U[c][v] - mean[c][i]) / scale[c][i] for c < 8, 0 for c in [8, 16)
@@ -712,7 +644,7 @@ __global__ void k_weights_bf16(int O, int C, const float *w, bf16 *wb, bf16 *wt)
     int c = q % C, t = (q / C) % 27, o = q / (27 * C);
     bf16 x = __float2bfloat16_rn(w[q]);
     wb[q] = x;
-    wt[((long long)c * 27 + t) * O + o] = x;
+    wt[((long long)c * 27 + (26 - t)) * O + o] = x;          // transposed, taps reversed
 }
 
 // volume-weighted 2x2x2 restriction of a fine solver state onto a coarse one (padded layouts)
@@ -761,9 +693,7 @@ bool tc_tensor_map(CUtensorMap *tm, const bf16 *buf, const Geo &g, int C)
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// persistent tcgen05 forward: one block per SM (at most one per tile)
-template <int C, int O, int ACT>
-void launch_fwd_tc(Geo g, const bf16 *in, const bf16 *w, const float *b, bf16 *out_pad, float *out_f, cudaStream_t s)
+template <int C, int O, int ACT> int tc_prepare()
 {
     static int sms = 0;
     if (!sms) {
@@ -772,14 +702,48 @@ void launch_fwd_tc(Geo g, const bf16 *in, const bf16 *w, const float *b, bf16 *o
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(k_conv_fwd_tc<C, O, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes<C, O>());
     }
+    return sms;
+}
+
+// persistent tcgen05 convolution over the interior of geometry g (one block per SM at most one per
+// work item); the input's tensor map tm, its coordinates shifted by coff
+template <int C, int O, int ACT>
+void launch_conv_tc(const CUtensorMap &tm, Geo g, const bf16 *w, const float *b, bf16 *out_pad, float *out_f, int coff,
+                    cudaStream_t s)
+{
+    const int sms = tc_prepare<C, O, ACT>();
+    const long long items = (long long)((g.n1 + 127) / 128) * g.n2 * ((g.n3 + TC_KC - 1) / TC_KC);
+    const unsigned int nb = (unsigned int)(items < sms ? items : sms);
+    k_conv_fwd_tc<C, O, ACT><<<nb, 128, tc_smem_bytes<C, O>(), s>>>(tm, g, w, b, out_pad, out_f, coff);
+}
+
+// forward: interior voxels of g from the padded input (ghosts filled)
+template <int C, int O, int ACT>
+void launch_fwd_tc(Geo g, const bf16 *in, const bf16 *w, const float *b, bf16 *out_pad, float *out_f, cudaStream_t s)
+{
     CUtensorMap tm;
     if (!tc_tensor_map(&tm, in, g, C)) {
         tc_host_error = true;
         return;
     }
-    const long long items = (long long)((g.n1 + 127) / 128) * g.n2 * ((g.n3 + TC_KC - 1) / TC_KC);
-    const unsigned int nb = (unsigned int)(items < sms ? items : sms);
-    k_conv_fwd_tc<C, O, ACT><<<nb, 128, tc_smem_bytes<C, O>(), s>>>(tm, g, w, b, out_pad, out_f);
+    launch_conv_tc<C, O, ACT>(tm, g, w, b, out_pad, out_f, 0, s);
+}
+
+// data gradient as the same convolution: every padded voxel z of g (the interior of a geometry
+// whose cells are g's padded cells) gets sum_t wt[c][26 - t][o] dpre[z + off_t][o], i.e.
+// sum_t w[o][t][c] dpre[z - off_t][o], with zeros beyond the padded box (the tensor copies fill
+// them); wt holds the transposed weights with the taps reversed
+template <int CIN, int COUT>
+void launch_dgrad_tc(Geo g, const bf16 *dpre, const bf16 *wt, float *din, cudaStream_t s)
+{
+    static float *zero_bias = nullptr;
+    if (!zero_bias) cudaGetSymbolAddress((void **)&zero_bias, tc_zero_bias);
+    CUtensorMap tm;
+    if (!tc_tensor_map(&tm, dpre, g, CIN)) {
+        tc_host_error = true;
+        return;
+    }
+    launch_conv_tc<CIN, COUT, 0>(tm, make_geo(g.q1, g.q2, g.q3), wt, zero_bias, nullptr, din, -1, s);
 }
 
 // a tcgen05 forward block whose MMA completion wait expired, or a tensor map that could not be
@@ -816,9 +780,8 @@ void launch_wgrad(int l, Geo g, const bf16 *dpre, const bf16 *in, float *dw, cud
 
 void launch_dgrad(int l, Geo g, const bf16 *dpre, const bf16 *wt, float *din, cudaStream_t s)
 {
-    const unsigned int nb = ccdiv(g.NP, 128);
-    if (l == 3) k_conv_dgrad<32, 16><<<nb, 128, 0, s>>>(g, dpre, wt, din);
-    else k_conv_dgrad<32, 32><<<nb, 128, 0, s>>>(g, dpre, wt, din);   // layers 1, 2 (layer 0 needs none)
+    if (l == 3) launch_dgrad_tc<16, 32>(g, dpre, wt, din, s);
+    else launch_dgrad_tc<32, 32>(g, dpre, wt, din, s);   // layers 1, 2 (layer 0 needs none)
 }
 
 void launch_dpre(int O, Geo g, const float *dout, int padded, const bf16 *act, bf16 *dpre, float *db, cudaStream_t s)
@@ -1154,10 +1117,10 @@ int icarus_conv3d_layer(int n1, int n2, int n3, int C, int O, int act, const flo
         launch_dpre(O, gg, gf, 0, act ? dout_ : nullptr, dpre, dbf, 0);
         launch_wgrad(l, gg, dpre, din_, dwf, 0);
         if (C == 32) {
-            if (O == 16) k_conv_dgrad<32, 16><<<ccdiv(gg.NP, 128), 128>>>(gg, dpre, wt, dinf);
-            else k_conv_dgrad<32, 32><<<ccdiv(gg.NP, 128), 128>>>(gg, dpre, wt, dinf);
+            if (O == 16) launch_dgrad_tc<16, 32>(gg, dpre, wt, dinf, 0);
+            else launch_dgrad_tc<32, 32>(gg, dpre, wt, dinf, 0);
         } else {
-            k_conv_dgrad<16, 32><<<ccdiv(gg.NP, 128), 128>>>(gg, dpre, wt, dinf);
+            launch_dgrad_tc<32, 16>(gg, dpre, wt, dinf, 0);
         }
         k_pad_fold<<<ccdiv(gg.NP, 256), 256>>>(gg, dinf, C);
         cudaError_t e = cudaDeviceSynchronize();
