@@ -427,23 +427,47 @@ int icarus_set_boundary(icarus_ctx *c, int n_maps, const double *t_maps, const d
         if (!(t_maps[m] > t_maps[m - 1])) return fail(ICARUS_EINVAL, "map times must increase");
     Params &P = c->P;
     const size_t per = (size_t)P.n2 * P.n3;
-    std::vector<double> hm((size_t)n_maps * 5 * per), ht(n_maps);
+    const size_t nm = (size_t)n_maps * 5 * per, nc = 10 * (size_t)(n_cme > 0 ? n_cme : 1);
+    // the previous tables may still be in flight from the staging buffer or in use on the device
+    CK(cudaStreamSynchronize(c->stream));
+    // code-unit tables written straight into pinned host memory (one DMA each, no driver staging);
+    // pageable fallback if pinned memory cannot be had
+    std::vector<double> fallback;
+    double *hm = nullptr;
+    if (nm + n_maps + nc > c->hstage_cap) {
+        if (c->hstage) cudaFreeHost(c->hstage);
+        c->hstage = nullptr;
+        c->hstage_cap = 0;
+        if (cudaHostAlloc((void **)&c->hstage, (nm + n_maps + nc) * sizeof(double), cudaHostAllocDefault) == cudaSuccess)
+            c->hstage_cap = nm + n_maps + nc;
+        else {
+            c->hstage = nullptr;
+            cudaGetLastError();
+        }
+    }
+    if (c->hstage) hm = c->hstage;
+    else {
+        fallback.resize(nm + n_maps + nc);
+        hm = fallback.data();
+    }
+    double *ht = hm + nm, *hc = ht + n_maps;
+    const double iv0 = 1.0 / V0, in0 = 1.0 / N0, ip0 = 1.0 / c->p0, ib0 = 1.0 / c->b0;
     for (int m = 0; m < n_maps; ++m) {
         ht[m] = t_maps[m] / c->t0;
         const double *src = maps + (size_t)m * 5 * per;
-        double *dst = hm.data() + (size_t)m * 5 * per;
+        double *dst = hm + (size_t)m * 5 * per;
         for (size_t q = 0; q < per; ++q) {
-            dst[q] = src[q] / V0;
-            dst[per + q] = src[per + q] / N0;
-            dst[2 * per + q] = src[2 * per + q] / c->p0;
-            dst[3 * per + q] = src[3 * per + q] / c->b0;
-            dst[4 * per + q] = src[4 * per + q] / c->b0;
+            dst[q] = src[q] * iv0;
+            dst[per + q] = src[per + q] * in0;
+            dst[2 * per + q] = src[2 * per + q] * ip0;
+            dst[3 * per + q] = src[3 * per + q] * ib0;
+            dst[4 * per + q] = src[4 * per + q] * ib0;
         }
     }
-    std::vector<double> hc(10 * (size_t)(n_cme > 0 ? n_cme : 1));
+    for (size_t q = 0; q < nc; ++q) hc[q] = 0.0;
     for (int q = 0; q < n_cme; ++q) {
         const double *s = cmes + 8 * q;
-        double *d = hc.data() + 10 * q;
+        double *d = hc + 10 * q;
         d[0] = s[0] / c->t0;
         d[1] = s[1] / c->t0;
         d[2] = cos(s[2]) * cos(s[3]);
@@ -457,24 +481,27 @@ int icarus_set_boundary(icarus_ctx *c, int n_maps, const double *t_maps, const d
         d[9] = c->grid.x1min * sin(s[4]);
         if (c->P.cme_model == ICARUS_CME_SPHERE) d[1] = 2.0 * d[9] / d[6];
     }
-    CK(cudaStreamSynchronize(c->stream));
-    if (hm.size() > c->maps_cap) {
-        c->maps = (double *)dalloc(c, hm.size() * sizeof(double));
+    if (nm > c->maps_cap || (size_t)n_maps > c->tmaps_cap) {
+        c->maps = (double *)dalloc(c, nm * sizeof(double));
         c->tmaps = (double *)dalloc(c, n_maps * sizeof(double));
         if (!c->maps || !c->tmaps) return fail(ICARUS_ENOMEM, "map allocation failed");
-        c->maps_cap = hm.size();
+        c->maps_cap = nm;
+        c->tmaps_cap = n_maps;
     }
-    if (hc.size() > c->cme_cap) {
-        c->cme = (double *)dalloc(c, hc.size() * sizeof(double));
+    if (nc > c->cme_cap) {
+        c->cme = (double *)dalloc(c, nc * sizeof(double));
         if (!c->cme) return fail(ICARUS_ENOMEM, "CME allocation failed");
-        c->cme_cap = hc.size();
+        c->cme_cap = nc;
     }
-    CK(cudaMemcpyAsync(c->maps, hm.data(), hm.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->tmaps, ht.data(), ht.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->cme, hc.data(), hc.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->maps, hm, nm * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->tmaps, ht, n_maps * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->cme, hc, nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    // the captured step reads the tables through these pointers and counts: a new graph only when
+    // one of them changes
+    if (P.maps != c->maps || P.t_maps != c->tmaps || P.cme != c->cme || P.n_maps != n_maps || P.n_cme != n_cme)
+        drop_graph(c);
     P.maps = c->maps; P.t_maps = c->tmaps; P.cme = c->cme;
     P.n_maps = n_maps; P.n_cme = n_cme;
-    drop_graph(c);
     c->have_boundary = true;
     if (!c->have_state) {
         if (c->grid.geometry != ICARUS_GEOM_SPHERICAL) return fail(ICARUS_EINVAL, "initial state from maps needs a spherical grid");
@@ -559,6 +586,7 @@ int icarus_destroy(icarus_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graph(c);
     dfree_all(c);
+    if (c->hstage) cudaFreeHost(c->hstage);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return ICARUS_OK;

@@ -21,7 +21,9 @@ struct icarus_ctx {
     double *metric = nullptr, *partial = nullptr, *stage_buf = nullptr;
     icarus::Scalars *sc = nullptr;
     double *maps = nullptr, *tmaps = nullptr, *cme = nullptr, *traj = nullptr, *ring = nullptr;
-    size_t maps_cap = 0, cme_cap = 0, traj_cap = 0;
+    size_t maps_cap = 0, tmaps_cap = 0, cme_cap = 0, traj_cap = 0;
+    double *hstage = nullptr;       // pinned host staging of the boundary tables (maps, times, CMEs)
+    size_t hstage_cap = 0;
     bool have_state = false, have_boundary = false;
     cudaGraphExec_t graph = nullptr;
     long long ring_tail = 0;

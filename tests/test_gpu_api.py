@@ -77,3 +77,28 @@ def test_full_size_single_precision_forms(ic, prec):
     assert err.max() <= 2e-5, err
     assert abs(tg - to) <= 1e-5 * abs(to - t)
     gpu.close()
+
+
+def test_new_maps_of_the_same_shape_reach_the_captured_step(ic):
+    """icarus_set_boundary with tables of unchanged shape keeps the captured step (the device
+    tables are rewritten in place): the next step must see the new values, bit for bit as a
+    context that was given them from the start."""
+    w = I.dynamic_cme(grid=I.Grid(48, 12, 24))
+    maps2 = w.maps * np.array([1.1, 0.9, 1.05, 1.0, 0.95])[None, :, None, None]
+    a = ic.from_workload(w)
+    U, _ = a.get_state()
+    t = 1.5 * I.DAY / a.scales()["t0"]
+    a.set_state(U, t)
+    a.step(1)                                   # the step is captured with the first tables
+    a.set_boundary(w.t_maps, maps2, w.cmes)
+    a.set_state(U, t)
+    a.step(1)
+    w2 = I.dynamic_cme(grid=I.Grid(48, 12, 24))
+    w2.maps = maps2
+    b = ic.from_workload(w2)
+    b.set_state(U, t)
+    b.step(1)
+    Ua, ta = a.get_state()
+    Ub, tb = b.get_state()
+    assert ta == tb and np.array_equal(Ua, Ub)
+    a.close(); b.close()
