@@ -66,8 +66,6 @@ __device__ __forceinline__ long long tap_off(const Geo &g, int t)
     return ((long long)d3 * g.q2 + d2) * g.q1 + d1;
 }
 
-__device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
-
 __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi)
 {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
