@@ -761,6 +761,14 @@ bool tc_timed_out()
     return v != 0;
 }
 
+// a tensor map that could not be encoded (the affected launch was skipped): host-side, no sync
+bool tc_map_failed()
+{
+    const bool f = tc_host_error;
+    tc_host_error = false;
+    return f;
+}
+
 void launch_fwd(int l, Geo g, const bf16 *in, const bf16 *w, const float *b, bf16 *out_pad, float *out_f, cudaStream_t s)
 {
     if (l == 0) launch_fwd_tc<16, 32, 1>(g, in, w, b, out_pad, out_f, s);
@@ -954,6 +962,7 @@ int icarus_closure_train_step(icarus_closure *c, const double *U_in, const doubl
     k_norm_in<<<ccdiv(g.N, 256), 256, 0, s>>>(g, U_in, c->mean, c->scale, c->act[0]);
     k_pad_fill<bf16><<<ccdiv(g.NP, 256), 256, 0, s>>>(g, c->act[0], 16);
     forward(c);
+    if (tc_map_failed()) return report_error(ICARUS_ECUDA, "tensor map encoding failed");
     CCK(cudaMemsetAsync(c->loss, 0, 8, s));
     k_mse<<<ccdiv(g.N, 256), 256, 0, s>>>(g, c->y, dU_target, c->oscale, c->dy, c->loss);
     for (int l = 0; l < 4; ++l) {
@@ -970,6 +979,7 @@ int icarus_closure_train_step(icarus_closure *c, const double *U_in, const doubl
             k_pad_fold<<<ccdiv(g.NP, 256), 256, 0, s>>>(g, c->din, LC[l]);
         }
     }
+    if (tc_map_failed()) return report_error(ICARUS_ECUDA, "tensor map encoding failed");   // before Adam
     c->step++;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)c->step), c2 = 1.f - powf(b2, (float)c->step);
@@ -999,6 +1009,7 @@ int icarus_closure_predict(icarus_closure *c, const double *U_in, double *dU_out
     k_norm_in<<<ccdiv(g.N, 256), 256, 0, s>>>(g, U_in, c->mean, c->scale, c->act[0]);
     k_pad_fill<bf16><<<ccdiv(g.NP, 256), 256, 0, s>>>(g, c->act[0], 16);
     forward(c);
+    if (tc_map_failed()) return report_error(ICARUS_ECUDA, "tensor map encoding failed");
     k_unpack_dU<<<ccdiv(g.N, 256), 256, 0, s>>>(g, c->y, c->oscale, dU_out);
     CCK(cudaGetLastError());
     return ICARUS_OK;
@@ -1021,6 +1032,7 @@ int icarus_closure_apply(icarus_closure *c, icarus_ctx *ctx)
     cudaStream_t keep = c->stream;
     c->stream = s;
     forward(c);
+    if (tc_map_failed()) return report_error(ICARUS_ECUDA, "tensor map encoding failed");
     c->stream = keep;
     k_apply<<<ccdiv(g.N, 256), 256, 0, s>>>(ctx->P, g, c->y, c->oscale, (double *)ctx->U);
     ctx->ops.prims(ctx->P, ctx->U, ctx->W, s);
