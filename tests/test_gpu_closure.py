@@ -55,3 +55,24 @@ def test_layer_forward_and_gradients_match_oracle(ic, C, Oc, act, shape):
     for got, ref in ((y, yo), (dx, dxo), (dw, dwo), (db, dbo)):
         scale = np.abs(ref).max()
         assert np.abs(got - ref).max() <= 2e-5 * scale, (np.abs(got - ref).max(), scale)
+
+
+def test_restriction_matches_oracle(ic):
+    """icarus_restrict (volume-weighted 2x2x2 average of a fine FP64 state onto the half-resolution
+    grid) against the oracle's restriction of the same fine state, on a stretched spherical grid
+    with a perturbed state (every cell different)."""
+    from oracle.oracle import Oracle, from_workload as oracle_workload
+    from paper_2501_15923_gb300 import inputs as I, learned
+    w = I.dynamic_cme(grid=I.Grid(32, 12, 16))
+    fine = ic.from_workload(w)
+    coarse = ic.from_workload(learned.coarse_workload(w))
+    U, t = fine.get_state()
+    U = U * I.perturbed_state(U.shape, 5, np.ones(U.shape), 1e-3)
+    fine.set_state(U, t)
+    ic.icarus_restrict(fine.ctx, coarse.ctx)
+    Uc, tc = coarse.get_state()
+    vol = oracle_workload(w).volumes()
+    ref = O.restrict(U, vol)
+    assert tc == t
+    np.testing.assert_allclose(Uc, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+    fine.close(); coarse.close()
