@@ -63,7 +63,7 @@ def test_restriction_matches_oracle(ic):
     with a perturbed state (every cell different)."""
     from oracle.oracle import Oracle, from_workload as oracle_workload
     from paper_2501_15923_gb300 import inputs as I, learned
-    w = I.dynamic_cme(grid=I.Grid(32, 12, 16))
+    w = I.dynamic_cme(grid=I.Grid(32, 24, 16))     # coarse 16 x 12 x 8 keeps its ghosts off the pole
     fine = ic.from_workload(w)
     coarse = ic.from_workload(learned.coarse_workload(w))
     U, t = fine.get_state()
