@@ -49,7 +49,7 @@ enum { BC_PERIODIC = 0, BC_CONT = 1, BC_REFLECT = 2, BC_DRIVEN = 3, BC_FIXED = 4
 enum { GEOM_SPH = 0, GEOM_CART = 1 };
 enum { LIM_MINMOD = 0, LIM_VANLEER = 1, LIM_MC = 2 };
 enum { FLUX_TVDLF = 0, FLUX_HLL = 1, FLUX_HLLD = 2 };
-enum { DIVB_NONE = 0, DIVB_LINDE = 1 };
+enum { DIVB_NONE = 0, DIVB_LINDE = 1, DIVB_GLM = 2 };
 
 #define NG 2
 
@@ -70,6 +70,11 @@ typedef struct {
     double t0, p0, b0;       /* code-unit scales */
     double *U, *U0, *U1, *L, *W, *F[3], *divB, *Ufix;
     int tracer;                     /* CME tracer on: T = rho c, c = 1 in inserted CME plasma */
+    /* GLM div-B control (divb = DIVB_GLM): psi and its stage copies (padded), the residual of
+     * psi, the face fluxes of psi; c_h of the current step, the damping constant alpha, the
+     * smallest cell width; Pcur = the psi the residual reads */
+    double *Psi, *Psi0, *Psi1, *LPsi, *FP[3], *Pcur;
+    double glm_alpha, glm_dmin, glm_ch;
     double *T, *T0, *T1, *LT, *C;   /* padded: rho c now / at the step start / stage 1, residual, c */
     double t;
     int n_maps; double *tm; double *maps;      /* code units, [n_maps][5][n2][n3] */
@@ -509,9 +514,30 @@ static void face_fluxes(orc_t *o, int d)
                     wl[v] = wm1[v] + 0.5 * da;
                     wr[v] = w0[v] - 0.5 * db;
                 }
-                if (wl[0] <= 0.0 || wr[0] <= 0.0 || wl[4] <= 0.0 || wr[4] <= 0.0)
+                const int first = wl[0] <= 0.0 || wr[0] <= 0.0 || wl[4] <= 0.0 || wr[4] <= 0.0;
+                if (first)
                     for (int v = 0; v < NV; v++) { wl[v] = wm1[v]; wr[v] = w0[v]; }
                 riemann(o, wl, wr, d, f);
+                if (o->divb == DIVB_GLM) {
+                    /* GLM (Dedner et al. 2002): the (B_n, psi) pair obeys B_n,t + psi_n = 0,
+                     * psi_t + c_h^2 B_n,n = 0 along the normal; its exact upwind face state replaces
+                     * the normal-field flux by psi* and gives psi the flux c_h^2 B_n*. psi is
+                     * reconstructed like the primitives (first order where they are). */
+                    const double *P = o->Pcur;
+                    long ib = IDX(o, i, j, k), s1 = IDX(o, i - sh[0], j - sh[1], k - sh[2]);
+                    long s2 = IDX(o, i - 2 * sh[0], j - 2 * sh[1], k - 2 * sh[2]);
+                    long s0 = IDX(o, i + sh[0], j + sh[1], k + sh[2]);
+                    double pl = P[s1], pr = P[ib];
+                    if (!first) {
+                        pl = P[s1] + 0.5 * limit(o->limiter, P[s1] - P[s2], P[ib] - P[s1]);
+                        pr = P[ib] - 0.5 * limit(o->limiter, P[ib] - P[s1], P[s0] - P[ib]);
+                    }
+                    double ch = o->glm_ch, bl = wl[B1 + d], brr = wr[B1 + d];
+                    double bs = 0.5 * (bl + brr) - 0.5 * (pr - pl) / ch;
+                    double ps = 0.5 * (pl + pr) - 0.5 * ch * (brr - bl);
+                    f[B1 + d] = ps;
+                    o->FP[d][ib] = ch * ch * bs;
+                }
                 store(o, o->F[d], IDX(o, i, j, k), f);
             }
 }
@@ -552,6 +578,7 @@ static void residual(orc_t *o, const double *U, double dt)
                 double Lc[NV], w[NV];
                 int sh[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
                 for (int v = 0; v < NV; v++) Lc[v] = 0.0;
+                if (o->divb == DIVB_GLM) o->LPsi[id] = 0.0;
                 /* flux divergence: -(1/V) sum_d (A+ F+ - A- F-) */
                 for (int d = 0; d < 3; d++) {
                     long idp = IDX(o, i + sh[d][0], j + sh[d][1], k + sh[d][2]);
@@ -559,6 +586,11 @@ static void residual(orc_t *o, const double *U, double dt)
                     double ap = area(o, d, i + sh[d][0], j + sh[d][1], k + sh[d][2]);
                     for (int v = 0; v < NV; v++)
                         Lc[v] -= (ap * o->F[d][v * o->nt + idp] - am * o->F[d][v * o->nt + id]) / V;
+                    if (o->divb == DIVB_GLM) {
+                        /* the flux form of grad psi leaves psi (A+ - A-) / V, as for p_tot */
+                        Lc[B1 + d] += o->Pcur[id] * (ap - am) / V;
+                        o->LPsi[id] -= (ap * o->FP[d][idp] - am * o->FP[d][id]) / V;
+                    }
                 }
                 load(o, o->W, id, w);
                 double rho = w[0], vr = w[1], vt = w[2], vp = w[3];
@@ -704,6 +736,7 @@ orc_t *orc_create(const int *ig, const double *dg, double gamma, double omega_si
     o->omega_si = omega_si;
     o->omega = omega_si * o->t0;
     o->cfl = od[0]; o->divb_coef = od[1]; o->rho_floor = od[2]; o->p_floor = od[3];
+    o->glm_alpha = od[4];
     o->limiter = oi[0]; o->flux = oi[1]; o->gravity = oi[2]; o->divb = oi[3]; o->init_vphi = oi[4];
     o->cme_model = oi[5];
     o->tracer = oi[6];
@@ -717,6 +750,16 @@ orc_t *orc_create(const int *ig, const double *dg, double gamma, double omega_si
     o->T = (double *)calloc(1, sizeof(double) * o->nt); o->T0 = (double *)calloc(1, sizeof(double) * o->nt);
     o->T1 = (double *)calloc(1, sizeof(double) * o->nt); o->LT = (double *)calloc(1, sizeof(double) * o->nt);
     o->C = (double *)calloc(1, sizeof(double) * o->nt);
+    o->Psi = (double *)calloc(1, sizeof(double) * o->nt); o->Psi0 = (double *)calloc(1, sizeof(double) * o->nt);
+    o->Psi1 = (double *)calloc(1, sizeof(double) * o->nt); o->LPsi = (double *)calloc(1, sizeof(double) * o->nt);
+    for (int d = 0; d < 3; d++) o->FP[d] = (double *)calloc(1, sizeof(double) * o->nt);
+    o->Pcur = o->Psi;
+    /* smallest cell width over the interior (dr, r dtheta, r sin(theta) dphi on the sphere) */
+    o->glm_dmin = 1e300;
+    for (int k = 0; k < o->n[2]; k++)
+        for (int j = 0; j < o->n[1]; j++)
+            for (int i = 0; i < o->n[0]; i++)
+                for (int d = 0; d < 3; d++) o->glm_dmin = fmin(o->glm_dmin, width(o, d, i, j, k));
     return o;
 }
 
@@ -726,6 +769,8 @@ void orc_destroy(orc_t *o)
     for (int d = 0; d < 3; d++) { free(o->e[d]); free(o->c[d]); free(o->F[d]); }
     free(o->U); free(o->U0); free(o->U1); free(o->L); free(o->W); free(o->Ufix); free(o->divB);
     free(o->T); free(o->T0); free(o->T1); free(o->LT); free(o->C);
+    free(o->Psi); free(o->Psi0); free(o->Psi1); free(o->LPsi);
+    for (int d = 0; d < 3; d++) free(o->FP[d]);
     free(o->tm); free(o->maps); free(o->cme);
     free(o);
 }
@@ -837,6 +882,29 @@ void orc_edges(const orc_t *o, int d, double *out)
 
 /* one SSP-RK2 step: U1 = U + dt L(U, t); U <- U/2 + (U1 + dt L(U1, t + dt))/2; floors after each
  * stage; dt = CFL bound, capped by dt_max when dt_max > 0. Returns dt, or -1 on non-finite state */
+/* ---- GLM psi: ghost layers copied like the other variables (zero gradient at the driven face),
+ * each direction over the ghost layers of the previous ones, as the MHD ghost fill does */
+static void psi_fill(orc_t *o, double *P)
+{
+    for (int d = 0; d < 3; d++)
+        for (int side = 0; side < 2; side++) {
+            int bc = o->bc[2 * d + side], n = o->n[d];
+            int a_lo = -NG, a_hi = o->n[(d + 1) % 3] + NG, b_lo = -NG, b_hi = o->n[(d + 2) % 3] + NG;
+            if (d == 0) { a_lo = 0; a_hi = o->n[1]; b_lo = 0; b_hi = o->n[2]; }
+            if (d == 1) { a_lo = 0; a_hi = o->n[2]; b_lo = -NG; b_hi = o->n[0] + NG; }
+            for (int b = b_lo; b < b_hi; b++)
+                for (int a = a_lo; a < a_hi; a++)
+                    for (int g = 1; g <= NG; g++) {
+                        int gi = side == 0 ? -g : n - 1 + g, src;
+                        if (bc == BC_CONT || bc == BC_DRIVEN) src = side == 0 ? 0 : n - 1;
+                        else if (bc == BC_REFLECT) src = side == 0 ? g - 1 : n - g;
+                        else if (bc == BC_PERIODIC) src = ((gi % n) + n) % n;
+                        else src = gi;   /* FIXED: keep */
+                        P[cell_id(o, d, gi, a, b)] = P[cell_id(o, d, src, a, b)];
+                    }
+        }
+}
+
 /* ---- CME tracer (a passive scalar c carried by the plasma; rho c is conserved) --------------
  * The paper marks inserted CME plasma with a tracer. Boundary: c = 1 in the ghost columns inside
  * the CME footprint while it is inserted, 0 elsewhere on the driven face; c is copied like the
@@ -932,6 +1000,14 @@ double orc_step(orc_t *o, double dt_max)
     double dt = cfl_dt(o, o->U);
     if (dt_max > 0.0 && dt > dt_max) dt = dt_max;
     long tot = NV * o->nt;
+    const int glm = o->divb == DIVB_GLM;
+    if (glm) {
+        /* c_h: the fastest speed the step's dt carries at the CFL number over the smallest cell */
+        o->glm_ch = o->cfl * o->glm_dmin / dt;
+        memcpy(o->Psi0, o->Psi, sizeof(double) * o->nt);
+        psi_fill(o, o->Psi);
+        o->Pcur = o->Psi;
+    }
     memcpy(o->U0, o->U, sizeof(double) * tot);
     fill_ghosts(o, o->U, o->t);
     residual(o, o->U, dt);
@@ -957,6 +1033,16 @@ double orc_step(orc_t *o, double dt_max)
                 }
     apply_floors(o, o->U1);
     if (o->tracer) tracer_clip(o, o->T1, o->U1);
+    if (glm) {
+        for (int k = 0; k < o->n[2]; k++)
+            for (int j = 0; j < o->n[1]; j++)
+                for (int i = 0; i < o->n[0]; i++) {
+                    long id = IDX(o, i, j, k);
+                    o->Psi1[id] = o->Psi0[id] + dt * o->LPsi[id];
+                }
+        psi_fill(o, o->Psi1);
+        o->Pcur = o->Psi1;
+    }
     fill_ghosts(o, o->U1, o->t + dt);
     residual(o, o->U1, dt);
     if (o->tracer) {
@@ -978,6 +1064,17 @@ double orc_step(orc_t *o, double dt_max)
                 }
     apply_floors(o, o->U);
     if (o->tracer) tracer_clip(o, o->T, o->U);
+    if (glm) {
+        /* second stage, then the damping source -(c_h^2 / c_p^2) psi integrated exactly over the
+         * step (operator split): psi *= exp(-alpha c_h dt / dmin) */
+        const double damp = exp(-o->glm_alpha * o->glm_ch * dt / o->glm_dmin);
+        for (int k = 0; k < o->n[2]; k++)
+            for (int j = 0; j < o->n[1]; j++)
+                for (int i = 0; i < o->n[0]; i++) {
+                    long id = IDX(o, i, j, k);
+                    o->Psi[id] = (0.5 * o->Psi0[id] + 0.5 * (o->Psi1[id] + dt * o->LPsi[id])) * damp;
+                }
+    }
     o->t = o->t + dt;
     return o->status ? -1.0 : dt;
 }
@@ -1002,6 +1099,24 @@ void orc_get_tracer(const orc_t *o, double *c)
                 c[((long)k * o->n[1] + j) * o->n[0] + i] = o->T[id] / o->U[RHO * o->nt + id];
             }
 }
+
+/* GLM psi of the interior cells [n3][n2][n1]: set / get; c_h of the last step */
+void orc_set_psi(orc_t *o, const double *p)
+{
+    for (int k = 0; k < o->n[2]; k++)
+        for (int j = 0; j < o->n[1]; j++)
+            for (int i = 0; i < o->n[0]; i++) o->Psi[IDX(o, i, j, k)] = p[((long)k * o->n[1] + j) * o->n[0] + i];
+}
+
+void orc_get_psi(const orc_t *o, double *p)
+{
+    for (int k = 0; k < o->n[2]; k++)
+        for (int j = 0; j < o->n[1]; j++)
+            for (int i = 0; i < o->n[0]; i++) p[((long)k * o->n[1] + j) * o->n[0] + i] = o->Psi[IDX(o, i, j, k)];
+}
+
+double orc_glm_ch(const orc_t *o) { return o->glm_ch; }
+double orc_glm_dmin(const orc_t *o) { return o->glm_dmin; }
 
 /* residual L(U) at the current state and time (ghosts filled at tau), interior [8][n3][n2][n1] */
 void orc_residual(orc_t *o, double tau, double dt, double *Lout)

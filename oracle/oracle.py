@@ -45,6 +45,10 @@ def lib():
             "orc_volumes": (None, [P, P]),
             "orc_centres": (None, [P, I, P]),
             "orc_edges": (None, [P, I, P]),
+            "orc_set_psi": (None, [P, P]),
+            "orc_get_psi": (None, [P, P]),
+            "orc_glm_ch": (D, [P]),
+            "orc_glm_dmin": (D, [P]),
             "orc_boundary_values": (None, [P, D, P, P]),
             "orc_floor_hits": (L, [P]),
             "orc_time": (D, [P]),
@@ -81,7 +85,7 @@ class Oracle:
                       dtype=np.int32)
         dg = np.array([grid.x1min, grid.x1max, grid.x2min, grid.x2max, grid.x3min, grid.x3max,
                        grid.band_lo, grid.band_hi])
-        od = np.array([opts.cfl, opts.divb_coef, opts.rho_floor, opts.p_floor])
+        od = np.array([opts.cfl, opts.divb_coef, opts.rho_floor, opts.p_floor, opts.glm_alpha])
         oi = np.array([opts.limiter, opts.flux, opts.gravity, opts.divb, opts.init_vphi, opts.cme_model,
                        opts.tracer], dtype=np.int32)
         self.h = lib().orc_create(_ptr(ig), _ptr(dg), gamma, omega, _ptr(od), _ptr(oi))
@@ -162,6 +166,23 @@ class Oracle:
         out = np.empty(n + 1)
         lib().orc_edges(self.h, d, _ptr(out))
         return out
+
+    def set_psi(self, p):
+        """GLM psi of the interior cells [n3][n2][n1]."""
+        a = _c(p)
+        assert a.shape == self.shape[1:]
+        lib().orc_set_psi(self.h, _ptr(a))
+
+    def get_psi(self) -> np.ndarray:
+        out = np.empty(self.shape[1:])
+        lib().orc_get_psi(self.h, _ptr(out))
+        return out
+
+    def glm_ch(self) -> float:
+        return lib().orc_glm_ch(self.h)
+
+    def glm_dmin(self) -> float:
+        return lib().orc_glm_dmin(self.h)
 
     def boundary_values(self, tau):
         g = self.grid

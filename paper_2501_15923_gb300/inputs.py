@@ -44,7 +44,7 @@ BC_PERIODIC, BC_CONT, BC_REFLECT, BC_DRIVEN, BC_FIXED = 0, 1, 2, 3, 4
 GEOM_SPHERICAL, GEOM_CARTESIAN = 0, 1
 LIM_MINMOD, LIM_VANLEER, LIM_MC = 0, 1, 2
 FLUX_TVDLF, FLUX_HLL, FLUX_HLLD = 0, 1, 2
-DIVB_NONE, DIVB_LINDE = 0, 1
+DIVB_NONE, DIVB_LINDE, DIVB_GLM = 0, 1, 2
 IC_COROTATING, IC_INERTIAL_RADIAL = 0, 1     # initial v_phi: at rest co-rotating / radial inertial flow
 CME_WINDOW, CME_SPHERE = 0, 1                # cone footprint over a fixed window / spherical cloud crossing
 
@@ -120,6 +120,7 @@ class Options:
     init_vphi: int = IC_COROTATING        # initial v_phi: IC_COROTATING (0) or IC_INERTIAL_RADIAL
     cme_model: int = CME_WINDOW           # CME_WINDOW (0) or CME_SPHERE (1)
     tracer: int = 0                       # 1: carry the CME tracer c (passive, rho c conserved)
+    glm_alpha: float = 0.1                # GLM (divb = DIVB_GLM): psi damped by exp(-alpha c_h dt / dmin)
 
 
 @dataclass

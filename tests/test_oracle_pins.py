@@ -971,3 +971,74 @@ def test_P11_band_uniform_rest_preserved():
     U, _ = o.get_state()
     assert np.max(np.abs(U[0] - 2.0)) < 1e-13 * 2.0
     assert np.max(np.abs(U[1:4])) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------------
+# P12: GLM div-B control. Along x in a periodic box with everything uniform but B_x, the pair
+# (B_x, psi) obeys B_x,t + psi_x = 0, psi_t + c_h^2 B_x,x = 0 exactly (the normal-field flux is
+# psi* alone, and v_x B_x - B_x v_x = 0), whatever the plasma does: a standing wave
+# B_x = B0 + eps sin(kx) cos(k c_h t), psi = -eps c_h cos(kx) sin(k c_h t). With dt fixed by the
+# cap, c_h = CFL dmin / dt is constant.
+def glm_box(n1, alpha=0.0):
+    g = cart_grid(n1, 4, 4, L=(1.0, 1.0, 1.0))
+    return g, Oracle(g, 1.5, 0.0, opts(divb=I.DIVB_GLM, glm_alpha=alpha, gravity=0))
+
+
+def glm_wave_errors(n1, eps=1e-4, t_end=0.25):
+    g, o = glm_box(n1)
+    x = (np.arange(n1) + 0.5) / n1
+    W = np.zeros((8, 4, 4, n1))
+    W[0], W[4] = 1.0, 1.0
+    W[5] = 0.5 + eps * np.sin(2 * np.pi * x)
+    W[6] = 0.3
+    o.set_state(cons_from_prim(W, 1.5))
+    dt = 0.25 / n1                                   # below the MHD CFL step at these sizes
+    n = int(round(t_end / dt))
+    for _ in range(n):
+        assert o.step(dt) == dt
+    ch = o.glm_ch()
+    assert abs(ch - 0.8 * (1.0 / n1) / dt) <= 1e-12 * ch
+    U, _ = o.get_state()
+    ph = 2 * np.pi * ch * n * dt
+    bx = 0.5 + eps * np.sin(2 * np.pi * x) * np.cos(ph)
+    ps = -eps * ch * np.cos(2 * np.pi * x) * np.sin(ph)
+    return np.abs(U[5] - bx).max() / eps, np.abs(o.get_psi() - ps).max() / (eps * ch)
+
+
+def test_P12_glm_standing_wave_second_order():
+    e32, p32 = glm_wave_errors(32)
+    e64, p64 = glm_wave_errors(64)
+    assert e64 < 0.05 and p64 < 0.05, (e64, p64)
+    assert np.log2(e32 / e64) > 1.7 and np.log2(p32 / p64) > 1.7, (e32, e64, p32, p64)
+
+
+def test_P12_glm_damping_exact():
+    """A uniform psi carries no flux divergence; the damping multiplies it by
+    exp(-alpha c_h dt / dmin) = exp(-alpha CFL) per step, and B stays as it is."""
+    g, o = glm_box(16, alpha=0.5)
+    W = np.zeros((8, 4, 4, 16))
+    W[0], W[4], W[5], W[6] = 1.0, 1.0, 0.4, -0.2
+    U0 = cons_from_prim(W, 1.5)
+    o.set_state(U0)
+    o.set_psi(np.full((4, 4, 16), 0.1))
+    for _ in range(5):
+        o.step()
+    np.testing.assert_allclose(o.get_psi(), 0.1 * np.exp(-0.5 * 0.8 * 5), rtol=1e-12)
+    U, _ = o.get_state()
+    assert np.abs(U[5:8] - U0[5:8]).max() < 1e-14
+
+
+def test_P12_glm_uniform_psi_balanced_on_the_sphere():
+    """Spherical shell at rest, B = 0, uniform psi: the flux form of grad psi and its face-area
+    terms cancel, so no field appears (a missing or mis-signed geometric term gives B_r ~ 2 psi
+    dt / r)."""
+    g = sph_grid(24, 8, 12, bc=(R, R, R, R, P, P))
+    o = Oracle(g, 1.5, 0.0, opts(gravity=0, divb=I.DIVB_GLM, glm_alpha=0.0))
+    W = np.zeros((8, g.n3, g.n2, g.n1))
+    W[0], W[4] = 2.0, 3.0
+    o.set_state(cons_from_prim(W, 1.5))
+    o.set_psi(np.full((g.n3, g.n2, g.n1), 0.3))
+    o.step()
+    U, _ = o.get_state()
+    assert np.abs(U[5:8]).max() < 1e-12
+    np.testing.assert_allclose(o.get_psi(), 0.3, rtol=1e-12)
