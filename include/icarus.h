@@ -58,7 +58,10 @@ enum { ICARUS_LIM_MINMOD = 0, ICARUS_LIM_VANLEER = 1, ICARUS_LIM_MC = 2 };
 /* face fluxes: TVDLF (Rusanov), HLL, HLLD (Miyoshi & Kusano 2005; not in the fused stage or the
  * batched form) */
 enum { ICARUS_FLUX_TVDLF = 0, ICARUS_FLUX_HLL = 1, ICARUS_FLUX_HLLD = 2 };
-enum { ICARUS_DIVB_NONE = 0, ICARUS_DIVB_LINDE = 1 };
+/* GLM (Dedner et al. 2002; a scheme variant, the paper names no div-B method): a scalar psi whose
+ * upwind (B_n, psi) face state replaces the normal-field flux, carried with flux c_h^2 B_n*,
+ * c_h = CFL dmin / dt, damped by exp(-glm_alpha c_h dt / dmin) per step; FP64 form only. */
+enum { ICARUS_DIVB_NONE = 0, ICARUS_DIVB_LINDE = 1, ICARUS_DIVB_GLM = 2 };
 /* FP64: everything in double. FP32: state and arithmetic in float. MIXED: state, update
  * accumulation and the dt reduction in double; primitives, reconstruction, fluxes and sources in
  * float, except the primitive (pressure / positivity) recovery of the first four radial cells,
@@ -115,6 +118,7 @@ typedef struct {
                               the driven face inside the CME footprint and 0 outside, rho c clipped
                               to [0, rho] after each stage; starts at c = 0 (icarus_set_tracer).
                               Not with the fused stage kernel or the batched form. */
+    double glm_alpha;      /* divb = ICARUS_DIVB_GLM: psi damping constant (>= 0; 0.1 is usual) */
 } icarus_options;
 
 #define ICARUS_IC_COROTATING 0
@@ -177,6 +181,12 @@ int icarus_set_state(icarus_ctx *ctx, const double *U, double t);
  * (so c changes with rho). */
 int icarus_set_tracer(icarus_ctx *ctx, const double *c);
 int icarus_get_tracer(icarus_ctx *ctx, double *c);
+
+/* GLM div-B control (divb = ICARUS_DIVB_GLM): psi of the interior cells as HOST doubles
+ * [n3][n2][n1] (code units of B times speed), set or read. Synchronous. EINVAL without GLM.
+ * psi starts at 0 and is kept by icarus_set_state. */
+int icarus_set_psi(icarus_ctx *ctx, const double *psi);
+int icarus_get_psi(icarus_ctx *ctx, double *psi);
 
 /* Copy the interior state into a DEVICE buffer U_dev [8][n3][n2][n1] (double, code units).
  * Synchronous. */

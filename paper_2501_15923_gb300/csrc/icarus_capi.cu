@@ -215,6 +215,20 @@ int build_metrics(icarus_ctx *c)
     MetricsT<float> &mf = c->P.mf;
     bind(mf, (const float *)mfb);
     mf.d2 = (float)m.d2; mf.d3 = (float)m.d3; mf.id2 = (float)m.id2; mf.id3 = (float)m.id3; mf.iv3 = (float)m.iv3;
+    // smallest interior cell width (dr, r dtheta, r sin(theta) dphi on the sphere): the GLM c_h
+    double dmin = 1e300;
+    for (int k = NG; k < NG + g.n3; ++k)
+        for (int j = NG; j < NG + g.n2; ++j)
+            for (int i = NG; i < NG + g.n1; ++i) {
+                const double w1 = e1[i + 1] - e1[i], w2 = e2[j + 1] - e2[j], w3 = e3[k + 1] - e3[k];
+                if (sph) {
+                    const double rc = ctr(e1, i);
+                    dmin = fmin(dmin, fmin(w1, fmin(rc * w2, rc * sin(ctr(e2, j)) * w3)));
+                } else {
+                    dmin = fmin(dmin, fmin(w1, fmin(w2, w3)));
+                }
+            }
+    c->P.glm_dmin = dmin;
     return ICARUS_OK;
 }
 
@@ -231,19 +245,26 @@ void enqueue_step(icarus_ctx *c)
         return;
     }
     // stage 1: U, W at t  ->  U1, W1 (tracer: rho c in T, c in C  ->  T1, C1, with the stage's mass fluxes)
-    const bool tr = c->opts.tracer != 0;
+    // (GLM: psi in Psi -> Psi1 -> Psi, its (B_n, psi) face states after the MHD fluxes)
+    const bool tr = c->opts.tracer != 0, glm = P.divb == ICARUS_DIVB_GLM;
     c->ops.fill_ghosts(P, c->U, c->W, 1, s);
     if (tr) c->ops.tracer_ghost(P, c->C, 1, s);
+    if (glm) c->ops.glm_ghost(P, c->Psi, s);
     c->ops.fluxes(P, c->W, c->F1, c->F2, c->F3, s);
+    if (glm) c->ops.glm_faces(P, c->W, c->Psi, c->F1, c->F2, c->F3, c->FP1, c->FP2, c->FP3, s);
     if (P.divb == 1) c->ops.divb(P, c->W, c->divB, s);
     c->ops.update(P, 1, c->U, c->W, c->U1, c->W1, c->F1, c->F2, c->F3, c->divB, s);
+    if (glm) c->ops.glm_update(P, 1, c->Psi, c->Psi1, c->FP1, c->FP2, c->FP3, s);
     if (tr) c->ops.tracer_update(P, 1, c->C, c->F1, c->F2, c->F3, c->T, c->T1, c->U1, c->C1, s);
     // stage 2: U1, W1 at t + dt  ->  U, W (in place), next dt, t += dt
     c->ops.fill_ghosts(P, c->U1, c->W1, 2, s);
     if (tr) c->ops.tracer_ghost(P, c->C1, 2, s);
+    if (glm) c->ops.glm_ghost(P, c->Psi1, s);
     c->ops.fluxes(P, c->W1, c->F1, c->F2, c->F3, s);
+    if (glm) c->ops.glm_faces(P, c->W1, c->Psi1, c->F1, c->F2, c->F3, c->FP1, c->FP2, c->FP3, s);
     if (P.divb == 1) c->ops.divb(P, c->W1, c->divB, s);
     c->ops.update(P, 2, c->U1, c->W1, c->U, c->W, c->F1, c->F2, c->F3, c->divB, s);
+    if (glm) c->ops.glm_update(P, 2, c->Psi1, c->Psi, c->FP1, c->FP2, c->FP3, s);
     if (tr) c->ops.tracer_update(P, 2, c->C1, c->F1, c->F2, c->F3, c->T1, c->T, c->U, c->C, s);
     if (P.n_probes > 0) c->ops.probe(P, c->W, s);
 }
@@ -251,7 +272,8 @@ void enqueue_step(icarus_ctx *c)
 int count_launches(const icarus_ctx *c)
 {
     int per_stage = (c->ops.fused_stage && c->opts.fused) ? 3 + 1
-                  : 3 + 3 + (c->P.divb == 1 ? 1 : 0) + 1 + (c->opts.tracer ? 2 : 0);
+                  : 3 + 3 + (c->P.divb == 1 ? 1 : 0) + 1 + (c->opts.tracer ? 2 : 0) +
+                        (c->P.divb == ICARUS_DIVB_GLM ? 5 : 0);
     return 2 * per_stage + (c->P.n_probes > 0 ? 1 : 0);
 }
 
@@ -321,7 +343,7 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     if (rc) return rc;
     if (!(gamma > 1.0)) return fail(ICARUS_EINVAL, "gamma must be > 1");
     if (!(opts->cfl > 0.0 && opts->cfl <= 1.0)) return fail(ICARUS_EINVAL, "cfl must be in (0, 1]");
-    if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 2 || opts->divb < 0 || opts->divb > 1 ||
+    if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 2 || opts->divb < 0 || opts->divb > 2 ||
         opts->init_vphi < 0 || opts->init_vphi > 1 || opts->cme_model < 0 || opts->cme_model > 1 ||
         opts->tracer < 0 || opts->tracer > 1)
         return fail(ICARUS_EINVAL, "bad limiter / flux / divb / init_vphi / cme_model / tracer option");
@@ -329,6 +351,9 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     if (opts->fused && opts->flux == ICARUS_FLUX_HLLD)
         return fail(ICARUS_EINVAL, "the fused stage kernel supports the TVDLF and HLL fluxes only");
     if (opts->fused && opts->tracer) return fail(ICARUS_EINVAL, "the fused stage kernel carries no CME tracer");
+    if (opts->divb == ICARUS_DIVB_GLM && (opts->precision != ICARUS_FP64 || opts->fused))
+        return fail(ICARUS_EINVAL, "GLM div-B control is built for the FP64 form with separate kernels");
+    if (opts->divb == ICARUS_DIVB_GLM && !(opts->glm_alpha >= 0.0)) return fail(ICARUS_EINVAL, "glm_alpha must be >= 0");
     if (opts->ring_capacity < 1) return fail(ICARUS_EINVAL, "ring_capacity must be >= 1");
     icarus_ctx *c = new icarus_ctx();
     c->grid = *grid;
@@ -354,6 +379,7 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     P.r_in = grid->x1min;
     P.gamma = gamma;
     P.divb_coef = opts->divb_coef; P.rho_floor = opts->rho_floor; P.p_floor = opts->p_floor;
+    P.glm_alpha = opts->glm_alpha;
     c->t0 = AU / V0;
     const double rho0 = MP * N0;
     c->p0 = rho0 * V0 * V0;
@@ -385,6 +411,21 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     c->partial = (double *)dalloc(c, (size_t)nblk * sizeof(double));
     c->sc = (Scalars *)dalloc(c, sizeof(Scalars));
     c->stage_buf = (double *)dalloc(c, NV * (size_t)ncell * sizeof(double));
+    if (opts->divb == ICARUS_DIVB_GLM) {
+        c->Psi = dalloc(c, nt * ts);
+        c->Psi1 = dalloc(c, nt * ts);
+        c->FP1 = dalloc(c, (size_t)P.n3 * P.n2 * (P.n1 + 1) * tw);
+        c->FP2 = dalloc(c, (size_t)P.n3 * (P.n2 + 1) * P.n1 * tw);
+        c->FP3 = dalloc(c, (size_t)(P.n3 + 1) * P.n2 * P.n1 * tw);
+        if (!c->Psi || !c->Psi1 || !c->FP1 || !c->FP2 || !c->FP3) {
+            icarus_destroy(c);
+            return fail(ICARUS_ENOMEM, "device allocation failed");
+        }
+        CK(cudaMemsetAsync(c->Psi, 0, nt * ts, c->stream));
+        CK(cudaMemsetAsync(c->Psi1, 0, nt * ts, c->stream));
+        P.psi0 = (const double *)c->Psi;
+        P.psi1 = (const double *)c->Psi1;
+    }
     if (opts->tracer) {
         c->T = dalloc(c, nt * ts);
         c->T1 = dalloc(c, nt * ts);
@@ -631,6 +672,31 @@ int icarus_set_state(icarus_ctx *c, const double *U, double t)
         return ICARUS_OK;   // dt is computed once the maps arrive
     }
     return first_dt(c);
+}
+
+int icarus_set_psi(icarus_ctx *c, const double *p)
+{
+    if (!c || !p) return fail(ICARUS_EINVAL, "NULL argument");
+    if (c->P.divb != ICARUS_DIVB_GLM) return fail(ICARUS_EINVAL, "the context carries no GLM psi (divb != GLM)");
+    const size_t n = (size_t)c->P.n1 * c->P.n2 * c->P.n3;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(c->stage_buf, p, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    c->ops.psi_copy(c->P, c->Psi, c->stage_buf, 1, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return ICARUS_OK;
+}
+
+int icarus_get_psi(icarus_ctx *c, double *p)
+{
+    if (!c || !p) return fail(ICARUS_EINVAL, "NULL argument");
+    if (c->P.divb != ICARUS_DIVB_GLM) return fail(ICARUS_EINVAL, "the context carries no GLM psi (divb != GLM)");
+    const size_t n = (size_t)c->P.n1 * c->P.n2 * c->P.n3;
+    c->ops.psi_copy(c->P, c->Psi, c->stage_buf, 0, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(p, c->stage_buf, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ICARUS_OK;
 }
 
 int icarus_set_tracer(icarus_ctx *c, const double *cin)

@@ -691,8 +691,9 @@ __device__ __forceinline__ void update_core(const Params &P, int i, int j, int k
     }
 }
 
-// the update of cell number tid (r fastest) with fluxes and div B read from their global arrays
-template <int STAGE, typename TS, typename TW>
+// the update of cell number tid (r fastest) with fluxes and div B read from their global arrays;
+// GLM: the flux form of grad psi leaves psi (A+ - A-) / V in the B_r and B_theta residuals
+template <int STAGE, typename TS, typename TW, bool GLM = false>
 __device__ __forceinline__ void update_cell(const Params &P, const TS *__restrict__ Us, const TW *__restrict__ Ws,
                                             TS *Uo, TW *__restrict__ Wo, const TW *__restrict__ F1,
                                             const TW *__restrict__ F2, const TW *__restrict__ F3,
@@ -720,10 +721,18 @@ __device__ __forceinline__ void update_cell(const Params &P, const TS *__restric
         dbn[2] = divB[c - q2]; dbn[3] = divB[c + q2];
         dbn[4] = divB[c - q3]; dbn[5] = divB[c + q3];
     }
+    if constexpr (GLM) {
+        if (P.geom == 0) {
+            const MetricsT<TW> &m = met<TW>(P);
+            const TW psic = (TW)(STAGE == 1 ? P.psi0 : P.psi1)[c];
+            L[B1] += psic * m.gp1[i + NG];
+            L[B2] += psic * (m.q1[i + NG] * m.gq2[j + NG]);
+        }
+    }
     update_core<STAGE, TS, TW>(P, i, j, k, w, L, dbn, Us, Uo, Wo, wo);
 }
 
-template <int STAGE, typename TS, typename TW>
+template <int STAGE, typename TS, typename TW, bool GLM = false>
 __device__ __forceinline__ void update_kernel_body(Params &P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo,
                                                    TW *__restrict__ Wo, const TW *__restrict__ F1,
                                                    const TW *__restrict__ F2, const TW *__restrict__ F3,
@@ -732,20 +741,20 @@ __device__ __forceinline__ void update_kernel_body(Params &P, const TS *__restri
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = tid < (long long)P.n1 * P.n2 * P.n3;
     TW wo[NV];
-    if (valid) update_cell<STAGE, TS, TW>(P, Us, Ws, Uo, Wo, F1, F2, F3, divB, tid, wo);
+    if (valid) update_cell<STAGE, TS, TW, GLM>(P, Us, Ws, Uo, Wo, F1, F2, F3, divB, tid, wo);
     if (STAGE == 2) {
         const int i = valid ? (int)(tid % P.n1) : 0, j = valid ? (int)((tid / P.n1) % P.n2) : 0;
         finish_dt(P, cfl_block_speed<TW>(P, wo, i + NG, j + NG, valid), 1);
     }
 }
 
-template <int STAGE, typename TS, typename TW>
+template <int STAGE, typename TS, typename TW, bool GLM = false>
 __global__ void __launch_bounds__(256)
 k_update(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo, TW *__restrict__ Wo,
          const TW *__restrict__ F1, const TW *__restrict__ F2, const TW *__restrict__ F3,
          const TW *__restrict__ divB)
 {
-    update_kernel_body<STAGE, TS, TW>(P, Us, Ws, Uo, Wo, F1, F2, F3, divB);
+    update_kernel_body<STAGE, TS, TW, GLM>(P, Us, Ws, Uo, Wo, F1, F2, F3, divB);
 }
 
 // the same update with at most 48 registers (5 blocks of 256 per SM): measured faster for the
@@ -840,6 +849,121 @@ k_update_pair(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS
         if (valid) sp = fmaxf(cell_speed_t<TW>(P, wo[0], i + NG, j + NG), cell_speed_t<TW>(P, wo[1], i + 1 + NG, j + NG));
         finish_dt(P, (double)block_max_all(sp), 1);
     }
+}
+
+// ---------------------------------------------------------------------------------------------
+// GLM div-B control (Dedner et al. 2002), FP64 form. Along each face normal the pair (B_n, psi)
+// obeys B_n,t + psi_n = 0, psi_t + c_h^2 B_n,n = 0; its exact upwind face state from the limited
+// reconstructions (first order where the primitives fall back to it) gives B_n* and psi*: psi*
+// replaces the normal-field flux of the MHD face flux, and psi is carried with flux c_h^2 B_n*.
+// c_h = CFL dmin / dt (the fastest speed the step's dt carries over the smallest cell); after the
+// second stage psi is damped by exp(-alpha c_h dt / dmin) = exp(-alpha CFL).
+// Ghost values of psi along each direction at interior indices of the other two: copied like the
+// MHD state, the driven face included (zero gradient).
+template <typename TS>
+__global__ void k_psi_ghost(Params P, TS *__restrict__ Psi)
+{
+    const long long nr = 2LL * NG * P.n2 * P.n3, nth = 2LL * NG * P.n1 * P.n3, nph = 2LL * NG * P.n1 * P.n2;
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nr + nth + nph) return;
+    int D = 0;
+    if (q >= nr) { q -= nr; D = 1; if (q >= nth) { q -= nth; D = 2; } }
+    const int g = (int)(q % NG) + 1;
+    long long r = q / NG;
+    const int side = (int)(r % 2);
+    r /= 2;
+    const int n = D == 0 ? P.n1 : (D == 1 ? P.n2 : P.n3);
+    const int na = D == 0 ? P.n2 : P.n1;
+    const int a = (int)(r % na), b = (int)(r / na);
+    const int gi = side == 0 ? -g : n - 1 + g;
+    const int bc = P.bc[2 * D + side];
+    auto at = [&](int s) -> long long {
+        return D == 0 ? cidx(P, s, a, b) : (D == 1 ? cidx(P, a, s, b) : cidx(P, a, b, s));
+    };
+    // continuation and driven (1, 3), mirror (2), periodic (0)
+    const int src = (bc == 1 || bc == 3) ? (side == 0 ? 0 : n - 1)
+                  : (bc == 2 ? (side == 0 ? g - 1 : n - g) : ((gi % n) + n) % n);
+    Psi[at(gi)] = Psi[at(src)];
+}
+
+// the faces along D (the lower face of cell (i, j, k), faces 0 .. n_D): B_n* and psi*; psi*
+// overwrites the normal-field component of F, FP gets c_h^2 B_n*
+template <int D, typename TS, typename TW>
+__global__ void k_glm_faces(Params P, const TW *__restrict__ W, const TS *__restrict__ Psi, TW *F, TW *FP)
+{
+    const int e1 = P.n1 + (D == 0), e2 = P.n2 + (D == 1), e3 = P.n3 + (D == 2);
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)e1 * e2 * e3) return;
+    const int i = (int)(tid % e1);
+    const long long r_ = tid / e1;
+    const int j = (int)(r_ % e2), k = (int)(r_ / e2);
+    const long long nt = P.nt, c = cidx(P, i, j, k);
+    const long long st = D == 0 ? 1 : (D == 1 ? (long long)P.p1 : (long long)P.p1 * P.p2);
+    // limited linear face states of field v (left from cells c-2, c-1, c; right from c-1, c, c+1)
+    auto recon = [&](const auto *a, TW &l, TW &r) {
+        const TW m2 = (TW)a[c - 2 * st], m1 = (TW)a[c - st], z = (TW)a[c], p1 = (TW)a[c + st];
+        l = m1 + TW(0.5) * limiter<TW>(P.limiter, m1 - m2, z - m1);
+        r = z - TW(0.5) * limiter<TW>(P.limiter, z - m1, p1 - z);
+    };
+    TW rl, rr, pl_, pr_, bl, br, sl, sr;
+    recon(W, rl, rr);
+    recon(W + 4 * nt, pl_, pr_);
+    recon(W + (5 + D) * nt, bl, br);
+    recon(Psi, sl, sr);
+    if (!(rl > TW(0)) || !(rr > TW(0)) || !(pl_ > TW(0)) || !(pr_ > TW(0))) {   // first order
+        bl = W[(5 + D) * nt + c - st]; br = W[(5 + D) * nt + c];
+        sl = (TW)Psi[c - st]; sr = (TW)Psi[c];
+    }
+    const double dt = P.sc->dt;                 // 0 only for steps past a stop time (no change then)
+    const TW ch = dt > 0.0 ? (TW)(P.sc->cfl * P.glm_dmin / dt) : TW(0);
+    const TW bs = dt > 0.0 ? TW(0.5) * (bl + br) - TW(0.5) * (sr - sl) / ch : TW(0.5) * (bl + br);
+    const TW ps = TW(0.5) * (sl + sr) - TW(0.5) * ch * (br - bl);
+    long long fi, fs;
+    if (D == 0) { fi = ((long long)k * P.n2 + j) * (P.n1 + 1) + i; fs = (long long)P.n3 * P.n2 * (P.n1 + 1); }
+    else if (D == 1) { fi = ((long long)k * (P.n2 + 1) + j) * P.n1 + i; fs = (long long)P.n3 * (P.n2 + 1) * P.n1; }
+    else { fi = ((long long)k * P.n2 + j) * P.n1 + i; fs = (long long)(P.n3 + 1) * P.n2 * P.n1; }
+    F[(5 + D) * fs + fi] = ps;
+    FP[fi] = ch * ch * bs;
+}
+
+// psi of every interior cell: stage 1 Psi1 = Psi + dt L; stage 2 Psi = (Psi/2 + (Psi1 + dt L)/2)
+// damped (the second stage runs after the MHD update has advanced t and dt: the step's dt is
+// dt_step)
+template <int STAGE, typename TS, typename TW>
+__global__ void k_glm_update(Params P, const TS *__restrict__ Ps, TS *Po, const TW *__restrict__ FP1,
+                             const TW *__restrict__ FP2, const TW *__restrict__ FP3)
+{
+    const unsigned int tid = blockIdx.x * blockDim.x + threadIdx.x;   // cells < 2^31
+    if (tid >= (unsigned int)(P.n1 * P.n2 * P.n3)) return;
+    const unsigned int r_ = tid / (unsigned int)P.n1;
+    const int i = (int)(tid - r_ * (unsigned int)P.n1), j = (int)(r_ % (unsigned int)P.n2),
+              k = (int)(r_ / (unsigned int)P.n2);
+    const long long c = cidx(P, i, j, k);
+    const long long f1 = ((long long)k * P.n2 + j) * (P.n1 + 1) + i;
+    const long long f2 = ((long long)k * (P.n2 + 1) + j) * P.n1 + i;
+    const long long f3 = ((long long)k * P.n2 + j) * P.n1 + i;
+    const DivFactors<TW> dv(met<TW>(P), i + NG, j + NG);
+    const TW L = dv.div(FP1[f1], FP1[f1 + 1], FP2[f2], FP2[f2 + P.n1], FP3[f3], FP3[f3 + (long long)P.n2 * P.n1]);
+    const double dt = STAGE == 1 ? P.sc->dt : P.sc->dt_step;
+    if (STAGE == 1) Po[c] = Ps[c] + (TS)dt * (TS)L;
+    else {
+        const TS damp = dt > 0.0 ? (TS)exp(-P.glm_alpha * P.sc->cfl) : TS(1);
+        Po[c] = (TS(0.5) * Po[c] + TS(0.5) * (Ps[c] + (TS)dt * (TS)L)) * damp;
+    }
+}
+
+// psi of the interior from / to host-layout doubles [n3][n2][n1] (staged on the device)
+template <typename TS>
+__global__ void k_psi_copy(Params P, TS *Psi, double *buf, int to_psi)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)P.n1 * P.n2 * P.n3) return;
+    const int i = (int)(tid % P.n1);
+    const long long r_ = tid / P.n1;
+    const int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
+    const long long c = cidx(P, i, j, k);
+    if (to_psi) Psi[c] = (TS)buf[tid];
+    else buf[tid] = (double)Psi[c];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1219,6 +1343,15 @@ template <typename TS, typename TW> struct Launch {
                     (TW *)Wo, (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
             return;
         }
+        if constexpr (sizeof(TS) == 8 && sizeof(TW) == 8) if (P.divb == 2) {   // GLM: FP64 form only
+            if (stage == 1)
+                k_update<1, TS, TW, true><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo,
+                    (TW *)Wo, (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
+            else
+                k_update<2, TS, TW, true><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo,
+                    (TW *)Wo, (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
+            return;
+        }
         if (stage == 1)
             k_update<1, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo, (TW *)Wo,
                 (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
@@ -1256,6 +1389,36 @@ template <typename TS, typename TW> struct Launch {
     {
         long long n = (long long)P.n1 * P.n2 * P.n3 * NV;
         k_unpack<TS><<<cdiv(n, 256), 256, 0, s>>>(P, (TS *)U, in);
+    }
+    static void glm_ghost(const Params &P, void *Psi, cudaStream_t s)
+    {
+        const long long n = 2LL * NG * ((long long)P.n2 * P.n3 + (long long)P.n1 * P.n3 + (long long)P.n1 * P.n2);
+        k_psi_ghost<TS><<<cdiv(n, 256), 256, 0, s>>>(P, (TS *)Psi);
+    }
+    static void glm_faces(const Params &P, const void *W, const void *Psi, void *F1, void *F2, void *F3, void *FP1,
+                          void *FP2, void *FP3, cudaStream_t s)
+    {
+        const long long n0 = (long long)(P.n1 + 1) * P.n2 * P.n3, n1 = (long long)P.n1 * (P.n2 + 1) * P.n3,
+                        n2 = (long long)P.n1 * P.n2 * (P.n3 + 1);
+        k_glm_faces<0, TS, TW><<<cdiv(n0, 256), 256, 0, s>>>(P, (const TW *)W, (const TS *)Psi, (TW *)F1, (TW *)FP1);
+        k_glm_faces<1, TS, TW><<<cdiv(n1, 256), 256, 0, s>>>(P, (const TW *)W, (const TS *)Psi, (TW *)F2, (TW *)FP2);
+        k_glm_faces<2, TS, TW><<<cdiv(n2, 256), 256, 0, s>>>(P, (const TW *)W, (const TS *)Psi, (TW *)F3, (TW *)FP3);
+    }
+    static void glm_update(const Params &P, int stage, const void *Ps, void *Po, const void *FP1, const void *FP2,
+                           const void *FP3, cudaStream_t s)
+    {
+        const long long n = (long long)P.n1 * P.n2 * P.n3;
+        if (stage == 1)
+            k_glm_update<1, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Ps, (TS *)Po, (const TW *)FP1,
+                (const TW *)FP2, (const TW *)FP3);
+        else
+            k_glm_update<2, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Ps, (TS *)Po, (const TW *)FP1,
+                (const TW *)FP2, (const TW *)FP3);
+    }
+    static void psi_copy(const Params &P, void *Psi, double *buf, int to_psi, cudaStream_t s)
+    {
+        const long long n = (long long)P.n1 * P.n2 * P.n3;
+        k_psi_copy<TS><<<cdiv(n, 256), 256, 0, s>>>(P, (TS *)Psi, buf, to_psi);
     }
     static void tracer_ghost(const Params &P, void *C, int stage, cudaStream_t s)
     {
@@ -1299,6 +1462,10 @@ template <typename TS, typename TW> struct Launch {
         o.unpack = unpack;
         o.fused_stage = nullptr;
         o.fused_blocks = nullptr;
+        o.glm_ghost = glm_ghost;
+        o.glm_faces = glm_faces;
+        o.glm_update = glm_update;
+        o.psi_copy = psi_copy;
         o.tracer_ghost = tracer_ghost;
         o.tracer_update = tracer_update;
         o.tracer_set = tracer_set;

@@ -21,6 +21,14 @@ struct Ops {
     // one whole stage (fluxes, div B, update) in a single kernel; null where not available
     void (*fused_stage)(const Params &, int stage, const void *Us, const void *Ws, void *Uo, void *Wo, cudaStream_t);
     unsigned int (*fused_blocks)(const Params &);
+    // GLM div-B control: psi ghosts; the (B_n, psi) face states of the three directions (after the
+    // MHD fluxes); the psi stage update (after the MHD update); psi from / to host-layout doubles
+    void (*glm_ghost)(const Params &, void *Psi, cudaStream_t);
+    void (*glm_faces)(const Params &, const void *W, const void *Psi, void *F1, void *F2, void *F3, void *FP1, void *FP2,
+                      void *FP3, cudaStream_t);
+    void (*glm_update)(const Params &, int stage, const void *Ps, void *Po, const void *FP1, const void *FP2,
+                       const void *FP3, cudaStream_t);
+    void (*psi_copy)(const Params &, void *Psi, double *buf, int to_psi, cudaStream_t);
     // CME tracer: ghost values of c at the stage time; the stage update of rho c (after update);
     // c of the interior from / to host-layout doubles [n3][n2][n1] (staged on the device)
     void (*tracer_ghost)(const Params &, void *C, int stage, cudaStream_t);

@@ -46,7 +46,7 @@ class icarus_options(C.Structure):
                 ("p_floor", C.c_double), ("precision", C.c_int), ("ring_capacity", C.c_int),
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
                 ("fused", C.c_int), ("init_vphi", C.c_int), ("cme_model", C.c_int),
-                ("tracer", C.c_int)]
+                ("tracer", C.c_int), ("glm_alpha", C.c_double)]
 
 
 _lib = None
@@ -63,6 +63,8 @@ SIGNATURES = {
     "icarus_set_stop_time": (C.c_int, [C.c_void_p, C.c_double]),
     "icarus_copy_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "icarus_set_tracer": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "icarus_set_psi": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "icarus_get_psi": (C.c_int, [C.c_void_p, C.c_void_p]),
     "icarus_get_tracer": (C.c_int, [C.c_void_p, C.c_void_p]),
     "icarus_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "icarus_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
@@ -155,6 +157,7 @@ def make_options(o: I.Options, precision=ICARUS_FP64, ring=4096, stream=None, al
     opt.init_vphi = int(o.init_vphi)
     opt.cme_model = int(o.cme_model)
     opt.tracer = int(o.tracer)
+    opt.glm_alpha = float(o.glm_alpha)
     opt.cfl, opt.limiter, opt.flux, opt.gravity, opt.divb = o.cfl, o.limiter, o.flux, o.gravity, o.divb
     opt.divb_coef, opt.rho_floor, opt.p_floor = o.divb_coef, o.rho_floor, o.p_floor
     opt.precision, opt.ring_capacity = precision, ring
@@ -329,6 +332,16 @@ class Solver:
 
     def get_tracer(self):
         return icarus_get_tracer(self.ctx, self.shape[1:])
+
+    def set_psi(self, p):
+        """GLM psi of the interior cells [n3][n2][n1] (divb = DIVB_GLM)."""
+        p = _f64(p)
+        _check(load().icarus_set_psi(self.ctx, _ptr(p)))
+
+    def get_psi(self):
+        p = np.empty(self.shape[1:])
+        _check(load().icarus_get_psi(self.ctx, _ptr(p)))
+        return p
 
     def set_stop_time(self, t_stop):
         icarus_set_stop_time(self.ctx, t_stop)

@@ -78,10 +78,14 @@ def test_bad_boundary_codes_rejected(ic):
     (1.5, I.Options(cfl=1.5), 0, "cfl"),
     (1.5, I.Options(limiter=3), 0, "limiter"),
     (1.5, I.Options(flux=3), 0, "flux"),
-    (1.5, I.Options(divb=2), 0, "divb"),
+    (1.5, I.Options(divb=-1), 0, "divb"),
     (1.5, I.Options(init_vphi=2), 0, "init_vphi"),
     (1.5, I.Options(cme_model=2), 0, "cme_model"),
     (1.5, I.Options(tracer=2), 0, "tracer"),
+    (1.5, I.Options(divb=3), 0, "divb"),
+    (1.5, I.Options(divb=I.DIVB_GLM), 1, "GLM"),
+    (1.5, I.Options(divb=I.DIVB_GLM), 2, "GLM"),
+    (1.5, I.Options(divb=I.DIVB_GLM, glm_alpha=-1.0), 0, "glm_alpha"),
     (1.5, I.Options(), 3, "precision"),
 ])
 def test_bad_options_rejected(ic, gamma, opts, precision, msg):
