@@ -28,7 +28,7 @@ def ic():
     return icarus
 
 
-def step_pair(gpu, orc, U, psi, t, dt_cap=0.0):
+def step_pair(gpu, orc, U, psi, t, dt_cap=0.0, mom_floor=0.0):
     for s in (gpu, orc):
         s.set_state(U, t)
         s.set_psi(psi)
@@ -40,6 +40,11 @@ def step_pair(gpu, orc, U, psi, t, dt_cap=0.0):
     Uo, to = orc.get_state()
     pg, po = gpu.get_psi(), orc.get_psi()
     err = field_errors(Ug, Uo)
+    if mom_floor:
+        # momenta that start at zero grow only by rounding-level amounts in a few steps: their
+        # scale is floored at rho c_s so that the relative bar stays meaningful
+        mscale = max(np.sqrt((Uo[1:4] ** 2).sum(0)).max(), mom_floor)
+        err[1:4] = np.abs(Ug[1:4] - Uo[1:4]).max() / mscale
     assert err.max() <= TOL, err
     assert abs(tg - to) <= 1e-13 * abs(to) + 1e-300
     assert np.abs(pg - po).max() <= TOL * max(np.abs(po).max(), 1e-300), np.abs(pg - po).max()
@@ -56,7 +61,7 @@ def test_glm_standing_wave(ic):
     W[5] = 0.5 + 1e-3 * np.sin(2 * np.pi * x)
     U, psi, t = cons_from_prim(W, 1.5), np.zeros((4, 4, 64)), 0.0
     for _ in range(6):
-        U, psi, t = step_pair(gpu, orc, U, psi, t, dt_cap=0.25 / 64)
+        U, psi, t = step_pair(gpu, orc, U, psi, t, dt_cap=0.25 / 64, mom_floor=np.sqrt(1.5))
     assert np.abs(psi).max() > 1e-5                 # the wave has moved field into psi
     gpu.close()
 
