@@ -55,6 +55,7 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     p.add_argument("--no-forms", action="store_true", help="skip the FP32 / mixed / batched side measurements")
     p.add_argument("--tracer", action="store_true", help="carry the CME tracer in the timed solver")
+    p.add_argument("--glm", action="store_true", help="GLM div-B control instead of Linde diffusion (FP64)")
     p.add_argument("--batch-members", type=int, default=64, help="members of the batched cone-CME ensemble")
     return p.parse_args(argv)
 
@@ -338,6 +339,8 @@ def main(argv=None):
     prec = {"f64": ic.ICARUS_FP64, "f32": ic.ICARUS_FP32, "mixed": ic.ICARUS_MIXED}[args.precision]
     w = workload(args.grid)
     w.opts.tracer = int(args.tracer)
+    if args.glm:
+        w.opts.divb = I.DIVB_GLM
     ncell = w.grid.ncell
     s = ic.from_workload(w, precision=prec)
     s.sample(w.traj, cap=1)
@@ -449,7 +452,8 @@ def main(argv=None):
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": w.name, "grid": args.grid, "cells": ncell, "precision": args.precision,
                        "l2": "inputs larger than L2 (state 8 x 8 B x padded cells per copy)",
-                       "parallelism": "replicas" if world > 1 else "single GPU", "cme_tracer": bool(args.tracer)},
+                       "parallelism": "replicas" if world > 1 else "single GPU", "cme_tracer": bool(args.tracer),
+                       "divb": "glm" if args.glm else "linde"},
             "clocks": clocks, "roofline": roof, "e2e": e2e, "floor_hits": floor_hits,
             "gpu_launches": s.launches_per_step * args.steps, "forms": forms}
     if rank == 0 and not args.no_cpu and world == 1:

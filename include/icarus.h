@@ -60,7 +60,8 @@ enum { ICARUS_LIM_MINMOD = 0, ICARUS_LIM_VANLEER = 1, ICARUS_LIM_MC = 2 };
 enum { ICARUS_FLUX_TVDLF = 0, ICARUS_FLUX_HLL = 1, ICARUS_FLUX_HLLD = 2 };
 /* GLM (Dedner et al. 2002; a scheme variant, the paper names no div-B method): a scalar psi whose
  * upwind (B_n, psi) face state replaces the normal-field flux, carried with flux c_h^2 B_n*,
- * c_h = CFL dmin / dt, damped by exp(-glm_alpha c_h dt / dmin) per step; FP64 form only. */
+ * c_h = CFL dmin / dt, damped by exp(-glm_alpha c_h dt / dmin) per step; all three precision
+ * forms (psi in the state's type), not the fused stage or the batched form. */
 enum { ICARUS_DIVB_NONE = 0, ICARUS_DIVB_LINDE = 1, ICARUS_DIVB_GLM = 2 };
 /* FP64: everything in double. FP32: state and arithmetic in float. MIXED: state, update
  * accumulation and the dt reduction in double; primitives, reconstruction, fluxes and sources in

@@ -351,8 +351,8 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     if (opts->fused && opts->flux == ICARUS_FLUX_HLLD)
         return fail(ICARUS_EINVAL, "the fused stage kernel supports the TVDLF and HLL fluxes only");
     if (opts->fused && opts->tracer) return fail(ICARUS_EINVAL, "the fused stage kernel carries no CME tracer");
-    if (opts->divb == ICARUS_DIVB_GLM && (opts->precision != ICARUS_FP64 || opts->fused))
-        return fail(ICARUS_EINVAL, "GLM div-B control is built for the FP64 form with separate kernels");
+    if (opts->divb == ICARUS_DIVB_GLM && opts->fused)
+        return fail(ICARUS_EINVAL, "GLM div-B control runs with the separate kernels, not the fused stage");
     if (opts->divb == ICARUS_DIVB_GLM && !(opts->glm_alpha >= 0.0)) return fail(ICARUS_EINVAL, "glm_alpha must be >= 0");
     if (opts->ring_capacity < 1) return fail(ICARUS_EINVAL, "ring_capacity must be >= 1");
     icarus_ctx *c = new icarus_ctx();
@@ -423,8 +423,8 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
         }
         CK(cudaMemsetAsync(c->Psi, 0, nt * ts, c->stream));
         CK(cudaMemsetAsync(c->Psi1, 0, nt * ts, c->stream));
-        P.psi0 = (const double *)c->Psi;
-        P.psi1 = (const double *)c->Psi1;
+        P.psi0 = c->Psi;
+        P.psi1 = c->Psi1;
     }
     if (opts->tracer) {
         c->T = dalloc(c, nt * ts);

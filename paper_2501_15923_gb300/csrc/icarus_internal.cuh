@@ -76,9 +76,9 @@ struct Params {
     int limiter, flux, gravity, divb, init_vphi, cme_model;
     double gamma, omega, divb_coef, rho_floor, p_floor;
     double r_in;                    // inner radius (AU; x1min of the grid)
-    // GLM div-B control (divb = 2, FP64): psi at the step start / after stage 1 (padded), the
-    // damping constant and the smallest cell width
-    const double *psi0, *psi1;
+    // GLM div-B control (divb = 2): psi at the step start / after stage 1 (padded, the state's
+    // type), the damping constant and the smallest cell width
+    const void *psi0, *psi1;
     double glm_alpha, glm_dmin;
     Metrics m;
     MetricsT<float> mf;             // float roundings of m

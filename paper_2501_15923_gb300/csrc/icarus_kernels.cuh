@@ -724,7 +724,7 @@ __device__ __forceinline__ void update_cell(const Params &P, const TS *__restric
     if constexpr (GLM) {
         if (P.geom == 0) {
             const MetricsT<TW> &m = met<TW>(P);
-            const TW psic = (TW)(STAGE == 1 ? P.psi0 : P.psi1)[c];
+            const TW psic = (TW)((const TS *)(STAGE == 1 ? P.psi0 : P.psi1))[c];
             L[B1] += psic * m.gp1[i + NG];
             L[B2] += psic * (m.q1[i + NG] * m.gq2[j + NG]);
         }
@@ -852,7 +852,7 @@ k_update_pair(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS
 }
 
 // ---------------------------------------------------------------------------------------------
-// GLM div-B control (Dedner et al. 2002), FP64 form. Along each face normal the pair (B_n, psi)
+// GLM div-B control (Dedner et al. 2002). Along each face normal the pair (B_n, psi)
 // obeys B_n,t + psi_n = 0, psi_t + c_h^2 B_n,n = 0; its exact upwind face state from the limited
 // reconstructions (first order where the primitives fall back to it) gives B_n* and psi*: psi*
 // replaces the normal-field flux of the MHD face flux, and psi is carried with flux c_h^2 B_n*.
@@ -1333,7 +1333,7 @@ template <typename TS, typename TW> struct Launch {
                        const void *F1, const void *F2, const void *F3, const void *D, cudaStream_t s)
     {
         long long n = (long long)P.n1 * P.n2 * P.n3;
-        if constexpr (sizeof(TS) == 4 && sizeof(TW) == 4) if (P.n1 % 2 == 0) {
+        if constexpr (sizeof(TS) == 4 && sizeof(TW) == 4) if (P.n1 % 2 == 0 && P.divb != 2) {
             const long long np = n / 2;
             if (stage == 1)
                 k_update_pair<1, TS, TW><<<cdiv(np, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo,
@@ -1343,7 +1343,7 @@ template <typename TS, typename TW> struct Launch {
                     (TW *)Wo, (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
             return;
         }
-        if constexpr (sizeof(TS) == 8 && sizeof(TW) == 8) if (P.divb == 2) {   // GLM: FP64 form only
+        if (P.divb == 2) {                        // GLM: the plain update with the grad-psi terms
             if (stage == 1)
                 k_update<1, TS, TW, true><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo,
                     (TW *)Wo, (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);

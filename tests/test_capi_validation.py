@@ -83,8 +83,6 @@ def test_bad_boundary_codes_rejected(ic):
     (1.5, I.Options(cme_model=2), 0, "cme_model"),
     (1.5, I.Options(tracer=2), 0, "tracer"),
     (1.5, I.Options(divb=3), 0, "divb"),
-    (1.5, I.Options(divb=I.DIVB_GLM), 1, "GLM"),
-    (1.5, I.Options(divb=I.DIVB_GLM), 2, "GLM"),
     (1.5, I.Options(divb=I.DIVB_GLM, glm_alpha=-1.0), 0, "glm_alpha"),
     (1.5, I.Options(), 3, "precision"),
 ])
@@ -99,6 +97,14 @@ def test_fused_stage_rejects_hlld(ic):
     ctx = C.c_void_p()
     rc = lib.icarus_init(C.byref(ic.make_grid(sph())), 1.5, 0.0, C.byref(o), C.byref(ctx))
     assert rc == EINVAL and "fused" in lib.icarus_last_error().decode()
+
+
+def test_fused_stage_rejects_glm(ic):
+    lib = ic.load()
+    o = ic.make_options(I.Options(divb=I.DIVB_GLM), 1, fused=True)
+    ctx = C.c_void_p()
+    rc = lib.icarus_init(C.byref(ic.make_grid(sph())), 1.5, 0.0, C.byref(o), C.byref(ctx))
+    assert rc == EINVAL and "GLM" in lib.icarus_last_error().decode()
 
 
 def test_fused_stage_rejects_tracer(ic):

@@ -1,4 +1,4 @@
-"""GLM div-B control on the GPU (divb = DIVB_GLM, FP64 form) against the oracle's GLM, one step at
+"""GLM div-B control on the GPU (divb = DIVB_GLM) against the oracle's GLM, one step at
 a time from the same state and psi: the Cartesian standing wave of the P12 pin (dt fixed by a stop
 time, so c_h is the same on both sides), a perturbed spherical state whose field has divergence,
 with a random psi, several steps, and the driven production workload inside its CME window.
@@ -77,6 +77,30 @@ def test_glm_perturbed_sphere(ic, alpha):
     U1, p1, t1 = step_pair(gpu, orc, cons_from_prim(Wp, w.gamma), psi, 0.01)
     for _ in range(3):
         U1, p1, t1 = step_pair(gpu, orc, U1, p1, t1)
+    gpu.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_glm_single_precision_forms(ic, prec):
+    """GLM in the FP32-state and MIXED forms: one step on the perturbed spherical state with psi,
+    within the single-precision bar (2e-5 of each field's and of psi's scale)."""
+    w = I.static_sheet()
+    w.opts = I.Options(divb=I.DIVB_GLM)
+    gpu, orc = ic.from_workload(w, precision=prec), oracle_workload(w)
+    U, _ = gpu.get_state()
+    Wp = I.perturbed_state(U.shape, 21, prim_from_cons(U, w.gamma), 2e-2)
+    psi = 1e-3 * (I.perturbed_state(U.shape[1:], 22, np.ones(U.shape[1:]), 1.0) - 1.0)
+    Up = cons_from_prim(Wp, w.gamma)
+    for s in (gpu, orc):
+        s.set_state(Up, 0.01)
+        s.set_psi(psi)
+    gpu.step(1)
+    orc.step()
+    Ug, _ = gpu.get_state()
+    Uo, _ = orc.get_state()
+    assert field_errors(Ug, Uo).max() <= 2e-5
+    po = orc.get_psi()
+    assert np.abs(gpu.get_psi() - po).max() <= 2e-5 * np.abs(po).max()
     gpu.close()
 
 
