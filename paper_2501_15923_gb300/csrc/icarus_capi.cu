@@ -250,8 +250,8 @@ void enqueue_step(icarus_ctx *c)
     c->ops.fill_ghosts(P, c->U, c->W, 1, s);
     if (tr) c->ops.tracer_ghost(P, c->C, 1, s);
     if (glm) c->ops.glm_ghost(P, c->Psi, s);
-    c->ops.fluxes(P, c->W, c->F1, c->F2, c->F3, s);
-    if (glm) c->ops.glm_faces(P, c->W, c->Psi, c->F1, c->F2, c->F3, c->FP1, c->FP2, c->FP3, s);
+    if (glm) c->ops.fluxes_glm(P, c->W, c->Psi, c->F1, c->F2, c->F3, c->FP1, c->FP2, c->FP3, s);
+    else c->ops.fluxes(P, c->W, c->F1, c->F2, c->F3, s);
     if (P.divb == 1) c->ops.divb(P, c->W, c->divB, s);
     c->ops.update(P, 1, c->U, c->W, c->U1, c->W1, c->F1, c->F2, c->F3, c->divB, s);
     if (glm) c->ops.glm_update(P, 1, c->Psi, c->Psi1, c->FP1, c->FP2, c->FP3, s);
@@ -260,8 +260,8 @@ void enqueue_step(icarus_ctx *c)
     c->ops.fill_ghosts(P, c->U1, c->W1, 2, s);
     if (tr) c->ops.tracer_ghost(P, c->C1, 2, s);
     if (glm) c->ops.glm_ghost(P, c->Psi1, s);
-    c->ops.fluxes(P, c->W1, c->F1, c->F2, c->F3, s);
-    if (glm) c->ops.glm_faces(P, c->W1, c->Psi1, c->F1, c->F2, c->F3, c->FP1, c->FP2, c->FP3, s);
+    if (glm) c->ops.fluxes_glm(P, c->W1, c->Psi1, c->F1, c->F2, c->F3, c->FP1, c->FP2, c->FP3, s);
+    else c->ops.fluxes(P, c->W1, c->F1, c->F2, c->F3, s);
     if (P.divb == 1) c->ops.divb(P, c->W1, c->divB, s);
     c->ops.update(P, 2, c->U1, c->W1, c->U, c->W, c->F1, c->F2, c->F3, c->divB, s);
     if (glm) c->ops.glm_update(P, 2, c->Psi1, c->Psi, c->FP1, c->FP2, c->FP3, s);
@@ -273,7 +273,7 @@ int count_launches(const icarus_ctx *c)
 {
     int per_stage = (c->ops.fused_stage && c->opts.fused) ? 3 + 1
                   : 3 + 3 + (c->P.divb == 1 ? 1 : 0) + 1 + (c->opts.tracer ? 2 : 0) +
-                        (c->P.divb == ICARUS_DIVB_GLM ? 5 : 0);
+                        (c->P.divb == ICARUS_DIVB_GLM ? 2 : 0);
     return 2 * per_stage + (c->P.n_probes > 0 ? 1 : 0);
 }
 

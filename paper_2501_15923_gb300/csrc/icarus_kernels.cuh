@@ -236,9 +236,14 @@ __global__ void k_bnd23(Params P, TS *__restrict__ U, TW *__restrict__ W)
 // A tile is BX x BY threads; along D it covers S - 1 faces (S = BX for D = 0, BY otherwise).
 // D = 0: faces f0 .. f0+BX-2 of BY consecutive (j) rows; D = 1, 2: BY-1 faces along D for BX
 // consecutive r. Must be called by every thread of the block (it synchronises the block).
-template <int D, int BX, int BY, typename TW, bool HD = false>
+// GLM (template flag, psi of type TP): psi is reconstructed alongside (cell and upper-face values
+// of the neighbour in sQW / sQP), and after the Riemann flux the (B_n, psi) star state replaces
+// the normal-field flux by psi* and writes c_h^2 B_n* to FP (the GLM div-B control's face step)
+template <int D, int BX, int BY, typename TW, bool HD = false, bool GLM = false, typename TP = TW>
 __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict__ W, TW *__restrict__ F,
-                                          int bx, int by, int bz, int tx, int ty, TW *sW, TW *sP)
+                                          int bx, int by, int bz, int tx, int ty, TW *sW, TW *sP,
+                                          const TP *__restrict__ Psi = nullptr, TW *__restrict__ FP = nullptr,
+                                          TW *sQW = nullptr, TW *sQP = nullptr)
 {
     constexpr int S = D == 0 ? BX : BY;
     const int ts = D == 0 ? tx : ty;
@@ -267,8 +272,17 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
     const long long st = D == 0 ? 1 : (D == 1 ? (long long)P.p1 : (long long)P.p1 * P.p2);
     const int sl = ty * BX + tx, sz = BX * BY;
     TW wc[NV], wm[NV];
+    TW qc = TW(0), qm = TW(0);
     if (valid) {
         const long long c = cidx(P, i, j, k);
+        if constexpr (GLM) {
+            const TW qa = (TW)Psi[c - st], qe = (TW)Psi[c + st];
+            qc = (TW)Psi[c];
+            const TW dq = limiter<TW>(P.limiter, qc - qa, qe - qc);
+            qm = qc - TW(0.5) * dq;
+            sQW[sl] = qc;
+            sQP[sl] = qc + TW(0.5) * dq;
+        }
         TW da[NV], db[NV], dl[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -328,7 +342,8 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
         const int pl = D == 0 ? sl - 1 : sl - BX;      // the neighbour one cell below along D
 #pragma unroll
         for (int v = 0; v < NV; ++v) { wl[v] = sP[v * sz + pl]; wr[v] = wm[v]; }
-        if (not_positive(wl[0]) || not_positive(wr[0]) || not_positive(wl[4]) || not_positive(wr[4])) {
+        const bool first = not_positive(wl[0]) || not_positive(wr[0]) || not_positive(wl[4]) || not_positive(wr[4]);
+        if (first) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) { wl[v] = sW[v * sz + pl]; wr[v] = wc[v]; }
         }
@@ -337,6 +352,15 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
         if (D == 0) { fi = ((long long)k * P.n2 + j) * (P.n1 + 1) + s; fs = (long long)P.n3 * P.n2 * (P.n1 + 1); }
         else if (D == 1) { fi = ((long long)k * (P.n2 + 1) + s) * P.n1 + i; fs = (long long)P.n3 * (P.n2 + 1) * P.n1; }
         else { fi = ((long long)s * P.n2 + j) * P.n1 + i; fs = (long long)(P.n3 + 1) * P.n2 * P.n1; }
+        if constexpr (GLM) {
+            const TW sl_ = first ? sQW[pl] : sQP[pl], sr_ = first ? qc : qm;
+            const TW bl = wl[5 + D], br = wr[5 + D];
+            const double dt = P.sc->dt;         // 0 only for steps past a stop time (no change then)
+            const TW ch = dt > 0.0 ? (TW)(P.sc->cfl * P.glm_dmin / dt) : TW(0);
+            const TW bs = dt > 0.0 ? TW(0.5) * (bl + br) - TW(0.5) * (sr_ - sl_) / ch : TW(0.5) * (bl + br);
+            f[5 + D] = TW(0.5) * (sl_ + sr_) - TW(0.5) * ch * (br - bl);
+            FP[fi] = ch * ch * bs;
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v * fs + fi] = f[v];
     }
@@ -363,6 +387,20 @@ k_flux(Params P, const TW *__restrict__ W, TW *__restrict__ F)
     __shared__ TW sW[NV * BY * BX];
     __shared__ TW sP[NV * BY * BX];
     flux_tile<D, BX, BY, TW, HD>(P, W, F, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, sW, sP);
+}
+
+// the same with the GLM face step (psi of type TP, its face fluxes into FP)
+template <int D, typename TW, bool HD, typename TP>
+__global__ void __launch_bounds__(FluxShape<D>::BX * FluxShape<D>::BY)
+k_flux_glm(Params P, const TW *__restrict__ W, TW *__restrict__ F, const TP *__restrict__ Psi, TW *__restrict__ FP)
+{
+    constexpr int BX = FluxShape<D>::BX, BY = FluxShape<D>::BY;
+    __shared__ TW sW[NV * BY * BX];
+    __shared__ TW sP[NV * BY * BX];
+    __shared__ TW sQW[BY * BX];
+    __shared__ TW sQP[BY * BX];
+    flux_tile<D, BX, BY, TW, HD, true, TP>(P, W, F, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, sW, sP,
+                                            Psi, FP, sQW, sQP);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -886,46 +924,6 @@ __global__ void k_psi_ghost(Params P, TS *__restrict__ Psi)
     Psi[at(gi)] = Psi[at(src)];
 }
 
-// the faces along D (the lower face of cell (i, j, k), faces 0 .. n_D): B_n* and psi*; psi*
-// overwrites the normal-field component of F, FP gets c_h^2 B_n*
-template <int D, typename TS, typename TW>
-__global__ void k_glm_faces(Params P, const TW *__restrict__ W, const TS *__restrict__ Psi, TW *F, TW *FP)
-{
-    const int e1 = P.n1 + (D == 0), e2 = P.n2 + (D == 1), e3 = P.n3 + (D == 2);
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (long long)e1 * e2 * e3) return;
-    const int i = (int)(tid % e1);
-    const long long r_ = tid / e1;
-    const int j = (int)(r_ % e2), k = (int)(r_ / e2);
-    const long long nt = P.nt, c = cidx(P, i, j, k);
-    const long long st = D == 0 ? 1 : (D == 1 ? (long long)P.p1 : (long long)P.p1 * P.p2);
-    // limited linear face states of field v (left from cells c-2, c-1, c; right from c-1, c, c+1)
-    auto recon = [&](const auto *a, TW &l, TW &r) {
-        const TW m2 = (TW)a[c - 2 * st], m1 = (TW)a[c - st], z = (TW)a[c], p1 = (TW)a[c + st];
-        l = m1 + TW(0.5) * limiter<TW>(P.limiter, m1 - m2, z - m1);
-        r = z - TW(0.5) * limiter<TW>(P.limiter, z - m1, p1 - z);
-    };
-    TW rl, rr, pl_, pr_, bl, br, sl, sr;
-    recon(W, rl, rr);
-    recon(W + 4 * nt, pl_, pr_);
-    recon(W + (5 + D) * nt, bl, br);
-    recon(Psi, sl, sr);
-    if (!(rl > TW(0)) || !(rr > TW(0)) || !(pl_ > TW(0)) || !(pr_ > TW(0))) {   // first order
-        bl = W[(5 + D) * nt + c - st]; br = W[(5 + D) * nt + c];
-        sl = (TW)Psi[c - st]; sr = (TW)Psi[c];
-    }
-    const double dt = P.sc->dt;                 // 0 only for steps past a stop time (no change then)
-    const TW ch = dt > 0.0 ? (TW)(P.sc->cfl * P.glm_dmin / dt) : TW(0);
-    const TW bs = dt > 0.0 ? TW(0.5) * (bl + br) - TW(0.5) * (sr - sl) / ch : TW(0.5) * (bl + br);
-    const TW ps = TW(0.5) * (sl + sr) - TW(0.5) * ch * (br - bl);
-    long long fi, fs;
-    if (D == 0) { fi = ((long long)k * P.n2 + j) * (P.n1 + 1) + i; fs = (long long)P.n3 * P.n2 * (P.n1 + 1); }
-    else if (D == 1) { fi = ((long long)k * (P.n2 + 1) + j) * P.n1 + i; fs = (long long)P.n3 * (P.n2 + 1) * P.n1; }
-    else { fi = ((long long)k * P.n2 + j) * P.n1 + i; fs = (long long)(P.n3 + 1) * P.n2 * P.n1; }
-    F[(5 + D) * fs + fi] = ps;
-    FP[fi] = ch * ch * bs;
-}
-
 // psi of every interior cell: stage 1 Psi1 = Psi + dt L; stage 2 Psi = (Psi/2 + (Psi1 + dt L)/2)
 // damped (the second stage runs after the MHD update has advanced t and dt: the step's dt is
 // dt_step)
@@ -1395,14 +1393,24 @@ template <typename TS, typename TW> struct Launch {
         const long long n = 2LL * NG * ((long long)P.n2 * P.n3 + (long long)P.n1 * P.n3 + (long long)P.n1 * P.n2);
         k_psi_ghost<TS><<<cdiv(n, 256), 256, 0, s>>>(P, (TS *)Psi);
     }
-    static void glm_faces(const Params &P, const void *W, const void *Psi, void *F1, void *F2, void *F3, void *FP1,
-                          void *FP2, void *FP3, cudaStream_t s)
+    template <bool HD>
+    static void fluxes_glm_t(const Params &P, const TW *w, const TS *psi, TW *F1, TW *F2, TW *F3, TW *FP1, TW *FP2,
+                             TW *FP3, cudaStream_t s)
     {
-        const long long n0 = (long long)(P.n1 + 1) * P.n2 * P.n3, n1 = (long long)P.n1 * (P.n2 + 1) * P.n3,
-                        n2 = (long long)P.n1 * P.n2 * (P.n3 + 1);
-        k_glm_faces<0, TS, TW><<<cdiv(n0, 256), 256, 0, s>>>(P, (const TW *)W, (const TS *)Psi, (TW *)F1, (TW *)FP1);
-        k_glm_faces<1, TS, TW><<<cdiv(n1, 256), 256, 0, s>>>(P, (const TW *)W, (const TS *)Psi, (TW *)F2, (TW *)FP2);
-        k_glm_faces<2, TS, TW><<<cdiv(n2, 256), 256, 0, s>>>(P, (const TW *)W, (const TS *)Psi, (TW *)F3, (TW *)FP3);
+        k_flux_glm<0, TW, HD, TS><<<dim3(cdiv(P.n1 + 1, 127), P.n2, P.n3), dim3(128, 1), 0, s>>>(P, w, F1, psi, FP1);
+        k_flux_glm<1, TW, HD, TS><<<dim3(cdiv(P.n1, 16), cdiv(P.n2 + 1, 15), P.n3), dim3(16, 16), 0, s>>>(P, w, F2, psi, FP2);
+        k_flux_glm<2, TW, HD, TS><<<dim3(cdiv(P.n1, 16), cdiv(P.n3 + 1, 15), P.n2), dim3(16, 16), 0, s>>>(P, w, F3, psi, FP3);
+    }
+    // the three flux kernels with the GLM face step
+    static void fluxes_glm(const Params &P, const void *W, const void *Psi, void *F1, void *F2, void *F3, void *FP1,
+                           void *FP2, void *FP3, cudaStream_t s)
+    {
+        if (P.flux == 2)
+            fluxes_glm_t<true>(P, (const TW *)W, (const TS *)Psi, (TW *)F1, (TW *)F2, (TW *)F3, (TW *)FP1, (TW *)FP2,
+                               (TW *)FP3, s);
+        else
+            fluxes_glm_t<false>(P, (const TW *)W, (const TS *)Psi, (TW *)F1, (TW *)F2, (TW *)F3, (TW *)FP1, (TW *)FP2,
+                                (TW *)FP3, s);
     }
     static void glm_update(const Params &P, int stage, const void *Ps, void *Po, const void *FP1, const void *FP2,
                            const void *FP3, cudaStream_t s)
@@ -1463,7 +1471,7 @@ template <typename TS, typename TW> struct Launch {
         o.fused_stage = nullptr;
         o.fused_blocks = nullptr;
         o.glm_ghost = glm_ghost;
-        o.glm_faces = glm_faces;
+        o.fluxes_glm = fluxes_glm;
         o.glm_update = glm_update;
         o.psi_copy = psi_copy;
         o.tracer_ghost = tracer_ghost;

@@ -21,11 +21,11 @@ struct Ops {
     // one whole stage (fluxes, div B, update) in a single kernel; null where not available
     void (*fused_stage)(const Params &, int stage, const void *Us, const void *Ws, void *Uo, void *Wo, cudaStream_t);
     unsigned int (*fused_blocks)(const Params &);
-    // GLM div-B control: psi ghosts; the (B_n, psi) face states of the three directions (after the
-    // MHD fluxes); the psi stage update (after the MHD update); psi from / to host-layout doubles
+    // GLM div-B control: psi ghosts; the three flux kernels with the (B_n, psi) face step; the psi
+    // stage update (after the MHD update); psi from / to host-layout doubles
     void (*glm_ghost)(const Params &, void *Psi, cudaStream_t);
-    void (*glm_faces)(const Params &, const void *W, const void *Psi, void *F1, void *F2, void *F3, void *FP1, void *FP2,
-                      void *FP3, cudaStream_t);
+    void (*fluxes_glm)(const Params &, const void *W, const void *Psi, void *F1, void *F2, void *F3, void *FP1, void *FP2,
+                       void *FP3, cudaStream_t);
     void (*glm_update)(const Params &, int stage, const void *Ps, void *Po, const void *FP1, const void *FP2,
                        const void *FP3, cudaStream_t);
     void (*psi_copy)(const Params &, void *Psi, double *buf, int to_psi, cudaStream_t);
