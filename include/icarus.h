@@ -259,6 +259,12 @@ int icarus_batch_step(icarus_batch *b, int n);
 /* ETIMEOUT if a barrier wait gave up, else the first member's sticky status. Synchronous. */
 int icarus_batch_status(icarus_batch *b);
 
+/* Self-test of the batched form's bounded grid barrier: `blocks` small blocks (1..64) meet at one
+ * barrier, block `absent` (-1: none) never arrives; the others wait at most spin_limit clock
+ * ticks, then record the failure and return. ETIMEOUT when the wait gave up, OK when every block
+ * arrived; the device stays usable either way. For tests of the failure path. */
+int icarus_batch_barrier_selftest(int blocks, int absent, long long spin_limit);
+
 /* info[3] = (members, blocks of the persistent launch, 1 if steps replay a CUDA graph). */
 int icarus_batch_info(icarus_batch *b, int *info);
 

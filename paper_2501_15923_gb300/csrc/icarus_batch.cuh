@@ -78,6 +78,14 @@ __device__ __forceinline__ bool grid_sync(const BatchArgs &A)
     return ok != 0;
 }
 
+// self-test of the bounded barrier: every block but `absent` (-1: none) meets at one barrier; a
+// block that never arrives makes the others give up after spin_limit clock ticks and record it
+static __global__ void k_barrier_selftest(BatchArgs A, int absent)
+{
+    if ((int)blockIdx.x == absent) return;
+    grid_sync(A);
+}
+
 template <int D, int BX, int BY, typename TW>
 __device__ __forceinline__ void flux_item(const Member &M, const TW *W, TW *F, long long local, const int *nt,
                                           TW *smem)

@@ -279,6 +279,26 @@ int icarus_batch_step(icarus_batch *b, int n)
     return ICARUS_OK;
 }
 
+int icarus_batch_barrier_selftest(int blocks, int absent, long long spin_limit)
+{
+    if (blocks < 1 || blocks > 64 || absent >= blocks || spin_limit < 1)
+        return report_error(ICARUS_EINVAL, "blocks in [1, 64], absent < blocks, spin_limit >= 1");
+    BarrierState *bar = nullptr;
+    BCK(cudaMalloc(&bar, sizeof(BarrierState)));
+    BCK(cudaMemset(bar, 0, sizeof(BarrierState)));
+    BatchArgs A{};
+    A.bar = bar;
+    A.spin_limit = spin_limit;
+    k_barrier_selftest<<<blocks, 32>>>(A, absent);
+    cudaError_t e = cudaDeviceSynchronize();
+    BarrierState s{};
+    if (e == cudaSuccess) e = cudaMemcpy(&s, bar, sizeof s, cudaMemcpyDeviceToHost);
+    cudaFree(bar);
+    if (e != cudaSuccess) return report_error(ICARUS_ECUDA, cudaGetErrorString(e));
+    if (s.err) return report_error(ICARUS_ETIMEOUT, "the barrier wait gave up (a block never arrived)");
+    return ICARUS_OK;
+}
+
 int icarus_batch_status(icarus_batch *b)
 {
     if (!b) return report_error(ICARUS_EINVAL, "NULL batch");

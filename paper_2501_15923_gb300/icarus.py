@@ -79,6 +79,7 @@ SIGNATURES = {
     "icarus_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
     "icarus_batch_set_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "icarus_batch_status": (C.c_int, [C.c_void_p]),
+    "icarus_batch_barrier_selftest": (C.c_int, [C.c_int, C.c_int, C.c_longlong]),
     "icarus_batch_info": (C.c_int, [C.c_void_p, C.c_void_p]),
     "icarus_batch_stream": (C.c_void_p, [C.c_void_p]),
     "icarus_batch_destroy": (C.c_int, [C.c_void_p]),

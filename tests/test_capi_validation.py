@@ -123,3 +123,10 @@ def test_null_context_and_negative_counts(ic):
     o = ic.make_options(I.Options())
     assert lib.icarus_init(None, 1.5, 0.0, C.byref(o), None) == EINVAL
     assert "NULL" in lib.icarus_last_error().decode()
+
+
+def test_barrier_selftest_rejects_bad_arguments(ic):
+    """The barrier self-test checks its sizes before any device call."""
+    lib = ic.load()
+    for blocks, absent, spin in [(0, -1, 1000), (65, -1, 1000), (4, 4, 1000), (4, -1, 0)]:
+        assert lib.icarus_batch_barrier_selftest(blocks, absent, spin) == EINVAL

@@ -82,3 +82,23 @@ def test_batch_probes_and_tile_variants(ic):
             info = b.info()
             assert info["members"] == 2 and info["blocks"] >= 152
             b.close()
+
+
+def test_barrier_wait_is_bounded(ic):
+    """A block that never reaches the batched form's grid barrier makes the others give up.
+
+    The failure is made by a block that skips the barrier (nothing else ever releases the
+    waiters), the wait limit is about a millisecond; the waiters record ETIMEOUT and return,
+    and the device stays usable: a full barrier and a batched step still succeed afterwards.
+    """
+    lib = ic.load()
+    ETIMEOUT = -6
+    assert lib.icarus_batch_barrier_selftest(16, -1, 2_000_000) == 0
+    assert lib.icarus_batch_barrier_selftest(16, 5, 2_000_000) == ETIMEOUT
+    assert "never arrived" in lib.icarus_last_error().decode()
+    assert lib.icarus_batch_barrier_selftest(16, 0, 2_000_000) == ETIMEOUT
+    assert lib.icarus_batch_barrier_selftest(64, -1, 2_000_000) == 0
+    b = ic.Batch(members()[:2], precision=2)
+    b.step(2)
+    assert b.status() == 0
+    b.close()
