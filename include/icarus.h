@@ -278,14 +278,21 @@ int icarus_batch_destroy(icarus_batch *b);
  * A 4-layer 3-D convolutional network (8 -> 32 -> 32 -> 32 -> 8 channels, 3x3x3 kernels, ReLU,
  * phi circular / r and theta replicate padding) that predicts the correction of a coarse state
  * towards the restricted fine solution (not in the paper). BF16 weights and activations, FP32
- * accumulation on the tensor cores (mma.sync), FP32 Adam master weights; device memory from
- * cudaMalloc, released by icarus_closure_destroy. */
+ * accumulation on the tensor cores (forward and data gradient with tcgen05, weight gradient with
+ * mma.sync), FP32 Adam master weights; device memory from cudaMalloc, released by
+ * icarus_closure_destroy. Every wait of the tcgen05 kernels is bounded: one that expires makes
+ * the call return ETIMEOUT. */
 typedef struct icarus_closure icarus_closure;
 
 /* Network for a coarse grid n1 x n2 x n3, weights initialised from seed; runs on cuda_stream. */
 int icarus_closure_create(int n1, int n2, int n3, unsigned long long seed, void *cuda_stream,
                           icarus_closure **out);
 int icarus_closure_destroy(icarus_closure *c);
+
+/* Self-test of the closure kernels' bounded barrier wait: one block waits on a shared-memory
+ * barrier that expects one arrival, which it gives (arrive = 1: OK) or not (arrive = 0: the wait
+ * gives up after `limit` polls and the call returns ETIMEOUT; the device stays usable). */
+int icarus_closure_wait_selftest(int arrive, int limit);
 
 /* Field-wise normalisation per radial index (host arrays [8][n1]): the input is (U - in_mean) /
  * in_scale, the network's output is multiplied by out_scale to give the correction dU. */

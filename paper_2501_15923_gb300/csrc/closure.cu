@@ -126,9 +126,9 @@ template <int O> __device__ __forceinline__ uint32_t umma_idesc()
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(O >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit = 1 << 22)
 {
-    for (int it = 0; it < (1 << 22); ++it) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}\n"
@@ -138,6 +138,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
         if (done) return true;
     }
     return false;
+}
+
+// self-test of the bounded wait: one barrier expecting one arrival, given it (arrive = 1) or not
+// (arrive = 0: nothing ever completes the phase); an expired wait records the failure in tc_status
+__global__ void k_wait_selftest(int arrive, int limit)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = saddr(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(b) : "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(b, 0, limit)) atomicExch(&tc_status, 1);
 }
 
 // one (line, channel group) block: 130 rows of 16 bytes, padded to 136 rows so that every block
@@ -874,6 +890,16 @@ void forward(icarus_closure *c)
 }  // namespace
 
 extern "C" {
+
+int icarus_closure_wait_selftest(int arrive, int limit)
+{
+    if ((arrive != 0 && arrive != 1) || limit < 1) return report_error(ICARUS_EINVAL, "arrive 0 or 1, limit >= 1");
+    k_wait_selftest<<<1, 32>>>(arrive, limit);
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return report_error(ICARUS_ECUDA, cudaGetErrorString(e));
+    if (tc_timed_out()) return report_error(ICARUS_ETIMEOUT, "the barrier wait expired (nothing arrived)");
+    return ICARUS_OK;
+}
 
 int icarus_closure_create(int n1, int n2, int n3, unsigned long long seed, void *cuda_stream, icarus_closure **out)
 {

@@ -85,6 +85,7 @@ SIGNATURES = {
     "icarus_batch_destroy": (C.c_int, [C.c_void_p]),
     "icarus_closure_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p, C.POINTER(C.c_void_p)]),
     "icarus_closure_destroy": (C.c_int, [C.c_void_p]),
+    "icarus_closure_wait_selftest": (C.c_int, [C.c_int, C.c_int]),
     "icarus_closure_set_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "icarus_closure_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     "icarus_closure_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -130,3 +130,9 @@ def test_barrier_selftest_rejects_bad_arguments(ic):
     lib = ic.load()
     for blocks, absent, spin in [(0, -1, 1000), (65, -1, 1000), (4, 4, 1000), (4, -1, 0)]:
         assert lib.icarus_batch_barrier_selftest(blocks, absent, spin) == EINVAL
+
+
+def test_closure_wait_selftest_rejects_bad_arguments(ic):
+    lib = ic.load()
+    for arrive, limit in [(2, 100), (-1, 100), (1, 0)]:
+        assert lib.icarus_closure_wait_selftest(arrive, limit) == EINVAL

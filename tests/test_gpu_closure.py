@@ -76,3 +76,20 @@ def test_restriction_matches_oracle(ic):
     assert tc == t
     np.testing.assert_allclose(Uc, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
     fine.close(); coarse.close()
+
+
+def test_tensor_core_wait_is_bounded(ic):
+    """The closure kernels' barrier wait gives up when nothing arrives, and the device stays usable.
+
+    The failure is a shared-memory barrier that expects one arrival and never gets it; after 4096
+    polls the wait records the failure and the call returns ETIMEOUT (the status is read and
+    cleared). The same wait with its arrival completes, and the tcgen05 forward and gradients
+    still match the oracle afterwards.
+    """
+    lib = ic.load()
+    ETIMEOUT = -6
+    assert lib.icarus_closure_wait_selftest(1, 4096) == 0
+    assert lib.icarus_closure_wait_selftest(0, 4096) == ETIMEOUT
+    assert "expired" in lib.icarus_last_error().decode()
+    assert lib.icarus_closure_wait_selftest(1, 4096) == 0
+    test_layer_forward_and_gradients_match_oracle(ic, 32, 32, 1, (9, 7, 4))
