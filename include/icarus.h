@@ -199,6 +199,13 @@ int icarus_set_stop_time(icarus_ctx *ctx, double t_stop);
 /* Current time and the dt of the next step (code units). Synchronous. */
 int icarus_time(icarus_ctx *ctx, double *t, double *dt);
 
+/* Check of the square root that the FP64 Riemann flux uses for the fast magnetosonic speeds (a
+ * single-precision reciprocal-root estimate and two Newton corrections, within one ulp of the
+ * correctly rounded root):
+ * for the n host values x, y[2i] receives that root of x[i] and y[2i + 1] the library's correctly
+ * rounded sqrt. Synchronous; a temporary device buffer. EINVAL for n outside [1, 2^24] or NULL. */
+int icarus_root_check(int n, const double *x, double *y);
+
 /* Sticky status (0 or ENONFINITE) and the number of floor activations. Synchronous. */
 int icarus_status(icarus_ctx *ctx, long long *floor_hits);
 

@@ -146,9 +146,42 @@ template <typename R> __device__ __forceinline__ void prim2cons(const R *w, R *u
     u[B3] = w[7];
 }
 
+// Square root of x >= 0 with five FP64 operations, for the wave speeds inside the Riemann flux.
+// x = m 2^(2k) with m in [1, 4) is split on the integer pipe (exponent halved exactly, so every
+// normal double is in range); y ~ 1/sqrt(m) comes from the single-precision rsqrt.approx (relative
+// error below 2^-22.9) on m's leading 23 bits, and r = y 2^-k is widened back on the integer pipe.
+// Then two Newton corrections of the root with the coupled reciprocal (Markstein, IBM J. Res. Dev.
+// 34 (1990)): s = x r, s += (r / 2)(x - s^2), twice. For an estimate error e the first leaves a
+// relative error of about 1.5 e^2 (~3e-14), the second e times that (~1e-21), so the result is the
+// correctly rounded root but for the final rounding: within one ulp of it, almost always equal.
+// Zero, negative, subnormal and non-finite x take the library sqrt.
+__device__ __forceinline__ double sqrt_nr(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned int lo = (unsigned int)__double2loint(x);
+    if ((unsigned int)hi - 0x00100000u >= 0x7fe00000u) return sqrt(x);   // not positive and normal
+    const int e = hi >> 20;
+    const int k = (e - 1023) >> 1;
+    const int mb = ((127 + e - 1023 - 2 * k) << 23) | ((hi & 0xfffff) << 3) | (int)(lo >> 29);
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__int_as_float(mb)));
+    const int yb = __float_as_int(y);
+    const int rhi = ((((yb >> 23) & 0xff) - 127 + 1023 - k) << 20) | ((yb & 0x7fffff) >> 3);
+    const int rlo = yb << 29;
+    const double r = __hiloint2double(rhi, rlo);               // ~ 1 / sqrt(x)
+    const double h = __hiloint2double(rhi - (1 << 20), rlo);   // r / 2
+    const double s = x * r;
+    const double s1 = fma(h, fma(-s, s, x), s);
+    return fma(h, fma(-s1, s1, x), s1);
+}
+
+template <bool NR> __device__ __forceinline__ double root(double x) { return NR ? sqrt_nr(x) : sqrt(x); }
+template <bool NR> __device__ __forceinline__ float root(float x) { return sqrtf(x); }
+
 // fast magnetosonic speed along direction d:
 // c_f^2 = ((a^2 + b^2) + sqrt((a^2 + b^2)^2 - 4 a^2 B_d^2 / rho)) / 2, a^2 = gamma p / rho
-template <typename R> __device__ __forceinline__ R fast_speed(const R *w, R irho, int d, R gamma)
+// (NR: the FP64 roots by sqrt_nr, used inside the Riemann flux; the time step keeps the library root)
+template <typename R, bool NR = false> __device__ __forceinline__ R fast_speed(const R *w, R irho, int d, R gamma)
 {
     R a2 = gamma * w[4] * irho;
     R bb = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
@@ -156,7 +189,7 @@ template <typename R> __device__ __forceinline__ R fast_speed(const R *w, R irho
     R bn = w[5 + d];
     R disc = s * s - R(4) * a2 * (bn * bn * irho);
     disc = rmax(disc, R(0));
-    return sqrt(R(0.5) * (s + sqrt(disc)));
+    return root<NR>(R(0.5) * (s + root<NR>(disc)));
 }
 
 // sign and zero tests on the bit patterns (integer pipe; the FP64 pipe is the scarce one)
@@ -331,7 +364,7 @@ __device__ __forceinline__ void riemann(const R *wl, const R *wr, int d, int flu
         irl = R(1) / wl[0];
         irr = R(1) / wr[0];
     }
-    R cl = fast_speed(wl, irl, d, gamma), cr = fast_speed(wr, irr, d, gamma);
+    R cl = fast_speed<R, true>(wl, irl, d, gamma), cr = fast_speed<R, true>(wr, irr, d, gamma);
     R fl[NV], fr[NV];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
