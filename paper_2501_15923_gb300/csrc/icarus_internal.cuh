@@ -117,6 +117,38 @@ template <typename R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ?
 template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 template <typename R> __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
 
+// Exact scalings by 1/2 and 4, |x|, max(x, 0) and the larger of two non-negative values, in
+// double on the integer pipe (exponent field, sign bit, bit-pattern order), since the FP64 pipe is
+// the scarce one; in single precision the plain arithmetic. A scaling is exact whenever its result
+// is normal; zero, infinities and NaN pass unchanged; below 2^-1021 (and, for 4x, above 2^1021) the
+// double is returned unscaled.
+__device__ __forceinline__ double half_r(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned int e = ((unsigned int)hi >> 20) & 0x7ffu;
+    return e - 2u < 2045u ? __hiloint2double(hi - 0x00100000, __double2loint(x)) : x;
+}
+__device__ __forceinline__ float half_r(float x) { return 0.5f * x; }
+__device__ __forceinline__ double quad_r(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned int e = ((unsigned int)hi >> 20) & 0x7ffu;
+    return e - 1u < 2044u ? __hiloint2double(hi + 0x00200000, __double2loint(x)) : x;
+}
+__device__ __forceinline__ float quad_r(float x) { return 4.f * x; }
+__device__ __forceinline__ double abs_r(double x)
+{
+    return __hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x));
+}
+__device__ __forceinline__ float abs_r(float x) { return rabs(x); }
+__device__ __forceinline__ double clamp0_r(double x) { return __double2hiint(x) < 0 ? 0.0 : x; }
+__device__ __forceinline__ float clamp0_r(float x) { return rmax(x, 0.f); }
+__device__ __forceinline__ double max_nonneg_r(double a, double b)   // a, b >= 0
+{
+    return __double_as_longlong(a) > __double_as_longlong(b) ? a : b;
+}
+__device__ __forceinline__ float max_nonneg_r(float a, float b) { return rmax(a, b); }
+
 // conserved -> primitive: v = m / rho, p = (gamma - 1)(e - rho v^2 / 2 - B^2 / 2)
 template <typename R> __device__ __forceinline__ void cons2prim(const R *u, R *w, R gm1)
 {
@@ -139,8 +171,8 @@ template <typename R> __device__ __forceinline__ void prim2cons(const R *w, R *u
     u[M1] = w[0] * w[1];
     u[M2] = w[0] * w[2];
     u[M3] = w[0] * w[3];
-    u[EN] = w[4] * igm1 + R(0.5) * (u[M1] * w[1] + u[M2] * w[2] + u[M3] * w[3])
-          + R(0.5) * (w[5] * w[5] + w[6] * w[6] + w[7] * w[7]);
+    u[EN] = w[4] * igm1 + half_r(u[M1] * w[1] + u[M2] * w[2] + u[M3] * w[3])
+          + half_r(w[5] * w[5] + w[6] * w[6] + w[7] * w[7]);
     u[B1] = w[5];
     u[B2] = w[6];
     u[B3] = w[7];
@@ -187,9 +219,14 @@ template <typename R, bool NR = false> __device__ __forceinline__ R fast_speed(c
     R bb = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
     R s = a2 + bb * irho;
     R bn = w[5 + d];
-    R disc = s * s - R(4) * a2 * (bn * bn * irho);
-    disc = rmax(disc, R(0));
-    return root<NR>(R(0.5) * (s + root<NR>(disc)));
+    if constexpr (NR) {
+        const R disc = clamp0_r(s * s - quad_r(a2) * (bn * bn * irho));
+        return root<NR>(half_r(s + root<NR>(disc)));
+    } else {
+        R disc = s * s - R(4) * a2 * (bn * bn * irho);
+        disc = rmax(disc, R(0));
+        return root<NR>(R(0.5) * (s + root<NR>(disc)));
+    }
 }
 
 // sign and zero tests on the bit patterns (integer pipe; the FP64 pipe is the scarce one)
@@ -389,9 +426,9 @@ __device__ __forceinline__ void riemann(const R *wl, const R *wr, int d, int flu
         (void)flux;
         hlld<R>(wl, wr, ul, ur, fl, fr, cl, cr, d, f);
     } else if (flux == 0) {
-        R c = rmax(rabs(wl[1 + d]) + cl, rabs(wr[1 + d]) + cr);
+        const R hc = half_r(max_nonneg_r(abs_r(wl[1 + d]) + cl, abs_r(wr[1 + d]) + cr));
 #pragma unroll
-        for (int v = 0; v < NV; ++v) f[v] = R(0.5) * (fl[v] + fr[v]) - R(0.5) * c * (ur[v] - ul[v]);
+        for (int v = 0; v < NV; ++v) f[v] = half_r(fl[v] + fr[v]) - hc * (ur[v] - ul[v]);
     } else {
         R sl = rmin(wl[1 + d] - cl, wr[1 + d] - cr);
         R sr = rmax(wl[1 + d] + cl, wr[1 + d] + cr);
