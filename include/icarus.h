@@ -199,12 +199,13 @@ int icarus_set_stop_time(icarus_ctx *ctx, double t_stop);
 /* Current time and the dt of the next step (code units). Synchronous. */
 int icarus_time(icarus_ctx *ctx, double *t, double *dt);
 
-/* Check of the square root that the FP64 Riemann flux uses for the fast magnetosonic speeds (a
- * single-precision reciprocal-root estimate and two Newton corrections, within one ulp of the
- * correctly rounded root):
- * for the n host values x, y[2i] receives that root of x[i] and y[2i + 1] the library's correctly
- * rounded sqrt. Synchronous; a temporary device buffer. EINVAL for n outside [1, 2^24] or NULL. */
-int icarus_root_check(int n, const double *x, double *y);
+/* Check of the square root and the reciprocal that the FP64 kernels use in place of the library's
+ * correctly rounded ones (the fast-speed roots in the Riemann flux; the reciprocals of the face
+ * densities, of the van Leer slope sums and of rho): single-precision estimates refined by two
+ * Newton steps, within one ulp of the correctly rounded results. For the n host values x,
+ * y[4i .. 4i + 3] receive that root of x[i], the library sqrt, that reciprocal and the library
+ * 1 / x[i]. Synchronous; a temporary device buffer. EINVAL for n outside [1, 2^24] or NULL. */
+int icarus_math_check(int n, const double *x, double *y);
 
 /* Sticky status (0 or ENONFINITE) and the number of floor activations. Synchronous. */
 int icarus_status(icarus_ctx *ctx, long long *floor_hits);

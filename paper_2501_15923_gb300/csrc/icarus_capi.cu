@@ -66,13 +66,16 @@ void *icarus::ctx_alloc(icarus_ctx *c, size_t bytes) { return dalloc(c, bytes); 
 
 namespace {
 
-// the Riemann flux's square root beside the library's, element by element: y[2i], y[2i + 1]
-__global__ void k_root_check(const double *x, double *y, int n)
+// the FP64 flux's square root and reciprocal beside the library's, element by element:
+// y[4i .. 4i + 3] = sqrt_nr, sqrt, rcp_nr, 1 / x
+__global__ void k_math_check(const double *x, double *y, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        y[2 * i] = sqrt_nr(x[i]);
-        y[2 * i + 1] = sqrt(x[i]);
+        y[4 * i] = sqrt_nr(x[i]);
+        y[4 * i + 1] = sqrt(x[i]);
+        y[4 * i + 2] = rcp_nr(x[i]);
+        y[4 * i + 3] = 1.0 / x[i];
     }
 }
 
@@ -773,19 +776,19 @@ int icarus_time(icarus_ctx *c, double *t, double *dt)
     return ICARUS_OK;
 }
 
-int icarus_root_check(int n, const double *x, double *y)
+int icarus_math_check(int n, const double *x, double *y)
 {
     if (n < 1 || n > (1 << 24) || !x || !y) return fail(ICARUS_EINVAL, "n in [1, 2^24], x and y host arrays");
     double *d = nullptr;
-    CK(cudaMalloc(&d, (size_t)3 * n * sizeof(double)));
+    CK(cudaMalloc(&d, (size_t)5 * n * sizeof(double)));
     cudaError_t e = cudaMemcpy(d, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        k_root_check<<<(n + 255) / 256, 256>>>(d, d + n, n);
+        k_math_check<<<(n + 255) / 256, 256>>>(d, d + n, n);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpy(y, d + n, (size_t)2 * n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(y, d + n, (size_t)4 * n * sizeof(double), cudaMemcpyDeviceToHost);
     cudaFree(d);
-    if (e != cudaSuccess) return fail(ICARUS_ECUDA, "root check: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(ICARUS_ECUDA, "math check: %s", cudaGetErrorString(e));
     return ICARUS_OK;
 }
 

@@ -117,6 +117,32 @@ template <typename R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ?
 template <typename R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
 template <typename R> __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
 
+// Reciprocal 1/q with four FP64 operations: q = +-m 2^E with m in [1, 2); y ~ 1/m from the
+// single-precision rcp.approx on m's leading 23 bits, r = +-y 2^-E assembled on the integer pipe,
+// then two Newton steps t = 1 - q r, r += r t (Markstein, IBM J. Res. Dev. 34 (1990)): the
+// estimate error e becomes e^2 (~6e-14), then e^4, so only the final rounding remains: within one
+// ulp of the correctly rounded reciprocal (equal to it in about 99.3 % of cases). q outside [2^-1021, 2^1021] in magnitude (zero,
+// subnormal, huge, non-finite) takes the library division.
+__device__ __forceinline__ double rcp_nr(double q)
+{
+    const int hi = __double2hiint(q);
+    const unsigned int lo = (unsigned int)__double2loint(q);
+    const unsigned int e = ((unsigned int)hi >> 20) & 0x7ffu;
+    if (e - 2u >= 2043u) return 1.0 / q;
+    const int mb = (127 << 23) | ((hi & 0xfffff) << 3) | (int)(lo >> 29);
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__int_as_float(mb)));
+    const int yb = __float_as_int(y);
+    const int rhi = (hi & (int)0x80000000) | ((((yb >> 23) & 0xff) + 1919 - (int)e) << 20) | ((yb & 0x7fffff) >> 3);
+    double r = __hiloint2double(rhi, yb << 29);
+    double t = fma(-q, r, 1.0);
+    r = fma(r, t, r);
+    t = fma(-q, r, 1.0);
+    return fma(r, t, r);
+}
+__device__ __forceinline__ double rcp_r(double q) { return rcp_nr(q); }
+__device__ __forceinline__ float rcp_r(float q) { return 1.f / q; }
+
 // Exact scalings by 1/2 and 4, |x|, max(x, 0) and the larger of two non-negative values, in
 // double on the integer pipe (exponent field, sign bit, bit-pattern order), since the FP64 pipe is
 // the scarce one; in single precision the plain arithmetic. A scaling is exact whenever its result
@@ -152,7 +178,7 @@ __device__ __forceinline__ float max_nonneg_r(float a, float b) { return rmax(a,
 // conserved -> primitive: v = m / rho, p = (gamma - 1)(e - rho v^2 / 2 - B^2 / 2)
 template <typename R> __device__ __forceinline__ void cons2prim(const R *u, R *w, R gm1)
 {
-    R irho = R(1) / u[RHO];
+    R irho = rcp_r(u[RHO]);
     w[0] = u[RHO];
     w[1] = u[M1] * irho;
     w[2] = u[M2] * irho;
@@ -390,7 +416,7 @@ __device__ __forceinline__ void riemann(const R *wl, const R *wr, int d, int flu
         const R q = wl[0] * wr[0];
         const int ex = (hi_bits(q) >> 20) & 0x7ff;
         if (ex > 60 && ex < 1990) {
-            const R iq = R(1) / q;
+            const R iq = rcp_nr(q);
             irl = wr[0] * iq;
             irr = wl[0] * iq;
         } else {

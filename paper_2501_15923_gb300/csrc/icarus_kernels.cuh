@@ -312,7 +312,7 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
             for (int v = 1; v < NV; ++v) pre[v] = pre[v - 1] * s[v];
             const int ex = (hi_bits(pre[NV - 1]) >> 20) & 0x7ff;     // biased exponent of the product
             if (ex > 60 && ex < 1990) {
-                TW inv = TW(1) / pre[NV - 1];
+                TW inv = rcp_r(pre[NV - 1]);
 #pragma unroll
                 for (int v = NV - 1; v > 0; --v) {
                     const TW iv = inv * pre[v - 1];     // 1 / s[v]

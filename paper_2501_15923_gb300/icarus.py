@@ -68,7 +68,7 @@ SIGNATURES = {
     "icarus_get_tracer": (C.c_int, [C.c_void_p, C.c_void_p]),
     "icarus_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "icarus_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
-    "icarus_root_check": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
+    "icarus_math_check": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
     "icarus_scales": (C.c_int, [C.c_void_p, C.c_void_p]),
     "icarus_launches_per_step": (C.c_int, [C.c_void_p]),
     "icarus_get_stream": (C.c_void_p, [C.c_void_p]),

@@ -138,10 +138,10 @@ def test_closure_wait_selftest_rejects_bad_arguments(ic):
         assert lib.icarus_closure_wait_selftest(arrive, limit) == EINVAL
 
 
-def test_root_check_rejects_bad_arguments(ic):
+def test_math_check_rejects_bad_arguments(ic):
     lib = ic.load()
     x = (C.c_double * 2)(1.0, 4.0)
-    y = (C.c_double * 4)()
-    assert lib.icarus_root_check(0, x, y) == EINVAL
-    assert lib.icarus_root_check(2, None, y) == EINVAL
-    assert lib.icarus_root_check(2, x, None) == EINVAL
+    y = (C.c_double * 8)()
+    assert lib.icarus_math_check(0, x, y) == EINVAL
+    assert lib.icarus_math_check(2, None, y) == EINVAL
+    assert lib.icarus_math_check(2, x, None) == EINVAL
