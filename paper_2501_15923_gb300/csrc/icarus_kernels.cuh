@@ -598,19 +598,36 @@ __global__ void __launch_bounds__(256) k_cfl(Params P, const TW *__restrict__ W)
 // the update of one interior cell (i, j, k) from its primitives w, the fluxes through its six
 // faces (lower / upper along r, theta, phi) and div B at its six neighbours; returns the cell's
 // CFL signal speed after a second stage (0 otherwise)
-// area / volume factors of the flux divergence of cell (i, j, k)
+// area / volume factors of the flux divergence of cell (i, j, k); in FP64 the area factors are
+// multiplied by 1/V once per cell, so that a field costs one product and four fused
+// multiply-adds on the FP64 pipe instead of three products and three
 template <typename TW> struct DivFactors {
     TW am, ap, iv, bm, bp, jv, kv;
     __device__ __forceinline__ DivFactors(const MetricsT<TW> &m, int ip, int jp)
         : am(m.a1[ip]), ap(m.a1[ip + 1]), iv(m.iv1[ip]), bm(m.a2[jp]), bp(m.a2[jp + 1]),
-          jv(m.q1[ip] * m.iv2[jp]), kv(m.q1[ip] * m.q2[jp] * m.iv3) {}
+          jv(m.q1[ip] * m.iv2[jp]), kv(m.q1[ip] * m.q2[jp] * m.iv3)
+    {
+        if constexpr (sizeof(TW) == 8) {
+            am *= iv;
+            ap *= iv;
+            bm *= jv;
+            bp *= jv;
+        }
+    }
     // -(1/V) sum_d (A+ F+ - A- F-) of one field
     __device__ __forceinline__ TW div(TW fr0, TW fr1, TW ft0, TW ft1, TW fp0, TW fp1) const
     {
-        TW l = -(ap * fr1 - am * fr0) * iv;
-        l -= (bp * ft1 - bm * ft0) * jv;
-        l -= (fp1 - fp0) * kv;
-        return l;
+        if constexpr (sizeof(TW) == 8) {
+            TW l = fma(am, fr0, -(ap * fr1));
+            l = fma(bm, ft0, l);
+            l = fma(-bp, ft1, l);
+            return fma(-kv, fp1 - fp0, l);
+        } else {
+            TW l = -(ap * fr1 - am * fr0) * iv;
+            l -= (bp * ft1 - bm * ft0) * jv;
+            l -= (fp1 - fp0) * kv;
+            return l;
+        }
     }
 };
 
