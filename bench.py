@@ -140,8 +140,9 @@ def kernel_source_hash():
 
 
 def profile_numbers():
-    """FP64 flops/face and DRAM bytes/face of the flux kernels from the committed ncu summary; the
-    traffic is dropped when the kernel sources changed since the capture."""
+    """FP64 flops/face and DRAM bytes/face of the flux kernels from the committed ncu summary; both
+    are dropped when the kernel sources changed since the capture (the counts would be another
+    kernel's)."""
     try:
         txt = open(PROFILE_SUMMARY).read()
     except OSError:
@@ -158,7 +159,7 @@ def profile_numbers():
     dram = {d: float(vals[f"dram_bytes_per_face_{d[0]}"]) for d in ("r", "theta", "phi")
             if f"dram_bytes_per_face_{d[0]}" in vals}
     if vals.get("kernel_hash") != kernel_source_hash():
-        dram = {}
+        return {}, {}
     return flops, dram
 
 
@@ -389,7 +390,8 @@ def main(argv=None):
                 "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2070 MHz (derived; measured DFMA rate 594 G/s)"}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "note": "flop count of this kernel not profiled yet"}
+                "frac": None, "traffic": None,
+                "note": "flop count of this kernel not profiled yet (or its sources changed since the capture)"}
     bytes_cell_update = 128 if args.precision in ("f64", "mixed") else 64
     roof["hbm_view"] = {"algorithmic_bytes_per_cell_update": bytes_cell_update,
                         "achieved_gbs": value / world * 1e6 * bytes_cell_update / 1e9, "peak_gbs": hbm_peak,

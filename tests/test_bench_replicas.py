@@ -40,3 +40,14 @@ def test_replica_aggregation_gloo_two_ranks():
     for rank, ms, value in res:
         assert ms == 250.0                                  # max over ranks
         assert abs(value - 2 * 1000 * 10 / 0.25 / 1e6) < 1e-12
+
+
+def test_profile_counts_dropped_when_kernel_sources_change(monkeypatch):
+    """The roofline's flop and DRAM counts per face come from the committed ncu summary only while
+    the flux kernels' sources hash to the value recorded there."""
+    import bench
+    flops, dram = bench.profile_numbers()
+    if flops:
+        assert set(flops) == {"r", "theta", "phi"} and all(v > 0 for v in flops.values())
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.profile_numbers() == ({}, {})
