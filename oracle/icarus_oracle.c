@@ -874,6 +874,9 @@ void orc_fill_ghosts(orc_t *o, double tau) { fill_ghosts(o, o->U, tau); }
 
 double orc_cfl_dt(orc_t *o) { return cfl_dt(o, o->U); }
 
+/* the floors of one stage end applied to the interior state (test access; counts into floor_hits) */
+void orc_apply_floors(orc_t *o) { apply_floors(o, o->U); }
+
 /* the n + 1 interior edges of direction d */
 void orc_edges(const orc_t *o, int d, double *out)
 {

@@ -21,7 +21,9 @@ NG = 2
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
+        # ORACLE_SO names another build of the same sources (the mutation tests load copies of
+        # the oracle with one planted mistake); by default the in-tree library is built and loaded
+        _lib = C.CDLL(os.environ.get("ORACLE_SO") or _build.build())
         P, D, I, L = C.c_void_p, C.c_double, C.c_int, C.c_long
         sig = {
             "orc_create": (P, [P, P, D, D, P, P]),
@@ -39,6 +41,7 @@ def lib():
             "orc_get_state_padded": (None, [P, P]),
             "orc_fill_ghosts": (None, [P, D]),
             "orc_cfl_dt": (D, [P]),
+            "orc_apply_floors": (None, [P]),
             "orc_step": (D, [P, D]),
             "orc_residual": (None, [P, D, D, P]),
             "orc_divb": (None, [P, P]),
@@ -132,6 +135,10 @@ class Oracle:
 
     def cfl_dt(self) -> float:
         return lib().orc_cfl_dt(self.h)
+
+    def apply_floors(self):
+        """The density and pressure floors of a stage end, applied to the interior state."""
+        lib().orc_apply_floors(self.h)
 
     def step(self, dt_max: float = 0.0) -> float:
         dt = lib().orc_step(self.h, float(dt_max))

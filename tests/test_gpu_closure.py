@@ -46,12 +46,18 @@ def test_layer_forward_and_gradients_match_oracle(ic, C, Oc, act, shape):
     w = bf16(rng.standard_normal((Oc, 27, C)) * 0.1)
     b = bf16(rng.standard_normal(Oc) * 0.1)
     g = bf16(rng.standard_normal((n3, n2, n1, Oc)))
-    y, dx, dw, db = ic.icarus_conv3d_layer(x, w, b, g, act)
     yo = O.conv3d_forward(x.astype(np.float64), w.astype(np.float64), b.astype(np.float64), act)
-    # the oracle's ReLU mask is taken from the GPU's activation (values within FP32 rounding of 0
-    # could otherwise fall on different sides of it)
-    dxo, dwo, dbo = O.conv3d_backward(x.astype(np.float64), w.astype(np.float64), y.astype(np.float64),
-                                      g.astype(np.float64), act)
+    if act:
+        # a pre-activation within the FP32 accumulation's rounding of 0 may fall on either side of
+        # the ReLU on the GPU; those outputs get a zero gradient on both sides (so the mask there
+        # does not matter), and their number is bounded explicitly
+        zo = O.conv3d_forward(x.astype(np.float64), w.astype(np.float64), b.astype(np.float64), 0)
+        edge = np.abs(zo) <= 1e-5 * np.abs(zo).max()
+        assert edge.sum() <= 1e-3 * edge.size + 2, edge.sum()
+        g = np.where(edge, np.float32(0), g).astype(np.float32)
+    y, dx, dw, db = ic.icarus_conv3d_layer(x, w, b, g, act)
+    # the oracle's backward pass takes its own forward output (its ReLU mask), nothing of the GPU's
+    dxo, dwo, dbo = O.conv3d_backward(x.astype(np.float64), w.astype(np.float64), yo, g.astype(np.float64), act)
     for got, ref in ((y, yo), (dx, dxo), (dw, dwo), (db, dbo)):
         scale = np.abs(ref).max()
         assert np.abs(got - ref).max() <= 2e-5 * scale, (np.abs(got - ref).max(), scale)

@@ -1,0 +1,118 @@
+"""Planted mistakes in the oracle, each caught by the pin that names it (CPU only).
+
+A pin is only worth what it catches. Each case below copies the oracle's C sources, plants one
+plausible mistake by a textual replacement (the replaced text must occur exactly once), compiles
+the copy with the oracle's flags and runs the named pins against it in a child process
+(ORACLE_SO points the oracle wrapper at the copy). The pins must fail there, and the same pins
+pass against the real oracle in the main suite. The in-tree oracle is never modified.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+from oracle import build as obuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (name, replaced text, replacement, -k expression selecting the pins that must catch it)
+MUTANTS = [
+    ("fast speed from |B|^2 instead of B_n^2",
+     "    double bn2 = w[5 + d] * w[5 + d] / w[0];\n", "    double bn2 = b2;\n",
+     "P13_cfl_dt_uniform_state_cartesian or P13_riemann_dissipation"),
+    ("phi width without sin(theta)",
+     "    return ctr(o, 0, i) * sin(ctr(o, 1, j)) * w;\n", "    return ctr(o, 0, i) * w;\n",
+     "P13_cfl_dt_spherical_widths"),
+    ("theta width from the inner radial edge instead of the centre",
+     "    if (d == 1) return ctr(o, 0, i) * w;\n", "    if (d == 1) return lo(o, 0, i) * w;\n",
+     "P13_cfl_dt_spherical_widths"),
+    ("CFL signal speed without |v_d|",
+     "s += (fabs(w[1 + d]) + fast_speed(o, w, d)) / width(o, d, i, j, k);",
+     "s += fast_speed(o, w, d) / width(o, d, i, j, k);",
+     "P13_cfl_dt_uniform_state_cartesian"),
+    ("TVDLF dissipation speed without |v_n|",
+     "double c = fmax(fabs(wl[1 + d]) + cl, fabs(wr[1 + d]) + cr);", "double c = fmax(cl, cr);",
+     "P13_riemann_dissipation"),
+    ("pressure floor that does not rebuild the energy",
+     "                    w[4] = o->p_floor;\n                    prim2cons(o, w, u);\n",
+     "                    w[4] = o->p_floor;\n",
+     "P14_floors"),
+    ("density floor not counted",
+     "if (u[RHO] < o->rho_floor) { u[RHO] = o->rho_floor; hits++; }",
+     "if (u[RHO] < o->rho_floor) { u[RHO] = o->rho_floor; }",
+     "P14_floors"),
+    ("density floor that keeps the velocity instead of the momentum",
+     "if (u[RHO] < o->rho_floor) { u[RHO] = o->rho_floor; hits++; }",
+     "if (u[RHO] < o->rho_floor) { double f = o->rho_floor / u[RHO]; u[RHO] = o->rho_floor; "
+     "u[M1] *= f; u[M2] *= f; u[M3] *= f; hits++; }",
+     "P14_floors"),
+    ("van Leer slope halved",
+     "if (lim == LIM_VANLEER) return 2.0 * a * b / (a + b);",
+     "if (lim == LIM_VANLEER) return a * b / (a + b);",
+     "test_P4_linear_waves_second_order and 1-0-0"),
+    ("energy flux without the -B_n (B.v) term",
+     "    f[EN] = (u[EN] + ptot) * vn - bn * bv;\n", "    f[EN] = (u[EN] + ptot) * vn;\n",
+     "test_P4_linear_waves_second_order and 2-0-0 or P3_brio_wu"),
+    ("geometric hoop term of m_theta with the wrong sign",
+     "+ cot * (rho * vp * vp - bp * bp)) / r;", "- cot * (rho * vp * vp - bp * bp)) / r;",
+     "P1b"),
+    ("Coriolis force without its factor 2",
+     "F[c] = rho * cen[c] + 2.0 * rho * cor[c];", "F[c] = rho * cen[c] + rho * cor[c];",
+     "P7"),
+    ("work of gravity dropped from the energy",
+     "                        Lc[EN] -= rho * vr * g;\n", "",
+     "P5_P7_wind_residual_second_order"),
+    ("Linde term with the wrong sign",
+     "Lc[B1] += gr[0]; Lc[B2] += gr[1]; Lc[B3] += gr[2];",
+     "Lc[B1] -= gr[0]; Lc[B2] -= gr[1]; Lc[B3] -= gr[2];",
+     "P6_linde"),
+    ("map time weight measured from the later map",
+     "    double ww = (tau - o->tm[m]) / (o->tm[m + 1] - o->tm[m]);\n",
+     "    double ww = (o->tm[m + 1] - tau) / (o->tm[m + 1] - o->tm[m]);\n",
+     "P8_boundary_time_interpolation"),
+    ("HLLD double-star energy with the wrong sign",
+     "uss[EN] = us[s][EN] + (s ? 1.0 : -1.0) * sq * (vbs - vbss) * sg;",
+     "uss[EN] = us[s][EN] - (s ? 1.0 : -1.0) * sq * (vbs - vbss) * sg;",
+     "P3c"),
+    ("HLLD double-star field weights swapped",
+     "bss[c] = (sqL * bt[1][c] + sqR * bt[0][c]", "bss[c] = (sqL * bt[0][c] + sqR * bt[1][c]",
+     "P3c or P3b"),
+    ("band cells as wide inside the band as outside",
+     "    else if (s <= sB) x = A + (s - sA) / f;\n", "    else if (s <= sB) x = A + (s - sA);\n",
+     "P11_band_edges"),
+    ("GLM psi star state with the wrong sign of the jump",
+     "double ps = 0.5 * (pl + pr) - 0.5 * ch * (brr - bl);", "double ps = 0.5 * (pl + pr) + 0.5 * ch * (brr - bl);",
+     "P12_glm_standing_wave"),
+    ("GLM psi flux c_h instead of c_h^2",
+     "o->FP[d][ib] = ch * ch * bs;", "o->FP[d][ib] = ch * bs;",
+     "P12_glm_standing_wave"),
+]
+
+
+@pytest.fixture(scope="module")
+def mutant_dir(tmp_path_factory):
+    return tmp_path_factory.mktemp("oracle_mutants")
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(mutant_dir, name, old, new, pins):
+    d = mutant_dir / name.replace(" ", "_").replace("/", "_").replace("|", "").replace("^", "")
+    d.mkdir()
+    srcs = []
+    for s in obuild.SRCS:
+        dst = d / os.path.basename(s)
+        shutil.copyfile(s, dst)
+        srcs.append(str(dst))
+    main = d / "icarus_oracle.c"
+    text = main.read_text()
+    assert text.count(old) == 1, f"the text to replace occurs {text.count(old)} times"
+    main.write_text(text.replace(old, new))
+    so = obuild.compile_so(srcs, str(d / "liboracle_mutant.so"))
+    env = dict(os.environ, ORACLE_SO=so, OMP_NUM_THREADS="4")
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
+                        "-p", "no:cacheprovider", "-k", pins], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    tail = r.stdout[-2000:]
+    assert r.returncode == 1 and " failed" in tail, f"pins [{pins}] did not catch it:\n{tail}"

@@ -21,7 +21,7 @@ from oracle.oracle import Oracle, cons_from_prim, prim_from_cons
 from paper_2501_15923_gb300 import inputs as I
 
 from . import exact
-from .helpers import cart_grid, centres, l1, opts, sph_grid
+from .helpers import cart_grid, centres, edges, l1, opts, sph_grid
 
 P, C, R, D, F = I.BC_PERIODIC, I.BC_CONT, I.BC_REFLECT, I.BC_DRIVEN, I.BC_FIXED
 T0 = I.AU / 1e5                       # code time unit, s
@@ -1042,3 +1042,168 @@ def test_P12_glm_uniform_psi_balanced_on_the_sphere():
     U, _ = o.get_state()
     assert np.abs(U[5:8]).max() < 1e-12
     np.testing.assert_allclose(o.get_psi(), 0.3, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------------
+# P13 fast magnetosonic speed, the CFL time step and the size of the Riemann dissipation.
+# The fast speed is pinned to the spectrum of the ideal-MHD equations written in primitive
+# variables for one direction (density, the three velocities, pressure, the two transverse field
+# components; the normal field is constant in 1-D): its seven eigenvalues are v_n, v_n +- c_a,
+# v_n +- c_s and v_n +- c_f, so the largest one minus v_n is c_f. numpy's eigenvalue routine works
+# on that matrix, which holds none of the closed form the oracle evaluates.
+
+def mhd_jacobian(w, d, gamma):
+    """Primitive-variable matrix A of dW/dt + A dW/dx_d = 0, W = (rho, v_n, v_t1, v_t2, p, B_t1,
+    B_t2) for the primitive state w = (rho, v1, v2, v3, p, B1, B2, B3) along direction d."""
+    t1, t2 = [c for c in range(3) if c != d]
+    rho, p = w[0], w[4]
+    vn, bn = w[1 + d], w[5 + d]
+    b1, b2 = w[5 + t1], w[5 + t2]
+    A = np.zeros((7, 7))
+    A[0, 0], A[0, 1] = vn, rho                                  # continuity
+    A[1, 1], A[1, 4], A[1, 5], A[1, 6] = vn, 1 / rho, b1 / rho, b2 / rho   # normal momentum (grad p_tot)
+    A[2, 2], A[2, 5] = vn, -bn / rho                            # transverse momentum (tension)
+    A[3, 3], A[3, 6] = vn, -bn / rho
+    A[4, 1], A[4, 4] = gamma * p, vn                            # pressure
+    A[5, 1], A[5, 2], A[5, 5] = b1, -bn, vn                     # transverse induction
+    A[6, 1], A[6, 3], A[6, 6] = b2, -bn, vn
+    return A
+
+
+def fast_speed_eig(w, d, gamma):
+    ev = np.linalg.eigvals(mhd_jacobian(w, d, gamma))
+    assert np.abs(ev.imag).max() <= 1e-9 * np.abs(ev).max()    # hyperbolic: a real spectrum
+    return float(ev.real.max() - w[1 + d])
+
+
+OBLIQUE = [  # primitive states (rho, v1, v2, v3, p, B1, B2, B3), code units; B oblique to every axis
+    np.array([1.3, 0.4, -0.7, 0.2, 0.9, 1.1, -0.6, 0.8]),
+    np.array([0.2, -2.0, 0.5, 1.5, 0.05, 0.3, 1.7, -1.2]),     # low beta, field-dominated
+    np.array([5.0, 0.1, 0.1, -0.3, 4.0, 0.05, -0.02, 0.07]),   # high beta, nearly hydrodynamic
+]
+
+
+def test_P13_eigen_harness_reduces_to_textbook_limits():
+    """The eigenvalue harness itself: with B = 0 its largest speed is the sound speed, with p = 0 and
+    B along the direction it is the Alfven speed |B_n| / sqrt(rho)."""
+    g = 5.0 / 3.0
+    w = np.array([2.0, 0.3, 0.0, 0.0, 1.5, 0.0, 0.0, 0.0])
+    assert abs(fast_speed_eig(w, 0, g) - math.sqrt(g * 1.5 / 2.0)) <= 1e-13
+    w = np.array([2.0, 0.0, 0.0, 0.0, 1e-30, 0.0, 0.0, 0.9])
+    assert abs(fast_speed_eig(w, 2, g) - 0.9 / math.sqrt(2.0)) <= 1e-9
+
+
+@pytest.mark.parametrize("case", range(len(OBLIQUE)))
+def test_P13_cfl_dt_uniform_state_cartesian(case):
+    """dt of a uniform oblique-field state on a Cartesian box with three different cell widths
+    equals CFL / sum_d (|v_d| + c_f,d) / dx_d with c_f,d from the eigenvalues: a fast speed built
+    from |B|^2 instead of B_d^2, a missing |v_d| or a wrong width changes it."""
+    g = cart_grid(6, 5, 4, L=(0.6, 1.5, 0.2))
+    gamma, cfl = 1.5, 0.8
+    o = Oracle(g, gamma, 0.0, opts(cfl=cfl, gravity=0, divb=I.DIVB_NONE))
+    w = OBLIQUE[case]
+    U = cons_from_prim(np.broadcast_to(w[:, None, None, None], (8, 4, 5, 6)).copy(), gamma)
+    o.set_state(U, 0.0)
+    dx = (0.1, 0.3, 0.05)
+    s = sum((abs(w[1 + d]) + fast_speed_eig(w, d, gamma)) / dx[d] for d in range(3))
+    assert abs(o.cfl_dt() - cfl / s) <= 1e-13 * (cfl / s)
+
+
+def test_P13_cfl_dt_spherical_widths():
+    """On a stretched spherical grid reaching close to the poles, with a state that varies from cell
+    to cell, dt is CFL over the largest sum_d (|v_d| + c_f,d) / dx_d, dx = (dr, r_c dtheta,
+    r_c sin(theta_c) dphi) with r_c, theta_c the cell centres, evaluated cell by cell here with the
+    eigenvalue fast speeds and independently built edges. The largest term sits in the cells next
+    to the poles, so a width without sin(theta) is caught, as is r_c taken as an edge."""
+    g = sph_grid(10, 12, 9, (C,) * 4 + (P, P), th=(math.radians(6), math.radians(174)))
+    gamma, cfl = 1.5, 0.7
+    o = Oracle(g, gamma, 0.0, opts(cfl=cfl, gravity=0, divb=I.DIVB_NONE))
+    rng = np.random.default_rng(13)
+    base = np.array([1.0, 2.0, 0.3, 1.4, 0.5, 0.8, 0.4, -0.6])
+    W = base[:, None, None, None] * (1.0 + 0.2 * rng.uniform(-1, 1, (8, g.n3, g.n2, g.n1)))
+    o.set_state(cons_from_prim(W, gamma), 0.0)
+    er, et, ep = (edges(g, d)[2:-2] for d in range(3))
+    rc, tc = 0.5 * (er[:-1] + er[1:]), 0.5 * (et[:-1] + et[1:])
+    smax = 0.0
+    for k in range(g.n3):
+        for j in range(g.n2):
+            for i in range(g.n1):
+                w = W[:, k, j, i]
+                dx = (er[i + 1] - er[i], rc[i] * (et[j + 1] - et[j]), rc[i] * math.sin(tc[j]) * (ep[k + 1] - ep[k]))
+                smax = max(smax, sum((abs(w[1 + d]) + fast_speed_eig(w, d, gamma)) / dx[d] for d in range(3)))
+    assert abs(o.cfl_dt() - cfl / smax) <= 1e-12 * (cfl / smax)
+
+
+@pytest.mark.parametrize("flux", [I.FLUX_TVDLF, I.FLUX_HLL])
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_P13_riemann_dissipation_size(flux, d):
+    """The size of the face flux's dissipation, which the smooth-wave order tests do not see.
+    A contact (equal v, p and B, different rho) moving at u through the face has the same physical
+    flux on both sides up to its mass and energy; with c = |u| + max(c_fL, c_fR) (eigenvalue fast
+    speeds of the two states) TVDLF's mass flux is u (rho_L + rho_R)/2 - c (rho_R - rho_L)/2. For a
+    stationary contact HLL (s_L = -s_R = -c) gives the same -c (rho_R - rho_L)/2."""
+    gamma = 1.5
+    o = Oracle(cart_grid(4), gamma, 0.0, opts(flux=flux, gravity=0, divb=I.DIVB_NONE))
+    for case, u in ((0, 0.0), (1, 0.35), (2, -0.8)):
+        if flux == I.FLUX_HLL and u != 0.0:
+            continue
+        wl = OBLIQUE[case].copy()
+        wl[1:4] = 0.0
+        wl[1 + d] = u
+        wr = wl.copy()
+        wr[0] = 2.7 * wl[0]
+        c = abs(u) + max(fast_speed_eig(wl, d, gamma), fast_speed_eig(wr, d, gamma))
+        f = o.riemann(wl, wr, d)
+        want = u * 0.5 * (wl[0] + wr[0]) - 0.5 * c * (wr[0] - wl[0])
+        assert abs(f[0] - want) <= 1e-13 * (abs(want) + c * wr[0]), (case, f[0], want)
+
+
+# ---------------------------------------------------------------------------------------------
+# P14 floors (reading 17): after a stage, a cell with rho < rho_floor takes rho = rho_floor with its
+# momentum and field kept; then a cell whose recovered pressure is below p_floor takes p = p_floor
+# with rho, velocity and field kept (its total energy rebuilt). Every reset is counted once.
+
+def test_P14_floors_closed_form_and_counts():
+    g = cart_grid(7, 6, 5)
+    gamma, rho_f, p_f = 1.5, 1e-3, 1e-2
+    o = Oracle(g, gamma, 0.0, opts(gravity=0, divb=I.DIVB_NONE, rho_floor=rho_f, p_floor=p_f))
+    rng = np.random.default_rng(14)
+    W = np.empty((8, g.n3, g.n2, g.n1))
+    W[0] = rng.uniform(0.5, 2.0, W.shape[1:])
+    W[1:4] = rng.uniform(-1, 1, (3,) + W.shape[1:])
+    W[4] = rng.uniform(0.1, 1.0, W.shape[1:])
+    W[5:8] = rng.uniform(-1, 1, (3,) + W.shape[1:])
+    U = cons_from_prim(W, gamma)
+    cells = rng.permutation(g.ncell)
+    low_p, low_rho, both = cells[:23], cells[23:35], cells[35:41]
+    Uf = U.reshape(8, -1)
+    ke = 0.5 * (Uf[1:4] ** 2).sum(0) / Uf[0]
+    me = 0.5 * (Uf[5:8] ** 2).sum(0)
+    Uf[4, low_p] = ke[low_p] + me[low_p] - rng.uniform(0.0, 0.3, low_p.size)     # p < 0
+    Uf[4, low_p[:5]] = ke[low_p[:5]] + me[low_p[:5]] + 0.5 * p_f / (gamma - 1)    # 0 < p < p_floor
+    Uf[0, low_rho] = rng.uniform(1e-5, 0.9e-3, low_rho.size)                       # rho < rho_floor
+    Uf[0, both] = 2e-4
+    Uf[4, both] = 0.5 * (Uf[1:4, both] ** 2).sum(0) / 2e-4 + me[both] - 0.1       # and p < 0
+    U0 = Uf.reshape(U.shape).copy()
+    o.set_state(U0, 0.0)
+    o.apply_floors()
+    Ua, _ = o.get_state()
+    A, B = U0.reshape(8, -1), Ua.reshape(8, -1)
+    rho_new = np.maximum(A[0], rho_f)
+    rho_hit = A[0] < rho_f
+    p_mid = (gamma - 1) * (A[4] - 0.5 * (A[1:4] ** 2).sum(0) / rho_new - 0.5 * (A[5:8] ** 2).sum(0))
+    p_hit = p_mid < p_f
+    assert o.floor_hits == int(rho_hit.sum() + p_hit.sum())
+    assert rho_hit.sum() == low_rho.size + both.size and p_hit.sum() >= low_p.size + both.size
+    untouched = ~(rho_hit | p_hit)
+    assert np.array_equal(A[:, untouched], B[:, untouched])          # bit for bit
+    assert np.array_equal(B[0], rho_new)
+    assert np.array_equal(A[5:8], B[5:8])
+    assert np.array_equal(A[1:4, ~p_hit], B[1:4, ~p_hit])          # the density floor keeps m
+    v_in, v_out = A[1:4, p_hit] / rho_new[p_hit], B[1:4, p_hit] / B[0, p_hit]
+    assert np.all(np.abs(v_out - v_in) <= 4e-16 * np.abs(v_in))     # the pressure floor keeps v
+    Wb = prim_from_cons(Ua, gamma).reshape(8, -1)
+    scale = B[4, p_hit]
+    assert np.all(np.abs(Wb[4, p_hit] - p_f) <= 1e-12 * scale * (gamma - 1))
+    keep_e = rho_hit & ~p_hit
+    assert np.array_equal(A[4, keep_e], B[4, keep_e])
