@@ -49,7 +49,9 @@ enum {
     ICARUS_ENOMEM = -3,      /* device allocation failed */
     ICARUS_ECUDA = -4,       /* a CUDA runtime call failed */
     ICARUS_ENONFINITE = -5,  /* the solution became non-finite (sticky) */
-    ICARUS_ETIMEOUT = -6     /* a bounded device wait gave up (batched form, tensor-core closure) */
+    ICARUS_ETIMEOUT = -6,    /* a bounded device wait gave up (batched form, tensor-core closure) */
+    ICARUS_EFLOOR = -7       /* a density or pressure floor acted while options.strict_floors is set
+                                (sticky; ENONFINITE takes precedence when both occurred) */
 };
 
 enum { ICARUS_BC_PERIODIC = 0, ICARUS_BC_CONT = 1, ICARUS_BC_REFLECT = 2, ICARUS_BC_DRIVEN = 3 };
@@ -103,7 +105,10 @@ typedef struct {
     icarus_free_fn free;   /* matching free (NULL: cudaFree) */
     void *alloc_user;      /* passed to alloc / free */
     int fused;             /* 1: one fused stage kernel (fluxes, div B, update) instead of the separate
-                              kernels, FP32 and MIXED only (slower on GB300; see the design notes) */
+                              kernels, FP32 and MIXED only. It keeps the face fluxes on chip, but on
+                              GB300 it is about 2x slower than the separate kernels: they are not
+                              bandwidth-bound, and the fused kernel runs at half their occupancy and
+                              recomputes each face's neighbouring slopes */
     int init_vphi;         /* initial state's v_phi (Sect. 2.1 names none): ICARUS_IC_COROTATING
                               (0: at rest in the co-rotating frame) or ICARUS_IC_INERTIAL_RADIAL
                               (1: v_phi = -Omega r sin(theta), the inertially radial flow, parallel
@@ -120,6 +125,10 @@ typedef struct {
                               to [0, rho] after each stage; starts at c = 0 (icarus_set_tracer).
                               Not with the fused stage kernel or the batched form. */
     double glm_alpha;      /* divb = ICARUS_DIVB_GLM: psi damping constant (>= 0; 0.1 is usual) */
+    int strict_floors;     /* 1: a floor activation is an error: the step still applies the floor (and
+                              counts it), and the context's sticky status becomes ICARUS_EFLOOR, which
+                              the synchronising calls and later icarus_step calls return; 0: floors
+                              are only counted (icarus_status) */
 } icarus_options;
 
 #define ICARUS_IC_COROTATING 0
@@ -151,7 +160,10 @@ int icarus_set_boundary(icarus_ctx *ctx, int n_maps, const double *t_maps, const
 /* Advance n >= 0 time steps (each: dt from the CFL bound, SSP-RK2 with the boundary refilled at
  * each stage time, probes recorded at the new time). Asynchronous on the context stream; the
  * steps run as replays of a captured CUDA graph. ESTATE before the first set_boundary /
- * set_state. Returns the sticky status of earlier steps without synchronising. */
+ * set_state. Returns, without synchronising, the sticky status of the steps that have completed
+ * on the device (each step's last kernel copies the status word into host-mapped memory):
+ * ENONFINITE or EFLOOR, and then launches nothing. Steps still in flight report at a later call;
+ * icarus_set_state clears the status. */
 int icarus_step(icarus_ctx *ctx, int n);
 
 /* Probe sampling (Sect. 2). traj[n_probes][n_knots][4] = (t s, r m, lat rad, lon rad in the
@@ -207,7 +219,17 @@ int icarus_time(icarus_ctx *ctx, double *t, double *dt);
  * 1 / x[i]. Synchronous; a temporary device buffer. EINVAL for n outside [1, 2^24] or NULL. */
 int icarus_math_check(int n, const double *x, double *y);
 
-/* Sticky status (0 or ENONFINITE) and the number of floor activations. Synchronous. */
+/* Measured fused multiply-add rate of the current GPU (not part of the paper's method; the
+ * denominator of the arithmetic roofline of the FP64 kernels, whose bound is the FP64 pipe):
+ * blocks_per_sm x SMs blocks of 256 threads, each thread `chains` (1, 4, 8 or 16) independent
+ * recurrences x <- x a + b in double (precision = ICARUS_FP64) or single (ICARUS_FP32) for `iters`
+ * rounds (a multiple of 4). *tflops = 2 x threads x chains x iters / duration of the timed launch
+ * (CUDA events, after one warm-up launch), *ms that duration. chains = 1 gives the dependent,
+ * latency-bound rate. Synchronous; creates and destroys its own stream. */
+int icarus_fma_rate(int precision, int chains, int blocks_per_sm, long long iters, double *tflops, double *ms);
+
+/* Sticky status (0, ENONFINITE or, with options.strict_floors, EFLOOR) and the number of floor
+ * activations. Synchronous. */
 int icarus_status(icarus_ctx *ctx, long long *floor_hits);
 
 /* Code-unit scales: s[0] = t0 s, s[1] = p0 Pa, s[2] = B0 T, s[3] = Omega in rad per t0,
@@ -343,12 +365,15 @@ int icarus_conv3d_layer(int n1, int n2, int n3, int C, int O, int act, const flo
  * step (a framework's fixed pool, a real-time loop that forbids allocation after start-up, an
  * embedder that only owns its own buffers). It computes the same quantity as the dt that
  * icarus_set_state / icarus_time report: CFL / max over cells of sum_d (|v_d| + c_f,d) / dx_d.
- *   grid   : the grid (as for icarus_init); at most ICARUS_NOALLOC_MAX_CELLS interior cells,
- *            otherwise EINVAL and nothing is launched
+ *   grid   : the grid (as for icarus_init, refined band included; a grid icarus_init rejects is
+ *            rejected here with the same EINVAL message); at most ICARUS_NOALLOC_MAX_CELLS
+ *            interior cells, otherwise EINVAL; nothing is launched after an EINVAL
  *   gamma  : adiabatic index; cfl: Courant number in (0, 1]
  *   U      : DEVICE pointer, interior conserved state [8][n3][n2][n1] doubles in code units
  *            (the layout of icarus_get_state)
- *   dt     : DEVICE pointer to one double that receives the time step (code units)
+ *   dt     : DEVICE pointer to one double that receives the time step (code units), or -1.0
+ *            when any cell's signal speed is not finite (a NaN or inf in the state; there is no
+ *            status word here, so the sentinel is the only signal)
  *   stream : cudaStream_t to run on (NULL: the legacy default stream); the call returns
  *            without synchronising
  * Scratch: the reduction's partial maxima and its completion counter live in one file-scope
@@ -358,7 +383,8 @@ int icarus_conv3d_layer(int n1, int n2, int n3, int C, int O, int act, const flo
  * cudaGetSymbolAddress while that device is current; make that first call before any stream
  * capture. All calls on a device share the array and its counter (cleared at the start of every
  * call), so calls that overlap on the GPU (different streams, concurrently) race and must be
- * ordered by the caller. */
+ * ordered by the caller. The array's first 256 bytes hold the counter and the non-finite flag; the
+ * call's last block clears both again. */
 int icarus_cfl_dt_noalloc(const icarus_grid *grid, double gamma, double cfl, const double *U, double *dt,
                           void *stream);
 

@@ -39,6 +39,13 @@ int fail(int code, const char *fmt, ...)
         if (e_ != cudaSuccess) return fail(ICARUS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
     } while (0)
 
+// the error of a non-zero status word (bit 0: non-finite state, bit 1: a floor in strict mode)
+int status_fail(int status)
+{
+    if (status & 1) return fail(ICARUS_ENONFINITE, "the solution became non-finite");
+    return fail(ICARUS_EFLOOR, "a density or pressure floor acted (options.strict_floors)");
+}
+
 }  // namespace
 
 namespace icarus {
@@ -104,16 +111,8 @@ void drop_graph(icarus_ctx *c)
 // from the inner edge reaches i / n1 of the total (ghost edges continue the outer spacing)
 double band_edge(const icarus_grid &g, int i)
 {
-    if (i == 0) return g.x1min;
-    if (i == g.n1) return g.x1max;
-    const bool lg = g.geometry == ICARUS_GEOM_SPHERICAL && g.stretch;
-    auto u = [lg](double r) { return lg ? log(r) : r; };
-    const double f = (double)g.band_refine;
-    const double u0 = u(g.x1min), ua = u(g.band_lo), ub = u(g.band_hi), u1 = u(g.x1max);
-    const double s = ((u1 - u0) + (f - 1.0) * (ub - ua)) * i / g.n1;   // density integral up to edge i
-    const double s_in = ua - u0, s_out = s_in + f * (ub - ua);         // ... at the band's two ends
-    const double x = s <= s_in ? u0 + s : (s <= s_out ? ua + (s - s_in) / f : ub + (s - s_out));
-    return lg ? exp(x) : x;
+    return band_edge_at(g.n1, g.x1min, g.x1max, g.band_lo, g.band_hi, g.band_refine,
+                        g.geometry == ICARUS_GEOM_SPHERICAL && g.stretch, i);
 }
 
 // edges of direction d at padded edge index e (cell i has lower edge i, i in [-2, n+2])
@@ -318,6 +317,10 @@ int first_dt(icarus_ctx *c)
     return ICARUS_OK;
 }
 
+}  // namespace
+
+namespace icarus {
+// the grids every entry point that takes an icarus_grid accepts (EINVAL with a message otherwise)
 int check_grid(const icarus_grid *g)
 {
     if (g->n1 < 1 || g->n2 < 1 || g->n3 < 1) return fail(ICARUS_EINVAL, "cell counts must be >= 1");
@@ -346,8 +349,7 @@ int check_grid(const icarus_grid *g)
     }
     return ICARUS_OK;
 }
-
-}  // namespace
+}  // namespace icarus
 
 extern "C" {
 
@@ -362,8 +364,8 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     if (!(opts->cfl > 0.0 && opts->cfl <= 1.0)) return fail(ICARUS_EINVAL, "cfl must be in (0, 1]");
     if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 2 || opts->divb < 0 || opts->divb > 2 ||
         opts->init_vphi < 0 || opts->init_vphi > 1 || opts->cme_model < 0 || opts->cme_model > 1 ||
-        opts->tracer < 0 || opts->tracer > 1)
-        return fail(ICARUS_EINVAL, "bad limiter / flux / divb / init_vphi / cme_model / tracer option");
+        opts->tracer < 0 || opts->tracer > 1 || opts->strict_floors < 0 || opts->strict_floors > 1)
+        return fail(ICARUS_EINVAL, "bad limiter / flux / divb / init_vphi / cme_model / tracer / strict_floors option");
     if (opts->precision < 0 || opts->precision > 2) return fail(ICARUS_EINVAL, "bad precision");
     if (opts->fused && opts->flux == ICARUS_FLUX_HLLD)
         return fail(ICARUS_EINVAL, "the fused stage kernel supports the TVDLF and HLL fluxes only");
@@ -397,6 +399,7 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     P.gamma = gamma;
     P.divb_coef = opts->divb_coef; P.rho_floor = opts->rho_floor; P.p_floor = opts->p_floor;
     P.glm_alpha = opts->glm_alpha;
+    P.strict_floors = opts->strict_floors;
     c->t0 = AU / V0;
     const double rho0 = MP * N0;
     c->p0 = rho0 * V0 * V0;
@@ -463,6 +466,15 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     }
     P.partial = c->partial;
     P.sc = c->sc;
+    // host-mapped status word: each step's last kernel copies the status there, so icarus_step can
+    // report it without synchronising
+    if (cudaHostAlloc((void **)&c->hstatus, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+        c->hstatus = nullptr;
+        icarus_destroy(c);
+        return fail(ICARUS_ENOMEM, "host-mapped status allocation failed");
+    }
+    *(volatile int *)c->hstatus = 0;
+    CK(cudaHostGetDevicePointer((void **)&P.hstatus, c->hstatus, 0));
     Scalars s0{};
     s0.cfl = opts->cfl;
     CK(cudaMemsetAsync(c->U, 0, NV * nt * ts, c->stream));
@@ -579,6 +591,11 @@ int icarus_step(icarus_ctx *c, int n)
     if (n < 0) return fail(ICARUS_EINVAL, "n must be >= 0");
     if (!c->have_state) return fail(ICARUS_ESTATE, "no state: call icarus_set_boundary or icarus_set_state first");
     if (c->grid.bc[0] == ICARUS_BC_DRIVEN && !c->have_boundary) return fail(ICARUS_ESTATE, "DRIVEN boundary without maps");
+    // sticky status of the steps completed so far (host-mapped copy; no synchronisation)
+    if (c->hstatus) {
+        const int st = *(volatile int *)c->hstatus;
+        if (st) return status_fail(st);
+    }
     if (!c->graph) {
         int rc = build_graph(c);
         if (rc) return rc;
@@ -634,7 +651,7 @@ int icarus_sample(icarus_ctx *c, int n_probes, int n_knots, const double *traj, 
         c->ring_tail = tail + nrec;
         if (n_written) *n_written = (int)nrec;
     }
-    if (s.status & 1) return fail(ICARUS_ENONFINITE, "the solution became non-finite");
+    if (s.status) return status_fail(s.status);
     return ICARUS_OK;
 }
 
@@ -645,6 +662,7 @@ int icarus_destroy(icarus_ctx *c)
     drop_graph(c);
     dfree_all(c);
     if (c->hstage) cudaFreeHost(c->hstage);
+    if (c->hstatus) cudaFreeHost(c->hstatus);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return ICARUS_OK;
@@ -662,7 +680,7 @@ int icarus_get_state(icarus_ctx *c, double *U, double *t)
     CK(cudaMemcpyAsync(&s, c->sc, sizeof s, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (t) *t = s.t;
-    if (s.status & 1) return fail(ICARUS_ENONFINITE, "the solution became non-finite");
+    if (s.status) return status_fail(s.status);
     return ICARUS_OK;
 }
 
@@ -681,6 +699,7 @@ int icarus_set_state(icarus_ctx *c, const double *U, double t)
     s.t = t;
     s.status = 0;
     s.done = 0;
+    if (c->hstatus) *(volatile int *)c->hstatus = 0;
     CK(cudaMemcpyAsync(c->sc, &s, sizeof s, cudaMemcpyHostToDevice, c->stream));
     if (c->opts.tracer) c->ops.tracer_set(P, nullptr, c->U, c->T, c->C, c->stream);   // keep rho c, c = rho c / rho
     c->have_state = true;
@@ -799,7 +818,7 @@ int icarus_status(icarus_ctx *c, long long *floor_hits)
     CK(cudaMemcpyAsync(&s, c->sc, sizeof s, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (floor_hits) *floor_hits = (long long)s.floor_hits;
-    if (s.status & 1) return fail(ICARUS_ENONFINITE, "the solution became non-finite");
+    if (s.status) return status_fail(s.status);
     return ICARUS_OK;
 }
 

@@ -24,6 +24,7 @@ struct icarus_ctx {
     double *maps = nullptr, *tmaps = nullptr, *cme = nullptr, *traj = nullptr, *ring = nullptr;
     size_t maps_cap = 0, tmaps_cap = 0, cme_cap = 0, traj_cap = 0;
     double *hstage = nullptr;       // pinned host staging of the boundary tables (maps, times, CMEs)
+    int *hstatus = nullptr;         // host-mapped copy of the status word, written by each step
     size_t hstage_cap = 0;
     bool have_state = false, have_boundary = false;
     cudaGraphExec_t graph = nullptr;

@@ -17,6 +17,24 @@ namespace icarus {
 
 enum { RHO = 0, M1 = 1, M2 = 2, M3 = 3, EN = 4, B1 = 5, B2 = 6, B3 = 7 };
 
+// radial edge i (0..n1) of a grid with a refined band [lo, hi]: in the coordinate u (ln r when lg,
+// else r) the cell density is f = band_refine inside the band and 1 outside, and edge i is where
+// its integral from the inner edge reaches i / n1 of the total. Host (metric tables) and device
+// (the allocation-free time step) evaluate the same expression.
+__host__ __device__ inline double band_edge_at(int n1, double x1min, double x1max, double lo, double hi, int band_refine,
+                                               bool lg, int i)
+{
+    if (i == 0) return x1min;
+    if (i == n1) return x1max;
+    const double f = (double)band_refine;
+    const double u0 = lg ? log(x1min) : x1min, ua = lg ? log(lo) : lo, ub = lg ? log(hi) : hi;
+    const double u1 = lg ? log(x1max) : x1max;
+    const double s = ((u1 - u0) + (f - 1.0) * (ub - ua)) * i / n1;   // density integral up to edge i
+    const double s_in = ua - u0, s_out = s_in + f * (ub - ua);       // ... at the band's two ends
+    const double x = s <= s_in ? u0 + s : (s <= s_out ? ua + (s - s_in) / f : ub + (s - s_out));
+    return lg ? exp(x) : x;
+}
+
 // per-axis metric arrays (device pointers) in the arithmetic type R: the double tables are the
 // host's FP64 values, the float tables their roundings (so single-precision kernels never convert
 // on the FP64 pipe). Index convention: padded index ip = i + NG.
@@ -63,7 +81,7 @@ struct Scalars {               // device-resident step state
     double t, dt, t_stop, cfl;
     unsigned long long smax_bits;   // batched form: this member's CFL maximum (bits of a double >= 0)
     unsigned int done;              // last-block counter of the CFL reduction
-    int status;                     // bit 0: non-finite state
+    int status;                     // bit 0: non-finite state; bit 1: a floor acted (strict_floors)
     unsigned long long floor_hits;
     long long ring_head;            // probe records written so far
     double dt_step;                 // dt of the step just completed (set when t advances)
@@ -96,6 +114,8 @@ struct Params {
     double t0, omega_si, b0, p0;
     Scalars *sc;
     double *partial;        // [n_blocks] CFL partial maxima (scratch)
+    int strict_floors;      // 1: a floor activation sets status bit 1
+    int *hstatus;           // device address of a host-mapped copy of sc->status (written each step)
 };
 
 template <typename R> __host__ __device__ inline const MetricsT<R> &met(const Params &P);

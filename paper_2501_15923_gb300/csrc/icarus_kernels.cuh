@@ -479,6 +479,8 @@ __device__ __forceinline__ void finish_dt(Params &P, double smax_block, int adva
         sc->t = t;
         sc->dt = dt;
         sc->done = 0;
+        // the step's status for icarus_step, which reads it on the host without synchronising
+        if (advance_t && P.hstatus) *(volatile int *)P.hstatus = atomicOr(&sc->status, 0);
     }
 }
 
@@ -725,7 +727,10 @@ __device__ __forceinline__ void update_math(const Params &P, int i, int j, int k
         // taking an atomic from every such cell each stage serialises the update)
         const unsigned act = __activemask();
         const unsigned tot = __reduce_add_sync(act, (unsigned)hits);
-        if ((int)(threadIdx.x & 31) == __ffs(act) - 1) atomicAdd(&P.sc->floor_hits, (unsigned long long)tot);
+        if ((int)(threadIdx.x & 31) == __ffs(act) - 1) {
+            atomicAdd(&P.sc->floor_hits, (unsigned long long)tot);
+            if (P.strict_floors) atomicOr(&P.sc->status, 2);
+        }
     }
 }
 

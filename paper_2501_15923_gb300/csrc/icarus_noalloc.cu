@@ -18,19 +18,24 @@ namespace {
 
 constexpr int NA_BLOCK = 256;
 constexpr long long NA_MAX_BLOCKS = ICARUS_NOALLOC_MAX_CELLS / NA_BLOCK;
-constexpr int NA_HEADER = 32;   // first 256 bytes: the last-block counter (an unsigned int)
+constexpr int NA_HEADER = 32;   // first 256 bytes: the last-block counter and the non-finite flag
+                                // (two unsigned ints), then padding
 
 // scratch shared by every call on a device: [counter | pad][partial maxima]
 static __device__ __align__(256) double g_cfl_scratch[NA_HEADER + NA_MAX_BLOCKS];
 
 struct NaGrid {
-    int n1, n2, n3, geom, stretch;
-    double x1min, x1max, x2min, d2, x3min, d3, gamma, cfl;
+    int n1, n2, n3, geom, stretch, band_refine;
+    double x1min, x1max, x2min, d2, x3min, d3, band_lo, band_hi, gamma, cfl;
 };
 
+// radial edge i: the refined band's edges when there is one, else geometric (stretched sphere) or
+// uniform spacing -- the edges the context builds for its metric tables
 __device__ double na_edge1(const NaGrid &g, int i)
 {
-    if (g.geom == ICARUS_GEOM_SPHERICAL && g.stretch) return g.x1min * pow(g.x1max / g.x1min, (double)i / g.n1);
+    const bool lg = g.geom == ICARUS_GEOM_SPHERICAL && g.stretch;
+    if (g.band_refine > 1) return band_edge_at(g.n1, g.x1min, g.x1max, g.band_lo, g.band_hi, g.band_refine, lg, i);
+    if (lg) return g.x1min * pow(g.x1max / g.x1min, (double)i / g.n1);
     return g.x1min + i * ((g.x1max - g.x1min) / g.n1);
 }
 
@@ -40,6 +45,7 @@ __global__ void __launch_bounds__(NA_BLOCK) k_cfl_noalloc(NaGrid g, const double
                                                           double *scratch)
 {
     unsigned int *done = reinterpret_cast<unsigned int *>(scratch);
+    unsigned int *nonfinite = done + 1;
     double *partial = scratch + NA_HEADER;
     const long long N = (long long)g.n1 * g.n2 * g.n3;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,9 +71,12 @@ __global__ void __launch_bounds__(NA_BLOCK) k_cfl_noalloc(NaGrid g, const double
           + (fabs(w[2]) + fast_speed<double>(w, irho, 1, g.gamma)) / w2
           + (fabs(w[3]) + fast_speed<double>(w, irho, 2, g.gamma)) / w3;
     }
+    // fmax in the reduction would drop a NaN: a non-finite speed is flagged on its own
+    const int bad = __syncthreads_or(!isfinite(s));
     s = block_max(s);
     __shared__ bool last;
     if (threadIdx.x == 0) {
+        if (bad) atomicOr(nonfinite, 1u);
         partial[blockIdx.x] = s;
         __threadfence();
         last = atomicAdd(done, 1u) == gridDim.x - 1;
@@ -79,8 +88,10 @@ __global__ void __launch_bounds__(NA_BLOCK) k_cfl_noalloc(NaGrid g, const double
     for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) v = fmax(v, ((volatile double *)partial)[b]);
     v = block_max(v);
     if (threadIdx.x == 0) {
-        *dt_out = v > 0.0 ? g.cfl / v : 0.0;
+        const bool any_bad = ((volatile unsigned int *)nonfinite)[0] != 0u;
+        *dt_out = any_bad ? -1.0 : (v > 0.0 ? g.cfl / v : 0.0);
         *done = 0;
+        *nonfinite = 0;
     }
 }
 
@@ -96,13 +107,12 @@ extern "C" int icarus_cfl_dt_noalloc(const icarus_grid *grid, double gamma, doub
                                      void *stream)
 {
     if (!grid || !U || !dt) return na_fail(ICARUS_EINVAL, "NULL argument");
-    if (grid->n1 < 1 || grid->n2 < 1 || grid->n3 < 1) return na_fail(ICARUS_EINVAL, "cell counts must be >= 1");
+    // the grids icarus_init accepts, no others (message from the shared check)
+    if (check_grid(grid) != ICARUS_OK) return ICARUS_EINVAL;
     const long long N = (long long)grid->n1 * grid->n2 * grid->n3;
     if (N > ICARUS_NOALLOC_MAX_CELLS)
         return na_fail(ICARUS_EINVAL, "grid has more cells than ICARUS_NOALLOC_MAX_CELLS (4194304); use icarus_set_state + icarus_time");
     if (!(gamma > 1.0) || !(cfl > 0.0 && cfl <= 1.0)) return na_fail(ICARUS_EINVAL, "need gamma > 1 and cfl in (0, 1]");
-    if (grid->geometry != ICARUS_GEOM_SPHERICAL && grid->geometry != ICARUS_GEOM_CARTESIAN)
-        return na_fail(ICARUS_EINVAL, "unknown geometry");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return na_fail(ICARUS_ECUDA, "no current CUDA device");
     {
@@ -118,14 +128,16 @@ extern "C" int icarus_cfl_dt_noalloc(const icarus_grid *grid, double gamma, doub
     }
     cudaStream_t s = (cudaStream_t)stream;
     double *scratch = g_scratch_dev[dev];
-    // the counter must start at zero even if an earlier call on this device was interrupted
-    if (cudaMemsetAsync(scratch, 0, sizeof(unsigned int), s) != cudaSuccess) return na_fail(ICARUS_ECUDA, "memset of the counter failed");
+    // counter and flag must start at zero even if an earlier call on this device was interrupted
+    if (cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned int), s) != cudaSuccess)
+        return na_fail(ICARUS_ECUDA, "memset of the counter failed");
     NaGrid g;
     g.n1 = grid->n1; g.n2 = grid->n2; g.n3 = grid->n3;
     g.geom = grid->geometry; g.stretch = grid->stretch;
     g.x1min = grid->x1min; g.x1max = grid->x1max;
     g.x2min = grid->x2min; g.d2 = (grid->x2max - grid->x2min) / grid->n2;
     g.x3min = grid->x3min; g.d3 = (grid->x3max - grid->x3min) / grid->n3;
+    g.band_refine = grid->band_refine; g.band_lo = grid->band_lo; g.band_hi = grid->band_hi;
     g.gamma = gamma; g.cfl = cfl;
     const unsigned int blocks = (unsigned int)((N + NA_BLOCK - 1) / NA_BLOCK);
     k_cfl_noalloc<<<blocks, NA_BLOCK, 0, s>>>(g, U, dt, scratch);

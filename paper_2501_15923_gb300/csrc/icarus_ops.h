@@ -3,6 +3,8 @@
 #include <cstddef>
 #include <cuda_runtime.h>
 
+#include "../../include/icarus.h"
+
 namespace icarus {
 struct Params;
 struct Ops {
@@ -39,6 +41,8 @@ struct Ops {
     size_t ts_size, tw_size;
 };
 int report_error(int code, const char *msg);
+// validation of a grid description (EINVAL and a message for what icarus_init rejects)
+int check_grid(const icarus_grid *g);
 Ops ops_fp64();
 Ops ops_fp32();
 Ops ops_mixed();

@@ -46,7 +46,7 @@ class icarus_options(C.Structure):
                 ("p_floor", C.c_double), ("precision", C.c_int), ("ring_capacity", C.c_int),
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
                 ("fused", C.c_int), ("init_vphi", C.c_int), ("cme_model", C.c_int),
-                ("tracer", C.c_int), ("glm_alpha", C.c_double)]
+                ("tracer", C.c_int), ("glm_alpha", C.c_double), ("strict_floors", C.c_int)]
 
 
 _lib = None
@@ -95,6 +95,7 @@ SIGNATURES = {
     "icarus_restrict": (C.c_int, [C.c_void_p, C.c_void_p]),
     "icarus_conv3d_layer": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int] + [C.c_void_p] * 8),
     "icarus_cfl_dt_noalloc": (C.c_int, [C.POINTER(icarus_grid), C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "icarus_fma_rate": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "icarus_last_error": (C.c_char_p, []),
 }
 
@@ -161,6 +162,7 @@ def make_options(o: I.Options, precision=ICARUS_FP64, ring=4096, stream=None, al
     opt.cme_model = int(o.cme_model)
     opt.tracer = int(o.tracer)
     opt.glm_alpha = float(o.glm_alpha)
+    opt.strict_floors = int(getattr(o, "strict_floors", 0))
     opt.cfl, opt.limiter, opt.flux, opt.gravity, opt.divb = o.cfl, o.limiter, o.flux, o.gravity, o.divb
     opt.divb_coef, opt.rho_floor, opt.p_floor = o.divb_coef, o.rho_floor, o.p_floor
     opt.precision, opt.ring_capacity = precision, ring
@@ -285,6 +287,13 @@ def icarus_cfl_dt_noalloc(grid: icarus_grid, gamma: float, cfl: float, U_dev_ptr
     pointers in and out; see include/icarus.h)."""
     _check(load().icarus_cfl_dt_noalloc(C.byref(grid), float(gamma), float(cfl), C.c_void_p(U_dev_ptr),
                                         C.c_void_p(dt_dev_ptr), C.c_void_p(stream or 0)))
+
+
+def icarus_fma_rate(precision: int, chains: int = 8, blocks_per_sm: int = 4, iters: int = 1 << 14):
+    """Measured FMA rate of the GPU: (TFLOP/s, ms of the timed launch)."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(load().icarus_fma_rate(int(precision), int(chains), int(blocks_per_sm), int(iters), C.byref(tf), C.byref(ms)))
+    return tf.value, ms.value
 
 
 # ---- convenience wrapper -----------------------------------------------------------------------

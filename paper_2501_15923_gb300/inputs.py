@@ -121,6 +121,7 @@ class Options:
     cme_model: int = CME_WINDOW           # CME_WINDOW (0) or CME_SPHERE (1)
     tracer: int = 0                       # 1: carry the CME tracer c (passive, rho c conserved)
     glm_alpha: float = 0.1                # GLM (divb = DIVB_GLM): psi damped by exp(-alpha c_h dt / dmin)
+    strict_floors: int = 0                # 1: a floor activation makes the solver's status EFLOOR
 
 
 @dataclass

@@ -56,6 +56,11 @@ def test_bad_grids_rejected(ic, grid, msg):
     rc, err, ctx = init_rc(ic, grid)
     assert rc == EINVAL and msg in err, (rc, err)
     assert not ctx.value
+    # the allocation-free time step accepts exactly the grids icarus_init accepts (rejected before
+    # any CUDA call; the pointers are never dereferenced)
+    lib = ic.load()
+    rc = lib.icarus_cfl_dt_noalloc(C.byref(ic.make_grid(grid)), 1.5, 0.8, C.c_void_p(16), C.c_void_p(16), None)
+    assert rc == EINVAL and msg in lib.icarus_last_error().decode()
 
 
 def test_bad_boundary_codes_rejected(ic):
@@ -82,6 +87,7 @@ def test_bad_boundary_codes_rejected(ic):
     (1.5, I.Options(init_vphi=2), 0, "init_vphi"),
     (1.5, I.Options(cme_model=2), 0, "cme_model"),
     (1.5, I.Options(tracer=2), 0, "tracer"),
+    (1.5, I.Options(strict_floors=2), 0, "strict_floors"),
     (1.5, I.Options(divb=3), 0, "divb"),
     (1.5, I.Options(divb=I.DIVB_GLM, glm_alpha=-1.0), 0, "glm_alpha"),
     (1.5, I.Options(), 3, "precision"),
@@ -145,3 +151,12 @@ def test_math_check_rejects_bad_arguments(ic):
     assert lib.icarus_math_check(0, x, y) == EINVAL
     assert lib.icarus_math_check(2, None, y) == EINVAL
     assert lib.icarus_math_check(2, x, None) == EINVAL
+
+
+def test_fma_rate_rejects_bad_arguments(ic):
+    """The FMA-rate measurement's argument checks (no GPU needed: rejected before any CUDA call)."""
+    lib = ic.load()
+    tf, ms = C.c_double(), C.c_double()
+    for args in ((3, 8, 4, 16), (0, 3, 4, 16), (0, 8, 0, 16), (0, 8, 9, 16), (1, 8, 4, 6), (1, 8, 4, 0)):
+        assert lib.icarus_fma_rate(*args, C.byref(tf), C.byref(ms)) == EINVAL, args
+    assert lib.icarus_fma_rate(0, 8, 4, 16, None, C.byref(ms)) == EINVAL

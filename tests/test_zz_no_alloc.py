@@ -42,10 +42,19 @@ def noalloc_dt(ic, torch, grid_c, gamma, cfl, U):
     return float(dt_dev.item())
 
 
-@pytest.mark.parametrize("shape", [(64, 16, 32), (512, 64, 128)])
-def test_noalloc_dt_matches_allocating_path_twice(env, shape):
+GRIDS = {
+    "stretched sphere 64x16x32": I.Grid(64, 16, 32),
+    "stretched sphere 512x64x128": I.Grid(512, 64, 128),
+    "uniform-radius sphere": I.Grid(48, 12, 20, stretch=0),
+    "stretched sphere with a refined band": I.Grid(72, 12, 24, band_refine=4, band_lo=0.8, band_hi=1.2),
+    "uniform sphere with a refined band": I.Grid(60, 10, 16, stretch=0, band_refine=3, band_lo=0.5, band_hi=1.1),
+}
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_noalloc_dt_matches_allocating_path_twice(env, name):
     ic, torch = env
-    w = I.dynamic_cme(grid=I.Grid(*shape))
+    w = I.dynamic_cme(grid=GRIDS[name])
     s = ic.from_workload(w)
     grid_c = ic.make_grid(w.grid)
     U_a, t = s.get_state()
@@ -55,6 +64,59 @@ def test_noalloc_dt_matches_allocating_path_twice(env, shape):
         got = noalloc_dt(ic, torch, grid_c, w.gamma, w.opts.cfl, U)
         assert ref > 0 and abs(got - ref) <= TOL * ref, (got, ref)
     s.close()
+
+
+def test_noalloc_dt_cartesian_grid(env):
+    """The Cartesian branch (widths dx, dy, dz) on a box with three different widths."""
+    ic, torch = env
+    g = I.Grid(40, 12, 9, geometry=I.GEOM_CARTESIAN, stretch=0, x1min=0.0, x1max=2.0, x2min=0.0,
+               x2max=0.3, x3min=-1.0, x3max=1.0, bc=(I.BC_PERIODIC,) * 6)
+    s = ic.Solver(g, 1.5, 0.0, I.Options(gravity=0))
+    rng = np.random.default_rng(5)
+    W = np.empty((8, g.n3, g.n2, g.n1))
+    W[0] = rng.uniform(0.5, 2.0, W.shape[1:])
+    W[1:4] = rng.uniform(-1.0, 1.0, (3,) + W.shape[1:])
+    W[4] = rng.uniform(0.2, 1.0, W.shape[1:])
+    W[5:8] = rng.uniform(-1.0, 1.0, (3,) + W.shape[1:])
+    U = np.empty_like(W)
+    U[0], U[1:4], U[5:8] = W[0], W[0] * W[1:4], W[5:8]
+    U[4] = W[4] / 0.5 + 0.5 * W[0] * (W[1:4] ** 2).sum(0) + 0.5 * (W[5:8] ** 2).sum(0)
+    for Uc in (U, U[:, :, :, ::-1].copy()):
+        ref = reference_dt(s, Uc, 0.0)
+        got = noalloc_dt(ic, torch, ic.make_grid(g), 1.5, 0.8, Uc)
+        assert ref > 0 and abs(got - ref) <= TOL * ref, (got, ref)
+    s.close()
+
+
+def test_noalloc_dt_flags_a_non_finite_state(env):
+    """A NaN in one cell gives the documented dt = -1 (fmax alone would drop it); the next call on
+    a finite state gives the right dt again (the flag does not stick between calls)."""
+    ic, torch = env
+    w = I.dynamic_cme(grid=I.Grid(64, 16, 32))
+    s = ic.from_workload(w)
+    U, t = s.get_state()
+    bad = U.copy()
+    bad[4, 7, 3, 11] = np.nan
+    assert noalloc_dt(ic, torch, ic.make_grid(w.grid), w.gamma, w.opts.cfl, bad) == -1.0
+    ref = reference_dt(s, U, t)
+    got = noalloc_dt(ic, torch, ic.make_grid(w.grid), w.gamma, w.opts.cfl, U)
+    assert abs(got - ref) <= TOL * ref
+    s.close()
+
+
+@pytest.mark.parametrize("change,msg", [(dict(x1min=0.0), "r_in"), (dict(x2min=0.02), "colatitude"),
+                                        (dict(band_refine=4, band_lo=0.05, band_hi=1.0), "band"),
+                                        (dict(x1max=0.05), "empty")])
+def test_noalloc_rejects_grids_icarus_init_rejects(env, change, msg):
+    ic, torch = env
+    kw = dict(n1=32, n2=8, n3=16)
+    kw.update(change)
+    g = ic.make_grid(I.Grid(**kw))
+    dt_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    U_dev = torch.zeros(8, dtype=torch.float64, device="cuda")  # never read: rejected before launch
+    with pytest.raises(ic.IcarusError) as e:
+        ic.icarus_cfl_dt_noalloc(g, 1.5, 0.8, U_dev.data_ptr(), dt_dev.data_ptr(), None)
+    assert e.value.code == -1 and msg in str(e.value)
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(env):
