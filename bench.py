@@ -36,9 +36,10 @@ from paper_2501_15923_gb300 import inputs as I  # noqa: E402
 
 METRIC = "Mcell-updates/s on one GB300: FP64 plain vs mixed/batched/learned at stated error"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 ALU peak of GB300: 152 SMs x 2 DFMA/clk/SM (4 flop) x 2070 MHz max SM clock
-FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+# nominal FP64 / FP32 ALU rates of GB300 (152 SMs x 2 DFMA or 128 FFMA per clock x 2070 MHz): context
+# only; the roofline divides by the FMA rate measured in the same run (icarus_fma_rate)
+FP64_NOMINAL_TFLOPS = 152 * 4 * 2070e6 / 1e12
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 # FP64 flops per face of the flux kernels (2 x DFMA + DADD + DMUL thread-instructions per face)
 # and their DRAM bytes per face come from the committed ncu summary below.
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_flux_r_fp64_256x64x128.md")
@@ -228,28 +229,51 @@ def run_reference(args):
 
 
 def run_batched(ic, torch, args):
-    """Cone-CME ensemble (seed 3, uneven grids) in mixed precision: one persistent launch per step,
-    each member with its own dt. value = sum of member cells x steps / time."""
+    """Cone-CME ensemble (seed 3, uneven grids) in mixed precision, each member with its own dt,
+    advanced four ways on the same members: the batched step as ONE persistent launch, as one launch
+    per phase over all members, as the members' own kernels in parallel branches of one graph (the
+    library default), and (the baseline) every member stepped alone through icarus_step, one after
+    another. value = sum of member cells x steps / time of the default form."""
     members = I.ensemble(seed=3, n_members=args.batch_members)
     b = ic.Batch(members, precision=ic.ICARUS_MIXED)
     b.register_probes()
     tiles = b.autotune(2)
     steps = max(2, min(args.steps, 10))
-    b.step(max(1, args.warmup))
-    torch.cuda.synchronize()
-    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(b.stream)
-    b.step(steps)
-    e.record(b.stream)
-    e.synchronize()
-    ms = a.elapsed_time(e)
-    rc = b.status()
-    info = b.info()
     cells = b.ncell
+
+    def timed(fn):
+        fn(max(1, args.warmup))
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(b.stream)
+        fn(steps)
+        e.record(b.stream)
+        e.synchronize()
+        ms = a.elapsed_time(e)
+        rc = b.status()
+        if rc != 0:
+            raise RuntimeError(f"batched ensemble status {rc}")
+        return {"value": cells * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps}
+
+    res = {}
+    for name, mode in (("persistent", ic.ICARUS_BATCH_PERSISTENT), ("phases", ic.ICARUS_BATCH_PHASES),
+                       ("concurrent", ic.ICARUS_BATCH_CONCURRENT)):
+        b.set_mode(mode)
+        if mode == ic.ICARUS_BATCH_PHASES:
+            res["phase_tiles"] = b.autotune(2)[0]
+        res[name] = timed(b.step)
+        res[name]["launches_per_step"] = {ic.ICARUS_BATCH_PERSISTENT: 1, ic.ICARUS_BATCH_PHASES: 18,
+                                          ic.ICARUS_BATCH_CONCURRENT: 17 * len(members)}[mode]
+    res["sequential"] = timed(b.step_sequential)
+    res["sequential"]["launches_per_step"] = len(members) * 17
+    default = "concurrent"      # the library's default form (icarus_batch_set_mode)
+    info = b.info()
     dts = sorted(b.time(m)[1] for m in range(len(members)))
-    out = {"value": cells * steps / (ms * 1e-3) / 1e6, "unit": "Mcell-updates/s", "members": len(members),
-           "cells": cells, "steps": steps, "ms_per_step": ms / steps, "status": rc, "persistent_blocks": info["blocks"],
-           "graph": info["graph"], "launches_per_step": 1,
+    out = {"value": res[default]["value"], "unit": "Mcell-updates/s", "mode": default, "members": len(members),
+           "cells": cells, "steps": steps, "ms_per_step": res[default]["ms_per_step"], "status": 0,
+           "persistent_blocks": info["blocks"], "graph": info["graph"], "modes": res,
+           "batched_over_sequential": {k: res[k]["value"] / res["sequential"]["value"] for k in ("persistent", "phases", "concurrent")},
+           "phase_tiles": res.pop("phase_tiles", None),
            "tiles_chosen": {f"{r}/{t}": sum(1 for x in tiles if x == (r, t)) for r in range(3) for t in range(2)
                             if any(x == (r, t) for x in tiles)},
            "member_dt_range_code": [dts[0], dts[-1]]}
@@ -304,6 +328,24 @@ def run_learned(ic, torch, args, fine_dt: float, fine_cells: int):
            "fallback_to_fine": acc.get("fallback") == "true"}
     net.close()
     c.close()
+    return out
+
+
+def alu_peaks(ic, index):
+    """FMA rates of this GPU measured now by the library's own kernel (icarus_fma_rate: 4 blocks of
+    256 threads per SM, 8 independent chains per thread, one launch of about 60 ms after a warm-up
+    launch and a calibration), with the SM clock sampled meanwhile."""
+    out = {}
+    with Clocks(index) as clk:
+        for name, prec, it0 in (("fp64", ic.ICARUS_FP64, 1 << 12), ("fp32", ic.ICARUS_FP32, 1 << 16)):
+            _, ms = ic.icarus_fma_rate(prec, 8, 4, it0)
+            it = max(4, int(it0 * 60.0 / max(ms, 1e-3)) // 4 * 4)
+            tf, ms = ic.icarus_fma_rate(prec, 8, 4, it)
+            out[f"{name}_tflops"] = tf
+            out[f"{name}_ms"] = ms
+    out["clocks"] = clk.summary()
+    out["source"] = "icarus_fma_rate: 4 x 256 threads per SM, 8 independent FMA chains per thread, CUDA events"
+    out["nominal_tflops"] = {"fp64": FP64_NOMINAL_TFLOPS, "fp32": FP32_NOMINAL_TFLOPS}
     return out
 
 
@@ -371,6 +413,8 @@ def main(argv=None):
     clocks = clk.summary()
     s.sample(None, cap=1 << 20)          # drain the timed steps' records
 
+    peaks_alu = alu_peaks(ic, local)
+    fp64_peak = peaks_alu["fp64_tflops"]
     # per-kernel durations (events around each launch, eager) -> roofline of the dominant kernel
     kms = s.time_kernels(3)
     per_step = {k: v * (2 if k not in ("probe", "update_1", "update_2", "fused_1", "fused_2") else 1) for k, v in kms.items()}
@@ -383,13 +427,15 @@ def main(argv=None):
     dkey = dom.split("_")[-1] if dom in faces else None
     if dkey in flops_face and args.precision == "f64":
         ach = flops_face[dkey] * faces[dom] / (kms[dom] * 1e-3) / 1e12
-        roof = {"kernel": f"k_flux ({dom})", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+        roof = {"kernel": f"k_flux ({dom})", "bound": "alu", "achieved": ach, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": ach / fp64_peak,
                 "traffic": dram_face[dkey] * faces[dom] if dkey in dram_face else None,
                 "traffic_note": "DRAM bytes/face from the 256x64x128 ncu capture scaled by the faces of one launch",
-                "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2070 MHz (derived; measured DFMA rate 594 G/s)"}
+                "peak_source": "measured in this run (icarus_fma_rate, FP64 FMA chains); "
+                               f"nominal {FP64_NOMINAL_TFLOPS:.3f} TFLOP/s",
+                "frac_of_nominal": ach / FP64_NOMINAL_TFLOPS}
     else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": None, "traffic": None,
                 "note": "flop count of this kernel not profiled yet (or its sources changed since the capture)"}
     bytes_cell_update = 128 if args.precision in ("f64", "mixed") else 64
@@ -424,8 +470,8 @@ def main(argv=None):
             b.record(sf.stream)
             b.synchronize()
             fms = a.elapsed_time(b)
-            forms[name] = {"value": ncell * args.steps / (fms * 1e-3) / 1e6, "unit": "Mcell-updates/s",
-                           "ms_per_step": fms / args.steps}
+            fval = ncell * args.steps / (fms * 1e-3) / 1e6
+            forms[name] = {"value": fval, "unit": "Mcell-updates/s", "ms_per_step": fms / args.steps}
             # HBM roofline of this form's dominant kernel, from per-launch event times and the
             # algorithmic bytes of one launch (each value read or written once): flux kernels read
             # the primitives (8 x sw per cell) and write the fluxes (8 x sw per face); the update
@@ -441,9 +487,17 @@ def main(argv=None):
             per_step = {k: fk[k] * (1 if k.startswith("update") else 2) for k in kbytes}
             dk = max(per_step, key=per_step.get)
             ach = kbytes[dk] / (fk[dk] * 1e-3) / 1e9
-            forms[name]["roofline"] = {"kernel": dk, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
-                                       "unit": "GB/s", "frac": ach / hbm_peak, "algorithmic_bytes": kbytes[dk],
-                                       "kernel_ms": fk, "peak_source": "measured (hbm_gbs)"}
+            # the form's roofline: the scope table's algorithmic bytes per cell-update (the state
+            # read and written once: 8 fields of the state type each way) / the measured step time
+            bcu = 2 * 8 * su
+            fach = fval * 1e6 * bcu / 1e9
+            forms[name]["roofline"] = {"bound": "hbm", "achieved": fach, "peak": hbm_peak, "unit": "GB/s",
+                                       "frac": fach / hbm_peak, "algorithmic_bytes_per_cell_update": bcu,
+                                       "peak_source": "measured (hbm_gbs)"}
+            forms[name]["dominant_kernel"] = {"kernel": dk, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                                              "unit": "GB/s", "frac": ach / hbm_peak,
+                                              "algorithmic_bytes": kbytes[dk], "kernel_ms": fk,
+                                              "note": "this launch's own bytes (face fluxes included)"}
             sf.close()
         if args.batch_members > 0:
             forms["batched_ensemble"] = run_batched(ic, torch, args)
@@ -456,7 +510,7 @@ def main(argv=None):
                        "l2": "inputs larger than L2 (state 8 x 8 B x padded cells per copy)",
                        "parallelism": "replicas" if world > 1 else "single GPU", "cme_tracer": bool(args.tracer),
                        "divb": "glm" if args.glm else "linde"},
-            "clocks": clocks, "roofline": roof, "e2e": e2e, "floor_hits": floor_hits,
+            "clocks": clocks, "roofline": roof, "alu_peaks": peaks_alu, "e2e": e2e, "floor_hits": floor_hits,
             "gpu_launches": s.launches_per_step * args.steps, "forms": forms}
     if rank == 0 and not args.no_cpu and world == 1:
         v, n, el, used = cpu_oracle_rate(w, steps=3, max_seconds=25.0)

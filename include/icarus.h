@@ -254,11 +254,13 @@ int icarus_time_kernels(icarus_ctx *ctx, int n_steps, double *ms);
 
 /* ---- batched ensemble -------------------------------------------------------------------
  * Many independent solves (members) with their own grids, drivers, CMEs, probes, dt and t,
- * advanced together: each batched step is ONE persistent, cooperatively launched kernel that runs
- * every phase of every member's step, with grid-wide barriers between phases (bounded waits: a
- * barrier that does not complete within about two seconds records ETIMEOUT and the kernel
- * returns). Steps are replayed from a CUDA graph when the driver allows capturing the
- * cooperative launch, else launched directly. Each member is an icarus_ctx (icarus_batch_member)
+ * advanced together by one graph launch per ensemble step, in one of three forms
+ * (icarus_batch_set_mode): the members' own step kernels as parallel graph branches (default);
+ * ONE persistent, cooperatively launched kernel that runs every phase of every member's step,
+ * with grid-wide barriers between phases (bounded waits: a barrier that does not complete within
+ * about two seconds records ETIMEOUT and the kernel returns); or one launch per phase over all
+ * members. Steps are replayed from a CUDA graph (the persistent form launches directly where the
+ * driver does not allow capturing the cooperative launch). Each member is an icarus_ctx (icarus_batch_member)
  * on which icarus_set_boundary / icarus_sample / icarus_get_state / icarus_time work as usual;
  * stepping a member with icarus_step runs it alone. */
 typedef struct icarus_batch icarus_batch;
@@ -272,13 +274,33 @@ int icarus_batch_init(int n_members, const icarus_grid *grids, double gamma, dou
 /* The member context m (owned by the batch; do not destroy it). */
 int icarus_batch_member(icarus_batch *b, int m, icarus_ctx **ctx);
 
-/* Pick the flux tile shape of every member by timed trials (reps launches per candidate) on its
- * current state, once per distinct grid shape (cached in the batch). Synchronous. */
+/* Pick the flux tile shapes by timed trials (reps launches per candidate) on the current states:
+ * per member, once per distinct grid shape (cached), in the persistent mode; per direction for the
+ * whole ensemble on the batched flux launches in the per-phase mode (set the mode first).
+ * Synchronous. */
 int icarus_batch_autotune(icarus_batch *b, int reps);
 
 /* The chosen tile candidates of member m: cfg[0] radial (0: 128x2, 1: 64x4, 2: 32x8 threads),
  * cfg[1] theta / phi (0: 16x16, 1: 32x8). */
 int icarus_batch_tiles(icarus_batch *b, int m, int *cfg);
+
+/* How a batched step is launched. ICARUS_BATCH_PERSISTENT: ONE cooperative persistent kernel per
+ * step, grid-wide barriers between the phases, flux tiles per member. ICARUS_BATCH_PHASES:
+ * one launch per phase (ghost r / theta / phi, the fluxes of each direction, div B, update, twice;
+ * per-member dt; probes: 18 launches per step whatever the number of members), each over the work
+ * items of all members, so that every phase runs with its own register budget; one flux tile shape
+ * per direction for the whole ensemble (icarus_batch_autotune times the candidates on the batched
+ * launch). ICARUS_BATCH_CONCURRENT: every member's own step (the single solver's kernels, 17 per
+ * member) captured into ONE graph per ensemble step as up to 16 parallel branches (members placed
+ * on the least-loaded branch, largest first), so that members' kernels overlap on the GPU; the
+ * default (on GB300 the fastest: each kernel keeps the single solver's register budget and reads
+ * its parameters from the constant bank, while the GPU fills one member's tails with others). All
+ * three replay a CUDA graph and give the same result up to the compiler's fused multiply-adds (the
+ * same per-cell and per-face arithmetic). Changing the mode keeps the states. */
+#define ICARUS_BATCH_PERSISTENT 0
+#define ICARUS_BATCH_PHASES 1
+#define ICARUS_BATCH_CONCURRENT 2
+int icarus_batch_set_mode(icarus_batch *b, int mode);
 
 /* Set the tile candidates of member m by hand (same codes as icarus_batch_tiles). */
 int icarus_batch_set_tiles(icarus_batch *b, int m, int cfg_r, int cfg_t);
@@ -295,7 +317,7 @@ int icarus_batch_status(icarus_batch *b);
  * arrived; the device stays usable either way. For tests of the failure path. */
 int icarus_batch_barrier_selftest(int blocks, int absent, long long spin_limit);
 
-/* info[3] = (members, blocks of the persistent launch, 1 if steps replay a CUDA graph). */
+/* info[4] = (members, blocks of the persistent launch, 1 if steps replay a CUDA graph, mode). */
 int icarus_batch_info(icarus_batch *b, int *info);
 
 /* The cudaStream_t of the batch. */

@@ -1,5 +1,6 @@
 // icarus_batch_capi.cu -- host side of the batched ensemble (include/icarus.h, icarus_batch_*):
 // member contexts, work-item tables, the tile autotuner, and the one-launch-per-step graph.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <map>
@@ -28,6 +29,12 @@ struct icarus_batch {
     bool use_graph = true;
     bool dirty = true;
     long long spin_limit = 4000000000LL;
+    int mode = ICARUS_BATCH_CONCURRENT;   // members' steps as graph branches (default: measured fastest)
+    int pcfg_r = 2, pcfg_t = 1;           // the per-phase form's flux tiles (one per direction, all members)
+    // concurrent form: lanes of members whose steps run as parallel branches of one graph
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> lane_events;  // [0]: fork; [1 + l]: join of lane l
+    long long items[BPH_N] = {};          // work items of each phase over all members
     std::map<std::tuple<int, int, int>, std::pair<int, int>> tune_cache;   // grid shape -> (cfg_r, cfg_t)
 };
 
@@ -64,8 +71,9 @@ int build_tables(icarus_batch *b)
         M.P = c->P;
         M.U = c->U; M.U1 = c->U1; M.W = c->W; M.W1 = c->W1;
         M.F1 = c->F1; M.F2 = c->F2; M.F3 = c->F3; M.divB = c->divB;
-        M.cfg_r = b->cfg_r[m];
-        M.cfg_t = b->cfg_t[m];
+        // per-member tiles in the persistent kernel; one choice for the ensemble in the per-phase form
+        M.cfg_r = b->mode == ICARUS_BATCH_PHASES ? b->pcfg_r : b->cfg_r[m];
+        M.cfg_t = b->mode == ICARUS_BATCH_PHASES ? b->pcfg_t : b->cfg_t[m];
         if (M.cfg_r == 0) tiles_of<0, 128, 2>(M.P, M.tr, &M.items_r);
         else if (M.cfg_r == 1) tiles_of<0, 64, 4>(M.P, M.tr, &M.items_r);
         else tiles_of<0, 32, 8>(M.P, M.tr, &M.items_r);
@@ -81,6 +89,9 @@ int build_tables(icarus_batch *b)
         it[BPH_DIVB] = P.divb == 1 ? chunks((long long)(P.n1 + 2) * (P.n2 + 2) * (P.n3 + 2)) : 0;
         it[BPH_UPD] = chunks((long long)P.n1 * P.n2 * P.n3);
         it[BPH_PROBE] = P.n_probes > 0 ? 1 : 0;
+        it[BPH_FR] = M.items_r;
+        it[BPH_FT] = M.items_t;
+        it[BPH_FP] = M.items_p;
         for (int ph = 0; ph < BPH_N; ++ph) off[(size_t)ph * (n + 1) + m + 1] = off[(size_t)ph * (n + 1) + m] + it[ph];
         b->versions[m] = c->p_version;
     }
@@ -91,6 +102,7 @@ int build_tables(icarus_batch *b)
         if (!b->d_members || !b->d_off || !b->d_bar) return report_error(ICARUS_ENOMEM, "batch table allocation failed");
         BCK(cudaMemsetAsync(b->d_bar, 0, sizeof(BarrierState), b->stream));
     }
+    for (int ph = 0; ph < BPH_N; ++ph) b->items[ph] = off[(size_t)ph * (n + 1) + n];
     BCK(cudaMemcpyAsync(b->d_members, hm.data(), sizeof(Member) * n, cudaMemcpyHostToDevice, b->stream));
     BCK(cudaMemcpyAsync(b->d_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, b->stream));
     BCK(cudaStreamSynchronize(b->stream));
@@ -105,9 +117,57 @@ int enqueue(icarus_batch *b)
     A.n = (int)b->members.size();
     A.bar = b->d_bar;
     A.spin_limit = b->spin_limit;
+    if (b->mode == ICARUS_BATCH_PHASES) {
+        BCK(b->ops.launch_phases(A, b->items, b->pcfg_r, b->pcfg_t, b->stream));
+        return ICARUS_OK;
+    }
     // the barrier counters start from zero at every step (the error word is kept)
     BCK(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned int), b->stream));
     BCK(b->ops.launch(A, b->blocks, b->stream));
+    return ICARUS_OK;
+}
+
+// concurrent form: every member's own step kernels (the single solver's, each launch with the
+// member's parameters) captured on one of up to kLanes parallel streams, members assigned to the
+// least-loaded lane in decreasing order of cells, joined into one graph per ensemble step
+constexpr int kLanes = 16;
+
+int capture_concurrent(icarus_batch *b, cudaGraph_t *g)
+{
+    const int n = (int)b->members.size();
+    const int L = n < kLanes ? n : kLanes;
+    while ((int)b->lanes.size() < L) {
+        cudaStream_t st;
+        BCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        b->lanes.push_back(st);
+    }
+    while ((int)b->lane_events.size() < L + 1) {
+        cudaEvent_t e;
+        BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->lane_events.push_back(e);
+    }
+    std::vector<int> order(n);
+    for (int m = 0; m < n; ++m) order[m] = m;
+    auto cells = [&](int m) { const Params &P = b->members[m]->P; return (long long)P.n1 * P.n2 * P.n3; };
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return cells(x) > cells(y); });
+    std::vector<long long> load(L, 0);
+    std::vector<std::vector<int>> lane_members(L);
+    for (int m : order) {
+        int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lane_members[l].push_back(m);
+        load[l] += cells(m);
+    }
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaEventRecord(b->lane_events[0], b->stream);
+    for (int l = 0; l < L && e == cudaSuccess; ++l) {
+        e = cudaStreamWaitEvent(b->lanes[l], b->lane_events[0], 0);
+        for (int m : lane_members[l]) enqueue_step_on(b->members[m], b->lanes[l]);
+        if (e == cudaSuccess) e = cudaEventRecord(b->lane_events[1 + l], b->lanes[l]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->lane_events[1 + l], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, g);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return report_error(ICARUS_ECUDA, cudaGetErrorString(e != cudaSuccess ? e : e2));
     return ICARUS_OK;
 }
 
@@ -123,6 +183,16 @@ int prepare(icarus_batch *b)
     if (rc) return rc;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
+    if (b->mode == ICARUS_BATCH_CONCURRENT) {
+        cudaGraph_t g;
+        rc = capture_concurrent(b, &g);
+        if (rc) return rc;
+        cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return report_error(ICARUS_ECUDA, cudaGetErrorString(e));
+        b->dirty = false;
+        return ICARUS_OK;
+    }
     if (b->use_graph) {
         cudaGraph_t g;
         if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
@@ -200,9 +270,50 @@ int icarus_batch_member(icarus_batch *b, int m, icarus_ctx **ctx)
     return ICARUS_OK;
 }
 
+// the per-phase form's autotuner: for each direction, every tile candidate times the flux launch
+// over all members (reps launches after an untimed one, on the members' current primitives)
+static int autotune_phases(icarus_batch *b, int reps)
+{
+    for (icarus_ctx *c : b->members)
+        if (!c->have_state) return report_error(ICARUS_ESTATE, "autotune needs member states");
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    int best[2] = {b->pcfg_r, b->pcfg_t};
+    for (int grp = 0; grp < 2; ++grp) {          // 0: r faces; 1: theta and phi faces (one shape code)
+        float best_ms = 1e30f;
+        for (int cfg = 0; cfg < (grp == 0 ? NCFG_R : NCFG_T); ++cfg) {
+            if (grp == 0) b->pcfg_r = cfg; else b->pcfg_t = cfg;
+            int rc = build_tables(b);
+            if (rc) return rc;
+            BatchArgs A{};
+            A.m = b->d_members; A.off = b->d_off; A.n = (int)b->members.size();
+            for (int q = 0; q <= reps; ++q) {
+                if (q == 1) BCK(cudaEventRecord(e0, b->stream));
+                if (grp == 0) BCK(b->ops.launch_flux_dir(A, 0, cfg, b->items[BPH_FR], 1, b->stream));
+                else {
+                    BCK(b->ops.launch_flux_dir(A, 1, cfg, b->items[BPH_FT], 1, b->stream));
+                    BCK(b->ops.launch_flux_dir(A, 2, cfg, b->items[BPH_FP], 1, b->stream));
+                }
+            }
+            BCK(cudaEventRecord(e1, b->stream));
+            BCK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) { best_ms = ms; best[grp] = cfg; }
+        }
+        if (grp == 0) b->pcfg_r = best[0]; else b->pcfg_t = best[1];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->dirty = true;
+    return ICARUS_OK;
+}
+
 int icarus_batch_autotune(icarus_batch *b, int reps)
 {
     if (!b || reps < 1) return report_error(ICARUS_EINVAL, "bad argument");
+    if (b->mode == ICARUS_BATCH_PHASES) return autotune_phases(b, reps);
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
@@ -246,11 +357,20 @@ int icarus_batch_autotune(icarus_batch *b, int reps)
     return ICARUS_OK;
 }
 
+int icarus_batch_set_mode(icarus_batch *b, int mode)
+{
+    if (!b || (mode != ICARUS_BATCH_PERSISTENT && mode != ICARUS_BATCH_PHASES && mode != ICARUS_BATCH_CONCURRENT))
+        return report_error(ICARUS_EINVAL, "mode must be ICARUS_BATCH_PERSISTENT, _PHASES or _CONCURRENT");
+    if (b->mode != mode) b->dirty = true;
+    b->mode = mode;
+    return ICARUS_OK;
+}
+
 int icarus_batch_tiles(icarus_batch *b, int m, int *cfg)
 {
     if (!b || !cfg || m < 0 || m >= (int)b->members.size()) return report_error(ICARUS_EINVAL, "bad argument");
-    cfg[0] = b->cfg_r[m];
-    cfg[1] = b->cfg_t[m];
+    cfg[0] = b->mode == ICARUS_BATCH_PHASES ? b->pcfg_r : b->cfg_r[m];
+    cfg[1] = b->mode == ICARUS_BATCH_PHASES ? b->pcfg_t : b->cfg_t[m];
     return ICARUS_OK;
 }
 
@@ -260,6 +380,10 @@ int icarus_batch_set_tiles(icarus_batch *b, int m, int cfg_r, int cfg_t)
         return report_error(ICARUS_EINVAL, "bad argument");
     b->cfg_r[m] = cfg_r;
     b->cfg_t[m] = cfg_t;
+    if (b->mode == ICARUS_BATCH_PHASES) {      // one shape for the whole ensemble in this form
+        b->pcfg_r = cfg_r;
+        b->pcfg_t = cfg_t;
+    }
     b->dirty = true;
     return ICARUS_OK;
 }
@@ -321,6 +445,7 @@ int icarus_batch_info(icarus_batch *b, int *info)
     info[0] = (int)b->members.size();
     info[1] = b->blocks;
     info[2] = b->graph != nullptr;
+    info[3] = b->mode;
     return ICARUS_OK;
 }
 
@@ -331,6 +456,8 @@ int icarus_batch_destroy(icarus_batch *b)
     if (!b) return ICARUS_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaStream_t st : b->lanes) cudaStreamDestroy(st);
+    for (cudaEvent_t e : b->lane_events) cudaEventDestroy(e);
     // members other than the first, then the first (it owns the batch tables)
     for (size_t m = b->members.size(); m-- > 0;) icarus_destroy(b->members[m]);
     if (b->own_stream) cudaStreamDestroy(b->stream);

@@ -248,10 +248,9 @@ int build_metrics(icarus_ctx *c)
     return ICARUS_OK;
 }
 
-void enqueue_step(icarus_ctx *c)
+void enqueue_step(icarus_ctx *c, cudaStream_t s)
 {
     const Params &P = c->P;
-    cudaStream_t s = c->stream;
     if (c->ops.fused_stage && c->opts.fused) {
         c->ops.fill_ghosts(P, c->U, c->W, 1, s);
         c->ops.fused_stage(P, 1, c->U, c->W, c->U1, c->W1, s);
@@ -298,7 +297,7 @@ int build_graph(icarus_ctx *c)
     drop_graph(c);
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_step(c);
+    enqueue_step(c, c->stream);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess) return fail(ICARUS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&c->graph, g, 0);
@@ -320,6 +319,10 @@ int first_dt(icarus_ctx *c)
 }  // namespace
 
 namespace icarus {
+// one time step of the context enqueued on stream s (the batched form captures members' steps on
+// parallel streams into one graph)
+void enqueue_step_on(icarus_ctx *c, cudaStream_t s) { enqueue_step(c, s); }
+
 // the grids every entry point that takes an icarus_grid accepts (EINVAL with a message otherwise)
 int check_grid(const icarus_grid *g)
 {

@@ -38,4 +38,6 @@ struct icarus_ctx {
 namespace icarus {
 // allocate through the context's allocator (tracked, released by icarus_destroy)
 void *ctx_alloc(icarus_ctx *c, size_t bytes);
+// enqueue one time step of the context on stream s (not captured, no graph)
+void enqueue_step_on(icarus_ctx *c, cudaStream_t s);
 }  // namespace icarus

@@ -759,9 +759,11 @@ __device__ __forceinline__ void update_cell(const Params &P, const TS *__restric
                                             const TW *__restrict__ F2, const TW *__restrict__ F3,
                                             const TW *__restrict__ divB, long long tid, TW *wo)
 {
-    const int i = (int)(tid % P.n1);
-    const long long r_ = tid / P.n1;
-    const int j = (int)(r_ % P.n2), k = (int)(r_ / P.n2);
+    // interior cell numbers stay below 2^31 (the padded grid is limited to 2^31 cells): 32-bit
+    // divisions instead of the 64-bit software sequence
+    const unsigned int t32 = (unsigned int)tid, n1u = (unsigned int)P.n1, r_ = t32 / n1u;
+    const int i = (int)(t32 - r_ * n1u);
+    const int j = (int)(r_ % (unsigned int)P.n2), k = (int)(r_ / (unsigned int)P.n2);
     const long long nt = P.nt, c = cidx(P, i, j, k);
     TW w[NV], L[NV], dbn[6];
     const long long s1 = (long long)P.n3 * P.n2 * (P.n1 + 1), f1 = ((long long)k * P.n2 + j) * (P.n1 + 1) + i;
@@ -803,7 +805,8 @@ __device__ __forceinline__ void update_kernel_body(Params &P, const TS *__restri
     TW wo[NV];
     if (valid) update_cell<STAGE, TS, TW, GLM>(P, Us, Ws, Uo, Wo, F1, F2, F3, divB, tid, wo);
     if (STAGE == 2) {
-        const int i = valid ? (int)(tid % P.n1) : 0, j = valid ? (int)((tid / P.n1) % P.n2) : 0;
+        const unsigned int t32 = (unsigned int)tid, n1u = (unsigned int)P.n1;
+        const int i = valid ? (int)(t32 % n1u) : 0, j = valid ? (int)((t32 / n1u) % (unsigned int)P.n2) : 0;
         finish_dt(P, cfl_block_speed<TW>(P, wo, i + NG, j + NG, valid), 1);
     }
 }

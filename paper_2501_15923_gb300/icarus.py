@@ -79,6 +79,7 @@ SIGNATURES = {
     "icarus_batch_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "icarus_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
     "icarus_batch_set_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "icarus_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "icarus_batch_status": (C.c_int, [C.c_void_p]),
     "icarus_batch_barrier_selftest": (C.c_int, [C.c_int, C.c_int, C.c_longlong]),
     "icarus_batch_info": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -418,9 +419,16 @@ def icarus_batch_status(b):
 
 
 def icarus_batch_info(b):
-    info = np.zeros(3, dtype=np.int32)
+    info = np.zeros(4, dtype=np.int32)
     _check(load().icarus_batch_info(b, _ptr(info)))
-    return dict(members=int(info[0]), blocks=int(info[1]), graph=bool(info[2]))
+    return dict(members=int(info[0]), blocks=int(info[1]), graph=bool(info[2]), mode=int(info[3]))
+
+
+ICARUS_BATCH_PERSISTENT, ICARUS_BATCH_PHASES, ICARUS_BATCH_CONCURRENT = 0, 1, 2
+
+
+def icarus_batch_set_mode(b, mode):
+    _check(load().icarus_batch_set_mode(b, int(mode)))
 
 
 def icarus_batch_destroy(b):
@@ -428,9 +436,11 @@ def icarus_batch_destroy(b):
 
 
 class Batch:
-    """An ensemble of independent members advanced by one persistent launch per step."""
+    """An ensemble of independent members advanced together by one graph launch per step: the
+    members' own kernels as parallel branches (ICARUS_BATCH_CONCURRENT, the default), one persistent
+    kernel (ICARUS_BATCH_PERSISTENT) or one launch per phase over all members (ICARUS_BATCH_PHASES)."""
 
-    def __init__(self, workloads, precision=ICARUS_MIXED, ring=4096, device="cuda"):
+    def __init__(self, workloads, precision=ICARUS_MIXED, ring=4096, device="cuda", mode=None):
         import torch
         self.torch = torch
         self._alloc = _TorchAllocator(torch.device(device))
@@ -444,6 +454,18 @@ class Batch:
         for c, w in zip(self.ctx, workloads):
             icarus_set_boundary(c, w.t_maps, w.maps, w.cmes)
         self.stream = torch.cuda.ExternalStream(int(load().icarus_batch_stream(self.b) or 0))
+        if mode is not None:
+            icarus_batch_set_mode(self.b, mode)
+
+    def set_mode(self, mode):
+        icarus_batch_set_mode(self.b, mode)
+
+    def step_sequential(self, n=1):
+        """Each member advanced alone through icarus_step (its own captured step), one after another
+        on the batch stream: the baseline the batched launch is measured against."""
+        for _ in range(n):
+            for c in self.ctx:
+                icarus_step(c, 1)
 
     def register_probes(self):
         for c, w in zip(self.ctx, self.workloads):

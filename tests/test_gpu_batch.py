@@ -102,3 +102,71 @@ def test_barrier_wait_is_bounded(ic):
     b.step(2)
     assert b.status() == 0
     b.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# production-size members against the FP64 oracle
+PROD_SHAPES = [(512, 64, 128), (128, 32, 64), (384, 48, 96), (256, 40, 80)]
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (2, 2e-5)])
+def test_batch_production_members_match_oracle(ic, mode, prec, tol):
+    """Members of the sizes the ensemble workload draws (the 512 x 64 x 128 grid among them), each
+    stepped by the batched launch (persistent kernel, mode 0; one launch per phase, mode 1; the
+    members' own kernels as parallel branches of one graph, mode 2) from a
+    perturbed state at a time inside its CME window, compared field by field with one oracle step
+    from the same state: FP64 within 1e-12 and MIXED within 2e-5 of each field's scale (the
+    single-solver bars), dt within 1e-13 (FP64). Two consecutive steps; the oracle restarts from the
+    batch's state at each."""
+    from oracle.oracle import from_workload as oracle_workload
+    from .test_gpu_parity import field_errors
+    ws = [I.dynamic_cme(seed=60 + q, grid=I.Grid(*s)) for q, s in enumerate(PROD_SHAPES)]
+    b = ic.Batch(ws, precision=prec, mode=mode)
+    b.autotune(1)
+    t0 = 1.495978707e11 / 1e5
+    starts = []
+    for m, w in enumerate(ws):
+        U, _ = b.get_state(m)
+        Up = I.perturbed_state(U.shape, 70 + m, U, 1e-3)
+        t = (w.cmes[0, 0] + 1800.0) / t0
+        b.set_state(m, Up, t)
+        starts.append((Up, t))
+    for _ in range(2):
+        b.step(1)
+        assert b.status() == 0
+        nxt = []
+        for m, w in enumerate(ws):
+            orc = oracle_workload(w)
+            orc.set_state(*starts[m])
+            orc.step()
+            Uo, to = orc.get_state()
+            Ub, tb = b.get_state(m)
+            err = field_errors(Ub, Uo)
+            assert err.max() <= tol, (m, w.grid.n1, err)
+            if prec == 0:
+                assert abs(tb - to) <= 1e-13 * to, (m, tb, to)
+            else:
+                assert abs(tb - to) <= 1e-5 * to, (m, tb, to)
+            nxt.append((Ub, tb))
+            del orc
+        starts = nxt
+    b.close()
+
+
+def test_batch_modes_agree(ic):
+    """The three launch forms give the same MIXED step (same per-cell arithmetic)."""
+    ws = members()
+    out = []
+    for mode in (0, 1, 2):
+        b = ic.Batch(ws, precision=2, mode=mode)
+        b.set_tiles(1, 1)
+        b.step(3)
+        assert b.status() == 0 and b.info()["mode"] == mode
+        out.append([b.get_state(m) for m in range(len(ws))])
+        b.close()
+    for other in out[1:]:
+        for (Ua, ta), (Ub, tb) in zip(out[0], other):
+            assert abs(ta - tb) <= 1e-6 * ta
+            scale = np.abs(Ua).reshape(8, -1).max(1)[:, None]
+            assert np.all(np.abs(Ua - Ub).reshape(8, -1) <= 1e-6 * scale)
