@@ -168,16 +168,37 @@ def evaluate(net, seed: int, spinup_days: float, window_days: float, k: int = 10
         ic.icarus_restrict(F.ctx, C.ctx)
         runs[name] = C
     t_end = t_start + window_days * I.DAY / F.scales()["t0"]
-    # fine reference with probes
+    # fine reference with probes; at every hour the fine state is also restricted onto the coarse
+    # grid and sampled there: the probe error of the exact restriction, the smallest any coarse
+    # state can reach at the probes (what is left is the coarse grid's interpolation at the probe)
     F.sample(w.traj, cap=1)
+    Rs = ic.from_workload(wc, precision=ic.ICARUS_FP64)
+
+    def restricted_sample():
+        ic.icarus_restrict(F.ctx, Rs.ctx)
+        rec, n = Rs.sample(w.traj, cap=4)       # registers the probes, samples once, drains
+        return rec[:n]
+
+    restricted = [restricted_sample()]
     torch.cuda.synchronize()
     tf = time.perf_counter()
-    advance_to(F, t_end)
-    torch.cuda.synchronize()
-    fine_seconds = time.perf_counter() - tf
+    hour = 3600.0 / F.scales()["t0"]
+    t_next = t_start
+    fine_seconds = 0.0
+    while t_next < t_end * (1 - 1e-15):
+        t_next = min(t_next + hour, t_end)
+        t1 = time.perf_counter()
+        advance_to(F, t_next)
+        torch.cuda.synchronize()
+        fine_seconds += time.perf_counter() - t1
+        restricted.append(restricted_sample())
     ref = probe_series(F)
+    Rs.close()
     fine_steps = len(ref) - 1
-    result = {"fine_steps": fine_steps, "fine_seconds": fine_seconds, "fine_cells": w.grid.ncell}
+    result = {"fine_steps": fine_steps, "fine_seconds": fine_seconds, "fine_cells": w.grid.ncell,
+              "restricted_fine": {"probe_error": series_error(ref, np.concatenate(restricted))}}
+    if log:
+        log(f"restricted fine state sampled on the coarse grid: {result['restricted_fine']}")
     shape_c = (8, wc.grid.n3, wc.grid.n2, wc.grid.n1)
     Rf = ic.from_workload(wc, precision=ic.ICARUS_FP64)
     ic.icarus_restrict(F.ctx, Rf.ctx)
@@ -215,6 +236,26 @@ def evaluate(net, seed: int, spinup_days: float, window_days: float, k: int = 10
     result["fine_mcell_updates_per_s"] = w.grid.ncell * fine_steps / fine_seconds / 1e6
     F.close(); Rf.close()
     return result
+
+
+def save_closure(path: str, net, norm, k: int):
+    """The trained network (FP32 master weights of the four layers), its normalisation and its
+    correction interval, as one .npz file."""
+    arrays = {"k": np.array(k), "shape": np.array(net.shape)}
+    for l, (w, b) in enumerate(net.weights()):
+        arrays[f"w{l}"], arrays[f"b{l}"] = w, b
+    arrays["in_mean"], arrays["in_scale"], arrays["out_scale"] = norm
+    np.savez_compressed(path, **arrays)
+
+
+def load_closure(path: str):
+    """(network on the GPU, correction interval k) from a file written by save_closure."""
+    z = np.load(path)
+    n1, n2, n3 = (int(x) for x in z["shape"])
+    net = ic.Closure(n1, n2, n3, seed=0)
+    net.set_norm(z["in_mean"], z["in_scale"], z["out_scale"])
+    net.set_weights([(z[f"w{l}"], z[f"b{l}"]) for l in range(4)])
+    return net, int(z["k"])
 
 
 def pair_gain(net, pairs: PairSet, indices):
@@ -280,7 +321,10 @@ def main(argv=None):
     p.add_argument("--lr", type=float, default=1e-3)
     p.add_argument("--eval-window", type=float, default=1.0)
     p.add_argument("--fine", default="512x64x128")
+    p.add_argument("--every", type=int, default=10, help="coarse steps per pair window and between corrections")
+    p.add_argument("--save", default="", help="write the trained network to this .npz file")
     p.add_argument("--time-only", action="store_true", help="only time the network kernels on the coarse grid")
+    p.add_argument("--load", default="", help="evaluate a network saved with --save instead of training one")
     a = p.parse_args(argv)
     fine = tuple(int(x) for x in a.fine.split("x"))
     torch.cuda.set_device(0)
@@ -288,8 +332,13 @@ def main(argv=None):
         print(json.dumps(time_network((fine[0] // 2, fine[1] // 2, fine[2] // 2))))
         return
     log = lambda s: print(s, flush=True)
+    if a.load:
+        net, k = load_closure(a.load)
+        print(json.dumps({"every": k, "evaluation": evaluate(net, 999, a.spinup, a.eval_window, k=k, fine=fine, log=log)},
+                         default=float))
+        return
     t0 = time.perf_counter()
-    pairs = generate_pairs(range(100, 100 + a.seeds), a.windows, a.spinup, fine=fine, log=log)
+    pairs = generate_pairs(range(100, 100 + a.seeds), a.windows, a.spinup, k=a.every, fine=fine, log=log)
     t_pairs = time.perf_counter() - t0
     hold = list(range(len(pairs) - a.windows, len(pairs)))           # the last seed's pairs: held out
     train_set = PairSet(torch)
@@ -299,8 +348,10 @@ def main(argv=None):
     net, info = train(train_set, cshape, epochs=a.epochs, lr=a.lr, log=log)
     gain_train = pair_gain(net, train_set, range(0, len(train_set), max(1, len(train_set) // 16)))
     gain_hold = pair_gain(net, pairs, hold)
-    ev = evaluate(net, 999, a.spinup, a.eval_window, fine=fine, log=log)
-    out = {"pairs": len(pairs), "train_pairs": len(train_set), "pair_seconds": t_pairs,
+    ev = evaluate(net, 999, a.spinup, a.eval_window, k=a.every, fine=fine, log=log)
+    if a.save:
+        save_closure(a.save, net, info["norm"], a.every)
+    out = {"every": a.every, "pairs": len(pairs), "train_pairs": len(train_set), "pair_seconds": t_pairs,
            "train_seconds": info["seconds"], "train_steps": info["steps"], "loss_first": info["loss"][0],
            "loss_last": info["loss"][-1], "pair_gain_train": gain_train, "pair_gain_heldout": gain_hold,
            "evaluation": ev}

@@ -71,9 +71,9 @@ def advancing_steps(series: np.ndarray) -> int:
     return int((np.diff(series[:, 0, 0]) > 0).sum())
 
 
-def run(days: float, grid=(512, 64, 128), chunk: int = 200, ring: int = 1 << 16, log=None):
+def run(days: float, grid=(512, 64, 128), chunk: int = 200, ring: int = 1 << 16, n_scale: float = 1.0, log=None):
     import torch
-    w = I.dynamic_cme(grid=I.Grid(*grid), days=days)
+    w = I.dynamic_cme(grid=I.Grid(*grid), days=days, n_scale=n_scale)
     res, states, series = {}, {}, {}
     for name, prec in (("fp64", ic.ICARUS_FP64), ("mixed", ic.ICARUS_MIXED), ("fp32", ic.ICARUS_FP32)):
         s = ic.from_workload(w, precision=prec, ring=ring)
@@ -107,10 +107,12 @@ def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--days", type=float, default=10.0)
     p.add_argument("--grid", default="512x64x128")
+    p.add_argument("--n-scale", type=float, default=1.0,
+                   help="boundary density factor (2: the inflow is super-Alfvenic and no floor acts before the CME)")
     a = p.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
-    res = run(a.days, tuple(int(x) for x in a.grid.split("x")), log=lambda s: print(s, flush=True))
+    res = run(a.days, tuple(int(x) for x in a.grid.split("x")), n_scale=a.n_scale, log=lambda s: print(s, flush=True))
     print(json.dumps(res))
 
 
