@@ -379,8 +379,16 @@ template <int D> struct FluxShape {
     static constexpr int BY = D == 0 ? 1 : 16;
 };
 
+// resident blocks per SM the FP64 TVDLF / HLL flux kernels are compiled for: at most 85 registers,
+// so that 3 blocks of 256 threads (6 of 128) fit in the register file instead of 2 (5) at the 88
+// the compiler takes unasked; the FP64 pipe is their bound, and more warps keep it busier. No
+// constraint for the single-precision and HLLD instantiations.
+template <int D, typename TW, bool HD> struct FluxMinBlocks {
+    static constexpr int value = (sizeof(TW) == 8 && !HD) ? (D == 0 ? 6 : 3) : 1;
+};
+
 template <int D, typename TW, bool HD = false>
-__global__ void __launch_bounds__(FluxShape<D>::BX * FluxShape<D>::BY)
+__global__ void __launch_bounds__(FluxShape<D>::BX * FluxShape<D>::BY, FluxMinBlocks<D, TW, HD>::value)
 k_flux(Params P, const TW *__restrict__ W, TW *__restrict__ F)
 {
     constexpr int BX = FluxShape<D>::BX, BY = FluxShape<D>::BY;

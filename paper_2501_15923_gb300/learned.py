@@ -154,10 +154,11 @@ def series_error(ref, got, fields=(1, 2, 9)):
 
 
 def evaluate(net, seed: int, spinup_days: float, window_days: float, k: int = 10, fine=(512, 64, 128),
-             threshold: float = 0.01, log=None):
-    """Fine plain solve vs coarse plain solve vs coarse + closure on a held-out seed."""
+             threshold: float = 0.01, n_scale: float = 1.0, log=None):
+    """Fine plain solve vs coarse plain solve vs coarse + closure on a held-out seed (n_scale: the
+    boundary density factor of the drivers)."""
     import torch
-    w = I.dynamic_cme(seed=seed, grid=I.Grid(*fine))
+    w = I.dynamic_cme(seed=seed, grid=I.Grid(*fine), n_scale=n_scale)
     wc = coarse_workload(w)
     F = ic.from_workload(w, precision=ic.ICARUS_FP64)
     t_start = spinup_days * I.DAY / F.scales()["t0"]
@@ -325,6 +326,7 @@ def main(argv=None):
     p.add_argument("--save", default="", help="write the trained network to this .npz file")
     p.add_argument("--time-only", action="store_true", help="only time the network kernels on the coarse grid")
     p.add_argument("--load", default="", help="evaluate a network saved with --save instead of training one")
+    p.add_argument("--n-scale", type=float, default=1.0, help="boundary density factor of the evaluation drivers")
     a = p.parse_args(argv)
     fine = tuple(int(x) for x in a.fine.split("x"))
     torch.cuda.set_device(0)
@@ -334,8 +336,8 @@ def main(argv=None):
     log = lambda s: print(s, flush=True)
     if a.load:
         net, k = load_closure(a.load)
-        print(json.dumps({"every": k, "evaluation": evaluate(net, 999, a.spinup, a.eval_window, k=k, fine=fine, log=log)},
-                         default=float))
+        ev = evaluate(net, 999, a.spinup, a.eval_window, k=k, fine=fine, n_scale=a.n_scale, log=log)
+        print(json.dumps({"every": k, "n_scale": a.n_scale, "evaluation": ev}, default=float))
         return
     t0 = time.perf_counter()
     pairs = generate_pairs(range(100, 100 + a.seeds), a.windows, a.spinup, k=a.every, fine=fine, log=log)
