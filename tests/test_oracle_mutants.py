@@ -72,6 +72,37 @@ MUTANTS = [
      "    double ww = (tau - o->tm[m]) / (o->tm[m + 1] - o->tm[m]);\n",
      "    double ww = (o->tm[m + 1] - tau) / (o->tm[m + 1] - o->tm[m]);\n",
      "P8_boundary_time_interpolation"),
+    ("probe longitude moved with the wrong sense of rotation",
+     "double ph = lon - o->omega_si * tsi;", "double ph = lon + o->omega_si * tsi;",
+     "P9_phi_wrap"),
+    ("trilinear radial weights swapped",
+     "double f = ((c & 1) ? wr : 1.0 - wr)", "double f = ((c & 1) ? 1.0 - wr : wr)",
+     "P9_sampling_cell_centre"),
+    ("probe v_phi left in the co-rotating frame",
+     "q[4] = (acc[3] + o->omega * r * sin(th)) * O_V0;", "q[4] = acc[3] * O_V0;",
+     "P9_probe_vphi"),
+    ("CME cone test against sin instead of cos of the half-width",
+     "double thr = cos(q[4]);", "double thr = sin(q[4]);",
+     "P10_cme_footprint"),
+    ("initial pressure falling as r^-gamma instead of r^-2 gamma",
+     "w[4] = b[2] * pow(x, 2.0 * o->gamma);", "w[4] = b[2] * pow(x, o->gamma);",
+     "IC_radial_expansion"),
+    ("initial Parker spiral wound the wrong way",
+     "w[7] = -w[5] * o->omega * r * sin(th) / w[1];", "w[7] = w[5] * o->omega * r * sin(th) / w[1];",
+     "IC_radial_expansion"),
+    ("driven face without the asymm flip of v_theta",
+     "w[2] = -wm[2]; w[3] = -wm[3]; w[6] = -wm[6];", "w[2] = wm[2]; w[3] = -wm[3]; w[6] = -wm[6];",
+     "P8_ghost_layers"),
+    ("outer radius B_r continued as r^-1",
+     "double f = (ctr(o, 0, src) / ctr(o, 0, gi)) * (ctr(o, 0, src) / ctr(o, 0, gi));",
+     "double f = (ctr(o, 0, src) / ctr(o, 0, gi));",
+     "P8_outer_radius"),
+    ("tracer taken from the downwind side",
+     "ft[s] = fr * (fr >= 0.0 ? cl : cr);", "ft[s] = fr * (fr >= 0.0 ? cr : cl);",
+     "tracer_conserved or tracer_advection"),
+    ("tracer clipped at zero only",
+     "T[id] = fmin(fmax(T[id], 0.0), rho);", "T[id] = fmax(T[id], 0.0);",
+     "tracer_clipped"),
     ("HLLD double-star energy with the wrong sign",
      "uss[EN] = us[s][EN] + (s ? 1.0 : -1.0) * sq * (vbs - vbss) * sg;",
      "uss[EN] = us[s][EN] - (s ? 1.0 : -1.0) * sq * (vbs - vbss) * sg;",

@@ -612,6 +612,14 @@ def test_P8_ghost_layers_same_value_and_asymm():
     w = I.static_sheet()
     from oracle.oracle import from_workload
     o = from_workload(w)
+    # give the cells next to the driven face a non-zero v_theta, v_phi and B_theta, so that the
+    # sign flip of asymm is visible
+    U, t = o.get_state()
+    Wi = prim_from_cons(U, 1.5)
+    rng = np.random.default_rng(8)
+    for f in (2, 3, 6):
+        Wi[f, :, :, :2] = rng.uniform(-0.5, 0.5, Wi[f, :, :, :2].shape) * np.abs(Wi[1, :, :, :2]).max()
+    o.set_state(cons_from_prim(Wi, 1.5), t)
     o.fill_ghosts(0.0)
     Up = o.get_state_padded()
     Wp = prim_from_cons(Up, 1.5)
@@ -622,8 +630,9 @@ def test_P8_ghost_layers_same_value_and_asymm():
             assert np.allclose(got, vals[v], rtol=1e-12, atol=1e-12 * np.abs(vals[v]).max())
     # asymm: ghost -1 mirrors interior 0, ghost -2 mirrors interior 1, sign flipped
     for f in (2, 3, 6):
-        assert np.allclose(Wp[f, 2:-2, 2:-2, 1], -Wp[f, 2:-2, 2:-2, 2], atol=1e-13)
-        assert np.allclose(Wp[f, 2:-2, 2:-2, 0], -Wp[f, 2:-2, 2:-2, 3], atol=1e-13)
+        assert np.abs(Wp[f, 2:-2, 2:-2, 2]).max() > 0.01
+        assert np.allclose(Wp[f, 2:-2, 2:-2, 1], -Wp[f, 2:-2, 2:-2, 2], rtol=1e-12, atol=1e-13)
+        assert np.allclose(Wp[f, 2:-2, 2:-2, 0], -Wp[f, 2:-2, 2:-2, 3], rtol=1e-12, atol=1e-13)
 
 
 def test_P8_outer_radius_continues_radial_flux():
@@ -757,6 +766,25 @@ def test_P9_phi_wrap_and_corotation():
         assert abs(q[1] / 1e6 - expect) < 1e-9
 
 
+def test_P9_probe_vphi_in_the_inertial_frame():
+    """Reading 14: the probe reports v_phi in the inertial frame. Plasma at rest in the co-rotating
+    frame (v = 0 in every cell) is seen from the inertial frame moving with the frame, so the
+    probe's v_phi is Omega r sin(theta) at the probe's own position (SI, r in m, theta the
+    colatitude), whatever the interpolation weights; every other velocity component is zero."""
+    g = sph_grid(12, 10, 16, bc=(C, C, C, C, P, P))
+    om = 2.8654e-6
+    o = Oracle(g, 1.5, om, opts())
+    W = np.zeros((8, g.n3, g.n2, g.n1))
+    W[0], W[4], W[5] = 2.0, 0.7, 0.3
+    o.set_state(cons_from_prim(W, 1.5), 0.2)
+    AU = 1.495978707e11
+    for r_au, lat, lon in ((1.0, 0.1, 0.3), (0.37, -0.6, 4.0), (1.83, 0.95, 2.2)):
+        q = o.sample(np.array([[[0.0, r_au * AU, lat, lon]]]))[0]
+        want = om * r_au * AU * math.cos(lat)
+        assert abs(q[4] - want) <= 1e-12 * want, (q[4], want)
+        assert q[2] == 0.0 and q[3] == 0.0
+
+
 def test_P10_sphere_cme_footprint_brute_force():
     """Spherical-cloud CME (cme_model 1): the footprint at r_in is the set of boundary column
     centres inside the moving sphere, checked by Cartesian distances to the sphere centre
@@ -866,6 +894,21 @@ def test_tracer_conserved_and_bounded():
     c = o.get_tracer()
     assert abs((U[0] * c).sum() - m0) <= 1e-12 * m0
     assert c.min() >= 0.0 and c.max() <= 1.0
+
+
+def test_tracer_clipped_to_zero_and_rho():
+    """Reading 9: after every stage rho c is clipped to [0, rho]. A tracer set outside [0, 1] (c of
+    -0.5 and 1.5 in blocks of cells, allowed as input) comes back inside after one step, with the
+    out-of-range blocks at exactly 0 and 1 away from their edges."""
+    o, rng = _tracer_box(seed=9)
+    c0 = np.full(o.shape[1:], 0.5)
+    c0[:, :, 2:6] = 1.5
+    c0[:, :, 12:16] = -0.5
+    o.set_tracer(c0)
+    o.step()
+    c = o.get_tracer()
+    assert c.min() >= 0.0 and c.max() <= 1.0
+    assert np.all(c[:, :, 3:5] == 1.0) and np.all(c[:, :, 13:15] == 0.0)
 
 
 def test_tracer_advection_second_order():
