@@ -103,6 +103,34 @@ MUTANTS = [
     ("tracer clipped at zero only",
      "T[id] = fmin(fmax(T[id], 0.0), rho);", "T[id] = fmax(T[id], 0.0);",
      "tracer_clipped"),
+    ("second SSP-RK2 stage without the average with U^n",
+     "o->U[id] = 0.5 * o->U0[id] + 0.5 * (o->U1[id] + dt * o->L[id]);", "o->U[id] = o->U1[id] + dt * o->L[id];",
+     "P3_sod_star_state or test_P4_linear_waves_second_order and 2-0-0"),
+    ("cell volume with 1/2 instead of 1/3",
+     "return (rp * rp * rp - rm * rm * rm) / 3.0 *", "return (rp * rp * rp - rm * rm * rm) / 2.0 *",
+     "P5_steady_wind or P5_gravity_sign"),
+    ("div B with the upper face's area on the lower face",
+     "s += area(o, d, pl[0], pl[1], pl[2]) * 0.5 * (bc + bp) - area(o, d, i, j, k) * 0.5 * (bm + bc);",
+     "s += area(o, d, pl[0], pl[1], pl[2]) * 0.5 * (bc + bp) - area(o, d, pl[0], pl[1], pl[2]) * 0.5 * (bm + bc);",
+     "P6_divb"),
+    ("Linde coefficient over the root of sum 1/dx^2",
+     "double eta = o->divb_coef / (dt * sinv);", "double eta = o->divb_coef / (dt * sqrt(sinv));",
+     "P6_linde"),
+    ("GLM damping without c_h",
+     "const double damp = exp(-o->glm_alpha * o->glm_ch * dt / o->glm_dmin);",
+     "const double damp = exp(-o->glm_alpha * dt / o->glm_dmin);",
+     "P12_glm_damping"),
+    ("map times past the table clamped to the first map",
+     "if (tau >= o->tm[n - 1]) { *m0 = *m1 = n - 1; *w = 0.0; return; }",
+     "if (tau >= o->tm[n - 1]) { *m0 = *m1 = 0; *w = 0.0; return; }",
+     "P8_boundary_time"),
+    ("work of the rotating-frame force dropped from the energy",
+     "Lc[EN] += vv[0] * F[0] + vv[1] * F[1] + vv[2] * F[2];", "Lc[EN] += 0.0;",
+     "P5_P7_wind_residual"),
+    ("HLL dissipation with the wrong sign",
+     "f[v] = (sr * fl[v] - sl * fr[v] + sl * sr * (ur[v] - ul[v])) / (sr - sl);",
+     "f[v] = (sr * fl[v] - sl * fr[v] - sl * sr * (ur[v] - ul[v])) / (sr - sl);",
+     "P3_sod"),
     ("HLLD double-star energy with the wrong sign",
      "uss[EN] = us[s][EN] + (s ? 1.0 : -1.0) * sq * (vbs - vbss) * sg;",
      "uss[EN] = us[s][EN] - (s ? 1.0 : -1.0) * sq * (vbs - vbss) * sg;",
