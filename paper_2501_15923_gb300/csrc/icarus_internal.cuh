@@ -467,6 +467,9 @@ __device__ __forceinline__ void riemann(const R *wl, const R *wr, int d, int flu
         ff[B1] = vn * w[5] - bn * w[1];
         ff[B2] = vn * w[6] - bn * w[2];
         ff[B3] = vn * w[7] - bn * w[3];
+        // the normal component v_n B_n - B_n v_n is exactly zero (the two products are equal; with
+        // a fused multiply-add it would come out as the product's rounding error instead)
+        ff[B1 + d] = R(0);
     }
     if constexpr (HD) {
         (void)flux;

@@ -243,7 +243,7 @@ template <int D, int BX, int BY, typename TW, bool HD = false, bool GLM = false,
 __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict__ W, TW *__restrict__ F,
                                           int bx, int by, int bz, int tx, int ty, TW *sW, TW *sP,
                                           const TP *__restrict__ Psi = nullptr, TW *__restrict__ FP = nullptr,
-                                          TW *sQW = nullptr, TW *sQP = nullptr)
+                                          TW *sQW = nullptr, TW *sQP = nullptr, TW *sD = nullptr)
 {
     constexpr int S = D == 0 ? BX : BY;
     const int ts = D == 0 ? tx : ty;
@@ -273,8 +273,9 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
     const int sl = ty * BX + tx, sz = BX * BY;
     TW wc[NV], wm[NV];
     TW qc = TW(0), qm = TW(0);
+    TW da[NV], db[NV], dl[NV];
+    const long long c = valid ? cidx(P, i, j, k) : 0;
     if (valid) {
-        const long long c = cidx(P, i, j, k);
         if constexpr (GLM) {
             const TW qa = (TW)Psi[c - st], qe = (TW)Psi[c + st];
             qc = (TW)Psi[c];
@@ -283,14 +284,41 @@ __device__ __forceinline__ void flux_tile(const Params &P, const TW *__restrict_
             sQW[sl] = qc;
             sQP[sl] = qc + TW(0.5) * dq;
         }
-        TW da[NV], db[NV], dl[NV];
+        if (sizeof(TW) == 8 && sD) {
+            // FP64: a cell's backward difference is its lower neighbour's forward difference; the
+            // forward differences go through shared memory (the FP64 pipe is the bound, the load
+            // / store path has room), and only the first cell of the tile subtracts its own
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            TW a = W[v * nt + c - st], b = W[v * nt + c], e = W[v * nt + c + st];
-            wc[v] = b;
-            da[v] = b - a;
-            db[v] = e - b;
+            for (int v = 0; v < NV; ++v) {
+                const TW b = W[v * nt + c], e = W[v * nt + c + st];
+                wc[v] = b;
+                db[v] = e - b;
+                sD[v * sz + sl] = db[v];
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                TW a = W[v * nt + c - st], b = W[v * nt + c], e = W[v * nt + c + st];
+                wc[v] = b;
+                da[v] = b - a;
+                db[v] = e - b;
+            }
         }
+    }
+    if (sizeof(TW) == 8 && sD) {
+        __syncthreads();                             // every thread: the forward differences are in sD
+        if (valid) {
+            const int pn = D == 0 ? sl - 1 : sl - BX;    // the neighbour one cell below along D
+            if (ts > 0) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) da[v] = sD[v * sz + pn];
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) da[v] = wc[v] - W[v * nt + c - st];
+            }
+        }
+    }
+    if (valid) {
         bool half = false;                       // dl holds half the limited slope
         if (P.limiter == 1 && sizeof(TW) == 8) {
             // FP64 van Leer 2ab/(a+b) for the eight fields with ONE division: batch inversion of
@@ -394,7 +422,10 @@ k_flux(Params P, const TW *__restrict__ W, TW *__restrict__ F)
     constexpr int BX = FluxShape<D>::BX, BY = FluxShape<D>::BY;
     __shared__ TW sW[NV * BY * BX];
     __shared__ TW sP[NV * BY * BX];
-    flux_tile<D, BX, BY, TW, HD>(P, W, F, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, sW, sP);
+    __shared__ TW sD[sizeof(TW) == 8 && !HD ? NV * BY * BX : 1];   // FP64: forward differences
+    flux_tile<D, BX, BY, TW, HD, false, TW>(P, W, F, blockIdx.x, blockIdx.y, blockIdx.z, threadIdx.x, threadIdx.y, sW,
+                                            sP, nullptr, nullptr, nullptr, nullptr,
+                                            sizeof(TW) == 8 && !HD ? sD : nullptr);
 }
 
 // the same with the GLM face step (psi of type TP, its face fluxes into FP)
@@ -657,7 +688,7 @@ __device__ __forceinline__ void update_math(const Params &P, int i, int j, int k
         const TW rho = w[0], vr = w[1], vt = w[2], vp = w[3];
         const TW br = w[5], bt = w[6], bp = w[7];
         const TW ir = m.ih2[ip], cot = m.ct[jp];
-        const TW pt = w[4] + TW(0.5) * (br * br + bt * bt + bp * bp);
+        const TW pt = w[4] + half_r(br * br + bt * bt + bp * bp);
         // geometric terms of the spherical divergence; p_tot through face-area differences
         L[M1] += pt * m.gp1[ip] + (rho * (vt * vt + vp * vp) - (bt * bt + bp * bp)) * ir;
         L[M2] += pt * (m.q1[ip] * m.gq2[jp]) + (-(rho * vr * vt - br * bt) + cot * (rho * vp * vp - bp * bp)) * ir;
@@ -706,9 +737,13 @@ __device__ __forceinline__ void update_math(const Params &P, int i, int j, int k
         const TS dts = (TS)dt;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            TW inc = v >= B1 ? lb[v - B1] : (v == EN ? w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2] : TW(0));
-            if (STAGE == 1) uo[v] = us(v) + dts * (TS)L[v] + (TS)inc;
-            else uo[v] = TS(0.5) * un(v) + TS(0.5) * (us(v) + dts * (TS)L[v] + (TS)inc);
+            // the Linde increment exists for e and B only (no addition of a zero for the others);
+            // the second stage's average (U^n + x) / 2 with the halving on the integer pipe: the
+            // same value as U^n / 2 + x / 2 (exact halvings, one rounding of the sum)
+            TS x = us(v) + dts * (TS)L[v];
+            if (v >= EN) x += (TS)(v >= B1 ? lb[v - B1] : w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2]);
+            if (STAGE == 1) uo[v] = x;
+            else uo[v] = half_r(un(v) + x);
         }
     }
     // non-finite check and floors
