@@ -202,9 +202,28 @@ int build_metrics(icarus_ctx *c)
             const double w1 = iw1[i], w2 = ih2[i] * (1.0 / d2), w3 = ih2[i] * is3[j] * (1.0 / d3);
             ldx2[(size_t)j * p1 + i] = 1.0 / (w1 * w1 + w2 * w2 + w3 * w3);
         }
+    // per-cell products of the per-axis factors (the FP64 update and div B read them); each formed
+    // in the order the device formed it before, so the values are the same
+    const double iv3 = 1.0 / d3;
+    const size_t ncf = (size_t)p1 * p2;
+    std::vector<double> cf((size_t)CF_N * ncf);
+    for (int j = 0; j < p2; ++j)
+        for (int i = 0; i < p1; ++i) {
+            const size_t q = (size_t)j * p1 + i;
+            const double jv = q1[i] * iv2[j];
+            cf[CF_AM * ncf + q] = a1[i] * iv1[i];
+            cf[CF_AP * ncf + q] = a1[i + 1] * iv1[i];
+            cf[CF_BM * ncf + q] = a2[j] * jv;
+            cf[CF_BP * ncf + q] = a2[j + 1] * jv;
+            cf[CF_KV * ncf + q] = q1[i] * q2[j] * iv3;
+            cf[CF_Q1GQ2 * ncf + q] = q1[i] * gq2[j];
+            cf[CF_IH2IG2 * ncf + q] = ih2[i] * ig2[j];
+            cf[CF_IH2IS3 * ncf + q] = ih2[i] * is3[j];
+            cf[CF_JV * ncf + q] = jv;
+        }
     push(x1c); push(a1); push(iv1); push(q1); push(gp1); push(iw1); push(ih2); push(ig1); push(gmr2);
     push(x2c); push(a2); push(iv2); push(q2); push(gq2); push(sn); push(cs); push(ct); push(is3); push(ig2);
-    push(x3c); push(ig3); push(col); push(ldx2);
+    push(x3c); push(ig3); push(col); push(ldx2); push(cf);
     c->metric = (double *)dalloc(c, buf.size() * sizeof(double));
     if (!c->metric) return fail(ICARUS_ENOMEM, "metric allocation failed");
     CK(cudaMemcpyAsync(c->metric, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -222,6 +241,9 @@ int build_metrics(icarus_ctx *c)
         m.x2c = b + off[q++]; m.a2 = b + off[q++]; m.iv2 = b + off[q++]; m.q2 = b + off[q++]; m.gq2 = b + off[q++];
         m.sn = b + off[q++]; m.cs = b + off[q++]; m.ct = b + off[q++]; m.is3 = b + off[q++]; m.ig2 = b + off[q++];
         m.x3c = b + off[q++]; m.ig3 = b + off[q++]; m.colvec = b + off[q++]; m.ldx2 = b + off[q++];
+        m.cf = b + off[q++];
+        m.cf_p1 = p1;
+        m.cf_n = (long long)ncf;
     };
     Metrics &m = c->P.m;
     bind(m, (const double *)c->metric);

@@ -69,10 +69,24 @@ template <typename R> struct MetricsT {
     const R *colvec;
     // Linde diffusion length^2: 1 / (dr^-2 + (r dtheta)^-2 + (r sin(theta) dphi)^-2), [p2][p1]
     const R *ldx2;
+    // per (theta, r) cell, index jp * cf_p1 + ip, [CF_N][p2][p1]: the products of per-axis factors
+    // the FP64 update and div B use, formed once on the host in the same order as the device
+    // would (so the values are the same to the bit): a1 iv1, a1+ iv1, a2 jv, a2+ jv, kv, q1 gq2,
+    // ih2 ig2, ih2 is3, jv, with jv = q1 iv2 and kv = q1 q2 iv3
+    const R *cf;
+    int cf_p1;
+    long long cf_n;
 };
 using Metrics = MetricsT<double>;
 
 // physics constants in the arithmetic type R
+enum { CF_AM = 0, CF_AP, CF_BM, CF_BP, CF_KV, CF_Q1GQ2, CF_IH2IG2, CF_IH2IS3, CF_JV, CF_N };
+
+template <typename R> __host__ __device__ inline R cfv(const MetricsT<R> &m, int q, int ip, int jp)
+{
+    return m.cf[q * m.cf_n + (long long)jp * m.cf_p1 + ip];
+}
+
 template <typename R> struct PhysT {
     R gamma, gm1, igm1, omega, divb_coef, rho_floor, p_floor;   // gm1 = gamma - 1, igm1 = 1 / gm1
 };

@@ -458,8 +458,10 @@ __device__ __forceinline__ void divb_cell(const Params &P, const TW *__restrict_
     const TW *b1 = W + 5 * nt, *b2 = W + 6 * nt, *b3 = W + 7 * nt;
     const long long s2 = P.p1, s3 = (long long)P.p1 * P.p2;
     TW d1 = (m.a1[ip + 1] * (b1[c] + b1[c + 1]) - m.a1[ip] * (b1[c - 1] + b1[c])) * m.iv1[ip];
-    TW d2 = (m.a2[jp + 1] * (b2[c] + b2[c + s2]) - m.a2[jp] * (b2[c - s2] + b2[c])) * (m.q1[ip] * m.iv2[jp]);
-    TW d3 = (b3[c + s3] - b3[c - s3]) * (m.q1[ip] * m.q2[jp] * m.iv3);
+    const TW jv = sizeof(TW) == 8 ? cfv(m, CF_JV, ip, jp) : m.q1[ip] * m.iv2[jp];
+    const TW kv = sizeof(TW) == 8 ? cfv(m, CF_KV, ip, jp) : m.q1[ip] * m.q2[jp] * m.iv3;
+    TW d2 = (m.a2[jp + 1] * (b2[c] + b2[c + s2]) - m.a2[jp] * (b2[c - s2] + b2[c])) * jv;
+    TW d3 = (b3[c + s3] - b3[c - s3]) * kv;
     divB[c] = TW(0.5) * (d1 + d2 + d3);
 }
 
@@ -645,14 +647,18 @@ __global__ void __launch_bounds__(256) k_cfl(Params P, const TW *__restrict__ W)
 template <typename TW> struct DivFactors {
     TW am, ap, iv, bm, bp, jv, kv;
     __device__ __forceinline__ DivFactors(const MetricsT<TW> &m, int ip, int jp)
-        : am(m.a1[ip]), ap(m.a1[ip + 1]), iv(m.iv1[ip]), bm(m.a2[jp]), bp(m.a2[jp + 1]),
-          jv(m.q1[ip] * m.iv2[jp]), kv(m.q1[ip] * m.q2[jp] * m.iv3)
     {
         if constexpr (sizeof(TW) == 8) {
-            am *= iv;
-            ap *= iv;
-            bm *= jv;
-            bp *= jv;
+            // the products a1 iv1, a2 jv, kv from the per-cell table (loads instead of seven
+            // products on the FP64 pipe; the same values)
+            am = cfv(m, CF_AM, ip, jp); ap = cfv(m, CF_AP, ip, jp);
+            bm = cfv(m, CF_BM, ip, jp); bp = cfv(m, CF_BP, ip, jp);
+            kv = cfv(m, CF_KV, ip, jp);
+            iv = jv = TW(0);
+        } else {
+            am = m.a1[ip]; ap = m.a1[ip + 1]; iv = m.iv1[ip]; bm = m.a2[jp]; bp = m.a2[jp + 1];
+            jv = m.q1[ip] * m.iv2[jp];
+            kv = m.q1[ip] * m.q2[jp] * m.iv3;
         }
     }
     // -(1/V) sum_d (A+ F+ - A- F-) of one field
@@ -691,7 +697,8 @@ __device__ __forceinline__ void update_math(const Params &P, int i, int j, int k
         const TW pt = w[4] + half_r(br * br + bt * bt + bp * bp);
         // geometric terms of the spherical divergence; p_tot through face-area differences
         L[M1] += pt * m.gp1[ip] + (rho * (vt * vt + vp * vp) - (bt * bt + bp * bp)) * ir;
-        L[M2] += pt * (m.q1[ip] * m.gq2[jp]) + (-(rho * vr * vt - br * bt) + cot * (rho * vp * vp - bp * bp)) * ir;
+        const TW qg = sizeof(TW) == 8 ? cfv(m, CF_Q1GQ2, ip, jp) : m.q1[ip] * m.gq2[jp];
+        L[M2] += pt * qg + (-(rho * vr * vt - br * bt) + cot * (rho * vp * vp - bp * bp)) * ir;
         L[M3] -= ((rho * vp * vr - bp * br) + cot * (rho * vp * vt - bp * bt)) * ir;
         L[B2] += (vr * bt - vt * br) * ir;
         L[B3] += ((vr * bp - vp * br) + cot * (vt * bp - vp * bt)) * ir;
@@ -719,8 +726,10 @@ __device__ __forceinline__ void update_math(const Params &P, int i, int j, int k
     if (P.divb == 1 && dt > 0.0) {
         const TW coef = ph.divb_coef * m.ldx2[(long long)jp * P.p1 + ip];
         lb[0] = coef * (dbn[1] - dbn[0]) * m.ig1[ip];
-        lb[1] = coef * (dbn[3] - dbn[2]) * (m.ih2[ip] * m.ig2[jp]);
-        lb[2] = coef * (dbn[5] - dbn[4]) * (m.ih2[ip] * m.is3[jp] * m.ig3[k + NG]);
+        const TW hg = sizeof(TW) == 8 ? cfv(m, CF_IH2IG2, ip, jp) : m.ih2[ip] * m.ig2[jp];
+        const TW hs = sizeof(TW) == 8 ? cfv(m, CF_IH2IS3, ip, jp) : m.ih2[ip] * m.is3[jp];
+        lb[1] = coef * (dbn[3] - dbn[2]) * hg;
+        lb[2] = coef * (dbn[5] - dbn[4]) * (hs * m.ig3[k + NG]);
     }
     if constexpr (Prec<TS, TW>::mixed) {
         // MIXED: the increment dt L + (Linde term) is formed in single precision like the fluxes it
