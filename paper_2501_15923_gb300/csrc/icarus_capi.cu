@@ -204,7 +204,7 @@ int build_metrics(icarus_ctx *c)
         }
     // per-cell products of the per-axis factors (the FP64 update and div B read them); each formed
     // in the order the device formed it before, so the values are the same
-    const double iv3 = 1.0 / d3;
+    const double iv3 = 1.0 / d3, opts_divb_coef = P.divb_coef;
     const size_t ncf = (size_t)p1 * p2;
     std::vector<double> cf((size_t)CF_N * ncf);
     for (int j = 0; j < p2; ++j)
@@ -220,6 +220,11 @@ int build_metrics(icarus_ctx *c)
             cf[CF_IH2IG2 * ncf + q] = ih2[i] * ig2[j];
             cf[CF_IH2IS3 * ncf + q] = ih2[i] * is3[j];
             cf[CF_JV * ncf + q] = jv;
+            cf[CF_ORS * ncf + q] = P.omega * x1c[i] * sn[j];
+            const double ld = opts_divb_coef * ldx2[q];
+            cf[CF_LD0 * ncf + q] = ld * ig1[i];
+            cf[CF_LD1 * ncf + q] = ld * (ih2[i] * ig2[j]);
+            cf[CF_LD2 * ncf + q] = ld * (ih2[i] * is3[j]);
         }
     push(x1c); push(a1); push(iv1); push(q1); push(gp1); push(iw1); push(ih2); push(ig1); push(gmr2);
     push(x2c); push(a2); push(iv2); push(q2); push(gq2); push(sn); push(cs); push(ct); push(is3); push(ig2);

@@ -72,7 +72,8 @@ template <typename R> struct MetricsT {
     // per (theta, r) cell, index jp * cf_p1 + ip, [CF_N][p2][p1]: the products of per-axis factors
     // the FP64 update and div B use, formed once on the host in the same order as the device
     // would (so the values are the same to the bit): a1 iv1, a1+ iv1, a2 jv, a2+ jv, kv, q1 gq2,
-    // ih2 ig2, ih2 is3, jv, with jv = q1 iv2 and kv = q1 q2 iv3
+    // ih2 ig2, ih2 is3, jv, with jv = q1 iv2 and kv = q1 q2 iv3; and (CF_ORS, CF_LD*) the rotating
+    // frame's and the Linde term's per-cell factors
     const R *cf;
     int cf_p1;
     long long cf_n;
@@ -80,7 +81,10 @@ template <typename R> struct MetricsT {
 using Metrics = MetricsT<double>;
 
 // physics constants in the arithmetic type R
-enum { CF_AM = 0, CF_AP, CF_BM, CF_BP, CF_KV, CF_Q1GQ2, CF_IH2IG2, CF_IH2IS3, CF_JV, CF_N };
+// CF_ORS: Omega r_c sin(theta_c); CF_LD0..2: the Linde coefficient C_d / sum_d dx_d^-2 times the
+// inverse central-difference widths ig1, ih2 ig2, ih2 is3 (the last times ig3 of the plane)
+enum { CF_AM = 0, CF_AP, CF_BM, CF_BP, CF_KV, CF_Q1GQ2, CF_IH2IG2, CF_IH2IS3, CF_JV, CF_ORS, CF_LD0, CF_LD1, CF_LD2,
+       CF_N };
 
 template <typename R> __host__ __device__ inline R cfv(const MetricsT<R> &m, int q, int ip, int jp)
 {

@@ -707,12 +707,24 @@ __device__ __forceinline__ void update_math(const Params &P, int i, int j, int k
             // (sin th, cos th, 0), Coriolis 2 rho Omega (v_phi sin th, v_phi cos th,
             // -(v_r sin th + v_th cos th)), work of the centrifugal force in e
             const TW Om = ph.omega, sn = m.sn[jp], cs = m.cs[jp], rc = m.x1c[ip];
-            const TW cen = rho * Om * Om * rc * sn;
             const TW vpar = vr * sn + vt * cs;
-            L[M1] += cen * sn + TW(2) * rho * Om * vp * sn;
-            L[M2] += cen * cs + TW(2) * rho * Om * vp * cs;
-            L[M3] -= TW(2) * rho * Om * vpar;
-            L[EN] += cen * vpar;
+            if constexpr (sizeof(TW) == 8) {
+                // cen = (rho Omega) (Omega r sin th) with the second factor from the per-cell
+                // table; the radial and polar parts share the bracket cen + 2 rho Omega v_phi
+                const TW ro = rho * Om, ro2 = ro + ro;
+                const TW cen = ro * cfv(m, CF_ORS, ip, jp);
+                const TW t = cen + ro2 * vp;
+                L[M1] += t * sn;
+                L[M2] += t * cs;
+                L[M3] -= ro2 * vpar;
+                L[EN] += cen * vpar;
+            } else {
+                const TW cen = rho * Om * Om * rc * sn;
+                L[M1] += cen * sn + TW(2) * rho * Om * vp * sn;
+                L[M2] += cen * cs + TW(2) * rho * Om * vp * cs;
+                L[M3] -= TW(2) * rho * Om * vpar;
+                L[EN] += cen * vpar;
+            }
         }
         if (P.gravity) {
             const TW g = m.gm_r2[ip];
@@ -724,12 +736,17 @@ __device__ __forceinline__ void update_math(const Params &P, int i, int j, int k
     // dbn = div B at (i-1, i+1, j-1, j+1, k-1, k+1)
     TW lb[3] = {TW(0), TW(0), TW(0)};
     if (P.divb == 1 && dt > 0.0) {
-        const TW coef = ph.divb_coef * m.ldx2[(long long)jp * P.p1 + ip];
-        lb[0] = coef * (dbn[1] - dbn[0]) * m.ig1[ip];
-        const TW hg = sizeof(TW) == 8 ? cfv(m, CF_IH2IG2, ip, jp) : m.ih2[ip] * m.ig2[jp];
-        const TW hs = sizeof(TW) == 8 ? cfv(m, CF_IH2IS3, ip, jp) : m.ih2[ip] * m.is3[jp];
-        lb[1] = coef * (dbn[3] - dbn[2]) * hg;
-        lb[2] = coef * (dbn[5] - dbn[4]) * (hs * m.ig3[k + NG]);
+        if constexpr (sizeof(TW) == 8) {
+            // coefficient times inverse widths from the per-cell table
+            lb[0] = (dbn[1] - dbn[0]) * cfv(m, CF_LD0, ip, jp);
+            lb[1] = (dbn[3] - dbn[2]) * cfv(m, CF_LD1, ip, jp);
+            lb[2] = (dbn[5] - dbn[4]) * (cfv(m, CF_LD2, ip, jp) * m.ig3[k + NG]);
+        } else {
+            const TW coef = ph.divb_coef * m.ldx2[(long long)jp * P.p1 + ip];
+            lb[0] = coef * (dbn[1] - dbn[0]) * m.ig1[ip];
+            lb[1] = coef * (dbn[3] - dbn[2]) * (m.ih2[ip] * m.ig2[jp]);
+            lb[2] = coef * (dbn[5] - dbn[4]) * (m.ih2[ip] * m.is3[jp] * m.ig3[k + NG]);
+        }
     }
     if constexpr (Prec<TS, TW>::mixed) {
         // MIXED: the increment dt L + (Linde term) is formed in single precision like the fluxes it
