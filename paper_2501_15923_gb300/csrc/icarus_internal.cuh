@@ -221,8 +221,8 @@ template <typename R> __device__ __forceinline__ void cons2prim(const R *u, R *w
     w[1] = u[M1] * irho;
     w[2] = u[M2] * irho;
     w[3] = u[M3] * irho;
-    R ke = R(0.5) * (u[M1] * w[1] + u[M2] * w[2] + u[M3] * w[3]);
-    R me = R(0.5) * (u[B1] * u[B1] + u[B2] * u[B2] + u[B3] * u[B3]);
+    R ke = half_r(u[M1] * w[1] + u[M2] * w[2] + u[M3] * w[3]);     // exact halvings (integer pipe in FP64)
+    R me = half_r(u[B1] * u[B1] + u[B2] * u[B2] + u[B3] * u[B3]);
     w[4] = gm1 * (u[EN] - ke - me);
     w[5] = u[B1];
     w[6] = u[B2];

@@ -457,12 +457,20 @@ __device__ __forceinline__ void divb_cell(const Params &P, const TW *__restrict_
     const int ip = i + NG, jp = j + NG;
     const TW *b1 = W + 5 * nt, *b2 = W + 6 * nt, *b3 = W + 7 * nt;
     const long long s2 = P.p1, s3 = (long long)P.p1 * P.p2;
-    TW d1 = (m.a1[ip + 1] * (b1[c] + b1[c + 1]) - m.a1[ip] * (b1[c - 1] + b1[c])) * m.iv1[ip];
-    const TW jv = sizeof(TW) == 8 ? cfv(m, CF_JV, ip, jp) : m.q1[ip] * m.iv2[jp];
-    const TW kv = sizeof(TW) == 8 ? cfv(m, CF_KV, ip, jp) : m.q1[ip] * m.q2[jp] * m.iv3;
-    TW d2 = (m.a2[jp + 1] * (b2[c] + b2[c + s2]) - m.a2[jp] * (b2[c - s2] + b2[c])) * jv;
-    TW d3 = (b3[c + s3] - b3[c - s3]) * kv;
-    divB[c] = TW(0.5) * (d1 + d2 + d3);
+    TW d1, d2, d3;
+    if constexpr (sizeof(TW) == 8) {
+        // the face areas already divided by the volume factor (per-cell table); the halving on the
+        // integer pipe
+        d1 = cfv(m, CF_AP, ip, jp) * (b1[c] + b1[c + 1]) - cfv(m, CF_AM, ip, jp) * (b1[c - 1] + b1[c]);
+        d2 = cfv(m, CF_BP, ip, jp) * (b2[c] + b2[c + s2]) - cfv(m, CF_BM, ip, jp) * (b2[c - s2] + b2[c]);
+        d3 = (b3[c + s3] - b3[c - s3]) * cfv(m, CF_KV, ip, jp);
+        divB[c] = half_r(d1 + d2 + d3);
+    } else {
+        d1 = (m.a1[ip + 1] * (b1[c] + b1[c + 1]) - m.a1[ip] * (b1[c - 1] + b1[c])) * m.iv1[ip];
+        d2 = (m.a2[jp + 1] * (b2[c] + b2[c + s2]) - m.a2[jp] * (b2[c - s2] + b2[c])) * (m.q1[ip] * m.iv2[jp]);
+        d3 = (b3[c + s3] - b3[c - s3]) * (m.q1[ip] * m.q2[jp] * m.iv3);
+        divB[c] = TW(0.5) * (d1 + d2 + d3);
+    }
 }
 
 template <typename TW>
