@@ -166,6 +166,23 @@ int icarus_set_boundary(icarus_ctx *ctx, int n_maps, const double *t_maps, const
  * icarus_set_state clears the status. */
 int icarus_step(icarus_ctx *ctx, int n);
 
+/* Advance n >= 0 time steps like icarus_step, recovering from a failed attempt. The explicit
+ * scheme of Sect. 2 is stable only below a Courant limit, and a run whose flow outgrows the
+ * configured number (a violent transient: colliding streams, a fast CME front) shows it as a
+ * negative pressure or density (a floor activation, reported when options.strict_floors is set)
+ * or a non-finite state. Before the steps the state, the CME tracer and GLM psi (when carried), the
+ * time, dt, probe-ring position and floor count are copied on the device into a snapshot
+ * (allocated on first use, one state's worth). The call then synchronises and reads the status:
+ * on ENONFINITE or EFLOOR it restores the snapshot, halves the CFL number (dt recomputed from the
+ * restored state) and runs the n steps again, at most max_retries times (0 <= max_retries <= 20).
+ * A retry's probe records replace the failed attempt's. After a retry succeeds, the configured CFL
+ * number is put back and the next dt recomputed with it. *halvings (may be NULL) receives the
+ * halvings the returned attempt used. Returns ICARUS_OK, or, once the retries are spent, the last
+ * attempt's ENONFINITE / EFLOOR with the snapshot restored (configured CFL, its dt) and that
+ * status kept (sticky, as after icarus_step). The status the context already had is returned at
+ * once, without stepping. Synchronous. */
+int icarus_step_recover(icarus_ctx *ctx, int n, int max_retries, int *halvings);
+
 /* Probe sampling (Sect. 2). traj[n_probes][n_knots][4] = (t s, r m, lat rad, lon rad in the
  * inertial frame, unwrapped), knots in increasing t. If traj is non-NULL it is registered for
  * the following steps and the current state is sampled once at the current time. Then the

@@ -634,6 +634,92 @@ int icarus_step(icarus_ctx *c, int n)
     return ICARUS_OK;
 }
 
+int icarus_step_recover(icarus_ctx *c, int n, int max_retries, int *halvings)
+{
+    if (halvings) *halvings = 0;
+    if (n < 0) return fail(ICARUS_EINVAL, "n must be >= 0");
+    if (max_retries < 0 || max_retries > 20) return fail(ICARUS_EINVAL, "max_retries must be in [0, 20]");
+    if (!c) return fail(ICARUS_EINVAL, "NULL context");
+    if (!c->have_state) return fail(ICARUS_ESTATE, "no state: call icarus_set_boundary or icarus_set_state first");
+    if (c->grid.bc[0] == ICARUS_BC_DRIVEN && !c->have_boundary) return fail(ICARUS_ESTATE, "DRIVEN boundary without maps");
+    const Params &P = c->P;
+    cudaStream_t s = c->stream;
+    const size_t nt = P.nt, ts = c->ops.ts_size, tw = c->ops.tw_size;
+    const bool tr = c->opts.tracer != 0, glm = P.divb == ICARUS_DIVB_GLM;
+    Scalars s0;
+    CK(cudaMemcpyAsync(&s0, c->sc, sizeof s0, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (s0.status) return status_fail(s0.status);
+    if (n == 0) return ICARUS_OK;
+    if (!c->snapU) {
+        c->snapU = dalloc(c, NV * nt * ts);
+        if (tr) { c->snapT = dalloc(c, nt * ts); c->snapC = dalloc(c, nt * tw); }
+        if (glm) c->snapPsi = dalloc(c, nt * ts);
+        if (!c->snapU || (tr && (!c->snapT || !c->snapC)) || (glm && !c->snapPsi)) {
+            c->snapU = c->snapT = c->snapC = c->snapPsi = nullptr;   // the allocations stay tracked
+            return fail(ICARUS_ENOMEM, "snapshot allocation failed");
+        }
+    }
+    // the snapshot: the padded state (the primitives are rebuilt from it), tracer, psi; the
+    // scalars (time, dt, ring head, floor count) stay in s0 on the host
+    CK(cudaMemcpyAsync(c->snapU, c->U, NV * nt * ts, cudaMemcpyDeviceToDevice, s));
+    if (tr) {
+        CK(cudaMemcpyAsync(c->snapT, c->T, nt * ts, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(c->snapC, c->C, nt * tw, cudaMemcpyDeviceToDevice, s));
+    }
+    if (glm) CK(cudaMemcpyAsync(c->snapPsi, c->Psi, nt * ts, cudaMemcpyDeviceToDevice, s));
+    // put the snapshot back with CFL number cfl and status word status
+    auto restore = [&](double cfl, int status) -> int {
+        CK(cudaMemcpyAsync(c->U, c->snapU, NV * nt * ts, cudaMemcpyDeviceToDevice, s));
+        c->ops.prims(P, c->U, c->W, s);
+        if (tr) {
+            CK(cudaMemcpyAsync(c->T, c->snapT, nt * ts, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(c->C, c->snapC, nt * tw, cudaMemcpyDeviceToDevice, s));
+        }
+        if (glm) CK(cudaMemcpyAsync(c->Psi, c->snapPsi, nt * ts, cudaMemcpyDeviceToDevice, s));
+        Scalars r = s0;
+        r.cfl = cfl;
+        r.status = status;
+        r.done = 0;
+        CK(cudaMemcpyAsync(c->sc, &r, sizeof r, cudaMemcpyHostToDevice, s));
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s));                      // r is on this frame
+        if (c->hstatus) *(volatile int *)c->hstatus = status;
+        return ICARUS_OK;
+    };
+    const double cfl0 = s0.cfl;
+    double cfl = cfl0;
+    int status = 0;
+    for (int h = 0; h <= max_retries; ++h) {
+        if (h > 0) {
+            cfl *= 0.5;
+            int rc = restore(cfl, 0);
+            if (!rc) rc = first_dt(c);                     // dt of the restored state at the halved CFL
+            if (rc) return rc;
+        }
+        int rc = icarus_step(c, n);
+        if (rc) return rc;
+        Scalars se;
+        CK(cudaMemcpyAsync(&se, c->sc, sizeof se, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        status = se.status;
+        if (!status) {
+            if (halvings) *halvings = h;
+            if (h > 0) {
+                // the configured CFL number back, and the next dt with it
+                se.cfl = cfl0;
+                CK(cudaMemcpyAsync(c->sc, &se, sizeof se, cudaMemcpyHostToDevice, s));
+                return first_dt(c);
+            }
+            return ICARUS_OK;
+        }
+        if (halvings) *halvings = h;
+    }
+    int rc = restore(cfl0, status);
+    if (rc) return rc;
+    return status_fail(status);
+}
+
 int icarus_sample(icarus_ctx *c, int n_probes, int n_knots, const double *traj, double *out, int cap, int *n_written)
 {
     if (!c) return fail(ICARUS_EINVAL, "NULL context");

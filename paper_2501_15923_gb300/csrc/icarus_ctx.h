@@ -25,6 +25,7 @@ struct icarus_ctx {
     size_t maps_cap = 0, tmaps_cap = 0, cme_cap = 0, traj_cap = 0;
     double *hstage = nullptr;       // pinned host staging of the boundary tables (maps, times, CMEs)
     int *hstatus = nullptr;         // host-mapped copy of the status word, written by each step
+    void *snapU = nullptr, *snapT = nullptr, *snapC = nullptr, *snapPsi = nullptr;   // icarus_step_recover's snapshot
     size_t hstage_cap = 0;
     bool have_state = false, have_boundary = false;
     cudaGraphExec_t graph = nullptr;

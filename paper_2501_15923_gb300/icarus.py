@@ -56,6 +56,7 @@ SIGNATURES = {
     "icarus_init": (C.c_int, [C.POINTER(icarus_grid), C.c_double, C.c_double, C.POINTER(icarus_options), C.POINTER(C.c_void_p)]),
     "icarus_set_boundary": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "icarus_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "icarus_step_recover": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "icarus_sample": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "icarus_destroy": (C.c_int, [C.c_void_p]),
     "icarus_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
@@ -189,6 +190,13 @@ def icarus_set_boundary(ctx, t_maps, maps, cmes=None):
 
 def icarus_step(ctx, n: int = 1):
     _check(load().icarus_step(ctx, int(n)))
+
+
+def icarus_step_recover(ctx, n: int = 1, max_retries: int = 3) -> int:
+    """n steps with restore-and-halve-CFL retries; returns the halvings used (raises on failure)."""
+    h = C.c_int(0)
+    _check(load().icarus_step_recover(ctx, int(n), int(max_retries), C.byref(h)))
+    return h.value
 
 
 _registered_probes = {}
@@ -329,6 +337,9 @@ class Solver:
 
     def step(self, n=1):
         icarus_step(self.ctx, n)
+
+    def step_recover(self, n=1, max_retries=3):
+        return icarus_step_recover(self.ctx, n, max_retries)
 
     def sample(self, traj=None, cap=1):
         return icarus_sample(self.ctx, traj, cap)

@@ -131,6 +131,18 @@ def test_null_context_and_negative_counts(ic):
     assert "NULL" in lib.icarus_last_error().decode()
 
 
+def test_step_recover_rejects_bad_arguments(ic):
+    lib = ic.load()
+    h = C.c_int(7)
+    assert lib.icarus_step_recover(None, -1, 3, C.byref(h)) == EINVAL and h.value == 0
+    assert "n must be" in lib.icarus_last_error().decode()
+    for bad in (-1, 21):
+        assert lib.icarus_step_recover(None, 1, bad, None) == EINVAL
+        assert "max_retries" in lib.icarus_last_error().decode()
+    assert lib.icarus_step_recover(None, 1, 3, None) == EINVAL
+    assert "NULL context" in lib.icarus_last_error().decode()
+
+
 def test_barrier_selftest_rejects_bad_arguments(ic):
     """The barrier self-test checks its sizes before any device call."""
     lib = ic.load()
