@@ -347,8 +347,8 @@ int icarus_batch_destroy(icarus_batch *b);
  * A 4-layer 3-D convolutional network (8 -> 32 -> 32 -> 32 -> 8 channels, 3x3x3 kernels, ReLU,
  * phi circular / r and theta replicate padding) that predicts the correction of a coarse state
  * towards the restricted fine solution (not in the paper). BF16 weights and activations, FP32
- * accumulation on the tensor cores (forward and data gradient with tcgen05, weight gradient with
- * mma.sync), FP32 Adam master weights; device memory from cudaMalloc, released by
+ * accumulation on the 5th-generation tensor cores (tcgen05: forward, data and weight gradients),
+ * FP32 Adam master weights; device memory from cudaMalloc, released by
  * icarus_closure_destroy. Every wait of the tcgen05 kernels is bounded: one that expires makes
  * the call return ETIMEOUT. */
 typedef struct icarus_closure icarus_closure;

@@ -8,8 +8,9 @@
 // convolution over the padded grid with the transposed, tap-reversed weights, rows = padded
 // voxels, K = 27 x C_out) on the 5th-generation tensor cores (tcgen05.mma, accumulators in tensor
 // memory, operands brought into shared memory by the tensor memory accelerator); the weight
-// gradient (rows = C_out, columns = C_in, K = voxels, split over blocks and summed with atomics)
-// with mma.sync m16n8k16 fed by ldmatrix. Activations are stored
+// gradient on the same tensor cores (rows = the three r shifts x C_out, columns = the nine
+// (theta, phi) lines x C_in, K = padded positions split over blocks, operands transposed into
+// shared memory with movmatrix, blocks' partial sums reduced by a second kernel). Activations are stored
 // channels-last on a grid padded by one ghost layer; a pad kernel fills the ghosts (replicate /
 // circular) and a fold kernel adds ghost gradients back to the cells they copy (the adjoint).
 // Channel counts are padded to multiples of 16 (layer 0 input 8 -> 16 zero channels, layer 3
@@ -51,33 +52,9 @@ __host__ __device__ __forceinline__ long long pidx(const Geo &g, int i, int j, i
     return ((long long)(k + 1) * g.q2 + (j + 1)) * g.q1 + (i + 1);
 }
 
-__device__ __forceinline__ long long pidx_of_voxel(const Geo &g, long long v)
-{
-    int i = (int)(v % g.n1);
-    long long r = v / g.n1;
-    int j = (int)(r % g.n2), k = (int)(r / g.n2);
-    return pidx(g, i, j, k);
-}
-
-// padded-index offset of tap t = (d3 + 1) * 9 + (d2 + 1) * 3 + (d1 + 1)
-__device__ __forceinline__ long long tap_off(const Geo &g, int t)
-{
-    int d1 = t % 3 - 1, d2 = (t / 3) % 3 - 1, d3 = t / 9 - 1;
-    return ((long long)d3 * g.q2 + d2) * g.q1 + d1;
-}
-
 __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi)
 {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-// D = A (16x16, row) * B (16x8, col) + D, BF16 inputs, FP32 accumulators
-__device__ __forceinline__ void mma16816(float *d, const uint32_t *a, uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};\n"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // ---- forward on the 5th-generation tensor cores (tcgen05, accumulators in tensor memory) ---------
@@ -463,92 +440,222 @@ __global__ void __launch_bounds__(256) k_dpre(Geo g, const float *__restrict__ d
     if (threadIdx.x < O) atomicAdd(&db[threadIdx.x], sdb[threadIdx.x]);
 }
 
-// ---- weight gradient: dw[o][t][c] += sum_x dpre[x][o] in[x + off_t][c] ----------------------------
-// block = 4 warps over a chunk of TC_WG voxels: the chunk's output gradients (and its voxels'
-// padded indices) are staged in shared memory once; per tap the (O x C) tile is accumulated over
-// the chunk in stages of 64 voxels (the tap's inputs staged with 16-byte loads) and added to dw
-// with atomics. Both operands are voxel-major in shared memory (rows padded by 8 elements so that
-// the eight 16-byte rows of a fragment fall in distinct banks) and reach the MMA fragments by
-// transposing ldmatrix loads.
-constexpr int TC_WG = 448;
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t *r, const void *p)
+// ---- weight gradient on the 5th-generation tensor cores ------------------------------------------
+// dw[o][t][c] += sum over interior voxels x of dpre[x][o] in[x + off_t][c], tap t = (d1, d2, d3).
+// With the output gradients zero on the ghost cells, one contiguous range of padded positions p
+// serves every tap: writing x = p - d1, the sum is sum_p dpre[p - d1][o] in[p + off(d2, d3)][c],
+// off(d2, d3) = (d3 q2 + d2) q1 (the line of the tap), over p in [(q2 + 1) q1, last interior + 2).
+// As one GEMM: D[(d1, o)][(line, c)] = sum_p A[(d1, o)][p] B[(line, c)][p], M = 3 O rows (padded
+// to 128), N = 9 C columns (the nine lines (d2, d3); two MMAs of N = 144 at C = 32), K = the
+// positions, split into one contiguous range per block (one block per SM; whole 64-position
+// stages, so only the last block runs past the range, where dpre is zero: every padded position
+// after the last interior cell is a ghost). The accumulator lives in tensor memory over the
+// block's whole range and is written out once as a partial sum; a second kernel adds the blocks'
+// partials into dw.
+// A stage's raw rows (66 rows of dpre, 64 rows of each of the nine input lines, channels-last)
+// arrive by ten tensor-memory-accelerator box copies with the 64-byte (32-byte at 16 channels)
+// swizzle, three stages ahead in a ring of four buffers. Each stage is transposed into the K-major
+// operand layout of the forward kernels (a 16-byte row holds 8 consecutive positions of one
+// channel) by ldmatrix.trans, warp w taking the 8 x 8 tiles of positions 8 w .. 8 w + 7 (one tile
+// per channel group and matrix of the ldmatrix; the swizzle puts the eight rows of a tile in
+// distinct banks), once the previous stage's MMAs, which read the single operand buffer, have
+// committed. Bounded waits; on expiry the block records the failure in tc_status.
+constexpr int WG_KS = 64;                                          // positions per stage
+constexpr int WG_RING = 4;                                         // raw-row buffers (fetch distance 3)
+template <int C> __host__ __device__ constexpr int wg_a_bytes() { return (WG_KS / 8) * 128 * 16; }
+template <int C> __host__ __device__ constexpr int wg_b_bytes() { return (WG_KS / 8) * 9 * C * 16; }
+// raw rows of dpre (rounded up to the 1024-byte alignment of a swizzled copy) and of the lines
+template <int O> __host__ __device__ constexpr int wg_ra_bytes() { return ((WG_KS + 2) * 2 * O + 1023) / 1024 * 1024; }
+template <int C> __host__ __device__ constexpr int wg_rb_bytes() { return 9 * WG_KS * 2 * C; }
+// [raw rows x WG_RING][operands][barriers: 128] + 1024 B of alignment
+template <int C, int O> __host__ __device__ constexpr int wg_smem_bytes()
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(saddr(p)));
+    return 1024 + WG_RING * (wg_ra_bytes<O>() + wg_rb_bytes<C>()) + wg_a_bytes<C>() + wg_b_bytes<C>() + 128;
 }
 
-__device__ __forceinline__ void ldsm_x2_t(uint32_t *r, const void *p)
+// byte offset of 16-byte piece grp of raw row r (G pieces of 16 bytes per row) in a 1024-byte
+// aligned buffer written by a swizzled tensor copy: the piece index is XORed with address bits 7-8
+// (64-byte swizzle, G = 4) or bit 7 (32-byte swizzle, G = 2)
+template <int G> __device__ __forceinline__ int wg_piece(int r, int grp)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(saddr(p)));
+    return r * (16 * G) + 16 * (grp ^ (G == 4 ? (r >> 1) & 3 : (r >> 2) & 1));
 }
+
+// the raw rows of the stage starting at p0: dpre rows p0 - 1 .. p0 + 64 into ra, rows p0 + off(line)
+// .. + 63 of the input into rb (line after line); rows past the arrays read as zero
 template <int C, int O>
-__global__ void __launch_bounds__(128) k_conv_wgrad(Geo g, const bf16 *__restrict__ dpre, const bf16 *__restrict__ in,
-                                                    float *dw)
+__device__ __forceinline__ void wg_fetch(const CUtensorMap *ta, const CUtensorMap *tb, const Geo &g, long long p0,
+                                         unsigned char *ra, unsigned char *rb, uint32_t bar)
 {
-    constexpr int MT = O / 16, NT = C / 8, TILES = MT * NT, PER = (TILES + 3) / 4;
-    __shared__ __align__(16) bf16 sD[TC_WG][O + 8];
-    __shared__ __align__(16) bf16 sX[64][C + 8];
-    __shared__ long long spb[TC_WG];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, grp = lane >> 2, tig = lane & 3;
-    const long long vb = (long long)blockIdx.x * TC_WG;
-    const int nv = (int)min((long long)TC_WG, g.N - vb);
-    for (int q = threadIdx.x; q < TC_WG; q += blockDim.x) spb[q] = q < nv ? pidx_of_voxel(g, vb + q) : -1;
-    __syncthreads();
-    for (int e = threadIdx.x; e < TC_WG * (O / 8); e += blockDim.x) {      // 16-byte pieces
-        const int row = e / (O / 8), cp = e % (O / 8);
-        const uint4 val = spb[row] >= 0 ? *reinterpret_cast<const uint4 *>(dpre + spb[row] * O + cp * 8) : make_uint4(0, 0, 0, 0);
-        *reinterpret_cast<uint4 *>(&sD[row][cp * 8]) = val;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
+                 "r"((WG_KS + 2) * 2 * O + 9 * WG_KS * 2 * C)
+                 : "memory");
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+                 ::"r"(saddr(ra)), "l"(ta), "r"(0), "r"((int)(p0 - 1)), "r"(bar)
+                 : "memory");
+#pragma unroll
+    for (int line = 0; line < 9; ++line) {
+        const long long row = p0 + ((long long)(line / 3 - 1) * g.q2 + (line % 3 - 1)) * g.q1;
+        asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+                     ::"r"(saddr(rb + line * WG_KS * 2 * C)), "l"(tb), "r"(0), "r"((int)row), "r"(bar)
+                     : "memory");
     }
+}
+
+// the 8 x 8 tiles of position group kc (this warp's) of one operand, sel = 0 .. NSEL - 1, channel
+// groups 0 .. G - 1: raw rows row0(sel) + 8 kc .. + 7, transposed by ldmatrix.trans (matrix =
+// channel group) into the core matrices at dst + kc kstride + (sel G + grp) 128
+template <int G, int NSEL, typename Row0>
+__device__ __forceinline__ void wg_transpose(const unsigned char *raw, Row0 row0, unsigned char *dst, int kstride, int kc,
+                                             int lane)
+{
+    const int m = (lane >> 3) % G, r = lane & 7;
+    const uint32_t base = saddr(raw);
+    uint32_t *out = reinterpret_cast<uint32_t *>(dst + kc * kstride) + lane;
+#pragma unroll
+    for (int sel = 0; sel < NSEL; ++sel) {
+        const uint32_t a = base + (uint32_t)wg_piece<G>(row0(sel) + 8 * kc + r, m);
+        if constexpr (G == 4) {
+            uint32_t t[4];
+            asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                         : "=r"(t[0]), "=r"(t[1]), "=r"(t[2]), "=r"(t[3]) : "r"(a));
+#pragma unroll
+            for (int j = 0; j < 4; ++j) out[(sel * G + j) * 32] = t[j];
+        } else {
+            uint32_t t[2];
+            asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(t[0]), "=r"(t[1]) : "r"(a));
+#pragma unroll
+            for (int j = 0; j < 2; ++j) out[(sel * G + j) * 32] = t[j];
+        }
+    }
+}
+
+template <int C, int O>
+__global__ void __launch_bounds__(256, 1) k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tm_a,
+                                                          const __grid_constant__ CUtensorMap tm_b, Geo g,
+                                                          float *__restrict__ part, long long p_lo, long long p_hi,
+                                                          long long chunk)
+{
+    constexpr int NC = 9 * C, NH = NC > 256 ? 2 : 1, NN = NC / NH, TCOLS = NC > 256 ? 512 : 256;
+    constexpr int AB = wg_a_bytes<C>(), KC = WG_KS / 8;
+    constexpr int RAB = wg_ra_bytes<O>(), RSB = RAB + wg_rb_bytes<C>();
+    static_assert(NN % 16 == 0 && NN <= 256 && 3 * O <= 128, "tile shape");
+    static_assert(KC == 8 && (O == 16 || O == 32) && (C == 16 || C == 32), "one warp per position group of 8");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *raw0 = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
+    // [raw rows x WG_RING][operands A | B][MMA barrier | ring barriers | tensor-memory address | flag]
+    unsigned char *sA = raw0 + WG_RING * RSB, *sB = sA + AB, *hdr = sB + wg_b_bytes<C>();
+    const uint32_t mbar = saddr(hdr), full0 = saddr(hdr + 8), slot = saddr(hdr + 8 + 8 * WG_RING);
+    volatile int *flag = reinterpret_cast<volatile int *>(hdr + 12 + 8 * WG_RING);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long b0 = p_lo + (long long)blockIdx.x * chunk, b1 = min(b0 + chunk, p_hi);
+    const int nst = b1 > b0 ? (int)((b1 - b0 + WG_KS - 1) / WG_KS) : 0;
+    // rows 3 O .. 127 of A (no output) are zero
+    for (int q = tid; q < KC * (128 - 3 * O) * 4; q += blockDim.x) {
+        const int w4 = q % 4, rq = q / 4, row = 3 * O + rq % (128 - 3 * O), kc = rq / (128 - 3 * O);
+        reinterpret_cast<uint32_t *>(sA + kc * 2048 + row * 16)[w4] = 0u;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot), "n"(TCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    int issued = 0;                                                // stages whose copies were started
+    if (tid == 0) {
+        for (int q = 0; q <= WG_RING; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar + 8 * q) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tm_a) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tm_b) : "memory");
+        for (; issued < WG_RING - 1 && issued < nst; ++issued)
+            wg_fetch<C, O>(&tm_a, &tm_b, g, b0 + (long long)issued * WG_KS, raw0 + issued * RSB, raw0 + issued * RSB + RAB,
+                           full0 + 8 * issued);
+        *flag = 1;
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    const int nstage = (nv + 63) / 64;
-    for (int tt = 0; tt < 27; ++tt) {
-        const int t = (tt + (int)(blockIdx.x % 27)) % 27;      // blocks start on different taps, so
-        const long long off = tap_off(g, t);                   // their atomics meet fewer addresses
-        float acc[PER][4];
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(hdr + 8 + 8 * WG_RING);
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    bool failed = false;
+    int consumed = 0;                                              // stages whose copies were waited for
+    for (int s = 0; s < nst; ++s) {
+        const int q = s % WG_RING;
+        unsigned char *ra = raw0 + q * RSB, *rb = ra + RAB;
+        const bool got = mbar_wait(full0 + 8 * q, (uint32_t)((s / WG_RING) & 1));   // every thread: its view of the copy
+        if (s >= 1 && tid == 0)                                    // stage s - 1's MMAs read the operands
+            *flag = mbar_wait(mbar, (uint32_t)((s - 1) & 1)) ? 1 : 0;
+        if (__syncthreads_or(!got) || *flag == 0) { failed = true; break; }
+        consumed = s + 1;
+        if (tid == 0 && issued < nst) {                            // into the buffer stage s - 1 left
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            const int qn = issued % WG_RING;
+            wg_fetch<C, O>(&tm_a, &tm_b, g, b0 + (long long)issued * WG_KS, raw0 + qn * RSB, raw0 + qn * RSB + RAB,
+                           full0 + 8 * qn);
+            ++issued;
+        }
+        wg_transpose<O / 8, 3>(ra, [](int sel) { return 2 - sel; }, sA, 2048, warp, lane);
+        wg_transpose<C / 8, 9>(rb, [](int line) { return line * WG_KS; }, sB, NC * 16, warp, lane);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();                                           // operands written, raw rows read
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-        for (int p = 0; p < PER; ++p)
+            for (int ks = 0; ks < KC / 2; ++ks) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[p][e] = 0.f;
-        for (int st = 0; st < nstage; ++st) {
-            const int rb = st * 64;
-            for (int e = threadIdx.x; e < 64 * (C / 8); e += blockDim.x) {
-                const int row = e / (C / 8), cp = e % (C / 8);
-                const long long pb = spb[rb + row];
-                const uint4 val = pb >= 0 ? *reinterpret_cast<const uint4 *>(in + (pb + off) * C + cp * 8) : make_uint4(0, 0, 0, 0);
-                *reinterpret_cast<uint4 *>(&sX[row][cp * 8]) = val;
-            }
-            __syncthreads();
-            const int lr = lane & 7, lj = lane >> 3;          // ldmatrix: row and matrix of this lane
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-                for (int p = 0; p < PER; ++p) {
-                    const int tile = warp + 4 * p;
-                    if (tile >= TILES) break;
-                    const int mt = tile / NT, nt = tile % NT;
-                    // A[o][k] = sD[k][o]: matrices (o 0-7 | 8-15) x (k 0-7 | 8-15); B[k][c] = sX[k][c]
-                    uint32_t a[4], bb[2];
-                    ldsm_x4_t(a, &sD[rb + kk * 16 + lr + (lj >> 1) * 8][mt * 16 + (lj & 1) * 8]);
-                    ldsm_x2_t(bb, &sX[kk * 16 + lr + (lj & 1) * 8][nt * 8]);
-                    mma16816(acc[p], a, bb[0], bb[1]);
+                for (int h = 0; h < NH; ++h) {
+                    const uint64_t ad = umma_desc(saddr(sA) + ks * 2 * 2048, 2048, 128);
+                    const uint64_t bd = umma_desc(saddr(sB) + ks * 2 * (NC * 16) + h * (NN / 8) * 128, NC * 16, 128);
+                    const uint32_t en = (s | ks) ? 1u : 0u;
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + (uint32_t)(h * NN)),
+                                 "l"(ad), "l"(bd), "r"(idesc), "r"(en)
+                                 : "memory");
                 }
             }
-            __syncthreads();
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar) : "memory");
         }
+    }
+    if (tid == 0) {
+        // copies started but not waited for (a failed block) end before the block does
+        for (int t = failed ? consumed : issued; t < issued; ++t) mbar_wait(full0 + 8 * (t % WG_RING), (uint32_t)((t / WG_RING) & 1));
+        if (!failed && nst > 0) *flag = mbar_wait(mbar, (uint32_t)((nst - 1) & 1)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*flag == 0) failed = true;
+    if (failed) {
+        if (tid == 0) atomicExch(&tc_status, 1);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const int qd = warp & 3, hf = warp >> 2, row = 32 * qd + lane;
+        float *dst = part + ((long long)blockIdx.x * 3 * O + row) * NC;
+        for (int c0 = hf * (NC / 2); c0 < (hf + 1) * (NC / 2); c0 += 8) {
+            uint32_t r[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                         : "r"(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (row < 3 * O) {
 #pragma unroll
-        for (int p = 0; p < PER; ++p) {
-            const int tile = warp + 4 * p;
-            if (tile >= TILES) break;
-            const int mt = tile / NT, nt = tile % NT;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int o = mt * 16 + grp + 8 * (e >> 1), c = nt * 8 + tig * 2 + (e & 1);
-                atomicAdd(&dw[((long long)o * 27 + t) * C + c], acc[p][e]);
+                for (int e = 0; e < 8; ++e) dst[c0 + e] = nst > 0 ? __uint_as_float(r[e]) : 0.f;
             }
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TCOLS) : "memory");
+}
+
+// dw[o][t][c] += the blocks' partial sums of row (d1 + 1) O + o, column line C + c, t = 3 line + d1 + 1
+template <int C, int O>
+__global__ void k_wgrad_reduce(const float *__restrict__ part, int nblk, float *dw)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= O * 27 * C) return;
+    const int c = e % C, t = (e / C) % 27, o = e / (27 * C);
+    const int row = (t % 3) * O + o, col = (t / 3) * C + c;
+    float s = 0.f;
+    for (int b = 0; b < nblk; ++b) s += part[((long long)b * 3 * O + row) * (9 * C) + col];
+    dw[e] += s;
 }
 
 
@@ -707,6 +814,27 @@ bool tc_tensor_map(CUtensorMap *tm, const bf16 *buf, const Geo &g, int C)
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2-D tensor map of a channels-last BF16 buffer [rows][ch] (ch = 16 or 32) read in boxes of
+// box_rows whole rows with the 32-byte (16 channels) or 64-byte (32 channels) swizzle
+bool wg_tensor_map(CUtensorMap *tm, const bf16 *buf, long long rows, int ch, int box_rows)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)ch, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ch * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)ch, (cuuint32_t)box_rows}, estr[2] = {1, 1};
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  ch == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int C, int O, int ACT> int tc_prepare()
 {
     static int sms = 0;
@@ -792,12 +920,46 @@ void launch_fwd(int l, Geo g, const bf16 *in, const bf16 *w, const float *b, bf1
     else launch_fwd_tc<32, 16, 0>(g, in, w, b, out_pad, out_f, s);
 }
 
-void launch_wgrad(int l, Geo g, const bf16 *dpre, const bf16 *in, float *dw, cudaStream_t s)
+// weight gradient of geometry g: one tensor-core block per SM over its range of padded positions,
+// then the reduction of the blocks' partials (part: wgrad_part_floats() floats) into dw
+template <int C, int O>
+void launch_wgrad_tc(Geo g, const bf16 *dpre, const bf16 *in, float *dw, float *part, cudaStream_t s)
 {
-    const unsigned int nb = ccdiv(g.N, TC_WG);
-    if (l == 0) k_conv_wgrad<16, 32><<<nb, 128, 0, s>>>(g, dpre, in, dw);
-    else if (l < 3) k_conv_wgrad<32, 32><<<nb, 128, 0, s>>>(g, dpre, in, dw);
-    else k_conv_wgrad<32, 16><<<nb, 128, 0, s>>>(g, dpre, in, dw);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_conv_wgrad_tc<C, O>, cudaFuncAttributeMaxDynamicSharedMemorySize, wg_smem_bytes<C, O>());
+    }
+    const long long p_lo = (long long)(g.q2 + 1) * g.q1;
+    const long long p_hi = ((long long)g.n3 * g.q2 + g.n2) * g.q1 + g.n1 + 2;
+    const long long span = p_hi - p_lo;
+    const long long chunk = (span + (long long)sms * WG_KS - 1) / ((long long)sms * WG_KS) * WG_KS;
+    const int nb = (int)((span + chunk - 1) / chunk);
+    CUtensorMap ta, tb;
+    if (!wg_tensor_map(&ta, dpre, g.NP, O, WG_KS + 2) || !wg_tensor_map(&tb, in, g.NP, C, WG_KS)) {
+        tc_host_error = true;
+        return;
+    }
+    k_conv_wgrad_tc<C, O><<<nb, 256, wg_smem_bytes<C, O>(), s>>>(ta, tb, g, part, p_lo, p_hi, chunk);
+    k_wgrad_reduce<C, O><<<ccdiv(O * 27 * C, 256), 256, 0, s>>>(part, nb, dw);
+}
+
+// floats of the partial-sum buffer of launch_wgrad (one block per SM, 3 x 32 rows x 9 x 32 columns)
+size_t wgrad_part_floats()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (size_t)(sms > 0 ? sms : 1) * 3 * 32 * 9 * 32;
+}
+
+void launch_wgrad(int l, Geo g, const bf16 *dpre, const bf16 *in, float *dw, float *part, cudaStream_t s)
+{
+    if (l == 0) launch_wgrad_tc<16, 32>(g, dpre, in, dw, part, s);
+    else if (l < 3) launch_wgrad_tc<32, 32>(g, dpre, in, dw, part, s);
+    else launch_wgrad_tc<32, 16>(g, dpre, in, dw, part, s);
 }
 
 void launch_dgrad(int l, Geo g, const bf16 *dpre, const bf16 *wt, float *din, cudaStream_t s)
@@ -825,6 +987,7 @@ struct icarus_closure {
     bf16 *act[4];          // padded activations: act[0] = normalised input (16 ch), act[l] = output of layer l-1
     bf16 *dpre;            // padded, max 32 channels
     float *din;            // padded fp32, 32 channels
+    float *wpart;          // partial sums of the weight-gradient blocks
     float *y, *dy;         // [N][16]
     double *mean, *scale, *oscale, *loss, *upack;
     int step = 0;
@@ -944,7 +1107,8 @@ int icarus_closure_create(int n1, int n2, int n3, unsigned long long seed, void 
         c->oscale = (double *)cl_alloc(c, 8 * n1 * 8);
         c->loss = (double *)cl_alloc(c, 8);
         c->upack = (double *)cl_alloc(c, 8 * g.N * 8);
-        ok = c->dpre && c->din && c->y && c->dy && c->mean && c->scale && c->oscale && c->loss && c->upack;
+        c->wpart = (float *)cl_alloc(c, wgrad_part_floats() * 4);
+        ok = c->dpre && c->din && c->y && c->dy && c->mean && c->scale && c->oscale && c->loss && c->upack && c->wpart;
     }
     if (!ok) {
         for (void *p : c->allocs) cudaFree(p);
@@ -999,7 +1163,7 @@ int icarus_closure_train_step(icarus_closure *c, const double *U_in, const doubl
     for (int l = 3; l >= 0; --l) {
         if (l == 3) launch_dpre(LO[l], g, c->dy, 0, nullptr, c->dpre, c->db[l], s);
         else launch_dpre(LO[l], g, c->din, 1, c->act[l + 1], c->dpre, c->db[l], s);
-        launch_wgrad(l, g, c->dpre, c->act[l], c->dw[l], s);
+        launch_wgrad(l, g, c->dpre, c->act[l], c->dw[l], c->wpart, s);
         if (l > 0) {
             launch_dgrad(l, g, c->dpre, c->wt[l], c->din, s);
             k_pad_fold<<<ccdiv(g.NP, 256), 256, 0, s>>>(g, c->din, LC[l]);
@@ -1130,7 +1294,7 @@ int icarus_conv3d_layer(int n1, int n2, int n3, int C, int O, int act, const flo
          *wt = (bf16 *)A(O * 27 * C * 2), *dpre = (bf16 *)A(gg.NP * O * 2);
     float *wf = (float *)A(O * 27 * C * 4), *bf = (float *)A(O * 4), *yf = (float *)A(gg.N * O * 4),
           *gf = (float *)A(gg.N * O * 4), *dinf = (float *)A(gg.NP * C * 4), *dwf = (float *)A(O * 27 * C * 4),
-          *dbf = (float *)A(O * 4);
+          *dbf = (float *)A(O * 4), *wpart = (float *)A(wgrad_part_floats() * 4);
     int rc = ICARUS_OK;
     for (void *p : mem) if (!p) rc = report_error(ICARUS_ENOMEM, "allocation failed");
     if (!rc) {
@@ -1151,7 +1315,7 @@ int icarus_conv3d_layer(int n1, int n2, int n3, int C, int O, int act, const flo
         launch_fwd(l, gg, din_, wb, bf, act ? dout_ : nullptr, yf, 0);
         if (act) k_pad_fill<bf16><<<ccdiv(gg.NP, 256), 256>>>(gg, dout_, O);
         launch_dpre(O, gg, gf, 0, act ? dout_ : nullptr, dpre, dbf, 0);
-        launch_wgrad(l, gg, dpre, din_, dwf, 0);
+        launch_wgrad(l, gg, dpre, din_, dwf, wpart, 0);
         if (C == 32) {
             if (O == 16) launch_dgrad_tc<16, 32>(gg, dpre, wt, dinf, 0);
             else launch_dgrad_tc<32, 32>(gg, dpre, wt, dinf, 0);

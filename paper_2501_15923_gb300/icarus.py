@@ -555,7 +555,10 @@ class Closure:
         _check(load().icarus_closure_create(n1, n2, n3, seed, C.c_void_p(stream), C.byref(self.h)))
 
     def set_norm(self, in_mean, in_scale, out_scale):
+        """Per-field, per-radial-index statistics, each [8][n1] (the C call reads 8 n1 doubles)."""
         a = [np.ascontiguousarray(x, dtype=np.float64) for x in (in_mean, in_scale, out_scale)]
+        if any(x.size != 8 * self.shape[0] for x in a):
+            raise ValueError(f"normalisation arrays must hold 8 x n1 = {8 * self.shape[0]} values")
         _check(load().icarus_closure_set_norm(self.h, *(_ptr(x) for x in a)))
 
     def train_step(self, U_dev_ptr, dU_dev_ptr, lr):

@@ -283,7 +283,7 @@ def time_network(shape=(256, 32, 64), reps: int = 20, seed: int = 5):
     import torch
     n1, n2, n3 = shape
     net = ic.Closure(n1, n2, n3, seed=seed, stream=torch.cuda.current_stream().cuda_stream)
-    net.set_norm(np.zeros(8), np.ones(8), np.ones(8))
+    net.set_norm(np.zeros((8, n1)), np.ones((8, n1)), np.ones((8, n1)))
     g = torch.Generator(device="cuda").manual_seed(seed)
     U = torch.randn((8, n3, n2, n1), dtype=torch.float64, device="cuda", generator=g)
     dU = torch.randn((8, n3, n2, n1), dtype=torch.float64, device="cuda", generator=g) * 0.01

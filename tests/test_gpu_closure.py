@@ -6,7 +6,9 @@ GPU result differs from the oracle only by its FP32 accumulation (relative ~1e-6
 GPU training uses (data, weight, bias), including the ReLU mask and the padding's adjoint. The
 shapes cover the tensor-core forward's tiling: ragged 128-voxel tiles along r, several tiles per
 r-line, columns walked along k in chunks of 8 with a ring of k-planes that wraps (n3 = 9, 19),
-and a single k-plane.
+and a single k-plane; and the weight gradient's split of the padded positions over one block per
+SM: one 64-position stage per block on the small shapes, four stages (both shared-memory buffers
+refilled) on 128 x 16 x 16.
 """
 import numpy as np
 import pytest
@@ -38,7 +40,7 @@ def bf16(a):
                                             (32, 32, 1, (40, 12, 10)), (32, 32, 1, (150, 5, 3)),
                                             (16, 32, 1, (256, 3, 2)), (32, 16, 0, (129, 4, 3)),
                                             (32, 32, 1, (140, 3, 19)), (16, 32, 1, (20, 2, 9)),
-                                            (32, 16, 0, (7, 3, 1))])
+                                            (32, 16, 0, (7, 3, 1)), (32, 32, 1, (128, 16, 16))])
 def test_layer_forward_and_gradients_match_oracle(ic, C, Oc, act, shape):
     n1, n2, n3 = shape
     rng = np.random.default_rng(C * 100 + Oc + n1)
