@@ -103,6 +103,8 @@ struct Scalars {               // device-resident step state
     unsigned long long floor_hits;
     long long ring_head;            // probe records written so far
     double dt_step;                 // dt of the step just completed (set when t advances)
+    unsigned int smax_seen;         // FP64 second-stage update: largest CFL speed estimate published
+                                    // by its blocks so far (float bits; zero between launches)
 };
 
 struct Params {

@@ -528,6 +528,7 @@ __device__ __forceinline__ void finish_dt(Params &P, double smax_block, int adva
         sc->t = t;
         sc->dt = dt;
         sc->done = 0;
+        sc->smax_seen = 0u;             // every block of this launch has published its estimate
         // the step's status for icarus_step, which reads it on the host without synchronising
         if (advance_t && P.hstatus) *(volatile int *)P.hstatus = atomicOr(&sc->status, 0);
     }
@@ -605,19 +606,29 @@ __device__ __forceinline__ float block_max_all(float v)
 }
 
 // block maximum of the CFL signal speed (valid in thread 0; every thread of the block calls it).
-// FP64: the single-precision estimate of every cell selects the cells within 1 % of the block's
-// largest estimate, and only those evaluate the exact FP64 speed. With estimate errors below 1e-3
-// the cell of the exact maximum always passes (its estimate is >= (1 - 1e-3) / (1 + 1e-3) of the
-// largest), so the result is the exact FP64 maximum, as if every cell had been evaluated
+// FP64: the single-precision estimate of every cell selects the cells within 1 % of the largest
+// estimate seen, and only those evaluate the exact FP64 speed. With estimate errors below 1e-3
+// the cell of the exact maximum always passes (its estimate is >= (1 - 1e-3) / (1 + 1e-3) of any
+// cell's), so the result is the exact FP64 maximum, as if every cell had been evaluated. "Seen" is
+// the block's own largest estimate, and, with glb (the launch's running maximum of the blocks'
+// largest estimates as float bits, zero at the launch start), every earlier block's too: the blocks
+// whose estimates all stay 1 % below one published by another block then evaluate no exact speed
 template <typename TW>
-__device__ __forceinline__ double cfl_block_speed(const Params &P, const TW *wo, int ip, int jp, bool valid)
+__device__ __forceinline__ double cfl_block_speed(const Params &P, const TW *wo, int ip, int jp, bool valid,
+                                                  unsigned int *glb = nullptr)
 {
     if constexpr (sizeof(TW) == 4) {
         // single precision: reduce the float speeds, convert the block maximum once
         return (double)block_max_all(valid ? cell_speed_t<TW>(P, wo, ip, jp) : 0.f);
     } else {
         const float e = valid ? cell_speed_est(P, wo, ip, jp) : 0.f;
-        const float top = block_max_all(e);
+        float top = block_max_all(e);
+        if (glb) {
+            __shared__ float seen;
+            if (threadIdx.x == 0) seen = fmaxf(top, __uint_as_float(atomicMax(glb, __float_as_uint(top))));
+            __syncthreads();
+            top = seen;
+        }
         return block_max(valid && e >= top * 0.99f ? cell_speed<TW>(P, wo, ip, jp) : 0.0);
     }
 }
@@ -884,7 +895,7 @@ __device__ __forceinline__ void update_kernel_body(Params &P, const TS *__restri
     if (STAGE == 2) {
         const unsigned int t32 = (unsigned int)tid, n1u = (unsigned int)P.n1;
         const int i = valid ? (int)(t32 % n1u) : 0, j = valid ? (int)((t32 / n1u) % (unsigned int)P.n2) : 0;
-        finish_dt(P, cfl_block_speed<TW>(P, wo, i + NG, j + NG, valid), 1);
+        finish_dt(P, cfl_block_speed<TW>(P, wo, i + NG, j + NG, valid, &P.sc->smax_seen), 1);
     }
 }
 
