@@ -769,14 +769,17 @@ __device__ __forceinline__ void update_math(const Params &P, int i, int j, int k
     }
     if constexpr (Prec<TS, TW>::mixed) {
         // MIXED: the increment dt L + (Linde term) is formed in single precision like the fluxes it
-        // comes from, and accumulated onto the FP64 state with one exact widening per field
+        // comes from, and accumulated onto the FP64 state with one exact widening per field; the
+        // second stage's average (U^n + U1 + increment) / 2 as in the FP64 form: two FP64 additions
+        // and an exact halving on the integer pipe (the FP64 pipe bounds this kernel)
         const TW dtw = narrow_d2f(dt);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const TW inc = v >= B1 ? lb[v - B1] : (v == EN ? w[5] * lb[0] + w[6] * lb[1] + w[7] * lb[2] : TW(0));
             const TW d = dtw * L[v] + inc;
-            if (STAGE == 1) uo[v] = us(v) + widen_f2d(d);
-            else uo[v] = TS(0.5) * (un(v) + us(v)) + widen_f2d(TW(0.5) * d);
+            const TS x = us(v) + widen_f2d(d);
+            if (STAGE == 1) uo[v] = x;
+            else uo[v] = half_r(un(v) + x);
         }
     } else {
         const TS dts = (TS)dt;
