@@ -64,7 +64,11 @@ enum { ICARUS_FLUX_TVDLF = 0, ICARUS_FLUX_HLL = 1, ICARUS_FLUX_HLLD = 2 };
  * upwind (B_n, psi) face state replaces the normal-field flux, carried with flux c_h^2 B_n*,
  * c_h = CFL dmin / dt, damped by exp(-glm_alpha c_h dt / dmin) per step; all three precision
  * forms (psi in the state's type), not the fused stage or the batched form. */
-enum { ICARUS_DIVB_NONE = 0, ICARUS_DIVB_LINDE = 1, ICARUS_DIVB_GLM = 2 };
+/* Powell (Powell et al. 1999; the eight-wave formulation): the source -(div B) (0, B, v.B, v) added
+ * to the residual, div B of the cell from the face averages of the cell-centred field (the same
+ * discrete divergence as the Linde term); all three precision forms, not the fused stage or the
+ * batched form. */
+enum { ICARUS_DIVB_NONE = 0, ICARUS_DIVB_LINDE = 1, ICARUS_DIVB_GLM = 2, ICARUS_DIVB_POWELL = 3 };
 /* FP64: everything in double. FP32: state and arithmetic in float. MIXED: state, update
  * accumulation and the dt reduction in double; primitives, reconstruction, fluxes and sources in
  * float, except the primitive (pressure / positivity) recovery of the first four radial cells,

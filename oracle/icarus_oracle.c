@@ -49,7 +49,7 @@ enum { BC_PERIODIC = 0, BC_CONT = 1, BC_REFLECT = 2, BC_DRIVEN = 3, BC_FIXED = 4
 enum { GEOM_SPH = 0, GEOM_CART = 1 };
 enum { LIM_MINMOD = 0, LIM_VANLEER = 1, LIM_MC = 2 };
 enum { FLUX_TVDLF = 0, FLUX_HLL = 1, FLUX_HLLD = 2 };
-enum { DIVB_NONE = 0, DIVB_LINDE = 1, DIVB_GLM = 2 };
+enum { DIVB_NONE = 0, DIVB_LINDE = 1, DIVB_GLM = 2, DIVB_POWELL = 3 };
 
 #define NG 2
 
@@ -662,6 +662,13 @@ static void residual(orc_t *o, const double *U, double dt)
                     }
                     Lc[B1] += gr[0]; Lc[B2] += gr[1]; Lc[B3] += gr[2];
                     Lc[EN] += br * gr[0] + bt * gr[1] + bp * gr[2];
+                }
+                if (o->divb == DIVB_POWELL) {
+                    /* Powell's eight-wave source -(div B) (0, B, v.B, v), the cell's own div B */
+                    double db = divb_cell(o, U, i, j, k);
+                    Lc[M1] -= db * br; Lc[M2] -= db * bt; Lc[M3] -= db * bp;
+                    Lc[EN] -= db * (vr * br + vt * bt + vp * bp);
+                    Lc[B1] -= db * vr; Lc[B2] -= db * vt; Lc[B3] -= db * vp;
                 }
                 store(o, o->L, id, Lc);
             }

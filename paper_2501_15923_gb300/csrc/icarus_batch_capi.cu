@@ -222,6 +222,7 @@ int icarus_batch_init(int n_members, const icarus_grid *grids, double gamma, dou
     if (opts->flux == ICARUS_FLUX_HLLD) return report_error(ICARUS_EINVAL, "the batched form supports the TVDLF and HLL fluxes only");
     if (opts->tracer) return report_error(ICARUS_EINVAL, "the batched form carries no CME tracer");
     if (opts->divb == ICARUS_DIVB_GLM) return report_error(ICARUS_EINVAL, "the batched form has no GLM div-B control");
+    if (opts->divb == ICARUS_DIVB_POWELL) return report_error(ICARUS_EINVAL, "the batched form has no Powell source");
     icarus_batch *b = new icarus_batch();
     b->opts = *opts;
     if (opts->cuda_stream) b->stream = (cudaStream_t)opts->cuda_stream;

@@ -294,7 +294,7 @@ void enqueue_step(icarus_ctx *c, cudaStream_t s)
     if (glm) c->ops.glm_ghost(P, c->Psi, s);
     if (glm) c->ops.fluxes_glm(P, c->W, c->Psi, c->F1, c->F2, c->F3, c->FP1, c->FP2, c->FP3, s);
     else c->ops.fluxes(P, c->W, c->F1, c->F2, c->F3, s);
-    if (P.divb == 1) c->ops.divb(P, c->W, c->divB, s);
+    if (P.divb == 1 || P.divb == 3) c->ops.divb(P, c->W, c->divB, s);
     c->ops.update(P, 1, c->U, c->W, c->U1, c->W1, c->F1, c->F2, c->F3, c->divB, s);
     if (glm) c->ops.glm_update(P, 1, c->Psi, c->Psi1, c->FP1, c->FP2, c->FP3, s);
     if (tr) c->ops.tracer_update(P, 1, c->C, c->F1, c->F2, c->F3, c->T, c->T1, c->U1, c->C1, s);
@@ -304,7 +304,7 @@ void enqueue_step(icarus_ctx *c, cudaStream_t s)
     if (glm) c->ops.glm_ghost(P, c->Psi1, s);
     if (glm) c->ops.fluxes_glm(P, c->W1, c->Psi1, c->F1, c->F2, c->F3, c->FP1, c->FP2, c->FP3, s);
     else c->ops.fluxes(P, c->W1, c->F1, c->F2, c->F3, s);
-    if (P.divb == 1) c->ops.divb(P, c->W1, c->divB, s);
+    if (P.divb == 1 || P.divb == 3) c->ops.divb(P, c->W1, c->divB, s);
     c->ops.update(P, 2, c->U1, c->W1, c->U, c->W, c->F1, c->F2, c->F3, c->divB, s);
     if (glm) c->ops.glm_update(P, 2, c->Psi1, c->Psi, c->FP1, c->FP2, c->FP3, s);
     if (tr) c->ops.tracer_update(P, 2, c->C1, c->F1, c->F2, c->F3, c->T1, c->T, c->U, c->C, s);
@@ -314,7 +314,7 @@ void enqueue_step(icarus_ctx *c, cudaStream_t s)
 int count_launches(const icarus_ctx *c)
 {
     int per_stage = (c->ops.fused_stage && c->opts.fused) ? 3 + 1
-                  : 3 + 3 + (c->P.divb == 1 ? 1 : 0) + 1 + (c->opts.tracer ? 2 : 0) +
+                  : 3 + 3 + (c->P.divb == 1 || c->P.divb == 3 ? 1 : 0) + 1 + (c->opts.tracer ? 2 : 0) +
                         (c->P.divb == ICARUS_DIVB_GLM ? 2 : 0);
     return 2 * per_stage + (c->P.n_probes > 0 ? 1 : 0);
 }
@@ -392,7 +392,7 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     if (rc) return rc;
     if (!(gamma > 1.0)) return fail(ICARUS_EINVAL, "gamma must be > 1");
     if (!(opts->cfl > 0.0 && opts->cfl <= 1.0)) return fail(ICARUS_EINVAL, "cfl must be in (0, 1]");
-    if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 2 || opts->divb < 0 || opts->divb > 2 ||
+    if (opts->limiter < 0 || opts->limiter > 2 || opts->flux < 0 || opts->flux > 2 || opts->divb < 0 || opts->divb > 3 ||
         opts->init_vphi < 0 || opts->init_vphi > 1 || opts->cme_model < 0 || opts->cme_model > 1 ||
         opts->tracer < 0 || opts->tracer > 1 || opts->strict_floors < 0 || opts->strict_floors > 1)
         return fail(ICARUS_EINVAL, "bad limiter / flux / divb / init_vphi / cme_model / tracer / strict_floors option");
@@ -402,6 +402,8 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     if (opts->fused && opts->tracer) return fail(ICARUS_EINVAL, "the fused stage kernel carries no CME tracer");
     if (opts->divb == ICARUS_DIVB_GLM && opts->fused)
         return fail(ICARUS_EINVAL, "GLM div-B control runs with the separate kernels, not the fused stage");
+    if (opts->divb == ICARUS_DIVB_POWELL && opts->fused)
+        return fail(ICARUS_EINVAL, "the Powell source runs with the separate kernels, not the fused stage");
     if (opts->divb == ICARUS_DIVB_GLM && !(opts->glm_alpha >= 0.0)) return fail(ICARUS_EINVAL, "glm_alpha must be >= 0");
     if (opts->ring_capacity < 1) return fail(ICARUS_EINVAL, "ring_capacity must be >= 1");
     icarus_ctx *c = new icarus_ctx();
@@ -990,7 +992,7 @@ int icarus_time_kernels(icarus_ctx *c, int n_steps, double *ms)
             rc |= timed(1, [&] { c->ops.flux_dir(P, 0, Ws, c->F1, s); });
             rc |= timed(2, [&] { c->ops.flux_dir(P, 1, Ws, c->F2, s); });
             rc |= timed(3, [&] { c->ops.flux_dir(P, 2, Ws, c->F3, s); });
-            if (P.divb == 1) rc |= timed(4, [&] { c->ops.divb(P, Ws, c->divB, s); });
+            if (P.divb == 1 || P.divb == 3) rc |= timed(4, [&] { c->ops.divb(P, Ws, c->divB, s); });
             rc |= timed(4 + stage, [&] { c->ops.update(P, stage, Us, Ws, Uo, Wo, c->F1, c->F2, c->F3, c->divB, s); });
         }
         if (P.n_probes > 0) rc |= timed(7, [&] { c->ops.probe(P, c->W, s); });

@@ -139,7 +139,7 @@ k_fused_stage(Params P, const TS *__restrict__ Us, const float *__restrict__ Ws,
         const int i = i0 + ti, j = j0 + tj;
         if (i < P.n1 && j < P.n2) {
             const DivFactors<float> dv(m, i + NG, j + NG);
-            float w[NV], L[NV], dbn[6];
+            float w[NV], L[NV], dbn[7];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 w[v] = S.w(k, v, tj + 2, ti + 2);

@@ -751,6 +751,13 @@ __device__ __forceinline__ void update_math(const Params &P, int i, int j, int k
             L[EN] -= rho * vr * g;
         }
     }
+    // Powell's eight-wave source -(div B) (0, B, v.B, v) with the cell's own div B (dbn[6])
+    if (P.divb == 3) {
+        const TW d = dbn[6];
+        L[M1] -= d * w[5]; L[M2] -= d * w[6]; L[M3] -= d * w[7];
+        L[EN] -= d * (w[1] * w[5] + w[2] * w[6] + w[3] * w[7]);
+        L[B1] -= d * w[1]; L[B2] -= d * w[2]; L[B3] -= d * w[3];
+    }
     // Linde div-B diffusion: increment C_d / (sum_d 1/dx_d^2) grad(div B) per stage;
     // dbn = div B at (i-1, i+1, j-1, j+1, k-1, k+1)
     TW lb[3] = {TW(0), TW(0), TW(0)};
@@ -856,7 +863,7 @@ __device__ __forceinline__ void update_cell(const Params &P, const TS *__restric
     const int i = (int)(t32 - r_ * n1u);
     const int j = (int)(r_ % (unsigned int)P.n2), k = (int)(r_ / (unsigned int)P.n2);
     const long long nt = P.nt, c = cidx(P, i, j, k);
-    TW w[NV], L[NV], dbn[6];
+    TW w[NV], L[NV], dbn[7];
     const long long s1 = (long long)P.n3 * P.n2 * (P.n1 + 1), f1 = ((long long)k * P.n2 + j) * (P.n1 + 1) + i;
     const long long s2 = (long long)P.n3 * (P.n2 + 1) * P.n1, f2 = ((long long)k * (P.n2 + 1) + j) * P.n1 + i;
     const long long s3 = (long long)(P.n3 + 1) * P.n2 * P.n1, f3 = ((long long)k * P.n2 + j) * P.n1 + i;
@@ -873,6 +880,8 @@ __device__ __forceinline__ void update_cell(const Params &P, const TS *__restric
         dbn[0] = divB[c - 1]; dbn[1] = divB[c + 1];
         dbn[2] = divB[c - q2]; dbn[3] = divB[c + q2];
         dbn[4] = divB[c - q3]; dbn[5] = divB[c + q3];
+    } else if (P.divb == 3) {
+        dbn[6] = divB[c];
     }
     if constexpr (GLM) {
         if (P.geom == 0) {
@@ -955,7 +964,7 @@ k_update_pair(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS
         const long long s3 = (long long)(P.n3 + 1) * P.n2 * P.n1, f3 = ((long long)k * P.n2 + j) * P.n1 + i;
         const long long o3 = (long long)P.n2 * P.n1;
         const DivFactors<TW> dv0(met<TW>(P), i + NG, j + NG), dv1(met<TW>(P), i + 1 + NG, j + NG);
-        TW w[2][NV], L[2][NV], dbn[2][6];
+        TW w[2][NV], L[2][NV], dbn[2][7];
         TS us[2][NV], un[2][NV], uo[2][NV];
         (void)us; (void)un;
 #pragma unroll
@@ -985,6 +994,9 @@ k_update_pair(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS
             const W2 dm3 = *reinterpret_cast<const W2 *>(divB + c - q3), dp3 = *reinterpret_cast<const W2 *>(divB + c + q3);
             dbn[0][0] = divB[c - 1]; dbn[0][1] = d0.y; dbn[0][2] = dm2.x; dbn[0][3] = dp2.x; dbn[0][4] = dm3.x; dbn[0][5] = dp3.x;
             dbn[1][0] = d0.x; dbn[1][1] = divB[c + 2]; dbn[1][2] = dm2.y; dbn[1][3] = dp2.y; dbn[1][4] = dm3.y; dbn[1][5] = dp3.y;
+        } else if (P.divb == 3) {
+            const W2 d0 = *reinterpret_cast<const W2 *>(divB + c);
+            dbn[0][6] = d0.x; dbn[1][6] = d0.y;
         }
         update_math<STAGE, TS, TW>(P, i, j, k, w[0], L[0], dbn[0], [&](int v) { return us[0][v]; },
                                    [&](int v) { return un[0][v]; }, uo[0], wo[0]);

@@ -44,7 +44,7 @@ BC_PERIODIC, BC_CONT, BC_REFLECT, BC_DRIVEN, BC_FIXED = 0, 1, 2, 3, 4
 GEOM_SPHERICAL, GEOM_CARTESIAN = 0, 1
 LIM_MINMOD, LIM_VANLEER, LIM_MC = 0, 1, 2
 FLUX_TVDLF, FLUX_HLL, FLUX_HLLD = 0, 1, 2
-DIVB_NONE, DIVB_LINDE, DIVB_GLM = 0, 1, 2
+DIVB_NONE, DIVB_LINDE, DIVB_GLM, DIVB_POWELL = 0, 1, 2, 3
 IC_COROTATING, IC_INERTIAL_RADIAL = 0, 1     # initial v_phi: at rest co-rotating / radial inertial flow
 CME_WINDOW, CME_SPHERE = 0, 1                # cone footprint over a fixed window / spherical cloud crossing
 

@@ -88,7 +88,7 @@ def test_bad_boundary_codes_rejected(ic):
     (1.5, I.Options(cme_model=2), 0, "cme_model"),
     (1.5, I.Options(tracer=2), 0, "tracer"),
     (1.5, I.Options(strict_floors=2), 0, "strict_floors"),
-    (1.5, I.Options(divb=3), 0, "divb"),
+    (1.5, I.Options(divb=4), 0, "divb"),
     (1.5, I.Options(divb=I.DIVB_GLM, glm_alpha=-1.0), 0, "glm_alpha"),
     (1.5, I.Options(), 3, "precision"),
 ])
@@ -111,6 +111,19 @@ def test_fused_stage_rejects_glm(ic):
     ctx = C.c_void_p()
     rc = lib.icarus_init(C.byref(ic.make_grid(sph())), 1.5, 0.0, C.byref(o), C.byref(ctx))
     assert rc == EINVAL and "GLM" in lib.icarus_last_error().decode()
+
+
+def test_fused_stage_and_batch_reject_powell(ic):
+    lib = ic.load()
+    o = ic.make_options(I.Options(divb=I.DIVB_POWELL), 2, fused=True)
+    ctx = C.c_void_p()
+    rc = lib.icarus_init(C.byref(ic.make_grid(sph())), 1.5, 0.0, C.byref(o), C.byref(ctx))
+    assert rc == EINVAL and "Powell" in lib.icarus_last_error().decode()
+    o = ic.make_options(I.Options(divb=I.DIVB_POWELL), 2)
+    grids = (ic.icarus_grid * 1)(ic.make_grid(sph()))
+    b = C.c_void_p()
+    rc = lib.icarus_batch_init(1, C.cast(grids, C.c_void_p), 1.5, 0.0, C.byref(o), C.byref(b))
+    assert rc == EINVAL and "Powell" in lib.icarus_last_error().decode()
 
 
 def test_fused_stage_rejects_tracer(ic):

@@ -88,6 +88,7 @@ def test_static_sheet_per_step_parity_20_steps(ic):
     (I.LIM_MINMOD, I.FLUX_TVDLF, I.DIVB_LINDE, 1),
     (I.LIM_MC, I.FLUX_HLL, I.DIVB_LINDE, 1),
     (I.LIM_VANLEER, I.FLUX_HLL, I.DIVB_NONE, 0),
+    (I.LIM_VANLEER, I.FLUX_TVDLF, I.DIVB_POWELL, 1),
 ])
 def test_options_perturbed_state(ic, lim, flux, divb, grav):
     """Randomly perturbed static-sheet state (every component nonzero, limiter branches mixed)."""

@@ -28,7 +28,8 @@ def ic():
 
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("shape", [(37, 9, 7), (64, 12, 37), (40, 10, 3), (33, 16, 16), (20, 10, 1), (96, 16, 48)])
-@pytest.mark.parametrize("flux,divb", [(I.FLUX_TVDLF, I.DIVB_LINDE), (I.FLUX_HLL, I.DIVB_NONE)])
+@pytest.mark.parametrize("flux,divb", [(I.FLUX_TVDLF, I.DIVB_LINDE), (I.FLUX_HLL, I.DIVB_NONE),
+                                       (I.FLUX_TVDLF, I.DIVB_POWELL)])
 def test_single_precision_steps_match_oracle(ic, prec, shape, flux, divb):
     w = I.dynamic_cme(grid=I.Grid(*shape))
     w.opts = I.Options(flux=flux, divb=divb)

@@ -64,6 +64,12 @@ MUTANTS = [
     ("work of gravity dropped from the energy",
      "                        Lc[EN] -= rho * vr * g;\n", "",
      "P5_P7_wind_residual_second_order"),
+    ("Powell energy source with the wrong sign",
+     "Lc[EN] -= db * (vr * br + vt * bt + vp * bp);", "Lc[EN] += db * (vr * br + vt * bt + vp * bp);",
+     "P6b_powell"),
+    ("Powell induction source from B instead of v",
+     "Lc[B1] -= db * vr; Lc[B2] -= db * vt; Lc[B3] -= db * vp;", "Lc[B1] -= db * br; Lc[B2] -= db * bt; Lc[B3] -= db * bp;",
+     "P6b_powell"),
     ("Linde term with the wrong sign",
      "Lc[B1] += gr[0]; Lc[B2] += gr[1]; Lc[B3] += gr[2];",
      "Lc[B1] -= gr[0]; Lc[B2] -= gr[1]; Lc[B3] -= gr[2];",

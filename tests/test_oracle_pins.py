@@ -7,7 +7,8 @@ Each test names the pin it is and what a plausible mistake in the oracle would b
   P3  Sod shock tube against the exact Riemann solution (flux, limiter, integrator), TVDLF + HLL
   P4  linear MHD waves converge at second order with the right phase speed (magnetic fluxes)
   P5  spherically symmetric wind with gravity (gravity in momentum and energy, stretched grid)
-  P6  Linde div-B term against its closed form on a Fourier mode; Gauss sum on the sphere
+  P6  Linde div-B term against its closed form on a Fourier mode; Gauss sum on the sphere;
+      Powell's source against -D (0, B, v.B, v) with the central difference D written out
   P7  rotating frame: inertially static fluid; inertially radial wind (Coriolis, centrifugal,
       work of the centrifugal force, induction source of B_phi)
   P8  boundary time interpolation; P9 probe sampling; P10 cone-CME footprint
@@ -538,6 +539,37 @@ def test_P6_linde_closed_form_fourier_mode():
     assert np.allclose(dL[5], expect, rtol=1e-10, atol=1e-14)
     assert np.allclose(dL[6], 0.0, atol=1e-14) and np.allclose(dL[7], 0.0, atol=1e-14)
     assert np.allclose(dL[4], W[5] * expect, rtol=1e-10, atol=1e-16)
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.2])
+def test_P6b_powell_source_closed_form(eps):
+    """Powell's eight-wave source on a periodic box with B_x = 1 + eps sin(k x) and a uniform
+    flow: the residual with the source minus the one without is -D (0, B, v.B, v), D the central
+    difference (B_x[i+1] - B_x[i-1]) / (2 dx) written out here; with eps = 0 (div B = 0) the two
+    residuals are identical."""
+    n, kx = 32, 2
+    g = cart_grid(n, 4, 2, L=(1.0, 0.5, 0.25))
+    x = (np.arange(n) + 0.5) / n
+    W = np.zeros((8, 2, 4, n))
+    W[0], W[4] = 1.3, 0.9
+    W[1], W[2], W[3] = 0.7, -0.4, 0.25
+    W[5] = 1.0 + eps * np.sin(2 * np.pi * kx * x)
+    W[6], W[7] = 0.3, -0.6
+    U = cons_from_prim(W, 5 / 3)
+    res = {}
+    for divb in (I.DIVB_NONE, I.DIVB_POWELL):
+        o = Oracle(g, 5 / 3, 0.0, opts(divb=divb, gravity=0))
+        o.set_state(U)
+        res[divb] = o.residual(0.0, 0.1)
+    dL = res[I.DIVB_POWELL] - res[I.DIVB_NONE]
+    if eps == 0.0:
+        assert np.array_equal(res[I.DIVB_POWELL], res[I.DIVB_NONE])
+        return
+    D = (np.roll(W[5], -1, axis=-1) - np.roll(W[5], 1, axis=-1)) / (2.0 / n)
+    vb = W[1] * W[5] + W[2] * W[6] + W[3] * W[7]
+    expect = [np.zeros_like(D), -D * W[5], -D * W[6], -D * W[7], -D * vb, -D * W[1], -D * W[2], -D * W[3]]
+    for v in range(8):
+        assert np.allclose(dL[v], expect[v], rtol=1e-11, atol=1e-12), v
 
 
 def test_P6_divb_gauss_and_convergence_spherical():
