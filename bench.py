@@ -194,6 +194,24 @@ def cpu_oracle_rate(w, steps: int, max_seconds: float = 30.0, min_seconds: float
     return w.grid.ncell * n / el / 1e6, n, el, used
 
 
+def cpu_small_case_full():
+    """The oracle on the small static-sheet workload (60 x 16 x 32, its 200 steps) in full, on all
+    host cores and on one thread."""
+    from oracle.oracle import from_workload as ofw, set_threads
+    from paper_2501_15923_gb300 import inputs as I
+    w0 = I.static_sheet()
+    out = {"workload": "static_sheet_60x16x32", "steps": w0.n_steps}
+    for label, thr in (("all_cores", os.cpu_count() or 1), ("single_thread", 1)):
+        used = set_threads(thr)
+        o = ofw(w0)
+        t0 = time.perf_counter()
+        for _ in range(w0.n_steps):
+            o.step()
+        el = time.perf_counter() - t0
+        out[label] = {"value": w0.grid.ncell * w0.n_steps / el / 1e6, "threads": used, "seconds": el}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if world > 1:
@@ -501,7 +519,8 @@ def main(argv=None):
         line["cpu_baseline"] = {"value": v, "unit": "Mcell-updates/s", "cores": used, "kind": "oracle",
                                 "cpu_model": cpu_model(),
                                 "sample": f"{n} full steps of {w.name} ({el:.1f} s, OpenMP on {used} threads)",
-                                "single_thread": {"value": v1, "sample": f"{n1} full steps ({el1:.1f} s, 1 thread)"}}
+                                "single_thread": {"value": v1, "sample": f"{n1} full steps ({el1:.1f} s, 1 thread)"},
+                                "small_case_full": cpu_small_case_full()}
     s.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
