@@ -439,12 +439,65 @@ __device__ __forceinline__ void hlld(const R *wl, const R *wr, const R *ul, cons
 }
 
 // Riemann flux across a face normal to d from left / right primitive states.
+// single-precision TVDLF with the left and right states in the two lanes of packed FP32
+// instructions (x = left, y = right): conserved states, fast speeds and physical fluxes of both
+// sides from one instruction stream; the combination (F_L + F_R)/2 - c_max (U_R - U_L)/2 per lane
+__device__ __forceinline__ float2 f2_(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ void tvdlf_paired(const float *wl, const float *wr, int d, float gamma, float igm1, float *f)
+{
+    float2 w[NV], u[NV], F[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = f2_(wl[v], wr[v]);
+    const float2 h = f2_(0.5f, 0.5f), irho = f2_(1.f / wl[0], 1.f / wr[0]);
+    u[RHO] = w[0];
+    u[M1] = __fmul2_rn(w[0], w[1]);
+    u[M2] = __fmul2_rn(w[0], w[2]);
+    u[M3] = __fmul2_rn(w[0], w[3]);
+    const float2 mv = __ffma2_rn(u[M1], w[1], __ffma2_rn(u[M2], w[2], __fmul2_rn(u[M3], w[3])));
+    const float2 bb = __ffma2_rn(w[5], w[5], __ffma2_rn(w[6], w[6], __fmul2_rn(w[7], w[7])));
+    u[EN] = __ffma2_rn(w[4], f2_(igm1, igm1), __fmul2_rn(h, __fadd2_rn(mv, bb)));
+    u[B1] = w[5];
+    u[B2] = w[6];
+    u[B3] = w[7];
+    // fast speeds: c_f^2 = (s + sqrt(s^2 - 4 a^2 b_n^2)) / 2, s = a^2 + b^2
+    const float2 a2 = __fmul2_rn(__fmul2_rn(f2_(gamma, gamma), w[4]), irho);
+    const float2 s = __ffma2_rn(bb, irho, a2);
+    const float2 bn = w[5 + d], vn = w[1 + d];
+    const float2 nq = __fmul2_rn(__fmul2_rn(f2_(-4.f, -4.f), a2), __fmul2_rn(__fmul2_rn(bn, bn), irho));
+    const float2 disc = __ffma2_rn(s, s, nq);
+    const float2 cf2 = __fmul2_rn(h, __fadd2_rn(s, f2_(sqrtf(fmaxf(disc.x, 0.f)), sqrtf(fmaxf(disc.y, 0.f)))));
+    const float cl = sqrtf(cf2.x), cr = sqrtf(cf2.y);
+    // physical fluxes
+    const float2 nbn = __fmul2_rn(bn, f2_(-1.f, -1.f));
+    const float2 bv = __ffma2_rn(w[5], w[1], __ffma2_rn(w[6], w[2], __fmul2_rn(w[7], w[3])));
+    const float2 pt = __ffma2_rn(h, bb, w[4]);
+    F[RHO] = __fmul2_rn(u[RHO], vn);
+    F[M1] = __ffma2_rn(u[M1], vn, __fmul2_rn(w[5], nbn));
+    F[M2] = __ffma2_rn(u[M2], vn, __fmul2_rn(w[6], nbn));
+    F[M3] = __ffma2_rn(u[M3], vn, __fmul2_rn(w[7], nbn));
+    F[M1 + d] = __fadd2_rn(F[M1 + d], pt);
+    F[EN] = __ffma2_rn(__fadd2_rn(u[EN], pt), vn, __fmul2_rn(nbn, bv));
+    F[B1] = __ffma2_rn(vn, w[5], __fmul2_rn(nbn, w[1]));
+    F[B2] = __ffma2_rn(vn, w[6], __fmul2_rn(nbn, w[2]));
+    F[B3] = __ffma2_rn(vn, w[7], __fmul2_rn(nbn, w[3]));
+    F[B1 + d] = f2_(0.f, 0.f);       // v_n B_n - B_n v_n: exactly zero
+    const float hc = 0.5f * fmaxf(fabsf(vn.x) + cl, fabsf(vn.y) + cr);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) f[v] = 0.5f * (F[v].x + F[v].y) - hc * (u[v].y - u[v].x);
+}
+
 // TVDLF: (F_L + F_R)/2 - c_max (U_R - U_L)/2; HLL with signal speeds from the fast speeds (flux
 // chosen at run time); HLLD when HD (a separate instantiation, so that the larger solver does not
 // weigh on the registers of the other two)
 template <typename R, bool HD = false>
 __device__ __forceinline__ void riemann(const R *wl, const R *wr, int d, int flux, R gamma, R igm1, R *f)
 {
+    if constexpr (sizeof(R) == 4 && !HD) {
+        if (flux == 0) {
+            tvdlf_paired(wl, wr, d, gamma, igm1, f);
+            return;
+        }
+    }
     R ul[NV], ur[NV];
     prim2cons(wl, ul, igm1);
     prim2cons(wr, ur, igm1);
