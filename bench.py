@@ -147,7 +147,7 @@ def profile_numbers():
     try:
         txt = open(PROFILE_SUMMARY).read()
     except OSError:
-        return {}, {}
+        return {}, {}, {}
     vals = {}
     for line in txt.splitlines():
         if line.startswith("machine:"):
@@ -159,9 +159,11 @@ def profile_numbers():
              if f"fp64_flops_per_face_{d[0]}" in vals}
     dram = {d: float(vals[f"dram_bytes_per_face_{d[0]}"]) for d in ("r", "theta", "phi")
             if f"dram_bytes_per_face_{d[0]}" in vals}
+    pipe = {d: float(vals[f"fp64_pipe_busy_{d[0]}"]) / 100.0 for d in ("r", "theta", "phi")
+            if f"fp64_pipe_busy_{d[0]}" in vals}
     if vals.get("kernel_hash") != kernel_source_hash():
-        return {}, {}
-    return flops, dram
+        return {}, {}, {}
+    return flops, dram, pipe
 
 
 # ---------------------------------------------------------------------------------------------
@@ -420,7 +422,7 @@ def main(argv=None):
     kms = s.time_kernels(3)
     per_step = {k: v * (2 if k not in ("probe", "update_1", "update_2", "fused_1", "fused_2") else 1) for k, v in kms.items()}
     dom = max(per_step, key=per_step.get)
-    flops_face, dram_face = profile_numbers()
+    flops_face, dram_face, pipe_face = profile_numbers()
     n1, n2, n3 = w.grid.n1, w.grid.n2, w.grid.n3
     faces = {"flux_r": (n1 + 1) * n2 * n3, "flux_theta": n1 * (n2 + 1) * n3, "flux_phi": n1 * n2 * (n3 + 1)}
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
@@ -435,6 +437,10 @@ def main(argv=None):
                 "peak_source": "measured in this run (icarus_fma_rate, FP64 FMA chains); "
                                f"nominal {FP64_NOMINAL_TFLOPS:.3f} TFLOP/s",
                 "frac_of_nominal": ach / FP64_NOMINAL_TFLOPS}
+        if dkey in pipe_face:
+            roof["fp64_pipe_busy"] = pipe_face[dkey]
+            roof["fp64_pipe_note"] = ("sm__pipe_fp64_cycles_active of the same ncu capture: the FP64 pipe's "
+                                      "issue limit; frac counts a DADD or DMUL as one flop, a DFMA as two")
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": None, "traffic": None,
