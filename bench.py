@@ -48,7 +48,7 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_flux_r_fp64_256x64x128.md")
 def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=80)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--grid", default="512x64x128")
