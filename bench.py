@@ -454,11 +454,13 @@ def main(argv=None):
     # end to end through the C ABI with host buffers: per step the boundary maps go host -> device
     # (icarus_set_boundary), one step runs, and the probe records come back (icarus_sample)
     maps_bytes = w.maps.nbytes + w.t_maps.nbytes + w.cmes.nbytes
+    # the step's inputs sit in pinned host memory (where a producer would write them)
+    maps_pinned = torch.from_numpy(np.ascontiguousarray(w.maps)).pin_memory().numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ne = max(3, min(args.steps, 10))
     for _ in range(ne):
-        s.set_boundary(w.t_maps, w.maps, w.cmes)
+        s.set_boundary(w.t_maps, maps_pinned, w.cmes)
         s.step(1)
         rec, _ = s.sample(None, cap=4)
     el = time.perf_counter() - t0

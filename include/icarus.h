@@ -157,7 +157,8 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot,
  * speed m/s, n m^-3, T K); inside the cone during [t_on, t_on + duration) the boundary takes
  * v_r = speed, n, p = 2 n k_B T (Sect. 3.2). The first call also sets the initial state from
  * the maps at the current time by radial expansion (Sect. 2.1) and computes the first dt.
- * Later calls replace the maps and CMEs only. Synchronous. */
+ * Later calls replace the maps and CMEs only. The maps are copied to the device as given (one DMA
+ * when the caller's array is in pinned host memory) and scaled to code units there. Synchronous. */
 int icarus_set_boundary(icarus_ctx *ctx, int n_maps, const double *t_maps, const double *maps,
                         int n_cme, const double *cmes);
 

@@ -73,6 +73,18 @@ void *icarus::ctx_alloc(icarus_ctx *c, size_t bytes) { return dalloc(c, bytes); 
 
 namespace {
 
+// boundary maps [n_maps][5][n2 n3] from SI to code units: field f scaled by s[f] (the same IEEE
+// products as a host loop would form)
+__global__ void k_maps_to_code(const double *__restrict__ raw, double *__restrict__ out, long long per, long long n,
+                               double s0, double s1, double s2, double s3, double s4)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int f = (int)((i / per) % 5);
+    const double s = f == 0 ? s0 : (f == 1 ? s1 : (f == 2 ? s2 : (f == 3 ? s3 : s4)));
+    out[i] = raw[i] * s;
+}
+
 // the FP64 flux's square root and reciprocal beside the library's, element by element:
 // y[4i .. 4i + 3] = sqrt_nr, sqrt, rcp_nr, 1 / x
 __global__ void k_math_check(const double *x, double *y, int n)
@@ -532,40 +544,27 @@ int icarus_set_boundary(icarus_ctx *c, int n_maps, const double *t_maps, const d
     const size_t nm = (size_t)n_maps * 5 * per, nc = 10 * (size_t)(n_cme > 0 ? n_cme : 1);
     // the previous tables may still be in flight from the staging buffer or in use on the device
     CK(cudaStreamSynchronize(c->stream));
-    // code-unit tables written straight into pinned host memory (one DMA each, no driver staging);
-    // pageable fallback if pinned memory cannot be had
+    // the small tables (map times, CME rows) in code units, written into pinned host memory
     std::vector<double> fallback;
-    double *hm = nullptr;
-    if (nm + n_maps + nc > c->hstage_cap) {
+    double *hs = nullptr;
+    if (n_maps + nc > c->hstage_cap) {
         if (c->hstage) cudaFreeHost(c->hstage);
         c->hstage = nullptr;
         c->hstage_cap = 0;
-        if (cudaHostAlloc((void **)&c->hstage, (nm + n_maps + nc) * sizeof(double), cudaHostAllocDefault) == cudaSuccess)
-            c->hstage_cap = nm + n_maps + nc;
+        if (cudaHostAlloc((void **)&c->hstage, (n_maps + nc) * sizeof(double), cudaHostAllocDefault) == cudaSuccess)
+            c->hstage_cap = n_maps + nc;
         else {
             c->hstage = nullptr;
             cudaGetLastError();
         }
     }
-    if (c->hstage) hm = c->hstage;
+    if (c->hstage) hs = c->hstage;
     else {
-        fallback.resize(nm + n_maps + nc);
-        hm = fallback.data();
+        fallback.resize(n_maps + nc);
+        hs = fallback.data();
     }
-    double *ht = hm + nm, *hc = ht + n_maps;
-    const double iv0 = 1.0 / V0, in0 = 1.0 / N0, ip0 = 1.0 / c->p0, ib0 = 1.0 / c->b0;
-    for (int m = 0; m < n_maps; ++m) {
-        ht[m] = t_maps[m] / c->t0;
-        const double *src = maps + (size_t)m * 5 * per;
-        double *dst = hm + (size_t)m * 5 * per;
-        for (size_t q = 0; q < per; ++q) {
-            dst[q] = src[q] * iv0;
-            dst[per + q] = src[per + q] * in0;
-            dst[2 * per + q] = src[2 * per + q] * ip0;
-            dst[3 * per + q] = src[3 * per + q] * ib0;
-            dst[4 * per + q] = src[4 * per + q] * ib0;
-        }
-    }
+    double *ht = hs, *hc = ht + n_maps;
+    for (int m = 0; m < n_maps; ++m) ht[m] = t_maps[m] / c->t0;
     for (size_t q = 0; q < nc; ++q) hc[q] = 0.0;
     for (int q = 0; q < n_cme; ++q) {
         const double *s = cmes + 8 * q;
@@ -590,12 +589,23 @@ int icarus_set_boundary(icarus_ctx *c, int n_maps, const double *t_maps, const d
         c->maps_cap = nm;
         c->tmaps_cap = n_maps;
     }
+    if (nm > c->maps_raw_cap) {
+        c->maps_raw = (double *)dalloc(c, nm * sizeof(double));
+        if (!c->maps_raw) return fail(ICARUS_ENOMEM, "map allocation failed");
+        c->maps_raw_cap = nm;
+    }
     if (nc > c->cme_cap) {
         c->cme = (double *)dalloc(c, nc * sizeof(double));
         if (!c->cme) return fail(ICARUS_ENOMEM, "CME allocation failed");
         c->cme_cap = nc;
     }
-    CK(cudaMemcpyAsync(c->maps, hm, nm * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    // the maps as given (one DMA when the caller's array is pinned), then scaled on the device; all
+    // in stream order after the steps already queued, which may still read the previous tables
+    CK(cudaMemcpyAsync(c->maps_raw, maps, nm * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    k_maps_to_code<<<(unsigned int)((nm + 255) / 256), 256, 0, c->stream>>>(c->maps_raw, c->maps, (long long)per,
+                                                                             (long long)nm, 1.0 / V0, 1.0 / N0,
+                                                                             1.0 / c->p0, 1.0 / c->b0, 1.0 / c->b0);
+    CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->tmaps, ht, n_maps * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->cme, hc, nc * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     // the captured step reads the tables through these pointers and counts: a new graph only when

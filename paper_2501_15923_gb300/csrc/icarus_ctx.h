@@ -23,7 +23,9 @@ struct icarus_ctx {
     icarus::Scalars *sc = nullptr;
     double *maps = nullptr, *tmaps = nullptr, *cme = nullptr, *traj = nullptr, *ring = nullptr;
     size_t maps_cap = 0, tmaps_cap = 0, cme_cap = 0, traj_cap = 0;
-    double *hstage = nullptr;       // pinned host staging of the boundary tables (maps, times, CMEs)
+    double *maps_raw = nullptr;     // the caller's maps as given (SI), scaled to code units on the device
+    size_t maps_raw_cap = 0;
+    double *hstage = nullptr;       // pinned host staging of the small boundary tables (times, CMEs)
     int *hstatus = nullptr;         // host-mapped copy of the status word, written by each step
     void *snapU = nullptr, *snapT = nullptr, *snapC = nullptr, *snapPsi = nullptr;   // icarus_step_recover's snapshot
     size_t hstage_cap = 0;
