@@ -58,6 +58,8 @@ def parse_args(argv=None):
     p.add_argument("--tracer", action="store_true", help="carry the CME tracer in the timed solver")
     p.add_argument("--glm", action="store_true", help="GLM div-B control instead of Linde diffusion (FP64)")
     p.add_argument("--batch-members", type=int, default=64, help="members of the batched cone-CME ensemble")
+    p.add_argument("--batch-only", default="", choices=["", "persistent", "phases", "concurrent"],
+                   help="only step the batched ensemble in this form (2 warm-up + 3 timed steps; for profiling)")
     return p.parse_args(argv)
 
 
@@ -301,6 +303,29 @@ def run_batched(ic, torch, args):
     return out
 
 
+def run_batch_only(ic, torch, args):
+    """The batched ensemble in one form only, 2 warm-up and 3 timed steps (a profiling target)."""
+    members = I.ensemble(seed=3, n_members=args.batch_members)
+    b = ic.Batch(members, precision=ic.ICARUS_MIXED)
+    b.register_probes()
+    b.autotune(2)
+    mode = {"persistent": ic.ICARUS_BATCH_PERSISTENT, "phases": ic.ICARUS_BATCH_PHASES,
+            "concurrent": ic.ICARUS_BATCH_CONCURRENT}[args.batch_only]
+    b.set_mode(mode)
+    if mode == ic.ICARUS_BATCH_PHASES:
+        b.autotune(2)
+    b.step(2)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(b.stream)
+    b.step(3)
+    e.record(b.stream)
+    e.synchronize()
+    print(json.dumps({"batch_form": args.batch_only, "members": len(members), "ms_per_step": a.elapsed_time(e) / 3,
+                      "status": b.status()}), flush=True)
+    b.close()
+
+
 CLOSURE_WEIGHTS = os.path.join(ROOT, "paper_2501_15923_gb300", "weights", "closure_256x32x64_k10.npz")
 
 
@@ -383,6 +408,8 @@ def main(argv=None):
     if dist:
         dist.barrier()
     from paper_2501_15923_gb300 import icarus as ic
+    if args.batch_only:
+        return run_batch_only(ic, torch, args)
     prec = {"f64": ic.ICARUS_FP64, "f32": ic.ICARUS_FP32, "mixed": ic.ICARUS_MIXED}[args.precision]
     w = workload(args.grid)
     w.opts.tracer = int(args.tracer)
