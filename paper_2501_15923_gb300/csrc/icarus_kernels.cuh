@@ -935,13 +935,16 @@ k_update_capped(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, 
 // two-element vector loads and stores (every array offset of such a pair is even: p1, n1, the
 // field strides and the base addresses are), which halves the memory instructions of this
 // latency-bound kernel; the arithmetic is update_math per cell. (Measured on the MIXED form it was
-// slower than one cell per thread: its FP64 state doubles the registers a pair needs.)
+// slower than one cell per thread: its FP64 state doubles the registers a pair needs.) Resident
+// blocks per SM, measured at 512 x 64 x 128: the first stage at three (at most 85 registers, 0.176
+// against 0.189 ms at two), the second, with U^n and the CFL reduction, at two (0.275 against 0.300
+// ms at three)
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using t = float2; };
 template <> struct Vec2<double> { using t = double2; };
 
 template <int STAGE, typename TS, typename TW>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, STAGE == 1 ? 3 : 2)
 k_update_pair(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo, TW *__restrict__ Wo,
               const TW *__restrict__ F1, const TW *__restrict__ F2, const TW *__restrict__ F3,
               const TW *__restrict__ divB)
