@@ -407,12 +407,14 @@ template <int D> struct FluxShape {
     static constexpr int BY = D == 0 ? 1 : 16;
 };
 
-// resident blocks per SM the FP64 TVDLF / HLL flux kernels are compiled for: at most 85 registers,
+// resident blocks per SM the TVDLF / HLL flux kernels are compiled for. FP64: at most 85 registers,
 // so that 3 blocks of 256 threads (6 of 128) fit in the register file instead of 2 (5) at the 88
-// the compiler takes unasked; the FP64 pipe is their bound, and more warps keep it busier. No
-// constraint for the single-precision and HLLD instantiations.
+// the compiler takes unasked; the FP64 pipe is their bound, and more warps keep it busier. Single
+// precision: at most 40 registers (6 blocks of 256, 12 of 128; a few bytes of spills) instead of
+// 48, measured 3-7 % faster per flux kernel (issue-bound, latency-limited at 53-56 % warps
+// active). No constraint for the HLLD instantiations.
 template <int D, typename TW, bool HD> struct FluxMinBlocks {
-    static constexpr int value = (sizeof(TW) == 8 && !HD) ? (D == 0 ? 6 : 3) : 1;
+    static constexpr int value = (sizeof(TW) == 8 && !HD) ? (D == 0 ? 6 : 3) : (!HD ? (D == 0 ? 12 : 6) : 1);
 };
 
 template <int D, typename TW, bool HD = false>
