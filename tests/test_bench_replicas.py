@@ -43,11 +43,12 @@ def test_replica_aggregation_gloo_two_ranks():
 
 
 def test_profile_counts_dropped_when_kernel_sources_change(monkeypatch):
-    """The roofline's flop and DRAM counts per face come from the committed ncu summary only while
-    the flux kernels' sources hash to the value recorded there."""
+    """The roofline's flop, DRAM and FP64-pipe figures per face come from the committed ncu summary
+    only while the flux kernels' sources hash to the value recorded there."""
     import bench
-    flops, dram = bench.profile_numbers()
+    flops, dram, pipe = bench.profile_numbers()
     if flops:
         assert set(flops) == {"r", "theta", "phi"} and all(v > 0 for v in flops.values())
+        assert set(pipe) == {"r", "theta", "phi"} and all(0 < v <= 1 for v in pipe.values())
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
-    assert bench.profile_numbers() == ({}, {})
+    assert bench.profile_numbers() == ({}, {}, {})
