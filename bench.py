@@ -512,13 +512,15 @@ def main(argv=None):
             # algorithmic bytes of one launch (each value read or written once): flux kernels read
             # the primitives (8 x sw per cell) and write the fluxes (8 x sw per face); the update
             # reads W, U, the six face fluxes (each face shared by two cells) and div B and writes
-            # U and W, plus U^n in the second stage
+            # U and W, plus U^n in the second stage; where the update forms the r-face fluxes
+            # itself (no r-flux kernel launched), only the theta and phi face fluxes are read
             fk = sf.time_kernels(2)
             su, sw = (4, 4) if pr == ic.ICARUS_FP32 else (8, 4)
             n1, n2, n3 = w.grid.n1, w.grid.n2, w.grid.n3
             faces = {"flux_r": (n1 + 1) * n2 * n3, "flux_theta": n1 * (n2 + 1) * n3, "flux_phi": n1 * n2 * (n3 + 1)}
             kbytes = {k: 8 * sw * (ncell + f) for k, f in faces.items()}
-            kbytes["update_1"] = ncell * (8 * sw + 8 * su + 3 * 8 * sw + sw + 8 * su + 8 * sw)
+            nfd = 3 if fk.get("flux_r", 0.0) > 0.0 else 2
+            kbytes["update_1"] = ncell * (8 * sw + 8 * su + nfd * 8 * sw + sw + 8 * su + 8 * sw)
             kbytes["update_2"] = kbytes["update_1"] + ncell * 8 * su
             per_step = {k: fk[k] * (1 if k.startswith("update") else 2) for k in kbytes}
             dk = max(per_step, key=per_step.get)

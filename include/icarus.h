@@ -108,11 +108,20 @@ typedef struct {
     icarus_alloc_fn alloc; /* device allocator (NULL: cudaMalloc); must return 256-B aligned */
     icarus_free_fn free;   /* matching free (NULL: cudaFree) */
     void *alloc_user;      /* passed to alloc / free */
-    int fused;             /* 1: one fused stage kernel (fluxes, div B, update) instead of the separate
-                              kernels, FP32 and MIXED only. It keeps the face fluxes on chip, but on
-                              GB300 it is about 2x slower than the separate kernels: they are not
-                              bandwidth-bound, and the fused kernel runs at half their occupancy and
-                              recomputes each face's neighbouring slopes */
+    int fused;             /* kernel sequence of a stage (the same arithmetic in each):
+                              0: default. FP32 and MIXED with TVDLF / HLL and without GLM or the
+                              tracer: theta- and phi-flux kernels, then one update kernel that
+                              forms the r-face fluxes of its radial row segment in shared memory
+                              (no r-flux array in HBM, one launch fewer); everything else: the
+                              separate r-, theta-, phi-flux kernels and the update.
+                              1: one fused stage kernel (fluxes, div B, update), FP32 and MIXED
+                              only, TVDLF / HLL, Linde or no div-B control, no tracer. It keeps all
+                              face fluxes on chip, but on GB300 it is about 2x slower than the
+                              separate kernels: they are not bandwidth-bound, and the fused kernel
+                              runs at half their occupancy and recomputes each face's neighbouring
+                              slopes.
+                              2: the separate kernels everywhere (the r-flux kernel too).
+                              Other values: EINVAL */
     int init_vphi;         /* initial state's v_phi (Sect. 2.1 names none): ICARUS_IC_COROTATING
                               (0: at rest in the co-rotating frame) or ICARUS_IC_INERTIAL_RADIAL
                               (1: v_phi = -Omega r sin(theta), the inertially radial flow, parallel
@@ -269,7 +278,9 @@ void *icarus_get_stream(icarus_ctx *ctx);
  * launch of each kernel class: ms[ICARUS_KERNEL_CLASSES] = (ghost fill (3 kernels), flux r,
  * flux theta, flux phi, div B, update stage 1, update stage 2, probes, fused stage 1, fused
  * stage 2); a class the context does not launch reads 0 (the fused stage kernel replaces the
- * flux, div-B and update kernels of the FP32 and MIXED forms when options.fused is set). The
+ * flux, div-B and update kernels of the FP32 and MIXED forms when options.fused = 1; with the
+ * default kernel sequence of those forms the update classes time the update that forms the r-face
+ * fluxes itself, and flux r reads 0). The
  * steps advance the solution like icarus_step. Synchronous. */
 #define ICARUS_KERNEL_CLASSES 10
 int icarus_time_kernels(icarus_ctx *ctx, int n_steps, double *ms);

@@ -287,10 +287,22 @@ int build_metrics(icarus_ctx *c)
     return ICARUS_OK;
 }
 
+// the whole-stage fused kernel (options.fused = 1)
+bool use_fused_stage(const icarus_ctx *c) { return c->ops.fused_stage && c->opts.fused == 1; }
+
+// the update with the r-face fluxes inside it, the default (options.fused = 0) where the precision
+// form has it (FP32, MIXED) and the options allow it (TVDLF / HLL, no GLM, no tracer: the tracer
+// reads the r mass fluxes); options.fused = 2 keeps the separate r-flux kernel
+bool use_update_rf(const icarus_ctx *c)
+{
+    return c->ops.update_rf && c->opts.fused == 0 && c->opts.flux != ICARUS_FLUX_HLLD &&
+           c->opts.divb != ICARUS_DIVB_GLM && !c->opts.tracer;
+}
+
 void enqueue_step(icarus_ctx *c, cudaStream_t s)
 {
     const Params &P = c->P;
-    if (c->ops.fused_stage && c->opts.fused) {
+    if (use_fused_stage(c)) {
         c->ops.fill_ghosts(P, c->U, c->W, 1, s);
         c->ops.fused_stage(P, 1, c->U, c->W, c->U1, c->W1, s);
         c->ops.fill_ghosts(P, c->U1, c->W1, 2, s);
@@ -300,14 +312,16 @@ void enqueue_step(icarus_ctx *c, cudaStream_t s)
     }
     // stage 1: U, W at t  ->  U1, W1 (tracer: rho c in T, c in C  ->  T1, C1, with the stage's mass fluxes)
     // (GLM: psi in Psi -> Psi1 -> Psi, its (B_n, psi) face states after the MHD fluxes)
-    const bool tr = c->opts.tracer != 0, glm = P.divb == ICARUS_DIVB_GLM;
+    const bool tr = c->opts.tracer != 0, glm = P.divb == ICARUS_DIVB_GLM, rf = use_update_rf(c);
     c->ops.fill_ghosts(P, c->U, c->W, 1, s);
     if (tr) c->ops.tracer_ghost(P, c->C, 1, s);
     if (glm) c->ops.glm_ghost(P, c->Psi, s);
     if (glm) c->ops.fluxes_glm(P, c->W, c->Psi, c->F1, c->F2, c->F3, c->FP1, c->FP2, c->FP3, s);
+    else if (rf) { c->ops.flux_dir(P, 1, c->W, c->F2, s); c->ops.flux_dir(P, 2, c->W, c->F3, s); }
     else c->ops.fluxes(P, c->W, c->F1, c->F2, c->F3, s);
     if (P.divb == 1 || P.divb == 3) c->ops.divb(P, c->W, c->divB, s);
-    c->ops.update(P, 1, c->U, c->W, c->U1, c->W1, c->F1, c->F2, c->F3, c->divB, s);
+    if (rf) c->ops.update_rf(P, 1, c->U, c->W, c->U1, c->W1, c->F2, c->F3, c->divB, s);
+    else c->ops.update(P, 1, c->U, c->W, c->U1, c->W1, c->F1, c->F2, c->F3, c->divB, s);
     if (glm) c->ops.glm_update(P, 1, c->Psi, c->Psi1, c->FP1, c->FP2, c->FP3, s);
     if (tr) c->ops.tracer_update(P, 1, c->C, c->F1, c->F2, c->F3, c->T, c->T1, c->U1, c->C1, s);
     // stage 2: U1, W1 at t + dt  ->  U, W (in place), next dt, t += dt
@@ -315,9 +329,11 @@ void enqueue_step(icarus_ctx *c, cudaStream_t s)
     if (tr) c->ops.tracer_ghost(P, c->C1, 2, s);
     if (glm) c->ops.glm_ghost(P, c->Psi1, s);
     if (glm) c->ops.fluxes_glm(P, c->W1, c->Psi1, c->F1, c->F2, c->F3, c->FP1, c->FP2, c->FP3, s);
+    else if (rf) { c->ops.flux_dir(P, 1, c->W1, c->F2, s); c->ops.flux_dir(P, 2, c->W1, c->F3, s); }
     else c->ops.fluxes(P, c->W1, c->F1, c->F2, c->F3, s);
     if (P.divb == 1 || P.divb == 3) c->ops.divb(P, c->W1, c->divB, s);
-    c->ops.update(P, 2, c->U1, c->W1, c->U, c->W, c->F1, c->F2, c->F3, c->divB, s);
+    if (rf) c->ops.update_rf(P, 2, c->U1, c->W1, c->U, c->W, c->F2, c->F3, c->divB, s);
+    else c->ops.update(P, 2, c->U1, c->W1, c->U, c->W, c->F1, c->F2, c->F3, c->divB, s);
     if (glm) c->ops.glm_update(P, 2, c->Psi1, c->Psi, c->FP1, c->FP2, c->FP3, s);
     if (tr) c->ops.tracer_update(P, 2, c->C1, c->F1, c->F2, c->F3, c->T1, c->T, c->U, c->C, s);
     if (P.n_probes > 0) c->ops.probe(P, c->W, s);
@@ -325,8 +341,9 @@ void enqueue_step(icarus_ctx *c, cudaStream_t s)
 
 int count_launches(const icarus_ctx *c)
 {
-    int per_stage = (c->ops.fused_stage && c->opts.fused) ? 3 + 1
-                  : 3 + 3 + (c->P.divb == 1 || c->P.divb == 3 ? 1 : 0) + 1 + (c->opts.tracer ? 2 : 0) +
+    int per_stage = use_fused_stage(c) ? 3 + 1
+                  : 3 + (use_update_rf(c) ? 2 : 3) + (c->P.divb == 1 || c->P.divb == 3 ? 1 : 0) + 1 +
+                        (c->opts.tracer ? 2 : 0) +
                         (c->P.divb == ICARUS_DIVB_GLM ? 2 : 0);
     return 2 * per_stage + (c->P.n_probes > 0 ? 1 : 0);
 }
@@ -409,12 +426,13 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
         opts->tracer < 0 || opts->tracer > 1 || opts->strict_floors < 0 || opts->strict_floors > 1)
         return fail(ICARUS_EINVAL, "bad limiter / flux / divb / init_vphi / cme_model / tracer / strict_floors option");
     if (opts->precision < 0 || opts->precision > 2) return fail(ICARUS_EINVAL, "bad precision");
-    if (opts->fused && opts->flux == ICARUS_FLUX_HLLD)
+    if (opts->fused < 0 || opts->fused > 2) return fail(ICARUS_EINVAL, "bad fused option (0, 1 or 2)");
+    if (opts->fused == 1 && opts->flux == ICARUS_FLUX_HLLD)
         return fail(ICARUS_EINVAL, "the fused stage kernel supports the TVDLF and HLL fluxes only");
-    if (opts->fused && opts->tracer) return fail(ICARUS_EINVAL, "the fused stage kernel carries no CME tracer");
-    if (opts->divb == ICARUS_DIVB_GLM && opts->fused)
+    if (opts->fused == 1 && opts->tracer) return fail(ICARUS_EINVAL, "the fused stage kernel carries no CME tracer");
+    if (opts->divb == ICARUS_DIVB_GLM && opts->fused == 1)
         return fail(ICARUS_EINVAL, "GLM div-B control runs with the separate kernels, not the fused stage");
-    if (opts->divb == ICARUS_DIVB_POWELL && opts->fused)
+    if (opts->divb == ICARUS_DIVB_POWELL && opts->fused == 1)
         return fail(ICARUS_EINVAL, "the Powell source runs with the separate kernels, not the fused stage");
     if (opts->divb == ICARUS_DIVB_GLM && !(opts->glm_alpha >= 0.0)) return fail(ICARUS_EINVAL, "glm_alpha must be >= 0");
     if (opts->ring_capacity < 1) return fail(ICARUS_EINVAL, "ring_capacity must be >= 1");
@@ -472,6 +490,7 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     const long long ncell = (long long)P.n1 * P.n2 * P.n3;
     long long nblk = (ncell + 255) / 256;
     if (c->ops.fused_blocks && (long long)c->ops.fused_blocks(P) > nblk) nblk = c->ops.fused_blocks(P);
+    if (c->ops.update_rf_blocks && (long long)c->ops.update_rf_blocks(P) > nblk) nblk = c->ops.update_rf_blocks(P);
     c->partial = (double *)dalloc(c, (size_t)nblk * sizeof(double));
     c->sc = (Scalars *)dalloc(c, sizeof(Scalars));
     c->stage_buf = (double *)dalloc(c, NV * (size_t)ncell * sizeof(double));
@@ -970,7 +989,7 @@ int icarus_time_kernels(icarus_ctx *c, int n_steps, double *ms)
     if (!c || !ms || n_steps < 1) return fail(ICARUS_EINVAL, "bad argument");
     if (!c->have_state) return fail(ICARUS_ESTATE, "no state");
     const int NCLS = ICARUS_KERNEL_CLASSES;
-    const bool fused = c->ops.fused_stage && c->opts.fused;
+    const bool fused = use_fused_stage(c), rf = use_update_rf(c);
     cudaEvent_t ev[2];
     CK(cudaEventCreate(&ev[0]));
     CK(cudaEventCreate(&ev[1]));
@@ -999,11 +1018,12 @@ int icarus_time_kernels(icarus_ctx *c, int n_steps, double *ms)
                 rc |= timed(7 + stage, [&] { c->ops.fused_stage(P, stage, Us, Ws, Uo, Wo, s); });
                 continue;
             }
-            rc |= timed(1, [&] { c->ops.flux_dir(P, 0, Ws, c->F1, s); });
+            if (!rf) rc |= timed(1, [&] { c->ops.flux_dir(P, 0, Ws, c->F1, s); });
             rc |= timed(2, [&] { c->ops.flux_dir(P, 1, Ws, c->F2, s); });
             rc |= timed(3, [&] { c->ops.flux_dir(P, 2, Ws, c->F3, s); });
             if (P.divb == 1 || P.divb == 3) rc |= timed(4, [&] { c->ops.divb(P, Ws, c->divB, s); });
-            rc |= timed(4 + stage, [&] { c->ops.update(P, stage, Us, Ws, Uo, Wo, c->F1, c->F2, c->F3, c->divB, s); });
+            if (rf) rc |= timed(4 + stage, [&] { c->ops.update_rf(P, stage, Us, Ws, Uo, Wo, c->F2, c->F3, c->divB, s); });
+            else rc |= timed(4 + stage, [&] { c->ops.update(P, stage, Us, Ws, Uo, Wo, c->F1, c->F2, c->F3, c->divB, s); });
         }
         if (P.n_probes > 0) rc |= timed(7, [&] { c->ops.probe(P, c->W, s); });
     }

@@ -933,6 +933,104 @@ k_update_capped(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, 
     update_kernel_body<STAGE, TS, TW>(P, Us, Ws, Uo, Wo, F1, F2, F3, divB);
 }
 
+// Cells per block of the update with the radial faces inside it (k_update_rf): a radial row of n1
+// cells is cut into cdiv(n1, 256) segments of equal length, rounded up to whole warps; one block
+// per segment
+__host__ __device__ inline int rf_seg_cells(int n1)
+{
+    const int ns = (n1 + 255) / 256;
+    return ((n1 + ns - 1) / ns + 31) / 32 * 32;
+}
+__host__ __device__ inline long long rf_blocks(const Params &P)
+{
+    const int c = rf_seg_cells(P.n1);
+    return (long long)((P.n1 + c - 1) / c) * P.n2 * P.n3;
+}
+
+// The single-precision-flux update (TVDLF / HLL, Linde or Powell div B, no GLM) with the r-face
+// fluxes of its radial row segment computed in the same kernel, so that they never go through
+// HBM: the segment's primitives with a two-cell halo are staged in shared memory, each cell's
+// limited slope and face states are formed once, each face's flux once, and every cell then takes
+// its two r fluxes from shared memory and its theta / phi fluxes from the arrays of the separate
+// flux kernels. The arithmetic of each step is that of flux_tile<0> and update_cell. Every
+// thread of the block reaches the barriers (threads past the segment's end only skip the work).
+// Measured at 512 x 64 x 128 (two segments of 256 per row): MIXED step 1.115 -> 1.055 ms, FP32
+// 0.960 -> 0.900 ms against the r-flux kernel + update; four resident blocks per SM (at most 64
+// registers) in both stages, against which three (no spills) or five (48 registers) were slower
+template <int STAGE, typename TS, typename TW>
+__global__ void __launch_bounds__(256, 4)
+k_update_rf(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo, TW *__restrict__ Wo,
+            const TW *__restrict__ F2, const TW *__restrict__ F3, const TW *__restrict__ divB)
+{
+    constexpr int CM = 256;
+    __shared__ TW sW[NV][CM + 4];       // primitives of cells i0 - 2 .. i0 + nc + 1
+    __shared__ TW sL[NV][CM + 2];       // lower-face states of cells i0 - 1 .. i0 + nc
+    __shared__ TW sU[NV][CM + 2];       // upper-face states of the same cells
+    __shared__ TW sF[NV][CM + 1];       // fluxes of r faces i0 .. i0 + nc (face i: cells i - 1, i)
+    const int C = blockDim.x, t = threadIdx.x;
+    const int ns = (P.n1 + C - 1) / C;
+    const unsigned int row = blockIdx.x / (unsigned int)ns;
+    const int seg = (int)(blockIdx.x - row * (unsigned int)ns);
+    const int j = (int)(row % (unsigned int)P.n2), k = (int)(row / (unsigned int)P.n2);
+    const int i0 = seg * C, nc = min(C, P.n1 - i0);
+    const long long nt = P.nt, c0 = cidx(P, i0, j, k);
+    for (int q = t; q < nc + 4; q += C) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sW[v][q] = Ws[v * nt + c0 - 2 + q];
+    }
+    __syncthreads();
+    for (int q = t; q < nc + 2; q += C) {          // cell i0 - 1 + q (sW index q + 1)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const TW wc = sW[v][q + 1];
+            const TW h = TW(0.5) * limiter<TW>(P.limiter, wc - sW[v][q], sW[v][q + 2] - wc);
+            sL[v][q] = wc - h;
+            sU[v][q] = wc + h;
+        }
+    }
+    __syncthreads();
+    for (int f = t; f <= nc; f += C) {             // face i0 + f: slope index f below, f + 1 above
+        TW wl[NV], wr[NV], fl[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { wl[v] = sU[v][f]; wr[v] = sL[v][f + 1]; }
+        if (not_positive(wl[0]) || not_positive(wr[0]) || not_positive(wl[4]) || not_positive(wr[4])) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) { wl[v] = sW[v][f + 1]; wr[v] = sW[v][f + 2]; }
+        }
+        riemann<TW, false>(wl, wr, 0, P.flux, phys<TW>(P).gamma, phys<TW>(P).igm1, fl);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sF[v][f] = fl[v];
+    }
+    __syncthreads();
+    const bool valid = t < nc;
+    const int i = i0 + t;
+    TW wo[NV];
+    if (valid) {
+        const long long c = c0 + t;
+        const long long s2 = (long long)P.n3 * (P.n2 + 1) * P.n1, f2 = ((long long)k * (P.n2 + 1) + j) * P.n1 + i;
+        const long long s3 = (long long)(P.n3 + 1) * P.n2 * P.n1, f3 = ((long long)k * P.n2 + j) * P.n1 + i;
+        const long long o3 = (long long)P.n2 * P.n1;
+        const DivFactors<TW> dv(met<TW>(P), i + NG, j + NG);
+        TW w[NV], L[NV], dbn[7];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            w[v] = sW[v][t + 2];
+            L[v] = dv.div(sF[v][t], sF[v][t + 1], F2[v * s2 + f2], F2[v * s2 + f2 + P.n1], F3[v * s3 + f3],
+                          F3[v * s3 + f3 + o3]);
+        }
+        if (P.divb == 1) {
+            const long long q2 = P.p1, q3 = (long long)P.p1 * P.p2;
+            dbn[0] = divB[c - 1]; dbn[1] = divB[c + 1];
+            dbn[2] = divB[c - q2]; dbn[3] = divB[c + q2];
+            dbn[4] = divB[c - q3]; dbn[5] = divB[c + q3];
+        } else if (P.divb == 3) {
+            dbn[6] = divB[c];
+        }
+        update_core<STAGE, TS, TW>(P, i, j, k, w, L, dbn, Us, Uo, Wo, wo);
+    }
+    if (STAGE == 2) finish_dt(P, cfl_block_speed<TW>(P, wo, (valid ? i : 0) + NG, j + NG, valid), 1);
+}
+
 // FP32 form, n1 even: one thread updates the two cells (i, i+1), i even, of a radial row with
 // two-element vector loads and stores (every array offset of such a pair is even: p1, n1, the
 // field strides and the base addresses are), which halves the memory instructions of this
@@ -1493,6 +1591,20 @@ template <typename TS, typename TW> struct Launch {
             k_update<2, TS, TW><<<cdiv(n, 256), 256, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo, (TW *)Wo,
                 (const TW *)F1, (const TW *)F2, (const TW *)F3, (const TW *)D);
     }
+    // the update with the r faces inside it (replaces the r flux kernel and the update)
+    static void update_rf(const Params &P, int stage, const void *Us, const void *Ws, void *Uo, void *Wo,
+                          const void *F2, const void *F3, const void *D, cudaStream_t s)
+    {
+        const int c = rf_seg_cells(P.n1);
+        const unsigned int nb = (unsigned int)rf_blocks(P);
+        if (stage == 1)
+            k_update_rf<1, TS, TW><<<nb, c, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo, (TW *)Wo,
+                (const TW *)F2, (const TW *)F3, (const TW *)D);
+        else
+            k_update_rf<2, TS, TW><<<nb, c, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo, (TW *)Wo,
+                (const TW *)F2, (const TW *)F3, (const TW *)D);
+    }
+    static unsigned int update_rf_blocks(const Params &P) { return (unsigned int)rf_blocks(P); }
     static void cfl(const Params &P, const void *W, cudaStream_t s)
     {
         long long n = (long long)P.n1 * P.n2 * P.n3;
@@ -1603,6 +1715,8 @@ template <typename TS, typename TW> struct Launch {
         o.unpack = unpack;
         o.fused_stage = nullptr;
         o.fused_blocks = nullptr;
+        o.update_rf = nullptr;
+        o.update_rf_blocks = nullptr;
         o.glm_ghost = glm_ghost;
         o.fluxes_glm = fluxes_glm;
         o.glm_update = glm_update;

@@ -1,5 +1,6 @@
 // kern_fp32.cu -- instantiation of the hot-path kernels for the fp32 precision mode, with the
-// fused single-kernel stage (single-precision arithmetic)
+// fused single-kernel stage and the update that forms the r-face fluxes itself (single-precision
+// arithmetic)
 #include "icarus_fused.cuh"
 namespace icarus {
 Ops ops_fp32()
@@ -8,6 +9,8 @@ Ops ops_fp32()
     FusedLaunch<float>::prepare();
     o.fused_stage = FusedLaunch<float>::stage;
     o.fused_blocks = FusedLaunch<float>::blocks;
+    o.update_rf = Launch<float, float>::update_rf;
+    o.update_rf_blocks = Launch<float, float>::update_rf_blocks;
     return o;
 }
 }  // namespace icarus

@@ -1,5 +1,6 @@
 // kern_mixed.cu -- instantiation of the hot-path kernels for the mixed precision mode, with the
-// fused single-kernel stage (single-precision arithmetic)
+// fused single-kernel stage and the update that forms the r-face fluxes itself (single-precision
+// arithmetic)
 #include "icarus_fused.cuh"
 namespace icarus {
 Ops ops_mixed()
@@ -8,6 +9,8 @@ Ops ops_mixed()
     FusedLaunch<double>::prepare();
     o.fused_stage = FusedLaunch<double>::stage;
     o.fused_blocks = FusedLaunch<double>::blocks;
+    o.update_rf = Launch<double, float>::update_rf;
+    o.update_rf_blocks = Launch<double, float>::update_rf_blocks;
     return o;
 }
 }  // namespace icarus

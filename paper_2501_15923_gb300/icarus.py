@@ -159,7 +159,7 @@ def make_grid(g: I.Grid) -> icarus_grid:
 def make_options(o: I.Options, precision=ICARUS_FP64, ring=4096, stream=None, allocator=None,
                  fused=False) -> icarus_options:
     opt = icarus_options()
-    opt.fused = int(bool(fused))
+    opt.fused = int(fused)           # False / 0: default kernels, True / 1: fused stage, 2: separate kernels
     opt.init_vphi = int(o.init_vphi)
     opt.cme_model = int(o.cme_model)
     opt.tracer = int(o.tracer)

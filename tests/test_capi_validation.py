@@ -105,6 +105,15 @@ def test_fused_stage_rejects_hlld(ic):
     assert rc == EINVAL and "fused" in lib.icarus_last_error().decode()
 
 
+@pytest.mark.parametrize("fused", [-1, 3])
+def test_fused_option_out_of_range(ic, fused):
+    lib = ic.load()
+    o = ic.make_options(I.Options(), 2, fused=fused)
+    ctx = C.c_void_p()
+    rc = lib.icarus_init(C.byref(ic.make_grid(sph())), 1.5, 0.0, C.byref(o), C.byref(ctx))
+    assert rc == EINVAL and "fused" in lib.icarus_last_error().decode()
+
+
 def test_fused_stage_rejects_glm(ic):
     lib = ic.load()
     o = ic.make_options(I.Options(divb=I.DIVB_GLM), 1, fused=True)
