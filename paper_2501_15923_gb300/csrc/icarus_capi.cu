@@ -488,10 +488,6 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
     c->F3 = dalloc(c, NV * (size_t)(P.n3 + 1) * P.n2 * P.n1 * tw);
     c->divB = dalloc(c, nt * tw);
     const long long ncell = (long long)P.n1 * P.n2 * P.n3;
-    long long nblk = (ncell + 255) / 256;
-    if (c->ops.fused_blocks && (long long)c->ops.fused_blocks(P) > nblk) nblk = c->ops.fused_blocks(P);
-    if (c->ops.update_rf_blocks && (long long)c->ops.update_rf_blocks(P) > nblk) nblk = c->ops.update_rf_blocks(P);
-    c->partial = (double *)dalloc(c, (size_t)nblk * sizeof(double));
     c->sc = (Scalars *)dalloc(c, sizeof(Scalars));
     c->stage_buf = (double *)dalloc(c, NV * (size_t)ncell * sizeof(double));
     if (opts->divb == ICARUS_DIVB_GLM) {
@@ -523,11 +519,10 @@ int icarus_init(const icarus_grid *grid, double gamma, double omega_rot, const i
         CK(cudaMemsetAsync(c->C, 0, nt * tw, c->stream));
         CK(cudaMemsetAsync(c->C1, 0, nt * tw, c->stream));
     }
-    if (!c->U || !c->U1 || !c->W || !c->W1 || !c->F1 || !c->F2 || !c->F3 || !c->divB || !c->partial || !c->sc || !c->stage_buf) {
+    if (!c->U || !c->U1 || !c->W || !c->W1 || !c->F1 || !c->F2 || !c->F3 || !c->divB || !c->sc || !c->stage_buf) {
         icarus_destroy(c);
         return fail(ICARUS_ENOMEM, "device allocation failed");
     }
-    P.partial = c->partial;
     P.sc = c->sc;
     // host-mapped status word: each step's last kernel copies the status there, so icarus_step can
     // report it without synchronising

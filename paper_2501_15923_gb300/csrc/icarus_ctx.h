@@ -19,7 +19,7 @@ struct icarus_ctx {
     void *F1 = nullptr, *F2 = nullptr, *F3 = nullptr, *divB = nullptr;
     void *T = nullptr, *T1 = nullptr, *C = nullptr, *C1 = nullptr;   // CME tracer: rho c (state type), c
     void *Psi = nullptr, *Psi1 = nullptr, *FP1 = nullptr, *FP2 = nullptr, *FP3 = nullptr;   // GLM psi, its face fluxes
-    double *metric = nullptr, *partial = nullptr, *stage_buf = nullptr;
+    double *metric = nullptr, *stage_buf = nullptr;
     icarus::Scalars *sc = nullptr;
     double *maps = nullptr, *tmaps = nullptr, *cme = nullptr, *traj = nullptr, *ring = nullptr;
     size_t maps_cap = 0, tmaps_cap = 0, cme_cap = 0, traj_cap = 0;

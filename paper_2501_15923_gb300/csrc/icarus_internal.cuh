@@ -133,7 +133,6 @@ struct Params {
     double *ring;           // [cap][P][13]
     double t0, omega_si, b0, p0;
     Scalars *sc;
-    double *partial;        // [n_blocks] CFL partial maxima (scratch)
     int strict_floors;      // 1: a floor activation sets status bit 1
     int *hstatus;           // device address of a host-mapped copy of sc->status (written each step)
 };

@@ -484,7 +484,7 @@ __global__ void k_divb(Params P, const TW *__restrict__ W, TW *__restrict__ divB
 }
 
 // ---------------------------------------------------------------------------------------------
-// block-wide max and the last-block finalisation of dt (scratch: P.partial[gridDim.x])
+// block-wide max and the last-block finalisation of dt
 __device__ __forceinline__ double block_max(double v)
 {
     __shared__ double red[32];
@@ -503,37 +503,38 @@ __device__ __forceinline__ double block_max(double v)
     return v;   // valid in thread 0
 }
 
-// advance_t: 1 after the second stage (t <- t + dt), 0 for a plain dt evaluation
+// advance_t: 1 after the second stage (t <- t + dt), 0 for a plain dt evaluation. Each block
+// publishes its maximum with one 64-bit atomicMax on the bits of the double (for values > 0 the
+// bit patterns order like the values; NaN, zeros and negatives are not published, as a maximum
+// over the blocks starting from 0 with fmax, which drops NaN, would ignore them), and the block
+// that arrives last reads the result: no pass over per-block partials after the grid
 __device__ __forceinline__ void finish_dt(Params &P, double smax_block, int advance_t)
 {
     __shared__ bool last;
+    Scalars *sc = P.sc;
     if (threadIdx.x == 0) {
-        P.partial[blockIdx.x] = smax_block;
+        if (smax_block > 0.0) atomicMax(&sc->smax_bits, (unsigned long long)__double_as_longlong(smax_block));
         __threadfence();
-        unsigned int ticket = atomicAdd(&P.sc->done, 1u);
+        unsigned int ticket = atomicAdd(&sc->done, 1u);
         last = ticket == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last) return;
+    if (!last || threadIdx.x != 0) return;
     __threadfence();
-    double v = 0.0;
-    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) v = fmax(v, ((volatile double *)P.partial)[b]);
-    v = block_max(v);
-    if (threadIdx.x == 0) {
-        Scalars *sc = P.sc;
-        double t = sc->t;
-        if (advance_t) t = __dadd_rn(t, sc->dt);
-        double dt = sc->cfl / v;
-        if (sc->t_stop > 0.0) dt = fmin(dt, fmax(__dsub_rn(sc->t_stop, t), 0.0));
-        if (!(v > 0.0)) dt = 0.0;
-        if (advance_t) sc->dt_step = sc->dt;
-        sc->t = t;
-        sc->dt = dt;
-        sc->done = 0;
-        sc->smax_seen = 0u;             // every block of this launch has published its estimate
-        // the step's status for icarus_step, which reads it on the host without synchronising
-        if (advance_t && P.hstatus) *(volatile int *)P.hstatus = atomicOr(&sc->status, 0);
-    }
+    const double v = __longlong_as_double((long long)*(volatile unsigned long long *)&sc->smax_bits);
+    double t = sc->t;
+    if (advance_t) t = __dadd_rn(t, sc->dt);
+    double dt = sc->cfl / v;
+    if (sc->t_stop > 0.0) dt = fmin(dt, fmax(__dsub_rn(sc->t_stop, t), 0.0));
+    if (!(v > 0.0)) dt = 0.0;
+    if (advance_t) sc->dt_step = sc->dt;
+    sc->t = t;
+    sc->dt = dt;
+    sc->done = 0;
+    sc->smax_bits = 0ull;
+    sc->smax_seen = 0u;                 // every block of this launch has published its estimate
+    // the step's status for icarus_step, which reads it on the host without synchronising
+    if (advance_t && P.hstatus) *(volatile int *)P.hstatus = atomicOr(&sc->status, 0);
 }
 
 // CFL signal speed of one cell: sum_d (|v_d| + c_f,d) / dx_d, in the arithmetic type TW
@@ -934,11 +935,11 @@ k_update_capped(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, 
 }
 
 // Cells per block of the update with the radial faces inside it (k_update_rf): a radial row of n1
-// cells is cut into cdiv(n1, 256) segments of equal length, rounded up to whole warps; one block
+// cells is cut into cdiv(n1, 128) segments of equal length, rounded up to whole warps; one block
 // per segment
 __host__ __device__ inline int rf_seg_cells(int n1)
 {
-    const int ns = (n1 + 255) / 256;
+    const int ns = (n1 + 127) / 128;
     return ((n1 + ns - 1) / ns + 31) / 32 * 32;
 }
 __host__ __device__ inline long long rf_blocks(const Params &P)
@@ -954,15 +955,16 @@ __host__ __device__ inline long long rf_blocks(const Params &P)
 // its two r fluxes from shared memory and its theta / phi fluxes from the arrays of the separate
 // flux kernels. The arithmetic of each step is that of flux_tile<0> and update_cell. Every
 // thread of the block reaches the barriers (threads past the segment's end only skip the work).
-// Measured at 512 x 64 x 128 (two segments of 256 per row): MIXED step 1.115 -> 1.055 ms, FP32
-// 0.960 -> 0.900 ms against the r-flux kernel + update; four resident blocks per SM (at most 64
-// registers) in both stages, against which three (no spills) or five (48 registers) were slower
+// Measured at 512 x 64 x 128 (four segments of 128 per row, eight resident blocks per SM at 64
+// registers): MIXED step 1.115 -> 1.012 ms, FP32 0.960 -> 0.877 ms against the r-flux kernel +
+// update. Segments of 256 (four blocks per SM) took 1.050 / 0.896 ms, of 64 (sixteen) 1.035 /
+// 0.927 ms; with 256, three or five resident blocks were slower than four
 template <int STAGE, typename TS, typename TW>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(128, 8)
 k_update_rf(Params P, const TS *__restrict__ Us, const TW *__restrict__ Ws, TS *Uo, TW *__restrict__ Wo,
             const TW *__restrict__ F2, const TW *__restrict__ F3, const TW *__restrict__ divB)
 {
-    constexpr int CM = 256;
+    constexpr int CM = 128;
     __shared__ TW sW[NV][CM + 4];       // primitives of cells i0 - 2 .. i0 + nc + 1
     __shared__ TW sL[NV][CM + 2];       // lower-face states of cells i0 - 1 .. i0 + nc
     __shared__ TW sU[NV][CM + 2];       // upper-face states of the same cells
@@ -1604,7 +1606,6 @@ template <typename TS, typename TW> struct Launch {
             k_update_rf<2, TS, TW><<<nb, c, 0, s>>>(P, (const TS *)Us, (const TW *)Ws, (TS *)Uo, (TW *)Wo,
                 (const TW *)F2, (const TW *)F3, (const TW *)D);
     }
-    static unsigned int update_rf_blocks(const Params &P) { return (unsigned int)rf_blocks(P); }
     static void cfl(const Params &P, const void *W, cudaStream_t s)
     {
         long long n = (long long)P.n1 * P.n2 * P.n3;
@@ -1714,9 +1715,7 @@ template <typename TS, typename TW> struct Launch {
         o.pack = pack;
         o.unpack = unpack;
         o.fused_stage = nullptr;
-        o.fused_blocks = nullptr;
         o.update_rf = nullptr;
-        o.update_rf_blocks = nullptr;
         o.glm_ghost = glm_ghost;
         o.fluxes_glm = fluxes_glm;
         o.glm_update = glm_update;

@@ -22,12 +22,10 @@ struct Ops {
     void (*unpack)(const Params &, void *U, const double *in, cudaStream_t);
     // one whole stage (fluxes, div B, update) in a single kernel; null where not available
     void (*fused_stage)(const Params &, int stage, const void *Us, const void *Ws, void *Uo, void *Wo, cudaStream_t);
-    unsigned int (*fused_blocks)(const Params &);
     // the stage update with the r-face fluxes computed inside it (the theta / phi fluxes and div B
-    // from the separate kernels), and its block count; null where not available
+    // from the separate kernels); null where not available
     void (*update_rf)(const Params &, int stage, const void *Us, const void *Ws, void *Uo, void *Wo, const void *F2,
                       const void *F3, const void *divB, cudaStream_t);
-    unsigned int (*update_rf_blocks)(const Params &);
     // GLM div-B control: psi ghosts; the three flux kernels with the (B_n, psi) face step; the psi
     // stage update (after the MHD update); psi from / to host-layout doubles
     void (*glm_ghost)(const Params &, void *Psi, cudaStream_t);

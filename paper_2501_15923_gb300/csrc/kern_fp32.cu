@@ -8,9 +8,7 @@ Ops ops_fp32()
     Ops o = Launch<float, float>::make();
     FusedLaunch<float>::prepare();
     o.fused_stage = FusedLaunch<float>::stage;
-    o.fused_blocks = FusedLaunch<float>::blocks;
     o.update_rf = Launch<float, float>::update_rf;
-    o.update_rf_blocks = Launch<float, float>::update_rf_blocks;
     return o;
 }
 }  // namespace icarus

@@ -8,9 +8,7 @@ Ops ops_mixed()
     Ops o = Launch<double, float>::make();
     FusedLaunch<double>::prepare();
     o.fused_stage = FusedLaunch<double>::stage;
-    o.fused_blocks = FusedLaunch<double>::blocks;
     o.update_rf = Launch<double, float>::update_rf;
-    o.update_rf_blocks = Launch<double, float>::update_rf_blocks;
     return o;
 }
 }  // namespace icarus

@@ -98,7 +98,7 @@ def test_update_rf_not_taken_where_not_available(ic, prec, opts):
 
 @pytest.mark.parametrize("prec", [FP32, MIXED])
 def test_update_rf_production_grid(ic, prec):
-    """The 512 x 64 x 128 production grid (two full row segments), three steps from the
+    """The 512 x 64 x 128 production grid (four full row segments), three steps from the
     relaxed-wind start: the two GPU paths within the path tolerance, dt likewise; MIXED bit for
     bit."""
     w = I.dynamic_cme()
