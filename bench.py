@@ -43,6 +43,7 @@ FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 # FP64 flops per face of the flux kernels (2 x DFMA + DADD + DMUL thread-instructions per face)
 # and their DRAM bytes per face come from the committed ncu summary below.
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_flux_r_fp64_256x64x128.md")
+KERNEL_SEQUENCES = {"default": 0, "fused": 1, "separate": 2}     # options.fused of the timed solver
 
 
 def parse_args(argv=None):
@@ -60,6 +61,9 @@ def parse_args(argv=None):
     p.add_argument("--batch-members", type=int, default=64, help="members of the batched cone-CME ensemble")
     p.add_argument("--batch-only", default="", choices=["", "persistent", "phases", "concurrent"],
                    help="only step the batched ensemble in this form (2 warm-up + 3 timed steps; for profiling)")
+    p.add_argument("--kernels", default="default", choices=list(KERNEL_SEQUENCES),
+                   help="kernel sequence of the timed solver (options.fused): default; fused (one fused stage "
+                        "kernel, FP32 / MIXED); separate (r-, theta-, phi-flux kernels and the update)")
     return p.parse_args(argv)
 
 
@@ -416,7 +420,7 @@ def main(argv=None):
     if args.glm:
         w.opts.divb = I.DIVB_GLM
     ncell = w.grid.ncell
-    s = ic.from_workload(w, precision=prec)
+    s = ic.from_workload(w, precision=prec, fused=KERNEL_SEQUENCES[args.kernels])
     s.sample(w.traj, cap=1)
     stream = s.stream
 
@@ -547,7 +551,7 @@ def main(argv=None):
             "config": {"workload": w.name, "grid": args.grid, "cells": ncell, "precision": args.precision,
                        "l2": "inputs larger than L2 (state 8 x 8 B x padded cells per copy)",
                        "parallelism": "replicas" if world > 1 else "single GPU", "cme_tracer": bool(args.tracer),
-                       "divb": "glm" if args.glm else "linde"},
+                       "divb": "glm" if args.glm else "linde", "kernels": args.kernels},
             "clocks": clocks, "roofline": roof, "alu_peaks": peaks_alu, "e2e": e2e, "floor_hits": floor_hits,
             "gpu_launches": s.launches_per_step * args.steps, "forms": forms}
     if rank == 0 and not args.no_cpu and world == 1:
