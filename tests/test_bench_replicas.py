@@ -52,3 +52,14 @@ def test_profile_counts_dropped_when_kernel_sources_change(monkeypatch):
         assert set(pipe) == {"r", "theta", "phi"} and all(0 < v <= 1 for v in pipe.values())
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.profile_numbers() == ({}, {}, {})
+
+
+def test_kernel_sequence_option_maps_to_options_fused():
+    """--kernels names the three values of options.fused that icarus_init accepts (0, 1, 2), the
+    default is 0, and a name outside them is refused by the parser."""
+    import bench
+    assert bench.KERNEL_SEQUENCES == {"default": 0, "fused": 1, "separate": 2}
+    assert bench.parse_args([]).kernels == "default"
+    assert bench.parse_args(["--kernels", "separate"]).kernels == "separate"
+    with pytest.raises(SystemExit):
+        bench.parse_args(["--kernels", "other"])
